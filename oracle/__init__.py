@@ -1,0 +1,251 @@
+"""ctypes front end of the FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+reference legs import this package.  It never imports the CUDA library and
+the CUDA library never imports it.  Arrays are numpy, on the host.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_NCV, LIB_HT, LIB_IDENTITY = 1, 2, 4
+I, CNOT, CV, CVDG, H, T, TDG = range(7)
+FIT_TRACE, FIT_PROB = 0, 1
+Q = 4096
+
+_u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+
+
+class Problem(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("L", C.c_uint32), ("P", C.c_uint32), ("library", C.c_uint32),
+                ("fitness_kind", C.c_uint32), ("run", C.c_uint32), ("seed", C.c_uint64),
+                ("p_mutation", C.c_double), ("mutation_range", C.c_double),
+                ("cost_weight", C.c_double), ("perm", C.c_uint8 * 32)]
+
+
+class Report(C.Structure):
+    _fields_ = [("generation", C.c_uint32), ("best_circuit", C.c_uint32),
+                ("best_fitness", C.c_double), ("gen_best_fitness", C.c_double),
+                ("mean_fitness", C.c_double), ("useful_flops", C.c_uint64),
+                ("best_cost", C.c_uint32), ("best_gen", C.c_uint32),
+                ("best_gates", C.c_uint8 * 64)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.oracle_num_gates.argtypes = [C.c_uint32, C.c_uint32]
+        L.oracle_num_gates.restype = C.c_uint32
+        L.oracle_num_regions.argtypes = [C.c_uint32, C.c_uint32]
+        L.oracle_num_regions.restype = C.c_uint32
+        L.oracle_gate_desc.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.oracle_gate_desc.restype = C.c_int
+        L.oracle_region_gate.argtypes = [C.c_uint32] * 4
+        L.oracle_region_gate.restype = C.c_uint32
+        L.oracle_segment_index.argtypes = [C.c_uint64] * 5
+        L.oracle_segment_index.restype = C.c_uint64
+        L.oracle_num_segments.argtypes = [C.POINTER(Problem)]
+        L.oracle_num_segments.restype = C.c_uint64
+        L.oracle_gate_matrix.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _f64p, _f64p]
+        L.oracle_compose.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p, _f64p, _f64p]
+        L.oracle_score.argtypes = [C.c_uint32, _f64p, _f64p, _u8p, C.c_uint32]
+        L.oracle_score.restype = C.c_double
+        L.oracle_cost.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p]
+        L.oracle_cost.restype = C.c_uint32
+        L.oracle_eval.argtypes = [C.POINTER(Problem), _u8p, C.c_uint32, _f64p, _u32p]
+        L.oracle_useful_flops.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p]
+        L.oracle_useful_flops.restype = C.c_uint64
+        L.oracle_init_state.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f64p]
+        L.oracle_sample.argtypes = [C.POINTER(Problem), _f32p, C.c_uint32, _u8p, _u32p]
+        L.oracle_update.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f64p, C.c_uint32, _u32p,
+                                    _f64p]
+        L.oracle_su3.argtypes = [_f64p, _f64p, _f64p, _f64p]
+        L.oracle_su3_angles.argtypes = [_f64p, _f64p, _f64p]
+        L.oracle_topk.argtypes = [_f64p, _u32p, C.c_uint32, C.c_uint32, _u32p]
+        L.oracle_step.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f64p, C.c_uint32,
+                                  C.c_uint32, _u8p, _u32p, _f64p, _u32p, _u32p,
+                                  C.POINTER(Report)]
+        L.oracle_ga_init.argtypes = [C.POINTER(Problem), C.c_uint32, _u8p]
+        L.oracle_ga_next.argtypes = [C.POINTER(Problem), C.c_uint32, C.c_uint32, C.c_double,
+                                     _u8p, _f64p, _u32p, _u8p]
+        _lib = L
+    return _lib
+
+
+def make_problem(n, L, P, library, perm, seed=0, run=0, fitness_kind=FIT_TRACE, p_mutation=0.1,
+                 mutation_range=np.pi / 4, cost_weight=0.0):
+    p = Problem()
+    p.n, p.L, p.P, p.library, p.fitness_kind, p.run = n, L, P, library, fitness_kind, run
+    p.seed = seed
+    p.p_mutation, p.mutation_range, p.cost_weight = p_mutation, mutation_range, cost_weight
+    perm = list(perm)
+    for j in range(32):
+        p.perm[j] = perm[j] if j < len(perm) else 0
+    return p
+
+
+def philox(ctr, key):
+    out = np.zeros(4, np.uint32)
+    lib().oracle_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def num_gates(n, library):
+    return lib().oracle_num_gates(n, library)
+
+
+def num_regions(n, library):
+    return lib().oracle_num_regions(n, library)
+
+
+def gate_desc(n, library, g):
+    k, c, t = C.c_int(), C.c_int(), C.c_int()
+    rc = lib().oracle_gate_desc(n, library, g, C.byref(k), C.byref(c), C.byref(t))
+    if rc != 0:
+        raise IndexError(g)
+    return k.value, c.value, t.value
+
+
+def region_gate(n, library, r, k):
+    return lib().oracle_region_gate(n, library, r, k)
+
+
+def segment_index(r, i, t, L, P):
+    return lib().oracle_segment_index(r, i, t, L, P)
+
+
+def num_segments(p):
+    return lib().oracle_num_segments(C.byref(p))
+
+
+def gate_matrix(n, library, g):
+    N = 1 << n
+    re = np.zeros(N * N)
+    im = np.zeros(N * N)
+    lib().oracle_gate_matrix(n, library, g, re, im)
+    return (re + 1j * im).reshape(N, N)
+
+
+def compose(n, library, gates):
+    N = 1 << n
+    g = np.ascontiguousarray(gates, np.uint8)
+    re = np.zeros(N * N)
+    im = np.zeros(N * N)
+    lib().oracle_compose(n, library, len(g), g, re, im)
+    return re.reshape(N, N), im.reshape(N, N)
+
+
+def score(n, S, perm, kind=FIT_TRACE):
+    S = np.asarray(S, np.complex128)
+    re = np.ascontiguousarray(S.real.ravel())
+    im = np.ascontiguousarray(S.imag.ravel())
+    return lib().oracle_score(n, re, im, np.ascontiguousarray(perm, np.uint8), kind)
+
+
+def cost(n, library, gates):
+    g = np.ascontiguousarray(gates, np.uint8)
+    return lib().oracle_cost(n, library, len(g), g)
+
+
+def useful_flops(n, library, gates):
+    g = np.ascontiguousarray(gates, np.uint8)
+    return lib().oracle_useful_flops(n, library, len(g), g)
+
+
+def eval_circuits(p, gates):
+    g = np.ascontiguousarray(gates, np.uint8).reshape(-1, p.L)
+    nc = g.shape[0]
+    F = np.zeros(max(nc, 1))
+    cost_ = np.zeros(max(nc, 1), np.uint32)
+    lib().oracle_eval(C.byref(p), g.ravel() if nc else np.zeros(1, np.uint8), nc, F, cost_)
+    return F[:nc], cost_[:nc]
+
+
+def init_state(p):
+    S = num_segments(p)
+    cur = np.zeros(8 * max(S, 1), np.float32)
+    best = np.zeros(8 * max(S, 1), np.float32)
+    bf = np.zeros(max(S, 1))
+    lib().oracle_init_state(C.byref(p), cur, best, bf)
+    return cur[:8 * S], best[:8 * S], bf[:S]
+
+
+def sample(p, cur, gen):
+    gi = np.zeros(p.P * p.L, np.uint8)
+    sid = np.zeros(p.P * p.L, np.uint32)
+    lib().oracle_sample(C.byref(p), np.ascontiguousarray(cur, np.float32), gen, gi, sid)
+    return gi.reshape(p.P, p.L), sid.reshape(p.P, p.L)
+
+
+def update(p, cur, best, best_f, gen, seg_id, fitness):
+    """In place on cur/best/best_f (numpy arrays)."""
+    assert cur.dtype == np.float32 and best.dtype == np.float32 and best_f.dtype == np.float64
+    lib().oracle_update(C.byref(p), cur, best, best_f, gen,
+                        np.ascontiguousarray(seg_id, np.uint32).ravel(),
+                        np.ascontiguousarray(fitness, np.float64))
+
+
+def su3(cosv, sinv):
+    Ur = np.zeros(9)
+    Ui = np.zeros(9)
+    lib().oracle_su3(np.ascontiguousarray(cosv, np.float64), np.ascontiguousarray(sinv, np.float64),
+                     Ur, Ui)
+    return (Ur + 1j * Ui).reshape(3, 3)
+
+
+def su3_angles(params):
+    Ur = np.zeros(9)
+    Ui = np.zeros(9)
+    lib().oracle_su3_angles(np.ascontiguousarray(params, np.float64), Ur, Ui)
+    return (Ur + 1j * Ui).reshape(3, 3)
+
+
+def topk(F, cost_, k):
+    F = np.ascontiguousarray(F, np.float64)
+    idx = np.zeros(max(k, 1), np.uint32)
+    lib().oracle_topk(F, np.ascontiguousarray(cost_, np.uint32), len(F), k, idx)
+    return idx[:min(k, len(F))]
+
+
+def new_report():
+    r = Report()
+    r.best_fitness = -1e308
+    r.best_cost = 0xFFFFFFFF
+    return r
+
+
+def step(p, cur, best, best_f, gen, k, rep):
+    gi = np.zeros(p.P * p.L, np.uint8)
+    sid = np.zeros(p.P * p.L, np.uint32)
+    F = np.zeros(p.P)
+    cost_ = np.zeros(p.P, np.uint32)
+    tk = np.zeros(max(k, 1), np.uint32)
+    lib().oracle_step(C.byref(p), cur, best, best_f, gen, k, gi, sid, F, cost_, tk, C.byref(rep))
+    return gi.reshape(p.P, p.L), sid.reshape(p.P, p.L), F, cost_, tk[:max(k, 1)]
+
+
+def ga_init(p, G):
+    g = np.zeros(p.P * p.L, np.uint8)
+    lib().oracle_ga_init(C.byref(p), G, g)
+    return g.reshape(p.P, p.L)
+
+
+def ga_next(p, G, gen, rate, genome, F, cost_):
+    out = np.zeros(p.P * p.L, np.uint8)
+    lib().oracle_ga_next(C.byref(p), G, gen, rate, np.ascontiguousarray(genome, np.uint8).ravel(),
+                         np.ascontiguousarray(F, np.float64), np.ascontiguousarray(cost_, np.uint32),
+                         out)
+    return out.reshape(p.P, p.L)
