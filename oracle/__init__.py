@@ -68,14 +68,15 @@ def lib():
         L.oracle_eval.argtypes = [C.POINTER(Problem), _u8p, C.c_uint32, _f64p, _u32p]
         L.oracle_useful_flops.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p]
         L.oracle_useful_flops.restype = C.c_uint64
-        L.oracle_init_state.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f64p]
+        L.oracle_init_state.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f32p]
         L.oracle_sample.argtypes = [C.POINTER(Problem), _f32p, C.c_uint32, _u8p, _u32p]
-        L.oracle_update.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f64p, C.c_uint32, _u32p,
+        L.oracle_update.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f32p, C.c_uint32, _u32p,
                                     _f64p]
         L.oracle_su3.argtypes = [_f64p, _f64p, _f64p, _f64p]
+        L.oracle_su3_f32.argtypes = [_f32p, _f32p, _f32p, _f32p]
         L.oracle_su3_angles.argtypes = [_f64p, _f64p, _f64p]
         L.oracle_topk.argtypes = [_f64p, _u32p, C.c_uint32, C.c_uint32, _u32p]
-        L.oracle_step.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f64p, C.c_uint32,
+        L.oracle_step.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f32p, C.c_uint32,
                                   C.c_uint32, _u8p, _u32p, _f64p, _u32p, _u32p,
                                   C.POINTER(Report)]
         L.oracle_ga_init.argtypes = [C.POINTER(Problem), C.c_uint32, _u8p]
@@ -178,7 +179,7 @@ def init_state(p):
     S = num_segments(p)
     cur = np.zeros(8 * max(S, 1), np.float32)
     best = np.zeros(8 * max(S, 1), np.float32)
-    bf = np.zeros(max(S, 1))
+    bf = np.zeros(max(S, 1), np.float32)
     lib().oracle_init_state(C.byref(p), cur, best, bf)
     return cur[:8 * S], best[:8 * S], bf[:S]
 
@@ -192,7 +193,7 @@ def sample(p, cur, gen):
 
 def update(p, cur, best, best_f, gen, seg_id, fitness):
     """In place on cur/best/best_f (numpy arrays)."""
-    assert cur.dtype == np.float32 and best.dtype == np.float32 and best_f.dtype == np.float64
+    assert cur.dtype == np.float32 and best.dtype == np.float32 and best_f.dtype == np.float32
     lib().oracle_update(C.byref(p), cur, best, best_f, gen,
                         np.ascontiguousarray(seg_id, np.uint32).ravel(),
                         np.ascontiguousarray(fitness, np.float64))
@@ -204,6 +205,14 @@ def su3(cosv, sinv):
     lib().oracle_su3(np.ascontiguousarray(cosv, np.float64), np.ascontiguousarray(sinv, np.float64),
                      Ur, Ui)
     return (Ur + 1j * Ui).reshape(3, 3)
+
+
+def su3_f32(cosv, sinv):
+    Ur = np.zeros(9, np.float32)
+    Ui = np.zeros(9, np.float32)
+    lib().oracle_su3_f32(np.ascontiguousarray(cosv, np.float32),
+                         np.ascontiguousarray(sinv, np.float32), Ur, Ui)
+    return (Ur.astype(np.float64) + 1j * Ui).reshape(3, 3)
 
 
 def su3_angles(params):

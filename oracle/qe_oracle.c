@@ -60,8 +60,10 @@ static void draw(const oracle_problem *p, uint32_t a, uint32_t b, uint32_t gen, 
 
 /* integer in [0, m) */
 static uint32_t below(uint32_t u, uint32_t m) { return (uint32_t)(((uint64_t)u * m) >> 32); }
-/* real in (0, 1) */
+/* real in (0, 1), binary64: (u + 1/2) 2^-32 */
 static double unit(uint32_t u) { return ((double)u + 0.5) * 0x1p-32; }
+/* real in (0, 1), binary32: the top 23 bits plus 1/2, times 2^-23 (exact) */
+static float unit32(uint32_t u) { return ((float)(u >> 9) + 0.5f) * 0x1p-23f; }
 
 /* streams of the Philox counter's last word */
 enum { ST_SAMPLE = 0, ST_MUT_DECIDE = 1, ST_MUT_SEG = 2, ST_GA = 4, ST_GA_INIT = 5 };
@@ -399,7 +401,7 @@ void oracle_eval(const oracle_problem *p, const uint8_t *gates, uint32_t n_circu
  * (3 complex amplitudes) and one qubit (2 real amplitudes).  Initial state is
  * uniform: qutrit amplitudes 1/sqrt(3), qubit amplitudes 1/sqrt(2).
  * ====================================================================== */
-void oracle_init_state(const oracle_problem *p, float *cur, float *best, double *best_f) {
+void oracle_init_state(const oracle_problem *p, float *cur, float *best, float *best_f) {
   uint64_t S = oracle_num_segments(p);
   float a = (float)(1.0 / sqrt(3.0));
   float b = (float)ORC_H_COEF;
@@ -414,7 +416,7 @@ void oracle_init_state(const oracle_problem *p, float *cur, float *best, double 
     q[6] = b;
     q[7] = b;
     memcpy(best + 8 * s, q, 8 * sizeof(float));
-    best_f[s] = -1.0;
+    best_f[s] = -1.0f;
   }
 }
 
@@ -436,19 +438,21 @@ void oracle_sample(const oracle_problem *p, const float *cur, uint32_t gen, uint
       uint32_t r = below(u[1], R);
       uint64_t seg = oracle_segment_index(r, i, t, p->L, p->P);
       const float *q = cur + 8 * seg;
-      /* qutrit measurement: outcome k with probability |q_k|^2 / sum */
-      double p0 = (double)q[0] * (double)q[0] + (double)q[1] * (double)q[1];
-      double p1 = (double)q[2] * (double)q[2] + (double)q[3] * (double)q[3];
-      double p2 = (double)q[4] * (double)q[4] + (double)q[5] * (double)q[5];
-      double s = (p0 + p1) + p2;
-      double x = unit(u[2]) * s;
-      uint32_t k = (x < p0) ? 0u : ((x < p0 + p1) ? 1u : 2u);
+      /* qutrit measurement: outcome k with probability |q_k|^2 / sum, the
+         cumulative comparison taken in binary32 */
+      float p0 = q[0] * q[0] + q[1] * q[1];
+      float p1 = q[2] * q[2] + q[3] * q[3];
+      float p2 = q[4] * q[4] + q[5] * q[5];
+      float p01 = p0 + p1;
+      float s = p01 + p2;
+      float x = unit32(u[2]) * s;
+      uint32_t k = (x < p0) ? 0u : ((x < p01) ? 1u : 2u);
       uint32_t g = oracle_region_gate(p->n, p->library, r, k);
       if (has_qubit) {
         /* qubit measurement: outcome 1 (gate present) with probability b1^2/(b0^2+b1^2) */
-        double B0 = (double)q[6] * (double)q[6];
-        double B1 = (double)q[7] * (double)q[7];
-        double y = unit(u[3]) * (B0 + B1);
+        float B0 = q[6] * q[6];
+        float B1 = q[7] * q[7];
+        float y = unit32(u[3]) * (B0 + B1);
         if (y < B0) g = 0; /* identity */
       }
       gate_idx[(uint64_t)c * p->L + t] = (uint8_t)g;
@@ -531,64 +535,134 @@ void oracle_su3_angles(const double params[8], double *U_re, double *U_im) {
  * ====================================================================== */
 static const double ORC_PI = 3.14159265358979323846;
 
-static void mutate_segment(const oracle_problem *p, float *q, double bf, uint32_t gen, uint64_t seg,
-                           int has_qubit) {
-  uint32_t w[4];
-  draw(p, (uint32_t)seg, 0, gen, ST_MUT_SEG, w);
-  double fc = bf < 0.0 ? 0.0 : (bf > 1.0 ? 1.0 : bf);
-  double e = 1.0 - fc; /* 1 - segmentFitness */
-  if (has_qubit && w[0] < 0x80000000u) {
-    /* qubit: rotate by +-(1 - f) * mutationRange, quantised to range/Q steps */
-    uint32_t m = (uint32_t)floor(e * (double)ORC_Q);
-    double step = p->mutation_range / (double)ORC_Q;
-    double ang = (double)m * step;
-    double c = cos(ang), s = sin(ang);
-    if (w[1] & 1u) s = -s;
-    double R[2][2] = {{c, -s}, {s, c}};
-    double b[2] = {(double)q[6], (double)q[7]};
-    for (int a = 0; a < 2; ++a) {
-      double acc = 0.0;
-      for (int k = 0; k < 2; ++k) acc = acc + R[a][k] * b[k];
-      q[6 + a] = (float)acc;
-    }
-    return;
-  }
-  /* qutrit: one of the eight SU(3) parameters drawn from its domain times (1 - f) */
-  uint32_t j = below(w[1], 8);
-  uint32_t m = (uint32_t)floor((unit(w[2]) * e) * (double)ORC_Q);
-  double domain = (j < 3) ? (ORC_PI / 2.0) : (2.0 * ORC_PI);
-  double ang = (double)m * (domain / (double)ORC_Q);
-  double cv[8], sv[8];
-  for (int k = 0; k < 8; ++k) {
-    cv[k] = 1.0;
-    sv[k] = 0.0;
-  }
-  cv[j] = cos(ang);
-  sv[j] = sin(ang);
-  double Ur[9], Ui[9];
-  oracle_su3(cv, sv, Ur, Ui);
-  cplx in[3] = {{(double)q[0], (double)q[1]}, {(double)q[2], (double)q[3]}, {(double)q[4], (double)q[5]}};
-  for (int a = 0; a < 3; ++a) {
-    cplx acc = {0.0, 0.0};
-    for (int k = 0; k < 3; ++k) acc = cadd(acc, cmul((cplx){Ur[3 * a + k], Ui[3 * a + k]}, in[k]));
-    q[2 * a] = (float)acc.re;
-    q[2 * a + 1] = (float)acc.im;
+/* binary32 complex helpers for the mutation arithmetic */
+typedef struct {
+  float re, im;
+} fcplx;
+static fcplx fmulc(fcplx a, fcplx b) {
+  fcplx r;
+  r.re = a.re * b.re - a.im * b.im;
+  r.im = a.re * b.im + a.im * b.re;
+  return r;
+}
+static fcplx faddc(fcplx a, fcplx b) {
+  fcplx r;
+  r.re = a.re + b.re;
+  r.im = a.im + b.im;
+  return r;
+}
+static fcplx fsubc(fcplx a, fcplx b) {
+  fcplx r;
+  r.re = a.re - b.re;
+  r.im = a.im - b.im;
+  return r;
+}
+static fcplx fscale(fcplx a, float s) {
+  fcplx r;
+  r.re = a.re * s;
+  r.im = a.im * s;
+  return r;
+}
+static fcplx fnegc(fcplx a) {
+  fcplx r;
+  r.re = -a.re;
+  r.im = -a.im;
+  return r;
+}
+
+/* Eq. (12) in binary32, the same evaluation order as oracle_su3 */
+void oracle_su3_f32(const float *cv, const float *sv, float *U_re, float *U_im) {
+  float c1 = cv[0], c2 = cv[1], c3 = cv[2];
+  float s1 = sv[0], s2 = sv[1], s3 = sv[2];
+#define EP(k) ((fcplx){cv[2 + (k)], sv[2 + (k)]})
+#define EM(k) ((fcplx){cv[2 + (k)], -sv[2 + (k)]})
+  fcplx U[9];
+  U[0] = fscale(fscale(EP(1), c1), c2);
+  U[1] = fscale(EP(3), s1);
+  U[2] = fscale(fscale(EP(4), c1), s2);
+  U[3] = fsubc(fscale(fscale(fmulc(EM(4), EM(5)), s2), s3),
+               fscale(fscale(fscale(fmulc(fmulc(EP(1), EP(2)), EM(3)), s1), c2), c3));
+  U[4] = fscale(fscale(EP(2), c1), c3);
+  U[5] = fsubc(fnegc(fscale(fscale(fmulc(EM(1), EM(5)), c2), s3)),
+               fscale(fscale(fscale(fmulc(fmulc(EP(2), EM(3)), EP(4)), s1), s2), c3));
+  U[6] = fsubc(fnegc(fscale(fscale(fmulc(EM(2), EM(4)), s2), c3)),
+               fscale(fscale(fscale(fmulc(fmulc(EP(1), EM(3)), EP(5)), s1), c2), s3));
+  U[7] = fscale(fscale(EP(5), c1), s3);
+  U[8] = fsubc(fscale(fscale(fmulc(EM(1), EM(2)), c2), c3),
+               fscale(fscale(fscale(fmulc(fmulc(EM(3), EP(4)), EP(5)), s1), s2), s3));
+#undef EP
+#undef EM
+  for (int e = 0; e < 9; ++e) {
+    U_re[e] = U[e].re;
+    U_im[e] = U[e].im;
   }
 }
 
-void oracle_update(const oracle_problem *p, float *cur, float *best, double *best_f, uint32_t gen,
+/* cos/sin of m * step for m in [0, Q], computed in binary64 and rounded */
+static void trig_f32(double step, uint32_t m, float *c, float *s) {
+  double ang = (double)m * step;
+  *c = (float)cos(ang);
+  *s = (float)sin(ang);
+}
+
+/* Adaptive mutation of one segment (Sec. IV-F).  e = 1 - segmentFitness.
+   - qubit: rotate (b0, b1) by +-(1 - f) * mutationRange, quantised to range/Q
+   - qutrit: one of the eight Eq. (12) parameters is set to a uniform draw from
+     its domain times (1 - f), quantised to domain/Q; the rest are zero. */
+static void mutate_segment(const oracle_problem *p, float *q, float bf, uint32_t gen, uint64_t seg,
+                           int has_qubit) {
+  uint32_t w[4];
+  draw(p, (uint32_t)seg, 0, gen, ST_MUT_SEG, w);
+  float fc = bf < 0.0f ? 0.0f : (bf > 1.0f ? 1.0f : bf);
+  float e = 1.0f - fc;
+  if (has_qubit && w[0] < 0x80000000u) {
+    uint32_t m = (uint32_t)floorf(e * (float)ORC_Q);
+    float c, s;
+    trig_f32(p->mutation_range / (double)ORC_Q, m, &c, &s);
+    if (w[1] & 1u) s = -s;
+    float R[2][2] = {{c, -s}, {s, c}};
+    float b[2] = {q[6], q[7]};
+    for (int a = 0; a < 2; ++a) {
+      float acc = 0.0f;
+      for (int k = 0; k < 2; ++k) acc = acc + R[a][k] * b[k];
+      q[6 + a] = acc;
+    }
+    return;
+  }
+  uint32_t j = below(w[1], 8);
+  uint32_t m = (uint32_t)floorf((unit32(w[2]) * e) * (float)ORC_Q);
+  double domain = (j < 3) ? (ORC_PI / 2.0) : (2.0 * ORC_PI);
+  float cv[8], sv[8];
+  for (int k = 0; k < 8; ++k) {
+    cv[k] = 1.0f;
+    sv[k] = 0.0f;
+  }
+  trig_f32(domain / (double)ORC_Q, m, &cv[j], &sv[j]);
+  float Ur[9], Ui[9];
+  oracle_su3_f32(cv, sv, Ur, Ui);
+  fcplx in[3] = {{q[0], q[1]}, {q[2], q[3]}, {q[4], q[5]}};
+  for (int a = 0; a < 3; ++a) {
+    fcplx acc = {0.0f, 0.0f};
+    for (int k = 0; k < 3; ++k) acc = faddc(acc, fmulc((fcplx){Ur[3 * a + k], Ui[3 * a + k]}, in[k]));
+    q[2 * a] = acc.re;
+    q[2 * a + 1] = acc.im;
+  }
+}
+
+void oracle_update(const oracle_problem *p, float *cur, float *best, float *best_f, uint32_t gen,
                    const uint32_t *seg_id, const double *fitness) {
   uint64_t S = oracle_num_segments(p);
   uint32_t R = oracle_num_regions(p->n, p->library);
   int has_qubit = (p->library & ORC_LIB_IDENTITY) != 0;
-  double *sf = (double *)malloc(sizeof(double) * (S ? S : 1));
+  float *sf = (float *)malloc(sizeof(float) * (S ? S : 1));
   uint8_t *touched = (uint8_t *)calloc(S ? S : 1, 1);
-  /* segment fitness: a segment takes the fitness of the circuit that used it;
-     when several circuits used it in this generation it takes the largest */
+  /* segment fitness: a segment takes the fitness of the circuit that used it
+     (rounded to binary32); when several circuits used it in this generation it
+     takes the largest */
   for (uint64_t c = 0; c < p->P; ++c)
     for (uint64_t t = 0; t < p->L; ++t) {
       uint64_t seg = seg_id[c * p->L + t];
-      double f = fitness[c];
+      float f = (float)fitness[c];
       if (!touched[seg] || f > sf[seg]) sf[seg] = f;
       touched[seg] = 1;
     }
@@ -652,7 +726,7 @@ void oracle_topk(const double *F, const uint32_t *cost, uint32_t n, uint32_t k, 
  * rep carries the best-so-far record in and out (best_fitness < -1e300 on
  * the first call means "none yet").
  * ====================================================================== */
-void oracle_step(const oracle_problem *p, float *cur, float *best, double *best_f, uint32_t gen,
+void oracle_step(const oracle_problem *p, float *cur, float *best, float *best_f, uint32_t gen,
                  uint32_t topk, uint8_t *gate_idx, uint32_t *seg_id, double *F, uint32_t *cost,
                  uint32_t *topk_idx, oracle_report *rep) {
   oracle_sample(p, cur, gen, gate_idx, seg_id);
@@ -688,8 +762,10 @@ void oracle_step(const oracle_problem *p, float *cur, float *best, double *best_
  * Classical GA on the same evaluation (the comparison algorithm of
  * Sec. V-B, with the integer-string encoding, one-point crossover and
  * per-gene mutation of the 5-qubit workload).
- *   - selection: stochastic universal sampling on max(F, 0) (uniform when
- *     every weight is 0), one pointer offset drawn per generation;
+ *   - selection: stochastic universal sampling on the weights
+ *     floor(clamp(F, 0, 1) 2^32) (integers, so every prefix sum is exact),
+ *     pointers s + m floor(W/P) with one offset s drawn per generation
+ *     (identity selection when floor(W/P) = 0);
  *   - the selected parents, in pointer order, are paired (2m, 2m+1) and
  *     crossed at cut = 1 + below(u, L-1) (no crossover when L == 1);
  *   - each gene is replaced with probability ga_rate by a uniform gate;
@@ -704,25 +780,32 @@ void oracle_ga_init(const oracle_problem *p, uint32_t G, uint8_t *genome) {
     }
 }
 
+/* SUS weight of a circuit: max(F, 0) clamped to 1, as a 32-bit fixed-point integer */
+static uint64_t sus_weight(double F) {
+  double x = F > 0.0 ? (F < 1.0 ? F : 1.0) : 0.0;
+  return (uint64_t)floor(x * 4294967296.0);
+}
+
 void oracle_ga_next(const oracle_problem *p, uint32_t G, uint32_t gen, double ga_rate,
                     const uint8_t *genome, const double *F, const uint32_t *cost, uint8_t *out) {
   uint32_t P = p->P, L = p->L;
-  double *cum = (double *)malloc(sizeof(double) * P);
-  double W = 0.0;
+  uint64_t *cum = (uint64_t *)malloc(sizeof(uint64_t) * P);
+  uint64_t W = 0;
   for (uint32_t c = 0; c < P; ++c) {
-    double w = F[c] > 0.0 ? F[c] : 0.0;
-    W = W + w;
+    W += sus_weight(F[c]);
     cum[c] = W;
   }
   uint32_t *parent = (uint32_t *)malloc(sizeof(uint32_t) * P);
   uint32_t u[4];
   draw(p, 0, 0, gen, ST_GA, u);
-  if (W > 0.0) {
-    double spacing = W / (double)P;
-    double start = unit(u[0]) * spacing;
+  uint64_t D = W / P; /* pointer spacing */
+  if (D > 0) {
+    /* pointers s + m D with s uniform in [0, D); parent = first c with cum[c] > pointer */
+    uint64_t r64 = ((uint64_t)u[1] << 32) | u[0];
+    uint64_t s0 = (uint64_t)(((unsigned __int128)r64 * D) >> 64);
     uint32_t c = 0;
     for (uint32_t m = 0; m < P; ++m) {
-      double ptr = start + (double)m * spacing;
+      uint64_t ptr = s0 + (uint64_t)m * D;
       while (c + 1 < P && !(cum[c] > ptr)) ++c;
       parent[m] = c;
     }

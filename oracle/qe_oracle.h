@@ -25,6 +25,11 @@
  *   - with the identity in the library every segment also carries a qubit
  *     whose outcome 1 means "gate present".
  *
+ * Measurement and mutation arithmetic is binary32 (the state's precision),
+ * each operation rounded in the written order; the decision "x < cdf" is thus
+ * taken in the same precision on both sides.  Composition and fitness are
+ * binary64.
+ *
  * Parity status: every function here is pinned by tests/test_oracle_*.py
  * (published Philox test vectors, Table 1 indices, Table 2/3 values,
  * textbook NCV identities, exact-arithmetic recomputation, brute force,
@@ -105,17 +110,19 @@ void oracle_eval(const oracle_problem *p, const uint8_t *gates, uint32_t n_circu
 uint64_t oracle_useful_flops(uint32_t n, uint32_t library, uint32_t L, const uint8_t *gates);
 
 /* ---- encoding state: 8 floats per segment {q0re,q0im,q1re,q1im,q2re,q2im,b0,b1} ---- */
-void oracle_init_state(const oracle_problem *p, float *cur, float *best, double *best_f);
+void oracle_init_state(const oracle_problem *p, float *cur, float *best, float *best_f);
 
 /* ---- circuit construction by measurement (Sec. IV-D, Eq. (10)) ---- */
 void oracle_sample(const oracle_problem *p, const float *cur, uint32_t gen, uint8_t *gate_idx,
                    uint32_t *seg_id);
 
 /* ---- segment fitness, elitism, adaptive mutation (Sec. IV-E1, IV-F) ---- */
-void oracle_update(const oracle_problem *p, float *cur, float *best, double *best_f, uint32_t gen,
+void oracle_update(const oracle_problem *p, float *cur, float *best, float *best_f, uint32_t gen,
                    const uint32_t *seg_id, const double *fitness);
 /* SU(3) operator of Eq. (12); params = {th1,th2,th3,ph1,...,ph5} given as cos/sin pairs */
 void oracle_su3(const double *cosv, const double *sinv, double *U_re, double *U_im);
+/* Eq. (12) evaluated in binary32 in the same order (used by the mutation) */
+void oracle_su3_f32(const float *cosv, const float *sinv, float *U_re, float *U_im);
 /* same from raw angles (libm cos/sin) */
 void oracle_su3_angles(const double params[8], double *U_re, double *U_im);
 
@@ -136,7 +143,7 @@ typedef struct {
   uint8_t best_gates[64];
 } oracle_report;
 
-void oracle_step(const oracle_problem *p, float *cur, float *best, double *best_f, uint32_t gen,
+void oracle_step(const oracle_problem *p, float *cur, float *best, float *best_f, uint32_t gen,
                  uint32_t topk, uint8_t *gate_idx, uint32_t *seg_id, double *F, uint32_t *cost,
                  uint32_t *topk_idx, oracle_report *rep);
 

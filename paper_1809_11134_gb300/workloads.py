@@ -135,7 +135,7 @@ def random_state(rng: np.random.Generator, n_segments: int, best_f_range=(-1.0, 
     """Random encoding state: per segment 8 floats {q0re,q0im,q1re,q1im,q2re,q2im,b0,b1}.
 
     Qutrits are normalised complex Gaussian vectors, qubits random real unit
-    vectors; best_f is uniform in best_f_range (float64)."""
+    vectors; best_f is uniform in best_f_range (float32)."""
     S = n_segments
     z = rng.standard_normal((S, 3, 2))
     z /= np.sqrt((z ** 2).sum(axis=(1, 2), keepdims=True))
@@ -151,7 +151,7 @@ def random_state(rng: np.random.Generator, n_segments: int, best_f_range=(-1.0, 
     ang2 = rng.uniform(0, 2 * np.pi, S)
     best[:, 6] = np.cos(ang2)
     best[:, 7] = np.sin(ang2)
-    best_f = rng.uniform(best_f_range[0], best_f_range[1], S)
+    best_f = rng.uniform(best_f_range[0], best_f_range[1], S).astype(np.float32)
     return cur.ravel(), best.ravel(), best_f
 
 

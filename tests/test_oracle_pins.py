@@ -311,6 +311,25 @@ def test_su3_unitary_det_one():
         assert abs(np.linalg.det(U) - 1) <= 1e-14
 
 
+def test_su3_binary32_matches_binary64():
+    """The mutation evaluates Eq. (12) in binary32 in the printed order; it agrees
+    with the binary64 evaluation to single precision, and single-parameter cases
+    reduce to the Givens / phase closed forms exactly (from the same cos/sin)."""
+    rng = np.random.default_rng(13)
+    for _ in range(200):
+        p = np.concatenate([rng.uniform(0, np.pi / 2, 3), rng.uniform(0, 2 * np.pi, 5)])
+        c32, s32 = np.cos(p).astype(np.float32), np.sin(p).astype(np.float32)
+        U32 = oracle.su3_f32(c32, s32)
+        U64 = oracle.su3(c32.astype(np.float64), s32.astype(np.float64))
+        assert np.abs(U32 - U64).max() <= 4e-7
+    c, s = np.float32(np.cos(0.3)), np.float32(np.sin(0.3))
+    cv = np.ones(8, np.float32)
+    sv = np.zeros(8, np.float32)
+    cv[0], sv[0] = c, s
+    U = oracle.su3_f32(cv, sv)
+    assert np.array_equal(U, np.array([[c, s, 0], [-s, c, 0], [0, 0, 1]], np.complex128))
+
+
 def test_su3_single_parameter_closed_forms():
     x = 0.7
     c, s = math.cos(x), math.sin(x)
@@ -394,13 +413,13 @@ def test_elitism_by_hand():
     cur0, best0 = cur.copy(), best.copy()
     seg = np.array([[1], [1]], np.uint32)  # both circuits used segment 1
     oracle.update(p, cur, best, bf, 0, seg, np.array([0.3, 0.6]))
-    assert bf[1] == 0.6 and np.all(bf[[0, 2, 3]] == -1.0)
+    assert bf[1] == np.float32(0.6) and np.all(bf[[0, 2, 3]] == -1.0)
     assert np.array_equal(best[8:16], cur0[8:16])  # improved: state kept as the new best
     assert np.array_equal(cur, cur0)
     assert np.array_equal(best[:8], best0[:8])
     cur[8:16] += 1.0  # pretend the state moved
     oracle.update(p, cur, best, bf, 1, seg, np.array([0.5, 0.55]))
-    assert bf[1] == 0.6  # not better: best fitness unchanged ...
+    assert bf[1] == np.float32(0.6)  # not better: best fitness unchanged ...
     assert np.array_equal(cur[8:16], cur0[8:16])  # ... and the state reverts to the best
 
 
