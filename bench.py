@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark: candidate circuits evaluated per second, batched binary32 vs plain
+binary64, on one GB300 per rank.
+
+Workload (default): the 3-qubit search of the benchmark set -- Toffoli, Fredkin
+and Peres targets, 28-gate NCV + H/T/T^dag + identity library, L = 16,
+P = 4096 each, Philox seed 1, binary32 composition with binary64 top-32
+rescoring.  One step = one whole generation of the three searches (sample ->
+compose/score -> rank/rescore -> update), 12288 candidate circuits.  The L2 is
+flushed (256 MB write) before every timed step; each step is timed with CUDA
+events on the library's stream.
+
+--impl reference times the CPU oracle (test infrastructure) on a bounded
+sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidate circuits evaluated/sec at n=3/4/5 qubits, FP32 batched vs FP64 plain"
+UNIT = "circuits/s"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.out.flush()
+        rows = []
+        for line in open(self.out.name):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9], f[4]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle as it stands, on a bounded sample of the same workload."""
+    import numpy as np
+    import oracle
+    from paper_1809_11134_gb300 import workloads as W
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    searches = W.config(2)
+    P = args.ref_population
+    probs = [oracle.make_problem(s.n, s.L, P, s.library, s.perm, seed=s.seed, run=r)
+             for r, s in enumerate(searches)]
+    states = [oracle.init_state(p) for p in probs]
+    reps = [oracle.new_report() for _ in probs]
+
+    def one(step):
+        j = step % len(probs)
+        cur, best, bf = states[j]
+        oracle.step(probs[j], cur, best, bf, step // len(probs), 32, reps[j])
+
+    for w in range(args.warmup):
+        one(w)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        one(args.warmup + k)
+    dt = time.perf_counter() - t0
+    value = P * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "3-qubit Toffoli/Fredkin/Peres search, 28-gate library, L=16, "
+                               "P=%d per step (sample of P=4096)" % P, "l2": "host"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "one generation of one of the three searches at P=%d per step "
+                                   "(sample, dense Kronecker compose, score, sort, update)" % P},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def cpu_baseline(seconds=10.0):
+    """Oracle (single thread, binary64, dense Kronecker + matmul) on circuits of
+    the benchmark workload: whole generations of the Toffoli search at P=4096
+    repeated until `seconds` elapsed."""
+    import oracle
+    from paper_1809_11134_gb300 import workloads as W
+    s = W.config(2)[0]
+    p = oracle.make_problem(s.n, s.L, s.P, s.library, s.perm, seed=s.seed)
+    cur, best, bf = oracle.init_state(p)
+    rep = oracle.new_report()
+    n = 0
+    t0 = time.perf_counter()
+    gen = 0
+    while time.perf_counter() - t0 < seconds:
+        oracle.step(p, cur, best, bf, gen, 32, rep)
+        gen += 1
+        n += s.P
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d whole generations of the Toffoli search (P=4096, L=16): sample, "
+                      "dense binary64 compose/score, full sort, update; %.1f s" % (gen, dt)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as G
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or ws > 1:
+        G.build()
+    from paper_1809_11134_gb300 import qe
+    from paper_1809_11134_gb300 import workloads as W
+
+    searches = W.config(2)
+    if rank:
+        for s in searches:
+            s.seed = s.seed + 1000 * rank  # independent replica per rank
+    n_circ = sum(s.P for s in searches)
+    stream = torch.cuda.Stream()
+    ctx = qe.Context(searches, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def do_flush():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+
+    for _ in range(args.warmup):
+        ctx.step(1)
+    # ---- timed region: K generations, L2 flushed before each
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            do_flush()
+            starts[k].record(stream)
+            ctx.step_raw(1, None)
+            ends[k].record(stream)
+        stream.synchronize()
+        wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    step_ms = [starts[k].elapsed_time(ends[k]) for k in range(args.steps)]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    reps = ctx.step(0) if False else None
+    value = ws * n_circ * args.steps / (total_ms / 1e3)
+    clocks = clk.summary()
+
+    # ---- per-stage times inside the generation graph (events between kernels)
+    ctx.stage_timing(True)
+    stages = []
+    for k in range(min(args.steps, 100)):
+        do_flush()
+        ctx.step_raw(1, None)
+        stages.append(ctx.stage_times())
+    ctx.stage_timing(False)
+    st = np.array(stages)
+    st_mean = st.mean(axis=0).tolist()
+    names = ["circuits", "rank_select", "rescore", "rank_sort", "update", "generation"]
+    stage = dict(zip(names, st_mean))
+
+    # ---- roofline of the dominant kernel
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    dom = max(names[:5], key=lambda n: stage[n])
+    last = [ctx.last_generation(r) for r in range(len(searches))]
+    roof = roofline(dom, stage[dom], searches, last, pk)
+
+    # ---- end to end through the public API with host buffers
+    e2e = end_to_end(qe, ctx, searches, last, args.steps)
+
+    ctx.close()
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "3-qubit QEQEA: Toffoli + Fredkin + Peres targets, 28-gate "
+                                   "NCV+H/T/T^dag+I library, L=16, P=4096 each, Philox seed 1, "
+                                   "binary32 compose with binary64 top-32 rescoring; one step = "
+                                   "one generation of the three searches",
+                       "circuits_per_step": n_circ, "parallelism": "replica per GPU",
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "stage_ms": {k: round(v, 5) for k, v in stage.items()}},
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": (len(set((s.n, s.precision == 0) for s in searches)) + 5) * args.steps,
+            "clocks": clocks,
+            "wall_s": wall,
+        }
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if not args.no_extra:
+            line["per_config"] = per_config(qe, torch, args)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline(dom, ms, searches, last, pk):
+    """Achieved algorithmic rate of the dominant kernel against its roofline."""
+    hbm = pk.get("hbm_gbs")
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
+    if dom == "circuits":
+        flops = 0
+        for s, l in zip(searches, last):
+            pass
+        # useful flops of the generation (gate-count model), counted exactly
+        flops = sum(r for r in (gen_flops(s, l) for s, l in zip(searches, last)))
+        ach = flops / (ms / 1e3) / 1e12
+        return {"kernel": "k_step (sample + compose + score + scatter)", "bound": "alu",
+                "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max}
+    if dom == "update":
+        b = update_bytes(searches, last)
+        ach = b / (ms / 1e3) / 1e9
+        return {"kernel": "k_update (elitism + mutation)", "bound": "hbm", "achieved": ach,
+                "peak": hbm, "unit": "GB/s", "frac": ach / hbm if hbm else None, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    # ranking kernels: bytes of the fitness arrays they read
+    b = sum(s.P * 8 for s in searches)
+    ach = b / (ms / 1e3) / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm if hbm else None, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+
+
+def gen_flops(s, last):
+    import oracle
+    g = last["gate_idx"]
+    return sum(oracle.useful_flops(s.n, s.library, row) for row in g)
+
+
+def update_bytes(searches, last):
+    """Algorithmic bytes of one update launch: every (circuit, slot) reads its
+    segment id and takes the segment key (4 + 4 B); every used segment moves its
+    32 B record once (read cur or best, write the other) and reads best_f; every
+    segment of a mutated individual reads and writes its 32 B record and reads
+    best_f and its key."""
+    import numpy as np
+    total = 0
+    for s, l in zip(searches, last):
+        sid = l["seg_id"]
+        used = len(np.unique(sid))
+        R = (s.n * (s.n - 1) if s.library & 1 else 0) + (s.n if s.library & 2 else 0)
+        mutated = s.p_mutation * s.P * R * s.L
+        total += sid.size * 8 + used * (32 + 32 + 4) + mutated * (32 + 32 + 4 + 4)
+    return total
+
+
+def end_to_end(qe, ctx_unused, searches, last, steps):
+    """qe_eval_host per step: the step's candidate circuits (one generation of the
+    three searches) go host -> device from pinned memory, binary32 evaluation and
+    binary64 top-32 ranking run on the GPU, fitness comes back to the host."""
+    import ctypes as C
+    import numpy as np
+    import torch
+    ctx = qe.Context(searches)
+    hosts, fits, tops = [], [], []
+    for s, l in zip(searches, last):
+        h = torch.from_numpy(np.ascontiguousarray(l["gate_idx"])).pin_memory()
+        f = torch.zeros(s.P, dtype=torch.float32).pin_memory()
+        hosts.append(h)
+        fits.append(f)
+        tops.append((qe.qe_ranked * max(s.topk, 1))())
+    for _ in range(3):
+        for r, s in enumerate(searches):
+            ctx.eval_host_ptr(r, hosts[r].data_ptr(), s.P, fits[r].data_ptr(), tops[r])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for r, s in enumerate(searches):
+            ctx.eval_host_ptr(r, hosts[r].data_ptr(), s.P, fits[r].data_ptr(), tops[r])
+    dt = time.perf_counter() - t0
+    ctx.close()
+    n = sum(s.P for s in searches)
+    return {"value": n * steps / dt, "unit": UNIT,
+            "h2d_bytes_per_step": sum(s.P * s.L for s in searches),
+            "d2h_bytes_per_step": sum(s.P * 4 + max(s.topk, 1) * 16 for s in searches),
+            "call": "qe_eval_host (binary32 eval + binary64 top-k) per search, pinned host buffers"}
+
+
+def per_config(qe, torch, args):
+    """Eval rate (sample + compose/score + rank) and step rate at n = 3, 4, 5,
+    binary32 vs plain binary64, a few generations each (context only)."""
+    from paper_1809_11134_gb300 import workloads as W
+    out = {}
+    for cfg, gens32, gens64 in ((2, 20, 5), (3, 6, 2), (5, 4, 1)):
+        res = {}
+        for prec, gens in ((W.PREC_FP32, gens32), (W.PREC_FP64, gens64)):
+            searches = W.config(cfg, precision=prec)
+            stream = torch.cuda.Stream()
+            ctx = qe.Context(searches, stream=stream)
+            ctx.step(1)
+            ctx.stage_timing(True)
+            times = []
+            for _ in range(gens):
+                ctx.step_raw(1, None)
+                times.append(ctx.stage_times())
+            ctx.close()
+            import numpy as np
+            t = np.array(times).mean(axis=0)
+            n = sum(s.P for s in searches)
+            res["fp32" if prec else "fp64"] = {
+                "eval_circuits_per_s": n / ((t[0] + t[1] + t[2] + t[3]) / 1e3),
+                "step_circuits_per_s": n / (t[5] / 1e3), "stage_ms": [round(x, 4) for x in t]}
+        res["fp32_over_fp64_eval"] = res["fp32"]["eval_circuits_per_s"] / res["fp64"]["eval_circuits_per_s"]
+        out["config%d" % cfg] = res
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-population", type=int, default=512)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

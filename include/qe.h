@@ -1,0 +1,233 @@
+/*
+ * qe.h -- C ABI of the GB300-native batched fitness engine for the Quantum
+ * Encoded Quantum Evolutionary Algorithm (QEQEA) of Krylov & Lukac,
+ * arXiv:1809.11134, and of the classical GA that shares its evaluation.
+ *
+ * One search ("problem") evolves circuits of circuit_len gates on n_qubits
+ * wires toward a permutation target.  Every generation the engine
+ *   1. measures the qubit/qutrit encoding into population circuits
+ *      (Sec. IV-D, segment index of Eq. (10)),
+ *   2. composes each circuit's 2^n x 2^n unitary (Sec. IV-C) and scores it with
+ *      Eq. (11) (minus an optional gate-cost penalty),
+ *   3. ranks the circuits, rescoring the best ones in binary64,
+ *   4. applies segment fitness, elitism and adaptive mutation (Sec. IV-E1, IV-F,
+ *      Eq. (12)).
+ * All four steps run as sm_103a CUDA kernels on one GPU; there is no CPU
+ * fallback.  Many independent searches of uneven shape share every launch.
+ *
+ * Conventions used throughout:
+ *   - wire w is bit (n-1-w) of a basis index (wire 0 = most significant bit);
+ *   - S = G_{L-1} ... G_1 G_0 (slot 0 acts first);
+ *   - gate library order: [I if QE_LIB_IDENTITY]; if QE_LIB_NCV, for control
+ *     c = 0..n-1, for target t = 0..n-1, t != c: CNOT, CV, CV^dag on (c -> t);
+ *     if QE_LIB_HT, for wire w = 0..n-1: H, T, T^dag.  V = (1/2)[[1+i,1-i],[1-i,1+i]];
+ *   - regions (Sec. IV-B): one per ordered wire pair (its qutrit picks
+ *     CNOT/CV/CV^dag), then one per wire (its qutrit picks H/T/T^dag); with
+ *     QE_LIB_IDENTITY every segment's qubit decides "gate present" vs I;
+ *   - segment index (Eq. (10)): seg = region*L*P + individual*L + slot.
+ *
+ * Memory: d_* arguments are caller-owned DEVICE pointers, h_* arguments are
+ * caller-owned HOST pointers; the library never frees either.  All search
+ * state is library-owned device memory, allocated once in qe_init.
+ * Streams: every call is ordered on the stream passed to qe_init; calls that
+ * return host data (qe_step, qe_eval/qe_eval_host with h_topk, qe_get_state,
+ * qe_last_generation) synchronise that stream.
+ * Errors: every call returns a qe_status and never aborts, traps or prints.
+ * QE_EINVAL leaves all state unchanged.  After QE_ECUDA or QE_ETIMEOUT the
+ * context is poisoned and every call except qe_last_error / qe_destroy
+ * returns QE_ESTATE.  qe_last_error gives the context's last message.
+ * Thread safety: a context may be used by one host thread at a time.
+ */
+#ifndef QE_H
+#define QE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qe_ctx qe_ctx;
+
+typedef enum {
+  QE_OK = 0,
+  QE_EINVAL = 1,       /* invalid argument; nothing changed */
+  QE_ENOMEM = 2,       /* device memory exhausted (qe_init) */
+  QE_ECUDA = 3,        /* a CUDA call failed; context poisoned */
+  QE_ETIMEOUT = 4,     /* a bounded device wait expired; context poisoned */
+  QE_ENUMERIC = 5,     /* device saw an invalid gate index or a non-finite fitness */
+  QE_ESTATE = 6,       /* context poisoned, or call invalid for this problem */
+  QE_EUNSUPPORTED = 7  /* valid request not implemented by this build / device */
+} qe_status;
+
+/* gate library bits */
+#define QE_LIB_NCV 1u
+#define QE_LIB_HT 2u
+#define QE_LIB_IDENTITY 4u
+
+/* arithmetic of the composition */
+#define QE_PREC_FP64 0u     /* binary64, fixed operation order: bit-identical to the oracle */
+#define QE_PREC_FP32 1u     /* binary32 in registers, binary64 rescoring of the top-k */
+#define QE_PREC_SPLIT_TC 2u /* hi/lo split binary32 products on tensor cores, binary64 rescoring */
+
+/* fitness kind (Sec. IV-E) */
+#define QE_FIT_TRACE 0u /* Eq. (11): 1 - sqrt((N - |tr(S^dag T)|)/N) */
+#define QE_FIT_PROB 1u  /* 1 - sqrt((N - sum_j |S_{perm[j] j}|^2)/N): Table 2 -> Table 3 reading */
+
+/* encoding */
+#define QE_ENC_QEQEA 0u /* qubit/qutrit encoding, Sec. IV */
+#define QE_ENC_GA 1u    /* classical GA on integer gate strings (Sec. V-B comparison) */
+
+#define QE_MAX_QUBITS 5u
+#define QE_MAX_LEN 64u
+#define QE_MAX_POP (1u << 20)
+#define QE_MAX_TOPK 1024u
+#define QE_MAX_PROBLEMS 4096u
+
+/* device error word bits (qe_report.error_word) */
+#define QE_ERRW_BAD_GATE 1u    /* a gate index >= the library size was evaluated */
+#define QE_ERRW_NONFINITE 2u   /* a fitness value was NaN or infinite */
+
+/* One search.  sizeOfIndividual = circuit_len, sizeOfPopulation = population,
+ * numberOfWires = n_qubits (Sec. IV-B). */
+typedef struct {
+  uint32_t n_qubits;      /* 1..5 */
+  uint32_t circuit_len;   /* L: 1..64 */
+  uint32_t population;    /* P: 1..2^20; regions*L*P must be < 2^32 */
+  uint32_t library;       /* QE_LIB_* bits; at least one region must exist */
+  uint32_t encoding;      /* QE_ENC_* */
+  uint32_t precision;     /* QE_PREC_* */
+  uint32_t fitness_kind;  /* QE_FIT_* */
+  uint32_t topk;          /* circuits rescored in binary64 and ranked per generation; 0..min(P,1024) */
+  uint64_t seed;          /* Philox4x32-10 key (low word, high word) */
+  double p_mutation;      /* probabilityOfMutation per individual per generation, [0,1] */
+  double mutation_range;  /* mutationRange in radians, finite, >= 0 */
+  double ga_mutation_rate;/* GA: per-gene replacement probability, [0,1] */
+  double cost_weight;     /* lambda: F = f - lambda * cost / L; cost = non-identity gates */
+  uint8_t target_perm[32];/* T|j> = |target_perm[j]>, a permutation of 0..2^n-1 */
+} qe_problem;
+
+/* one ranked circuit: index in the population, gate cost, binary64 fitness */
+typedef struct {
+  uint32_t circuit;
+  uint32_t cost;
+  double fitness;
+} qe_ranked;
+
+/* per-search report after qe_step */
+typedef struct {
+  uint32_t generation;      /* generations completed */
+  uint32_t best_gen;        /* generation in which best_fitness was found */
+  double best_fitness;      /* best binary64 F seen so far */
+  double gen_best_fitness;  /* best binary64 F of the last generation */
+  double mean_fitness;      /* mean F (working precision) of the last generation */
+  uint64_t useful_flops;    /* real operations of the last generation's compositions */
+  uint32_t best_cost;
+  uint32_t best_len;
+  uint32_t error_word;      /* QE_ERRW_* bits seen so far */
+  uint32_t reserved;
+  uint8_t best_gates[64];   /* gate indices of the best circuit, best_len of them */
+} qe_report;
+
+/* Library geometry without a context: number of gate types and of regions
+ * (Sec. IV-B) for n_qubits and library bits.  QE_EINVAL on bad arguments. */
+qe_status qe_library_info(uint32_t n_qubits, uint32_t library, uint32_t *n_gates,
+                          uint32_t *n_regions);
+
+/* Create a context holding n_probs independent searches on the current CUDA
+ * device; cuda_stream (a cudaStream_t, NULL = legacy default stream) orders
+ * every later call.  Validates every problem before touching the GPU
+ * (QE_EINVAL), allocates all state in one device arena (QE_ENOMEM when
+ * cudaMemGetInfo says it cannot fit), initialises the encoding to uniform
+ * amplitudes (qutrit 1/sqrt(3) each, qubit 1/sqrt(2) each, best fitness -1)
+ * and sets the generation counter to 0.  *out is set only on QE_OK. */
+qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void *cuda_stream);
+
+/* Circuit construction by measurement (Sec. IV-D, Eq. (10)) for search prob at
+ * generation gen: writes d_gate_idx[c*L + t] (uint8 library index) and
+ * d_seg_id[c*L + t] (uint32 segment index) for c < P, t < L.  A pure function
+ * of (encoding state, seed, gen, prob).  QEQEA searches only. */
+qe_status qe_sample(qe_ctx *ctx, uint32_t prob, uint32_t gen, uint8_t *d_gate_idx,
+                    uint32_t *d_seg_id);
+
+/* Fitness of n_circuits circuits d_gate_idx[c*L + t] of search prob
+ * (Sec. IV-C composition, Eq. (11) score, minus lambda*cost/L).  d_fitness is
+ * float[n] for QE_PREC_FP32/SPLIT_TC and double[n] for QE_PREC_FP64; d_cost
+ * (uint32[n], may be NULL) receives the gate costs.  If h_topk is not NULL the
+ * best min(topk, n) circuits (topk from the problem, at least 1) are rescored
+ * in binary64 and written to h_topk sorted by (fitness desc, cost asc, index
+ * asc); this needs n_circuits <= P and synchronises.  Invalid gate indices
+ * give NaN fitness and QE_ENUMERIC (when h_topk is given) or the error bit. */
+qe_status qe_eval(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_t n_circuits,
+                  void *d_fitness, uint32_t *d_cost, qe_ranked *h_topk);
+
+/* qe_eval on HOST buffers: copies h_gate_idx to the device, evaluates, copies
+ * the fitness (float or double by precision) back to h_fitness and fills
+ * h_topk if not NULL.  n_circuits <= P.  Synchronises.  Pinned host memory
+ * makes the copies asynchronous with respect to other host work. */
+qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
+                       uint32_t n_circuits, void *h_fitness, qe_ranked *h_topk);
+
+/* The composed unitaries themselves: d_unitary receives n_circuits row-major
+ * N x N complex matrices, (re, im) interleaved, float for QE_PREC_FP32 and
+ * SPLIT_TC, double for QE_PREC_FP64 (same arithmetic as qe_eval). */
+qe_status qe_compose(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_t n_circuits,
+                     void *d_unitary);
+
+/* Segment fitness, elitism and adaptive mutation (Sec. IV-E1, IV-F) of search
+ * prob at generation gen, given the d_seg_id[P*L] of that generation's
+ * circuits and their d_fitness[P] (double).  A pure function of (state, seed,
+ * gen, seg_id, fitness).  QEQEA searches only. */
+qe_status qe_update(qe_ctx *ctx, uint32_t prob, uint32_t gen, const uint32_t *d_seg_id,
+                    const double *d_fitness);
+
+/* Run n_gen whole generations of every search (sample -> compose/score ->
+ * rank with binary64 rescoring -> update, or the GA's eval -> rank -> select /
+ * cross / mutate), replayed as one CUDA graph per generation.  With h_reports
+ * (n_probs entries) the call then copies one qe_report per search, synchronises
+ * and returns QE_ENUMERIC if any search's error_word is set; with h_reports ==
+ * NULL it only enqueues the generations on the stream and returns. */
+qe_status qe_step(qe_ctx *ctx, uint32_t n_gen, qe_report *h_reports);
+
+/* Stage timing.  qe_stage_timing(ctx, 1) rebuilds the generation graph with
+ * CUDA events recorded between its kernels (on the stream each kernel runs
+ * on); qe_stage_times then gives, for the last generation run, ms[0] circuit
+ * kernels (sample + compose + score + segment-fitness scatter), ms[1] ranking
+ * selection, ms[2] binary64 rescoring, ms[3] ranking sort, ms[4] update
+ * (elitism + mutation, concurrent with ms[1..3]), ms[5] the whole generation.
+ * qe_stage_times synchronises.  Timing adds a few event records per generation. */
+qe_status qe_stage_timing(qe_ctx *ctx, int enable);
+qe_status qe_stage_times(qe_ctx *ctx, float *ms);
+
+/* The last generation of search prob as run by qe_step: its circuits
+ * h_gate_idx[P*L], segment ids h_seg_id[P*L] (QEQEA), working-precision
+ * fitness widened to double h_fitness[P], and top-k h_topk[max(topk,1)].
+ * Any pointer may be NULL.  Synchronises. */
+qe_status qe_last_generation(qe_ctx *ctx, uint32_t prob, uint8_t *h_gate_idx, uint32_t *h_seg_id,
+                             double *h_fitness, qe_ranked *h_topk);
+
+/* Bytes of one search's encoding state in the qe_get_state layout:
+ *   QEQEA: cur[S][8] float, best[S][8] float, best_f[S] float, S = R*P*L, with
+ *          the 8 floats of a segment {q0.re, q0.im, q1.re, q1.im, q2.re, q2.im,
+ *          b0, b1} (qutrit amplitudes, then qubit amplitudes);
+ *   GA:    genome[P][L] uint8. */
+qe_status qe_state_bytes(const qe_ctx *ctx, uint32_t prob, size_t *bytes);
+/* Copy the state out to / in from host memory of exactly qe_state_bytes bytes.
+ * Synchronises. */
+qe_status qe_get_state(qe_ctx *ctx, uint32_t prob, void *h_buf, size_t bytes);
+qe_status qe_set_state(qe_ctx *ctx, uint32_t prob, const void *h_buf, size_t bytes);
+
+/* Generations completed by qe_step. */
+qe_status qe_generation(const qe_ctx *ctx, uint32_t *gen);
+
+/* Last error message of ctx ("" if none); static text when ctx is NULL. */
+const char *qe_last_error(const qe_ctx *ctx);
+
+/* Free all device and host memory of ctx (NULL is allowed). */
+void qe_destroy(qe_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -615,6 +615,7 @@ static void mutate_segment(const oracle_problem *p, float *q, float bf, uint32_t
   draw(p, (uint32_t)seg, 0, gen, ST_MUT_SEG, w);
   float fc = bf < 0.0f ? 0.0f : (bf > 1.0f ? 1.0f : bf);
   float e = 1.0f - fc;
+  if (!(e == e)) e = 1.0f; /* a NaN best fitness mutates fully */
   if (has_qubit && w[0] < 0x80000000u) {
     uint32_t m = (uint32_t)floorf(e * (float)ORC_Q);
     float c, s;

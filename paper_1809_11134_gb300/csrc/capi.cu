@@ -1,0 +1,796 @@
+// capi.cu -- the C ABI of include/qe.h: context, validation, device arena,
+// host-built tables, CUDA-graph capture of one generation, and the calls.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/qe.h"
+#include "qe_dev.cuh"
+#include "qe_host.h"
+
+using namespace qe;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct Group {
+  bool canon = false;
+  uint32_t n = 0;  // qubit count of every search in the group
+  std::vector<uint32_t> ids;
+  uint32_t *d_ids = nullptr, *d_prefix = nullptr;
+  uint32_t total = 0;
+};
+
+}  // namespace
+
+struct qe_ctx {
+  int device = 0;
+  cudaStream_t user = nullptr;
+  cudaStream_t cap = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::vector<qe_problem> probs;
+  std::vector<DevProblem> hp;
+  DevProblem *d_probs = nullptr;
+  DevGlobal g{};
+  LaunchCfg lc;
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  std::vector<Group> groups;  // QEQEA circuit launches, one per (arithmetic, qubit count)
+  bool rescore_nq[QE_MAX_QUBITS + 1] = {false};  // widths with binary32 searches
+  // all QEQEA searches (update launch)
+  uint32_t n_upd = 0, upd_totalA = 0, upd_totalB = 0;
+  uint32_t *d_upd_ids = nullptr, *d_upd_prefA = nullptr, *d_upd_prefB = nullptr;
+  // per-search single arrays for qe_update: {id}, {0, P*L}, {0, ceil(P/32)}
+  uint32_t *d_single = nullptr;
+  RankJob *d_jobs = nullptr;
+  uint32_t n_jobs = 0;
+  Best *d_recs = nullptr;
+  Best *h_recs = nullptr;  // pinned
+  uint8_t *d_stage_gates = nullptr;
+  void *d_stage_fit = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  // stage timing: events recorded inside the generation graph
+  bool timing = false;
+  cudaEvent_t tev[8] = {nullptr};
+  uint32_t gen = 0;
+  bool poisoned = false;
+  std::string err;
+};
+
+namespace {
+
+qe_status fail(qe_ctx *ctx, qe_status st, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  else g_init_error = msg;
+  return st;
+}
+
+qe_status cuda_fail(qe_ctx *ctx, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (ctx) ctx->poisoned = true;
+  return fail(ctx, QE_ECUDA, m);
+}
+
+#define QE_CUDA(ctx, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+uint32_t regions(uint32_t n, uint32_t lib) {
+  uint32_t r = 0;
+  if (lib & QE_LIB_NCV) r += n * (n - 1);
+  if (lib & QE_LIB_HT) r += n;
+  return r;
+}
+
+uint32_t gates(uint32_t n, uint32_t lib) {
+  return ((lib & QE_LIB_IDENTITY) ? 1u : 0u) + 3u * regions(n, lib);
+}
+
+// op byte of every library index (see k_circuit.cu for the op numbering)
+void build_ops(uint32_t n, uint32_t lib, uint8_t *gop) {
+  uint32_t g = 0;
+  if (lib & QE_LIB_IDENTITY) gop[g++] = kOpIdentity;
+  if (lib & QE_LIB_NCV)
+    for (uint32_t c = 0; c < n; ++c)
+      for (uint32_t t = 0; t < n; ++t) {
+        if (t == c) continue;
+        const uint32_t tt = t > c ? t - 1 : t;
+        const uint32_t pair = c * (n - 1) + tt;
+        gop[g++] = (uint8_t)(2 * pair);               // CNOT
+        gop[g++] = (uint8_t)(2 * pair + 1);           // CV
+        gop[g++] = (uint8_t)((2 * pair + 1) | kOpNeg);  // CV^dag
+      }
+  if (lib & QE_LIB_HT)
+    for (uint32_t w = 0; w < n; ++w) {
+      const uint32_t base = 2 * n * (n - 1) + 2 * w;
+      gop[g++] = (uint8_t)base;                  // H
+      gop[g++] = (uint8_t)(base + 1);            // T
+      gop[g++] = (uint8_t)((base + 1) | kOpNeg);  // T^dag
+    }
+}
+
+qe_status validate(const qe_problem &p, uint32_t idx) {
+  char b[256];
+  auto bad = [&](const char *what) {
+    snprintf(b, sizeof b, "problem %u: %s", idx, what);
+    return fail(nullptr, QE_EINVAL, b);
+  };
+  if (p.n_qubits < 1 || p.n_qubits > QE_MAX_QUBITS) return bad("n_qubits must be 1..5");
+  if (p.circuit_len < 1 || p.circuit_len > QE_MAX_LEN) return bad("circuit_len must be 1..64");
+  if (p.population < 1 || p.population > QE_MAX_POP) return bad("population must be 1..2^20");
+  if (p.library & ~(QE_LIB_NCV | QE_LIB_HT | QE_LIB_IDENTITY)) return bad("unknown library bits");
+  const uint32_t R = regions(p.n_qubits, p.library);
+  if (R == 0) return bad("library has no gates for this n_qubits");
+  if (p.encoding > QE_ENC_GA) return bad("unknown encoding");
+  if (p.precision > QE_PREC_SPLIT_TC) return bad("unknown precision");
+  if (p.fitness_kind > QE_FIT_PROB) return bad("unknown fitness_kind");
+  if (p.topk > QE_MAX_TOPK || p.topk > p.population) return bad("topk must be <= min(P, 1024)");
+  if (!(p.p_mutation >= 0.0 && p.p_mutation <= 1.0)) return bad("p_mutation must be in [0,1]");
+  if (!(std::isfinite(p.mutation_range) && p.mutation_range >= 0.0))
+    return bad("mutation_range must be finite and >= 0");
+  if (!(p.ga_mutation_rate >= 0.0 && p.ga_mutation_rate <= 1.0))
+    return bad("ga_mutation_rate must be in [0,1]");
+  if (!std::isfinite(p.cost_weight)) return bad("cost_weight must be finite");
+  const uint64_t S = (uint64_t)R * p.circuit_len * p.population;
+  if (S >= (1ull << 32)) return bad("regions * L * P must be < 2^32");
+  const uint32_t N = 1u << p.n_qubits;
+  bool seen[32] = {false};
+  for (uint32_t j = 0; j < N; ++j) {
+    const uint32_t v = p.target_perm[j];
+    if (v >= N || seen[v]) return bad("target_perm is not a permutation of 0..2^n-1");
+    seen[v] = true;
+  }
+  if (p.precision == QE_PREC_SPLIT_TC) {
+    snprintf(b, sizeof b, "problem %u: QE_PREC_SPLIT_TC is not available in this build", idx);
+    return fail(nullptr, QE_EUNSUPPORTED, b);
+  }
+  return QE_OK;
+}
+
+// device arena: bump allocation with 256-byte alignment
+struct Arena {
+  size_t off = 0;
+  std::vector<std::pair<void **, size_t>> req;
+  template <typename T>
+  void take(T **p, size_t bytes) {
+    req.push_back({(void **)p, off});
+    off += (bytes + 255) & ~(size_t)255;
+  }
+  void bind(char *base) {
+    for (auto &r : req) *r.first = base + r.second;
+  }
+};
+
+// bound on |d32 - d64| of the binary32 composition after L gates: every gate
+// application perturbs each unit column by at most a few ulps of binary32, so
+// the error of every column grows by <= ~4 * 2^-24 * sqrt(2) per gate, |tr|
+// changes by at most N times the column error, d = (N - |tr|)/N by at most
+// the column error; the probability form doubles it.  Generous by a factor 2.
+float eps_d_for(uint32_t L) { return (float)((double)L * 8e-7 + 2e-6); }
+
+unsigned long long threshold(double p) {
+  // number of u in [0, 2^32) with (u + 1/2) 2^-32 < p
+  const double X = p * 4294967296.0;
+  if (X <= 0.5) return 0ull;
+  const double y = std::ceil(X - 0.5);
+  if (y >= 4294967296.0) return 4294967296ull;
+  return (unsigned long long)y;
+}
+
+qe_status check_ctx(qe_ctx *ctx, uint32_t prob) {
+  if (!ctx) return fail(nullptr, QE_EINVAL, "null context");
+  if (ctx->poisoned) return fail(ctx, QE_ESTATE, "context is poisoned by an earlier CUDA error");
+  if (prob >= ctx->probs.size()) return fail(ctx, QE_EINVAL, "problem index out of range");
+  return QE_OK;
+}
+
+// stage events (when timing): 0 start, 1 after the circuit kernels, 2 after
+// ranking selection, 3 after rescoring, 4 after the sort (main stream);
+// 5 before and 6 after the update (side stream); 7 end of the generation
+qe_status build_graph(qe_ctx *ctx) {
+  cudaStream_t cs = ctx->cap;
+  QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  auto mark = [&](int k, cudaStream_t st) {
+    if (e == cudaSuccess && ctx->timing) e = cudaEventRecordWithFlags(ctx->tev[k], st, cudaEventRecordExternal);
+  };
+  mark(0, cs);
+  for (auto &gr : ctx->groups) {
+    if (e == cudaSuccess)
+      e = launch_step(ctx->lc, gr.n, ctx->d_probs, gr.d_ids, gr.d_prefix,
+                      (uint32_t)gr.ids.size(), gr.total, gr.canon, ctx->g, cs);
+  }
+  mark(1, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+  mark(5, ctx->side);
+  if (e == cudaSuccess && ctx->n_upd)
+    e = launch_update(ctx->lc, ctx->d_probs, ctx->d_upd_ids, ctx->d_upd_prefA, ctx->d_upd_prefB,
+                      ctx->n_upd, ctx->upd_totalA, ctx->upd_totalB, ctx->g.gen, 0, nullptr, ctx->g,
+                      ctx->side);
+  mark(6, ctx->side);
+  RankJob none{};
+  if (e == cudaSuccess)
+    e = launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, none, ctx->g, cs);
+  mark(2, cs);
+  for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
+    if (e == cudaSuccess && ctx->rescore_nq[nq])
+      e = launch_rescore(ctx->lc, nq, ctx->d_probs, nullptr, ctx->g, cs);
+  mark(3, cs);
+  if (e == cudaSuccess) e = launch_rank_sort(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, none, ctx->g, cs);
+  mark(4, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
+  if (e == cudaSuccess) e = launch_finish(ctx->g, cs);
+  mark(7, cs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(ctx, e, "capturing the generation graph");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+  ctx->graph = graph;
+  QE_CUDA(ctx, cudaGraphInstantiate(&ctx->gexec, graph, 0));
+  return QE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qe_status qe_library_info(uint32_t n_qubits, uint32_t library, uint32_t *n_gates,
+                          uint32_t *n_regions) {
+  if (n_qubits < 1 || n_qubits > QE_MAX_QUBITS) return QE_EINVAL;
+  if (library & ~(QE_LIB_NCV | QE_LIB_HT | QE_LIB_IDENTITY)) return QE_EINVAL;
+  if (n_gates) *n_gates = gates(n_qubits, library);
+  if (n_regions) *n_regions = regions(n_qubits, library);
+  return QE_OK;
+}
+
+const char *qe_last_error(const qe_ctx *ctx) {
+  if (!ctx) return g_init_error.c_str();
+  return ctx->err.c_str();
+}
+
+void qe_destroy(qe_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  for (auto &ev : ctx->tev)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->h_recs) cudaFreeHost(ctx->h_recs);
+  if (ctx->arena) cudaFree(ctx->arena);
+  delete ctx;
+}
+
+qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void *cuda_stream) {
+  g_init_error.clear();
+  if (!out || !probs) return fail(nullptr, QE_EINVAL, "null argument");
+  if (n_probs < 1 || n_probs > QE_MAX_PROBLEMS) return fail(nullptr, QE_EINVAL, "n_probs must be 1..4096");
+  for (uint32_t i = 0; i < n_probs; ++i) {
+    qe_status st = validate(probs[i], i);
+    if (st != QE_OK) return st;
+  }
+  if (std::getenv("QE_FAULT_ALLOC"))
+    return fail(nullptr, QE_ENOMEM, "device allocation refused (QE_FAULT_ALLOC)");
+
+  qe_ctx *ctx = new qe_ctx();
+  ctx->user = (cudaStream_t)cuda_stream;
+  ctx->probs.assign(probs, probs + n_probs);
+  auto bail = [&](qe_status st) {
+    g_init_error = ctx->err;
+    qe_destroy(ctx);
+    return st;
+  };
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaGetDevice"));
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, ctx->device);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaGetDeviceProperties"));
+  if (!(prop.major == 10 && prop.minor == 3))
+    return bail(fail(ctx, QE_EUNSUPPORTED,
+                     std::string("this library is built for sm_103a only; device is ") +
+                         prop.name));
+  ctx->lc.num_sms = (uint32_t)prop.multiProcessorCount;
+  e = query_circuit_occupancy(ctx->lc);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "occupancy query"));
+
+  // ---- arena layout
+  Arena ar;
+  ctx->hp.resize(n_probs);
+  size_t total_P = 0, max_PL = 0, max_P = 0;
+  for (uint32_t i = 0; i < n_probs; ++i) {
+    const qe_problem &q = probs[i];
+    DevProblem &d = ctx->hp[i];
+    memset(&d, 0, sizeof d);
+    d.n = q.n_qubits;
+    d.N = 1u << d.n;
+    d.L = q.circuit_len;
+    d.P = q.population;
+    d.R = regions(d.n, q.library);
+    d.G = gates(d.n, q.library);
+    d.LP = d.L * d.P;
+    d.lib = q.library;
+    d.prec = q.precision;
+    d.fit_kind = q.fitness_kind;
+    d.enc = q.encoding;
+    d.topk = q.topk;
+    d.k = q.topk ? q.topk : 1;
+    d.run = i;
+    d.has_qubit = (q.library & QE_LIB_IDENTITY) ? 1u : 0u;
+    d.base = d.has_qubit;
+    d.key0 = (uint32_t)q.seed;
+    d.key1 = (uint32_t)(q.seed >> 32);
+    d.eps_d = eps_d_for(d.L);
+    d.p_mut = q.p_mutation;
+    d.cost_weight = q.cost_weight;
+    d.ga_rate = q.ga_mutation_rate;
+    d.mut_T = threshold(q.p_mutation);
+    d.nseg = (uint64_t)d.R * d.L * d.P;
+    for (uint32_t j = 0; j < 32; ++j) d.perm[j] = j < d.N ? q.target_perm[j] : 0;
+    memset(d.gop, kOpIdentity, sizeof d.gop);
+    build_ops(d.n, q.library, d.gop);
+    const size_t P = d.P, PL = (size_t)d.P * d.L;
+    if (q.encoding == QE_ENC_QEQEA) {
+      ar.take(&d.cur, d.nseg * 32);
+      ar.take(&d.best, d.nseg * 32);
+      ar.take(&d.best_f, d.nseg * 4);
+      ar.take(&d.sfkey, d.nseg * 4);
+      ar.take(&d.seg_id, PL * 4);
+      ar.take(&d.qubit_tab, (kQ + 1) * sizeof(float2));
+    } else {
+      ar.take(&d.genome_next, PL);
+      ar.take(&d.ga_cum, P * 8);
+    }
+    ar.take(&d.gate_idx, PL);
+    if (q.precision == QE_PREC_FP64) ar.take(&d.fit64, P * 8);
+    else ar.take(&d.fit32, P * 4);
+    ar.take(&d.meta, P * 4);
+    ar.take(&d.cand, P * 4);
+    ar.take(&d.cand_f, P * 8);
+    ar.take(&d.cand_n, 4);
+    ar.take(&d.topk_out, d.k * sizeof(Ranked));
+    total_P += P;
+    if (PL > max_PL) max_PL = PL;
+    if (P > max_P) max_P = P;
+  }
+  ar.take(&ctx->d_recs, n_probs * sizeof(Best));
+  ar.take(&ctx->d_probs, n_probs * sizeof(DevProblem));
+  ar.take(&ctx->g.th_tab, (kQ + 1) * sizeof(float2));
+  ar.take(&ctx->g.ph_tab, (kQ + 1) * sizeof(float2));
+  ar.take(&ctx->g.gen, 4);
+  ar.take(&ctx->g.err, 4);
+  ar.take(&ctx->g.rescore_n, 4);
+  ar.take(&ctx->g.rescore_list, total_P * 4);
+  ar.take(&ctx->d_jobs, n_probs * sizeof(RankJob));
+  ar.take(&ctx->d_single, n_probs * 5 * 4);
+  ar.take(&ctx->d_stage_gates, max_PL);
+  ar.take(&ctx->d_stage_fit, max_P * 8);
+  // groups: QEQEA searches by (arithmetic, qubit count), widest first
+  std::vector<uint32_t> upd;
+  for (int k = 0; k < 2; ++k)
+    for (uint32_t nq = QE_MAX_QUBITS; nq >= 1; --nq) {
+      Group gr;
+      gr.canon = k == 1;
+      gr.n = nq;
+      for (uint32_t i = 0; i < n_probs; ++i) {
+        if (probs[i].encoding != QE_ENC_QEQEA || probs[i].n_qubits != nq) continue;
+        if ((probs[i].precision == QE_PREC_FP64) != gr.canon) continue;
+        gr.ids.push_back(i);
+      }
+      if (!gr.ids.empty()) ctx->groups.push_back(gr);
+    }
+  for (uint32_t i = 0; i < n_probs; ++i) {
+    if (probs[i].encoding == QE_ENC_QEQEA) upd.push_back(i);
+    if (probs[i].precision != QE_PREC_FP64) ctx->rescore_nq[probs[i].n_qubits] = true;
+  }
+  for (auto &gr : ctx->groups) {
+    ar.take(&gr.d_ids, gr.ids.size() * 4);
+    ar.take(&gr.d_prefix, (gr.ids.size() + 1) * 4);
+  }
+  ctx->n_upd = (uint32_t)upd.size();
+  ar.take(&ctx->d_upd_ids, (upd.size() + 1) * 4);
+  ar.take(&ctx->d_upd_prefA, (upd.size() + 1) * 4);
+  ar.take(&ctx->d_upd_prefB, (upd.size() + 1) * 4);
+
+  size_t free_b = 0, total_b = 0;
+  e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaMemGetInfo"));
+  if (ar.off + (64u << 20) > free_b) {
+    char b[160];
+    snprintf(b, sizeof b, "needs %.3f GB of device memory, %.3f GB free", ar.off / 1e9,
+             free_b / 1e9);
+    return bail(fail(ctx, QE_ENOMEM, b));
+  }
+  e = cudaMalloc(&ctx->arena, ar.off);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(ctx, QE_ENOMEM, "cudaMalloc of the state arena failed"));
+  }
+  ctx->arena_bytes = ar.off;
+  ar.bind((char *)ctx->arena);
+
+  // ---- host-side tables and descriptors
+  std::vector<float2> tab(kQ + 1);
+  auto trig = [&](double step, float2 *dst, cudaStream_t st) -> cudaError_t {
+    for (int m = 0; m <= kQ; ++m) {
+      const double ang = (double)m * step;
+      tab[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    cudaError_t r = cudaMemcpyAsync(dst, tab.data(), tab.size() * sizeof(float2),
+                                    cudaMemcpyHostToDevice, st);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(st);
+    return r;
+  };
+  const double pi = 3.14159265358979323846;
+  cudaStream_t us = ctx->user;
+  if ((e = trig((pi / 2.0) / (double)kQ, ctx->g.th_tab, us)) != cudaSuccess)
+    return bail(cuda_fail(ctx, e, "uploading tables"));
+  if ((e = trig((2.0 * pi) / (double)kQ, ctx->g.ph_tab, us)) != cudaSuccess)
+    return bail(cuda_fail(ctx, e, "uploading tables"));
+  std::vector<Best> recs(n_probs);
+  std::vector<RankJob> jobs(n_probs);
+  std::vector<uint32_t> single(n_probs * 5);
+  for (uint32_t i = 0; i < n_probs; ++i) {
+    DevProblem &d = ctx->hp[i];
+    d.rec = ctx->d_recs + i;
+    if (d.qubit_tab && (e = trig(probs[i].mutation_range / (double)kQ, d.qubit_tab, us)) != cudaSuccess)
+      return bail(cuda_fail(ctx, e, "uploading tables"));
+    Best &b = recs[i];
+    memset(&b, 0, sizeof b);
+    b.best_fitness = -HUGE_VAL;
+    b.gen_best_fitness = -HUGE_VAL;
+    b.best_cost = 0xffffffffu;
+    RankJob &j = jobs[i];
+    j.prob = i;
+    j.n = d.P;
+    j.fit = d.prec == QE_PREC_FP64 ? (const void *)d.fit64 : (const void *)d.fit32;
+    j.meta = d.meta;
+    j.gsrc = d.gate_idx;
+    j.update_record = 1;
+    single[5 * i + 0] = i;
+    single[5 * i + 1] = 0;
+    single[5 * i + 2] = d.P * d.L;
+    single[5 * i + 3] = 0;
+    single[5 * i + 4] = (d.P + 31) / 32;
+  }
+  ctx->n_jobs = n_probs;
+  std::vector<uint32_t> host_u32;
+  auto put = [&](uint32_t *dst, const std::vector<uint32_t> &v) -> cudaError_t {
+    if (v.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(dst, v.data(), v.size() * 4, cudaMemcpyHostToDevice, us);
+  };
+  e = cudaMemcpyAsync(ctx->d_probs, ctx->hp.data(), n_probs * sizeof(DevProblem),
+                      cudaMemcpyHostToDevice, us);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->d_recs, recs.data(), n_probs * sizeof(Best), cudaMemcpyHostToDevice, us);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->d_jobs, jobs.data(), n_probs * sizeof(RankJob), cudaMemcpyHostToDevice, us);
+  if (e == cudaSuccess) e = put(ctx->d_single, single);
+  for (auto &gr : ctx->groups) {
+    std::vector<uint32_t> pre(gr.ids.size() + 1, 0);
+    for (size_t k = 0; k < gr.ids.size(); ++k) pre[k + 1] = pre[k] + ctx->hp[gr.ids[k]].P;
+    gr.total = pre.back();
+    if (e == cudaSuccess) e = put(gr.d_ids, gr.ids);
+    if (e == cudaSuccess) e = put(gr.d_prefix, pre);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
+  }
+  {
+    std::vector<uint32_t> pa(upd.size() + 1, 0), pb(upd.size() + 1, 0);
+    for (size_t k = 0; k < upd.size(); ++k) {
+      pa[k + 1] = pa[k] + ctx->hp[upd[k]].P * ctx->hp[upd[k]].L;
+      pb[k + 1] = pb[k] + (ctx->hp[upd[k]].P + 31) / 32;
+    }
+    ctx->upd_totalA = pa.back();
+    ctx->upd_totalB = pb.back();
+    if (e == cudaSuccess) e = put(ctx->d_upd_ids, upd);
+    if (e == cudaSuccess) e = put(ctx->d_upd_prefA, pa);
+    if (e == cudaSuccess) e = put(ctx->d_upd_prefB, pb);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.gen, 0, 4, us);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.err, 0, 4, us);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.rescore_n, 0, 4, us);
+  for (uint32_t i = 0; i < n_probs && e == cudaSuccess; ++i) {
+    const DevProblem &d = ctx->hp[i];
+    if (d.enc == QE_ENC_QEQEA) e = launch_init_state(ctx->d_probs, i, d.nseg, us);
+    else e = cudaMemsetAsync(d.gate_idx, 0, (size_t)d.P * d.L, us);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(us);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "initialising the state"));
+  e = cudaMallocHost(&ctx->h_recs, n_probs * sizeof(Best));
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaMallocHost"));
+  e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "creating streams"));
+  *out = ctx;
+  return QE_OK;
+}
+
+qe_status qe_sample(qe_ctx *ctx, uint32_t prob, uint32_t gen, uint8_t *d_gate_idx,
+                    uint32_t *d_seg_id) {
+  qe_status st = check_ctx(ctx, prob);
+  if (st != QE_OK) return st;
+  const DevProblem &d = ctx->hp[prob];
+  if (d.enc != QE_ENC_QEQEA) return fail(ctx, QE_ESTATE, "qe_sample needs a QEQEA search");
+  if (!d_gate_idx || !d_seg_id) return fail(ctx, QE_EINVAL, "null output buffer");
+  QE_CUDA(ctx, launch_sample(ctx->lc, ctx->d_probs, prob, d.P, d.L, gen, d_gate_idx, d_seg_id,
+                             ctx->user));
+  return QE_OK;
+}
+
+static qe_status rank_single(qe_ctx *ctx, uint32_t prob, uint32_t n, const void *fit,
+                             const uint32_t *meta, const uint8_t *gsrc, qe_ranked *h_topk) {
+  const DevProblem &d = ctx->hp[prob];
+  RankJob j{};
+  j.prob = prob;
+  j.n = n;
+  j.fit = fit;
+  j.meta = meta;
+  j.gsrc = gsrc;
+  j.update_record = 0;
+  cudaStream_t us = ctx->user;
+  QE_CUDA(ctx, launch_reset_counter(ctx->g, us));
+  QE_CUDA(ctx, launch_rank_select(ctx->d_probs, nullptr, 1, j, ctx->g, us));
+  if (d.prec != QE_PREC_FP64)
+    QE_CUDA(ctx, launch_rescore(ctx->lc, d.n, ctx->d_probs, gsrc, ctx->g, us));
+  QE_CUDA(ctx, launch_rank_sort(ctx->d_probs, nullptr, 1, j, ctx->g, us));
+  QE_CUDA(ctx, launch_reset_counter(ctx->g, us));
+  const uint32_t k = d.k < n ? d.k : n;
+  std::vector<Ranked> tmp(k);
+  uint32_t errw = 0;
+  if (k) QE_CUDA(ctx, cudaMemcpyAsync(tmp.data(), d.topk_out, k * sizeof(Ranked),
+                                      cudaMemcpyDeviceToHost, us));
+  QE_CUDA(ctx, cudaMemcpyAsync(&errw, ctx->g.err, 4, cudaMemcpyDeviceToHost, us));
+  QE_CUDA(ctx, cudaStreamSynchronize(us));
+  for (uint32_t s = 0; s < k; ++s) {
+    h_topk[s].circuit = tmp[s].circuit;
+    h_topk[s].cost = tmp[s].cost;
+    h_topk[s].fitness = tmp[s].fitness;
+  }
+  if (errw) {
+    QE_CUDA(ctx, cudaMemsetAsync(ctx->g.err, 0, 4, us));
+    QE_CUDA(ctx, cudaStreamSynchronize(us));
+    return fail(ctx, QE_ENUMERIC, (errw & kErrBadGate) ? "invalid gate index in the circuits"
+                                                       : "non-finite fitness");
+  }
+  return QE_OK;
+}
+
+qe_status qe_eval(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_t n_circuits,
+                  void *d_fitness, uint32_t *d_cost, qe_ranked *h_topk) {
+  qe_status st = check_ctx(ctx, prob);
+  if (st != QE_OK) return st;
+  const DevProblem &d = ctx->hp[prob];
+  if (!d_fitness || (n_circuits && !d_gate_idx)) return fail(ctx, QE_EINVAL, "null buffer");
+  if (n_circuits > (1u << 24)) return fail(ctx, QE_EINVAL, "n_circuits must be <= 2^24");
+  if (h_topk && n_circuits > d.P)
+    return fail(ctx, QE_EINVAL, "ranking needs n_circuits <= population");
+  uint32_t *cost = d_cost ? d_cost : (h_topk ? d.meta : nullptr);
+  QE_CUDA(ctx, launch_eval(ctx->lc, d.n, ctx->d_probs, prob, d.prec == QE_PREC_FP64, d_gate_idx,
+                           n_circuits, d_fitness, cost, nullptr, ctx->g, ctx->user));
+  if (!h_topk || n_circuits == 0) return QE_OK;
+  return rank_single(ctx, prob, n_circuits, d_fitness, cost, d_gate_idx, h_topk);
+}
+
+qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
+                       uint32_t n_circuits, void *h_fitness, qe_ranked *h_topk) {
+  qe_status st = check_ctx(ctx, prob);
+  if (st != QE_OK) return st;
+  const DevProblem &d = ctx->hp[prob];
+  if (!h_fitness || (n_circuits && !h_gate_idx)) return fail(ctx, QE_EINVAL, "null buffer");
+  if (n_circuits > d.P) return fail(ctx, QE_EINVAL, "n_circuits must be <= population");
+  const size_t fb = d.prec == QE_PREC_FP64 ? 8 : 4;
+  cudaStream_t us = ctx->user;
+  QE_CUDA(ctx, cudaMemcpyAsync(ctx->d_stage_gates, h_gate_idx, (size_t)n_circuits * d.L,
+                               cudaMemcpyHostToDevice, us));
+  QE_CUDA(ctx, launch_eval(ctx->lc, d.n, ctx->d_probs, prob, d.prec == QE_PREC_FP64,
+                           ctx->d_stage_gates, n_circuits, ctx->d_stage_fit, d.meta, nullptr,
+                           ctx->g, us));
+  if (h_topk && n_circuits) {
+    st = rank_single(ctx, prob, n_circuits, ctx->d_stage_fit, d.meta, ctx->d_stage_gates, h_topk);
+    if (st != QE_OK && st != QE_ENUMERIC) return st;
+  }
+  QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, ctx->d_stage_fit, n_circuits * fb,
+                               cudaMemcpyDeviceToHost, us));
+  QE_CUDA(ctx, cudaStreamSynchronize(us));
+  return st;
+}
+
+qe_status qe_compose(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_t n_circuits,
+                     void *d_unitary) {
+  qe_status st = check_ctx(ctx, prob);
+  if (st != QE_OK) return st;
+  const DevProblem &d = ctx->hp[prob];
+  if (!d_unitary || (n_circuits && !d_gate_idx)) return fail(ctx, QE_EINVAL, "null buffer");
+  if (n_circuits > (1u << 20)) return fail(ctx, QE_EINVAL, "n_circuits must be <= 2^20");
+  QE_CUDA(ctx, launch_eval(ctx->lc, d.n, ctx->d_probs, prob, d.prec == QE_PREC_FP64, d_gate_idx,
+                           n_circuits, nullptr, nullptr, d_unitary, ctx->g, ctx->user));
+  return QE_OK;
+}
+
+qe_status qe_update(qe_ctx *ctx, uint32_t prob, uint32_t gen, const uint32_t *d_seg_id,
+                    const double *d_fitness) {
+  qe_status st = check_ctx(ctx, prob);
+  if (st != QE_OK) return st;
+  const DevProblem &d = ctx->hp[prob];
+  if (d.enc != QE_ENC_QEQEA) return fail(ctx, QE_ESTATE, "qe_update needs a QEQEA search");
+  if (!d_seg_id || !d_fitness) return fail(ctx, QE_EINVAL, "null buffer");
+  cudaStream_t us = ctx->user;
+  QE_CUDA(ctx, launch_scatter(ctx->d_probs, prob, d.P, d.L, d_seg_id, d_fitness, ctx->g.err, us));
+  const uint32_t *s = ctx->d_single + 5 * prob;
+  QE_CUDA(ctx, launch_update(ctx->lc, ctx->d_probs, s, s + 1, s + 3, 1, d.P * d.L,
+                             (d.P + 31) / 32, nullptr, gen, d_seg_id, ctx->g, us));
+  return QE_OK;
+}
+
+qe_status qe_step(qe_ctx *ctx, uint32_t n_gen, qe_report *h_reports) {
+  if (!ctx) return fail(nullptr, QE_EINVAL, "null context");
+  if (ctx->poisoned) return fail(ctx, QE_ESTATE, "context is poisoned by an earlier CUDA error");
+  if (ctx->groups.empty()) return fail(ctx, QE_EUNSUPPORTED, "no QEQEA search in this context");
+  if (!ctx->gexec) {
+    qe_status st = build_graph(ctx);
+    if (st != QE_OK) return st;
+  }
+  for (uint32_t k = 0; k < n_gen; ++k) QE_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->user));
+  ctx->gen += n_gen;
+  if (!h_reports) return QE_OK;  // enqueued only
+  const uint32_t np = (uint32_t)ctx->probs.size();
+  QE_CUDA(ctx, cudaMemcpyAsync(ctx->h_recs, ctx->d_recs, np * sizeof(Best), cudaMemcpyDeviceToHost,
+                               ctx->user));
+  QE_CUDA(ctx, cudaStreamSynchronize(ctx->user));
+  uint32_t errw = 0;
+  for (uint32_t i = 0; i < np; ++i) {
+    const Best &b = ctx->h_recs[i];
+    errw |= b.error_word;
+    qe_report &r = h_reports[i];
+    r.generation = b.generation;
+    r.best_gen = b.best_gen;
+    r.best_fitness = b.best_fitness;
+    r.gen_best_fitness = b.gen_best_fitness;
+    r.mean_fitness = b.mean_fitness;
+    r.useful_flops = b.useful_flops;
+    r.best_cost = b.best_cost;
+    r.best_len = b.best_len;
+    r.error_word = b.error_word;
+    r.reserved = 0;
+    memcpy(r.best_gates, b.best_gates, 64);
+  }
+  if (errw) return fail(ctx, QE_ENUMERIC, "a search reported an invalid gate or non-finite fitness");
+  return QE_OK;
+}
+
+qe_status qe_stage_timing(qe_ctx *ctx, int enable) {
+  if (!ctx) return fail(nullptr, QE_EINVAL, "null context");
+  if (ctx->poisoned) return fail(ctx, QE_ESTATE, "context is poisoned by an earlier CUDA error");
+  const bool want = enable != 0;
+  if (want == ctx->timing) return QE_OK;
+  QE_CUDA(ctx, cudaStreamSynchronize(ctx->user));
+  if (want && !ctx->tev[0])
+    for (auto &ev : ctx->tev) QE_CUDA(ctx, cudaEventCreate(&ev));
+  if (ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  if (ctx->graph) {
+    cudaGraphDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  ctx->timing = want;
+  return QE_OK;
+}
+
+qe_status qe_stage_times(qe_ctx *ctx, float *ms) {
+  if (!ctx || !ms) return fail(ctx, QE_EINVAL, "null argument");
+  if (!ctx->timing || !ctx->gexec) return fail(ctx, QE_ESTATE, "stage timing is not enabled");
+  QE_CUDA(ctx, cudaStreamSynchronize(ctx->user));
+  const int pairs[6][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {5, 6}, {0, 7}};
+  for (int k = 0; k < 6; ++k)
+    QE_CUDA(ctx, cudaEventElapsedTime(&ms[k], ctx->tev[pairs[k][0]], ctx->tev[pairs[k][1]]));
+  return QE_OK;
+}
+
+qe_status qe_generation(const qe_ctx *ctx, uint32_t *gen) {
+  if (!ctx || !gen) return QE_EINVAL;
+  *gen = ctx->gen;
+  return QE_OK;
+}
+
+qe_status qe_last_generation(qe_ctx *ctx, uint32_t prob, uint8_t *h_gate_idx, uint32_t *h_seg_id,
+                             double *h_fitness, qe_ranked *h_topk) {
+  qe_status st = check_ctx(ctx, prob);
+  if (st != QE_OK) return st;
+  const DevProblem &d = ctx->hp[prob];
+  cudaStream_t us = ctx->user;
+  const size_t PL = (size_t)d.P * d.L;
+  std::vector<float> f32;
+  std::vector<Ranked> tk;
+  if (h_gate_idx) QE_CUDA(ctx, cudaMemcpyAsync(h_gate_idx, d.gate_idx, PL, cudaMemcpyDeviceToHost, us));
+  if (h_seg_id && d.seg_id)
+    QE_CUDA(ctx, cudaMemcpyAsync(h_seg_id, d.seg_id, PL * 4, cudaMemcpyDeviceToHost, us));
+  if (h_fitness) {
+    if (d.prec == QE_PREC_FP64) {
+      QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, d.fit64, (size_t)d.P * 8, cudaMemcpyDeviceToHost, us));
+    } else {
+      f32.resize(d.P);
+      QE_CUDA(ctx, cudaMemcpyAsync(f32.data(), d.fit32, (size_t)d.P * 4, cudaMemcpyDeviceToHost, us));
+    }
+  }
+  if (h_topk) {
+    tk.resize(d.k);
+    QE_CUDA(ctx, cudaMemcpyAsync(tk.data(), d.topk_out, d.k * sizeof(Ranked),
+                                 cudaMemcpyDeviceToHost, us));
+  }
+  QE_CUDA(ctx, cudaStreamSynchronize(us));
+  if (h_fitness && !f32.empty())
+    for (uint32_t c = 0; c < d.P; ++c) h_fitness[c] = (double)f32[c];
+  if (h_topk)
+    for (uint32_t s = 0; s < d.k; ++s) {
+      h_topk[s].circuit = tk[s].circuit;
+      h_topk[s].cost = tk[s].cost;
+      h_topk[s].fitness = tk[s].fitness;
+    }
+  return QE_OK;
+}
+
+qe_status qe_state_bytes(const qe_ctx *ctx, uint32_t prob, size_t *bytes) {
+  if (!ctx || !bytes || prob >= ctx->probs.size()) return QE_EINVAL;
+  const DevProblem &d = ctx->hp[prob];
+  if (d.enc == QE_ENC_QEQEA) *bytes = (size_t)d.nseg * (32 + 32 + 4);
+  else *bytes = (size_t)d.P * d.L;
+  return QE_OK;
+}
+
+static qe_status state_copy(qe_ctx *ctx, uint32_t prob, void *h, size_t bytes, bool out) {
+  qe_status st = check_ctx(ctx, prob);
+  if (st != QE_OK) return st;
+  size_t need = 0;
+  qe_state_bytes(ctx, prob, &need);
+  if (!h || bytes != need) return fail(ctx, QE_EINVAL, "state buffer must be qe_state_bytes long");
+  const DevProblem &d = ctx->hp[prob];
+  cudaStream_t us = ctx->user;
+  const cudaMemcpyKind kd = out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+  char *hb = (char *)h;
+  if (d.enc == QE_ENC_QEQEA) {
+    const size_t S = d.nseg;
+    void *parts[3] = {d.cur, d.best, d.best_f};
+    const size_t sz[3] = {S * 32, S * 32, S * 4};
+    size_t off = 0;
+    for (int k = 0; k < 3; ++k) {
+      if (out) QE_CUDA(ctx, cudaMemcpyAsync(hb + off, parts[k], sz[k], kd, us));
+      else QE_CUDA(ctx, cudaMemcpyAsync(parts[k], hb + off, sz[k], kd, us));
+      off += sz[k];
+    }
+  } else {
+    if (out) QE_CUDA(ctx, cudaMemcpyAsync(hb, d.gate_idx, need, kd, us));
+    else QE_CUDA(ctx, cudaMemcpyAsync(d.gate_idx, hb, need, kd, us));
+  }
+  QE_CUDA(ctx, cudaStreamSynchronize(us));
+  return QE_OK;
+}
+
+qe_status qe_get_state(qe_ctx *ctx, uint32_t prob, void *h_buf, size_t bytes) {
+  return state_copy(ctx, prob, h_buf, bytes, true);
+}
+
+qe_status qe_set_state(qe_ctx *ctx, uint32_t prob, const void *h_buf, size_t bytes) {
+  return state_copy(ctx, prob, const_cast<void *>(h_buf), bytes, false);
+}
+
+}  // extern "C"

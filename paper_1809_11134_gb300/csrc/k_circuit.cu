@@ -1,0 +1,621 @@
+// k_circuit.cu -- one warp per circuit: measure the encoding into gates
+// (Sec. IV-D), compose the circuit unitary in registers (Sec. IV-C), score it
+// (Eq. (11)) and scatter the fitness to the segments that built it
+// (Sec. IV-E1).
+//
+// Gate application.  A library gate becomes an "op" byte: ops 0 .. 2n(n-1)-1
+// are pair gates (2*pair + 0 = CNOT, 2*pair + 1 = CV or CV^dag), the next 2n
+// ops are wire gates (2*n(n-1) + 2w + 0 = H, + 1 = T or T^dag); bit 7 carries
+// the sign sigma (-1 for the daggers) and 0xff is the identity.  Every op is a
+// compile-time case of one switch, so the row pairs it touches are fixed
+// register indices (or one lane-xor shuffle when the target wire is a lane
+// bit); the op is warp-uniform, so the switch never diverges.
+//
+// Two arithmetics:
+//  * binary32 (working precision): any operation order, FMA allowed;
+//  * binary64 canonical: every nonzero term of the dense product
+//    G_t * S (k ascending, complex product (ar br - ai bi, ar bi + ai br),
+//    every operation rounded) computed with _rn intrinsics in the same order,
+//    so results equal the dense oracle's (terms with a zero coefficient add
+//    exact zeros; only signs of zero can differ).  The score sums
+//    S[perm[j]][j] with j ascending.
+#include "qe_dev.cuh"
+#include "qe_host.h"
+
+namespace qe {
+
+enum Kind { kCnot = 0, kCvx = 1, kHad = 2, kTx = 3 };
+
+// ------------------------------------------------------------------ arithmetic
+template <typename R, bool CANON>
+struct Ar;
+
+template <>
+struct Ar<float, false> {
+  // CV (s=+1) / CV^dag (s=-1) on a register pair (x = bit-0 row, y = bit-1 row)
+  static __device__ __forceinline__ void cvx_pair(float &xr, float &xi, float &yr, float &yi,
+                                                  float s) {
+    const float s1 = xr + yr, s2 = xi + yi, d1 = xr - yr, d2 = xi - yi;
+    const float h1 = 0.5f * s1, h2 = 0.5f * s2, hs = 0.5f * s;
+    xr = fmaf(-hs, d2, h1);
+    xi = fmaf(hs, d1, h2);
+    yr = fmaf(hs, d2, h1);
+    yi = fmaf(-hs, d1, h2);
+  }
+  // new value of this lane's row given the partner's: A(m) + B(p) for both rows
+  static __device__ __forceinline__ void cvx_lane(float &mr, float &mi, float pr, float pi,
+                                                  float s) {
+    const float a = mr + pr, b = mi + pi, c = mi - pi, d = mr - pr;
+    const float hs = 0.5f * s;
+    mr = fmaf(-hs, c, 0.5f * a);
+    mi = fmaf(hs, d, 0.5f * b);
+  }
+  static __device__ __forceinline__ void had_pair(float &xr, float &xi, float &yr, float &yi) {
+    const float s1 = xr + yr, s2 = xi + yi, d1 = xr - yr, d2 = xi - yi;
+    xr = kH32 * s1;
+    xi = kH32 * s2;
+    yr = kH32 * d1;
+    yi = kH32 * d2;
+  }
+  static __device__ __forceinline__ void had_lane(float &mr, float &mi, float pr, float pi,
+                                                  bool up) {
+    mr = kH32 * (up ? pr - mr : mr + pr);
+    mi = kH32 * (up ? pi - mi : mi + pi);
+  }
+  // y <- (h + i s h) y
+  static __device__ __forceinline__ void tx(float &yr, float &yi, float s) {
+    const float r = yr, i = yi;
+    yr = kH32 * fmaf(-s, i, r);
+    yi = kH32 * fmaf(s, r, i);
+  }
+};
+
+template <>
+struct Ar<double, true> {
+  // x' = A(x) + B(y), y' = B(x) + A(y) with A(z) = (1+si)/2 z, B(z) = (1-si)/2 z:
+  // each half-product is 0.5 * (z.re -+ s z.im) (one rounding: fma with s = +-1
+  // is exact up to the final rounding), the row sum adds the two.
+  static __device__ __forceinline__ void cvx_pair(double &xr, double &xi, double &yr, double &yi,
+                                                  double s) {
+    const double a1 = __fma_rn(-s, xi, xr), a2 = __fma_rn(s, xr, xi);
+    const double b1 = __fma_rn(s, yi, yr), b2 = __fma_rn(-s, yr, yi);
+    const double c1 = __fma_rn(s, xi, xr), c2 = __fma_rn(-s, xr, xi);
+    const double d1 = __fma_rn(-s, yi, yr), d2 = __fma_rn(s, yr, yi);
+    xr = __dmul_rn(0.5, __dadd_rn(a1, b1));
+    xi = __dmul_rn(0.5, __dadd_rn(a2, b2));
+    yr = __dmul_rn(0.5, __dadd_rn(c1, d1));
+    yi = __dmul_rn(0.5, __dadd_rn(c2, d2));
+  }
+  static __device__ __forceinline__ void cvx_lane(double &mr, double &mi, double pr, double pi,
+                                                  double s) {
+    const double a1 = __fma_rn(-s, mi, mr), a2 = __fma_rn(s, mr, mi);
+    const double b1 = __fma_rn(s, pi, pr), b2 = __fma_rn(-s, pr, pi);
+    mr = __dmul_rn(0.5, __dadd_rn(a1, b1));
+    mi = __dmul_rn(0.5, __dadd_rn(a2, b2));
+  }
+  // x' = h x + h y, y' = h x + (-h) y, each product rounded, then the sum
+  static __device__ __forceinline__ void had_pair(double &xr, double &xi, double &yr,
+                                                  double &yi) {
+    const double hxr = __dmul_rn(kH64, xr), hxi = __dmul_rn(kH64, xi);
+    const double hyr = __dmul_rn(kH64, yr), hyi = __dmul_rn(kH64, yi);
+    xr = __dadd_rn(hxr, hyr);
+    xi = __dadd_rn(hxi, hyi);
+    yr = __dsub_rn(hxr, hyr);
+    yi = __dsub_rn(hxi, hyi);
+  }
+  static __device__ __forceinline__ void had_lane(double &mr, double &mi, double pr, double pi,
+                                                  bool up) {
+    const double hm_r = __dmul_rn(kH64, mr), hm_i = __dmul_rn(kH64, mi);
+    const double hp_r = __dmul_rn(kH64, pr), hp_i = __dmul_rn(kH64, pi);
+    mr = up ? __dsub_rn(hp_r, hm_r) : __dadd_rn(hm_r, hp_r);
+    mi = up ? __dsub_rn(hp_i, hm_i) : __dadd_rn(hm_i, hp_i);
+  }
+  // y' = (h, s h) y = (h yr - s (h yi), h yi + s (h yr))
+  static __device__ __forceinline__ void tx(double &yr, double &yi, double s) {
+    const double hr = __dmul_rn(kH64, yr), hi = __dmul_rn(kH64, yi);
+    yr = __fma_rn(-s, hi, hr);
+    yi = __fma_rn(s, hr, hi);
+  }
+};
+
+// ------------------------------------------------------------------ one gate
+template <int NQ, typename R, bool CANON, int KIND, int CW, int TW>
+__device__ __forceinline__ void apply_gate(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>::ROWS],
+                                           int lane, R s) {
+  using Ly = Lay<NQ>;
+  using A = Ar<R, CANON>;
+  constexpr int tb = NQ - 1 - TW;                 // target row bit
+  constexpr int cb = CW < 0 ? -1 : NQ - 1 - CW;   // control row bit
+  constexpr bool T_REG = tb < Ly::RBR;
+  constexpr bool C_REG = cb >= 0 && cb < Ly::RBR;
+  constexpr bool C_LANE = cb >= Ly::RBR;
+  bool cl = true;
+  if constexpr (C_LANE) cl = (lane >> (NQ + cb - Ly::RBR)) & 1;
+
+  if constexpr (KIND == kTx) {
+    // diagonal: rows whose target bit is 1 take the phase
+    if constexpr (T_REG) {
+#pragma unroll
+      for (int r = 0; r < Ly::ROWS; ++r)
+        if ((r >> tb) & 1) A::tx(re[r], im[r], s);
+    } else {
+      const bool up = (lane >> (NQ + tb - Ly::RBR)) & 1;
+#pragma unroll
+      for (int r = 0; r < Ly::ROWS; ++r) {
+        R a = re[r], b = im[r];
+        A::tx(a, b, s);
+        re[r] = up ? a : re[r];
+        im[r] = up ? b : im[r];
+      }
+    }
+  } else if constexpr (T_REG) {
+#pragma unroll
+    for (int r0 = 0; r0 < Ly::ROWS; ++r0) {
+      if ((r0 >> tb) & 1) continue;
+      if (C_REG && !((r0 >> cb) & 1)) continue;
+      const int r1 = r0 | (1 << tb);
+      R xr = re[r0], xi = im[r0], yr = re[r1], yi = im[r1];
+      if constexpr (KIND == kCnot) {
+        R t0 = xr, t1 = xi;
+        xr = yr;
+        xi = yi;
+        yr = t0;
+        yi = t1;
+      } else if constexpr (KIND == kCvx) {
+        A::cvx_pair(xr, xi, yr, yi, s);
+      } else {
+        A::had_pair(xr, xi, yr, yi);
+      }
+      if constexpr (C_LANE) {
+        re[r0] = cl ? xr : re[r0];
+        im[r0] = cl ? xi : im[r0];
+        re[r1] = cl ? yr : re[r1];
+        im[r1] = cl ? yi : im[r1];
+      } else {
+        re[r0] = xr;
+        im[r0] = xi;
+        re[r1] = yr;
+        im[r1] = yi;
+      }
+    }
+  } else {
+    constexpr int tl = NQ + tb - Ly::RBR;  // lane bit of the target
+    const bool up = (lane >> tl) & 1;
+#pragma unroll
+    for (int r = 0; r < Ly::ROWS; ++r) {
+      if (C_REG && !((r >> cb) & 1)) continue;
+      const R pr = __shfl_xor_sync(kFull, re[r], 1 << tl);
+      const R pi = __shfl_xor_sync(kFull, im[r], 1 << tl);
+      R mr = re[r], mi = im[r];
+      if constexpr (KIND == kCnot) {
+        mr = pr;
+        mi = pi;
+      } else if constexpr (KIND == kCvx) {
+        A::cvx_lane(mr, mi, pr, pi, s);
+      } else {
+        A::had_lane(mr, mi, pr, pi, up);
+      }
+      re[r] = cl ? mr : re[r];
+      im[r] = cl ? mi : im[r];
+    }
+  }
+}
+
+constexpr int pair_ctrl(int nq, int pr) { return nq > 1 ? pr / (nq - 1) : 0; }
+constexpr int pair_tgt(int nq, int pr) {
+  return nq > 1 ? ((pr % (nq - 1)) >= pair_ctrl(nq, pr) ? (pr % (nq - 1)) + 1 : (pr % (nq - 1)))
+                : 0;
+}
+
+template <int NQ, typename R, bool CANON, int OP>
+__device__ __forceinline__ void apply_op(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>::ROWS], int lane,
+                                         R s) {
+  constexpr int NP = NQ * (NQ - 1);
+  if constexpr (OP < 2 * NP) {
+    constexpr int pr = OP >> 1;
+    apply_gate<NQ, R, CANON, (OP & 1) ? kCvx : kCnot, pair_ctrl(NQ, pr), pair_tgt(NQ, pr)>(
+        re, im, lane, s);
+  } else {
+    constexpr int w = (OP - 2 * NP) >> 1;
+    apply_gate<NQ, R, CANON, (OP & 1) ? kTx : kHad, -1, w>(re, im, lane, s);
+  }
+}
+
+#define QE_CASE(k)                                                      \
+  case k:                                                               \
+    if constexpr ((k) < 2 * NQ * NQ) apply_op<NQ, R, CANON, (k)>(re, im, lane, s); \
+    break;
+
+template <int NQ, typename R, bool CANON>
+__device__ __forceinline__ void dispatch(int op, R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>::ROWS],
+                                         int lane, R s) {
+  switch (op) {
+    QE_CASE(0) QE_CASE(1) QE_CASE(2) QE_CASE(3) QE_CASE(4) QE_CASE(5) QE_CASE(6) QE_CASE(7)
+    QE_CASE(8) QE_CASE(9) QE_CASE(10) QE_CASE(11) QE_CASE(12) QE_CASE(13) QE_CASE(14)
+    QE_CASE(15) QE_CASE(16) QE_CASE(17) QE_CASE(18) QE_CASE(19) QE_CASE(20) QE_CASE(21)
+    QE_CASE(22) QE_CASE(23) QE_CASE(24) QE_CASE(25) QE_CASE(26) QE_CASE(27) QE_CASE(28)
+    QE_CASE(29) QE_CASE(30) QE_CASE(31) QE_CASE(32) QE_CASE(33) QE_CASE(34) QE_CASE(35)
+    QE_CASE(36) QE_CASE(37) QE_CASE(38) QE_CASE(39) QE_CASE(40) QE_CASE(41) QE_CASE(42)
+    QE_CASE(43) QE_CASE(44) QE_CASE(45) QE_CASE(46) QE_CASE(47) QE_CASE(48) QE_CASE(49)
+    default:
+      break;
+  }
+}
+#undef QE_CASE
+
+// real operations of one op on an N x N state (gate-count work model)
+__device__ __forceinline__ uint32_t op_work(const DevProblem &p, int op) {
+  if (op == kOpIdentity) return 0;
+  const int o = op & 0x7f;
+  const uint32_t NN = p.N * p.N;
+  const int np2 = 2 * (int)(p.n * (p.n - 1));
+  if (o < np2) return (o & 1) ? 4 * NN : 0;  // CV: 4N^2, CNOT: 0
+  return (o & 1) ? 2 * NN : 4 * NN;          // T: 2N^2, H: 4N^2
+}
+
+// ------------------------------------------------------------------ sampling
+// Sec. IV-D: draw whichIndividual and whichRotationOrInteraction, form the
+// segment index (Eq. (10)), measure the segment's qutrit (and qubit) in binary32.
+__device__ __forceinline__ void sample_slot(const DevProblem &p, uint32_t c, uint32_t t,
+                                            uint32_t gen, uint32_t &g_out, uint32_t &seg_out) {
+  const uint4 u = draw(p, c, t, gen, kStSample);
+  const uint32_t i = below(u.x, p.P), r = below(u.y, p.R);
+  const uint32_t seg = r * p.LP + i * p.L + t;
+  const float4 a = __ldg(p.cur + 2 * (size_t)seg);
+  const float4 b = __ldg(p.cur + 2 * (size_t)seg + 1);
+  const float p0 = __fadd_rn(__fmul_rn(a.x, a.x), __fmul_rn(a.y, a.y));
+  const float p1 = __fadd_rn(__fmul_rn(a.z, a.z), __fmul_rn(a.w, a.w));
+  const float p2 = __fadd_rn(__fmul_rn(b.x, b.x), __fmul_rn(b.y, b.y));
+  const float p01 = __fadd_rn(p0, p1);
+  const float s = __fadd_rn(p01, p2);
+  const float x = __fmul_rn(unit32(u.z), s);
+  const uint32_t k = (x < p0) ? 0u : ((x < p01) ? 1u : 2u);
+  uint32_t g = p.base + 3u * r + k;
+  if (p.has_qubit) {
+    const float B0 = __fmul_rn(b.z, b.z), B1 = __fmul_rn(b.w, b.w);
+    const float y = __fmul_rn(unit32(u.w), __fadd_rn(B0, B1));
+    if (y < B0) g = 0;
+  }
+  g_out = g;
+  seg_out = seg;
+}
+
+// ------------------------------------------------------------------ one circuit
+struct CircuitOut {
+  double F;       // fitness (binary64 for CANON; widened binary32 otherwise)
+  uint32_t cost;  // non-identity gates
+  uint32_t work;  // useful real operations
+  bool bad;       // an op byte was invalid
+};
+
+// ops0/ops1: this lane's op bytes for slots lane and lane + 32
+template <int NQ, typename R, bool CANON>
+__device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lane, uint32_t ops0,
+                                                    uint32_t ops1, R *S_out) {
+  using Ly = Lay<NQ>;
+  constexpr int N = Ly::N;
+  const int j = lane & (N - 1);
+  const int grp = (lane >> NQ) & ((1 << Ly::RBL) - 1);
+  const bool shadow = (lane >> (NQ + Ly::RBL)) != 0;
+  R re[Ly::ROWS], im[Ly::ROWS];
+#pragma unroll
+  for (int r = 0; r < Ly::ROWS; ++r) {
+    re[r] = (((grp << Ly::RBR) | r) == j) ? R(1) : R(0);
+    im[r] = R(0);
+  }
+  uint32_t cost = 0, work = 0;
+  for (uint32_t t = 0; t < p.L; ++t) {
+    const uint32_t src = t < 32 ? ops0 : ops1;
+    const int op = __shfl_sync(kFull, (int)src, (int)(t & 31));
+    if (op == kOpIdentity) continue;
+    cost += 1;
+    work += op_work(p, op);
+    const R s = (op & kOpNeg) ? R(-1) : R(1);
+    dispatch<NQ, R, CANON>(op & 0x7f, re, im, lane, s);
+  }
+  CircuitOut out;
+  out.cost = cost;
+  out.work = work + 2u * N;
+  out.bad = false;
+  if (S_out) {
+    if (!shadow) {
+#pragma unroll
+      for (int r = 0; r < Ly::ROWS; ++r) {
+        const int i = (grp << Ly::RBR) | r;
+        S_out[2 * (i * N + j)] = re[r];
+        S_out[2 * (i * N + j) + 1] = im[r];
+      }
+    }
+  }
+  // this lane's S[perm[j]][j], if it holds that row.  Picked by an arithmetic
+  // blend (exact: one term has weight 1, the rest weight 0) so that the state
+  // array is never indexed dynamically and stays in registers.
+  const int pj = p.perm[j];
+  R vr = R(0), vi = R(0);
+  {
+    const uint32_t own = (!shadow && (pj >> Ly::RBR) == grp) ? (1u << (pj & (Ly::ROWS - 1))) : 0u;
+#pragma unroll
+    for (int r = 0; r < Ly::ROWS; ++r) {
+      const R m = (R)((own >> r) & 1u);
+      vr = fma(m, re[r], vr);
+      vi = fma(m, im[r], vi);
+    }
+  }
+  const double pen =
+      p.cost_weight == 0.0 ? 0.0 : __dmul_rn(p.cost_weight, __ddiv_rn((double)cost, (double)p.L));
+  if constexpr (CANON) {
+    // sequential sum over j ascending, every lane runs the same sequence
+    double a = 0.0, b = 0.0;
+    for (int jj = 0; jj < N; ++jj) {
+      const int owner = ((p.perm[jj] >> Ly::RBR) << NQ) | jj;
+      const double xr = __shfl_sync(kFull, vr, owner), xi = __shfl_sync(kFull, vi, owner);
+      if (p.fit_kind == 1) {
+        a = __dadd_rn(a, __dadd_rn(__dmul_rn(xr, xr), __dmul_rn(xi, xi)));
+      } else {
+        a = __dadd_rn(a, xr);
+        b = __dadd_rn(b, -xi);
+      }
+    }
+    const double size = (double)N;
+    double d;
+    if (p.fit_kind == 1) {
+      d = __ddiv_rn(__dsub_rn(size, a), size);
+    } else {
+      const double m = __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
+      d = __ddiv_rn(__dsub_rn(size, m), size);
+    }
+    if (d < 0.0) d = 0.0;
+    const double f = __dsub_rn(1.0, __dsqrt_rn(d));
+    out.F = __dsub_rn(f, pen);
+  } else {
+    float a, b;
+    if (p.fit_kind == 1) {
+      a = vr * vr + vi * vi;
+      b = 0.f;
+    } else {
+      a = vr;
+      b = vi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+    }
+    const float size = (float)N;
+    float d;
+    if (p.fit_kind == 1) {
+      d = (size - a) / size;
+    } else {
+      d = (size - sqrtf(a * a + b * b)) / size;
+    }
+    d = fmaxf(d, 0.f);
+    const float f = 1.f - sqrtf(d);
+    out.F = pen == 0.0 ? (double)f : (double)(float)((double)f - pen);
+  }
+  return out;
+}
+
+// op byte of library gate g (kOpIdentity also for out-of-range g; bad flags it)
+__device__ __forceinline__ uint32_t op_of(const DevProblem &p, uint32_t g, bool &bad) {
+  if (g >= p.G) {
+    bad = true;
+    return kOpIdentity;
+  }
+  return p.gop[g];
+}
+
+__device__ __forceinline__ uint32_t find_problem(const uint32_t *prefix, uint32_t n, uint32_t x) {
+  // largest q with prefix[q] <= x
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(prefix + mid) <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------ kernels
+// Whole generation for a group of searches: sample, compose, score, scatter.
+// minimum resident 256-thread blocks per SM: the 5-qubit binary32 kernel is
+// capped at 128 registers (its 64 state registers plus temporaries); the
+// scheduler otherwise interleaves every row pair of a gate and asks for ~190.
+template <int NQ, bool CANON>
+constexpr int min_blocks() {
+  return (NQ == 5 && !CANON) ? 2 : 1;
+}
+
+template <int NQ, typename R, bool CANON>
+__global__ void __launch_bounds__(256, min_blocks<NQ, CANON>()) k_step(const DevProblem *__restrict__ probs,
+                                              const uint32_t *__restrict__ group,
+                                              const uint32_t *__restrict__ prefix,
+                                              uint32_t n_group, uint32_t total, DevGlobal g) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t gen = *g.gen;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+    const uint32_t q = find_problem(prefix, n_group, w);
+    const DevProblem &p = probs[group[q]];
+    const uint32_t c = w - prefix[q];
+    uint32_t o0 = kOpIdentity, o1 = kOpIdentity, seg0 = 0, seg1 = 0;
+    bool bad = false;
+    if ((uint32_t)lane < p.L) {
+      uint32_t gg;
+      sample_slot(p, c, lane, gen, gg, seg0);
+      p.gate_idx[(size_t)c * p.L + lane] = (uint8_t)gg;
+      p.seg_id[(size_t)c * p.L + lane] = seg0;
+      o0 = op_of(p, gg, bad);
+    }
+    if ((uint32_t)lane + 32 < p.L) {
+      uint32_t gg;
+      sample_slot(p, c, lane + 32, gen, gg, seg1);
+      p.gate_idx[(size_t)c * p.L + lane + 32] = (uint8_t)gg;
+      p.seg_id[(size_t)c * p.L + lane + 32] = seg1;
+      o1 = op_of(p, gg, bad);
+    }
+    CircuitOut out = compose_score<NQ, R, CANON>(p, lane, o0, o1, (R *)nullptr);
+    const bool nonfinite = !isfinite(out.F);
+    if (lane == 0) {
+      if constexpr (CANON) p.fit64[c] = out.F;
+      else p.fit32[c] = (float)out.F;
+      p.meta[c] = out.cost | (out.work << 8);
+      if (nonfinite) atomicOr(g.err, kErrNonFinite);
+    }
+    if (!nonfinite) {
+      const uint32_t key = fkey((float)out.F);
+      if ((uint32_t)lane < p.L) atomicMax(p.sfkey + seg0, key);
+      if ((uint32_t)lane + 32 < p.L) atomicMax(p.sfkey + seg1, key);
+    }
+  }
+}
+
+// Measurement only (qe_sample).
+__global__ void __launch_bounds__(256) k_sample(const DevProblem *__restrict__ probs,
+                                                uint32_t prob, uint32_t gen, uint8_t *gate_idx,
+                                                uint32_t *seg_id) {
+  const DevProblem &p = probs[prob];
+  const size_t n = (size_t)p.P * p.L;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t c = (uint32_t)(e / p.L), t = (uint32_t)(e % p.L);
+    uint32_t gg, seg;
+    sample_slot(p, c, t, gen, gg, seg);
+    gate_idx[e] = (uint8_t)gg;
+    seg_id[e] = seg;
+  }
+}
+
+// Fitness (and optionally the unitaries) of caller-provided gate strings.
+template <int NQ, typename R, bool CANON>
+__global__ void __launch_bounds__(256, min_blocks<NQ, CANON>()) k_eval(const DevProblem *__restrict__ probs, uint32_t prob,
+                                              const uint8_t *__restrict__ gates, uint32_t n,
+                                              R *fit, uint32_t *cost, R *S, DevGlobal g) {
+  const DevProblem &p = probs[prob];
+  const int lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const size_t NN2 = 2 * (size_t)p.N * p.N;
+  for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n; c += nw) {
+    bool bad = false;
+    uint32_t o0 = kOpIdentity, o1 = kOpIdentity;
+    if ((uint32_t)lane < p.L) o0 = op_of(p, gates[(size_t)c * p.L + lane], bad);
+    if ((uint32_t)lane + 32 < p.L) o1 = op_of(p, gates[(size_t)c * p.L + lane + 32], bad);
+    const bool anybad = __any_sync(kFull, bad);
+    CircuitOut out = compose_score<NQ, R, CANON>(p, lane, o0, o1, S ? S + NN2 * c : (R *)nullptr);
+    if (lane == 0) {
+      double F = anybad ? __longlong_as_double(0x7ff8000000000000ll) : out.F;
+      if (fit) fit[c] = (R)F;
+      if (cost) cost[c] = out.cost;
+      if (anybad) atomicOr(g.err, kErrBadGate);
+      else if (!isfinite(F)) atomicOr(g.err, kErrNonFinite);
+    }
+  }
+}
+
+// Binary64 rescoring of ranking candidates: list entries are problem << 20 | slot,
+// the circuit is cand[slot] of that problem, gates come from gsrc (NULL = the
+// problem's own generation buffer).  One launch per qubit count present;
+// entries of other widths are skipped.
+template <int NQ>
+__global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ probs,
+                                                 const uint8_t *__restrict__ gsrc, DevGlobal g) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t total = *g.rescore_n;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+    const uint32_t ent = g.rescore_list[w];
+    const DevProblem &p = probs[ent >> 20];
+    if (p.n != (uint32_t)NQ) continue;
+    const uint32_t slot = ent & 0xfffffu;
+    const uint32_t c = p.cand[slot];
+    const uint8_t *gates = (gsrc ? gsrc : p.gate_idx) + (size_t)c * p.L;
+    bool bad = false;
+    uint32_t o0 = kOpIdentity, o1 = kOpIdentity;
+    if ((uint32_t)lane < p.L) o0 = op_of(p, gates[lane], bad);
+    if ((uint32_t)lane + 32 < p.L) o1 = op_of(p, gates[lane + 32], bad);
+    const bool anybad = __any_sync(kFull, bad);
+    CircuitOut out = compose_score<NQ, double, true>(p, lane, o0, o1, (double *)nullptr);
+    if (lane == 0) p.cand_f[slot] = anybad ? __longlong_as_double(0x7ff8000000000000ll) : out.F;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+#define QE_NQ_SWITCH(n, X) \
+  switch (n) {             \
+    case 1: X(1); break;   \
+    case 2: X(2); break;   \
+    case 3: X(3); break;   \
+    case 4: X(4); break;   \
+    default: X(5); break;  \
+  }
+
+cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs,
+                        const uint32_t *group, const uint32_t *prefix, uint32_t n_group,
+                        uint32_t total, bool canon, const DevGlobal &g, cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  const uint32_t per = canon ? lc.step64[n] : lc.step32[n];
+  const uint32_t blocks = grid_for(lc, total, per);
+#define QE_L(NQ)                                                                               \
+  if (canon)                                                                                   \
+    k_step<NQ, double, true><<<blocks, 256, 0, st>>>(probs, group, prefix, n_group, total, g); \
+  else                                                                                         \
+    k_step<NQ, float, false><<<blocks, 256, 0, st>>>(probs, group, prefix, n_group, total, g);
+  QE_NQ_SWITCH(n, QE_L)
+#undef QE_L
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const LaunchCfg &lc, const DevProblem *probs, uint32_t prob, uint32_t P,
+                          uint32_t L, uint32_t gen, uint8_t *gate_idx, uint32_t *seg_id,
+                          cudaStream_t st) {
+  const size_t n = (size_t)P * L;
+  uint32_t blocks = (uint32_t)((n + 255) / 256);
+  const uint32_t cap = lc.num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  k_sample<<<blocks, 256, 0, st>>>(probs, prob, gen, gate_idx, seg_id);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *probs, uint32_t prob,
+                        bool canon, const uint8_t *gates, uint32_t n, void *fit, uint32_t *cost,
+                        void *S, const DevGlobal &g, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const uint32_t per = canon ? lc.step64[nq] : lc.step32[nq];
+  const uint32_t blocks = grid_for(lc, n, per);
+#define QE_L(NQ)                                                                      \
+  if (canon)                                                                          \
+    k_eval<NQ, double, true><<<blocks, 256, 0, st>>>(probs, prob, gates, n, (double *)fit, \
+                                                     cost, (double *)S, g);           \
+  else                                                                                \
+    k_eval<NQ, float, false><<<blocks, 256, 0, st>>>(probs, prob, gates, n, (float *)fit,  \
+                                                     cost, (float *)S, g);
+  QE_NQ_SWITCH(nq, QE_L)
+#undef QE_L
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, const DevProblem *probs,
+                           const uint8_t *gsrc, const DevGlobal &g, cudaStream_t st) {
+  const uint32_t blocks = lc.num_sms * lc.step64[nq];
+#define QE_L(NQ) k_rescore<NQ><<<blocks, 256, 0, st>>>(probs, gsrc, g);
+  QE_NQ_SWITCH(nq, QE_L)
+#undef QE_L
+  return cudaGetLastError();
+}
+
+cudaError_t query_circuit_occupancy(LaunchCfg &lc) {
+  cudaError_t e = cudaSuccess;
+  int b = 0;
+#define QE_Q(NQ)                                                                            \
+  if (e == cudaSuccess)                                                                     \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, float, false>, 256, 0); \
+  lc.step32[NQ] = b > 0 ? b : 1;                                                            \
+  if (e == cudaSuccess)                                                                     \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, double, true>, 256, 0); \
+  lc.step64[NQ] = b > 0 ? b : 1;
+  QE_Q(1) QE_Q(2) QE_Q(3) QE_Q(4) QE_Q(5)
+#undef QE_Q
+  return e;
+}
+
+}  // namespace qe

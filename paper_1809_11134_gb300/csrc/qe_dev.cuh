@@ -1,0 +1,154 @@
+// qe_dev.cuh -- device-side data layout and primitives of the QEQEA engine.
+//
+// One search's state lives in a single device arena (see capi.cu):
+//   cur/best   : S segments x 32 B  {q0re,q0im,q1re,q1im,q2re,q2im,b0,b1} as 2 float4
+//   best_f     : S floats (segment's best fitness, binary32)
+//   sfkey      : S uint32 (this generation's segment fitness as an order-preserving
+//                key; 0 = untouched), reset to 0 by the update kernel
+//   gate_idx   : P*L uint8, seg_id: P*L uint32 (the generation's circuits)
+//   fit32/fit64: P (working-precision fitness), meta: P (cost | work << 8)
+// where S = R*P*L and seg = r*L*P + i*L + t (Eq. (10)).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qe {
+
+constexpr int kQ = 4096;            // mutation magnitude quantisation
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr uint8_t kOpIdentity = 0xff;
+constexpr uint8_t kOpNeg = 0x80;    // sign bit of the op byte: sigma = -1 (CV^dag, T^dag)
+// 1/sqrt(2) rounded to binary64 and to binary32
+constexpr double kH64 = 0x1.6a09e667f3bcdp-1;
+constexpr float kH32 = 0x1.6a09e6p-1f;
+
+// Philox4x32-10 counter words: (a, b, gen, run << 4 | stream)
+enum Stream : uint32_t { kStSample = 0, kStMutDecide = 1, kStMutSeg = 2, kStGa = 4, kStGaInit = 5 };
+
+// device error word bits (mirrors QE_ERRW_*)
+constexpr uint32_t kErrBadGate = 1u, kErrNonFinite = 2u;
+
+struct Ranked {
+  uint32_t circuit, cost;
+  double fitness;
+};
+
+// best-so-far record and the per-generation report fields of one search
+struct Best {
+  uint32_t generation, best_gen;
+  double best_fitness, gen_best_fitness, mean_fitness;
+  unsigned long long useful_flops;
+  uint32_t best_cost, best_len, error_word, reserved;
+  uint8_t best_gates[64];
+};
+
+struct DevProblem {
+  uint32_t n, N, L, P, R, G, LP;
+  uint32_t lib, prec, fit_kind, enc, topk, k;  // k = max(topk, 1)
+  uint32_t run, has_qubit, base;                // base = 1 if I is library index 0
+  uint32_t key0, key1;
+  float eps_d;        // bound on |d32 - d64|, d = (N - |tr|)/N, for the binary32 path
+  float pad0;
+  double p_mut, cost_weight, ga_rate;
+  // an individual mutates when its Philox word u < mut_T, i.e. when
+  // (u + 1/2) 2^-32 < p_mut (mut_T = ceil(p_mut 2^32 - 1/2), clamped to [0, 2^32])
+  unsigned long long mut_T;
+  uint64_t nseg;
+  uint8_t perm[32];
+  uint8_t gop[80];    // library index -> op byte (see k_circuit.cu), kOpIdentity for I
+  // state and per-generation buffers
+  float4 *cur, *best;
+  float *best_f;
+  uint32_t *sfkey;
+  uint8_t *gate_idx;
+  uint32_t *seg_id;
+  float *fit32;
+  double *fit64;
+  uint32_t *meta;
+  // ranking scratch
+  uint32_t *cand;
+  double *cand_f;
+  uint32_t *cand_n;
+  Ranked *topk_out;
+  Best *rec;
+  // mutation table: cos/sin of m * mutation_range / Q, m = 0..Q
+  float2 *qubit_tab;
+  // GA buffers
+  uint8_t *genome_next;
+  unsigned long long *ga_cum;
+};
+
+// context-wide device pointers
+struct DevGlobal {
+  float2 *th_tab;     // cos/sin of m * (pi/2) / Q
+  float2 *ph_tab;     // cos/sin of m * (2 pi) / Q
+  uint32_t *gen;      // generation counter (graph replays read it)
+  uint32_t *err;      // error word
+  uint32_t *rescore_list;  // (problem << 20 | slot) pairs to rescore in binary64
+  uint32_t *rescore_n;
+};
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11: ten rounds; each round multiplies counter
+// words 0 and 2 by the two round multipliers and xors the high halves into the
+// other words with the key, which is bumped by the two Weyl constants.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 draw(const DevProblem &p, uint32_t a, uint32_t b, uint32_t gen,
+                                      uint32_t stream) {
+  return philox(make_uint4(a, b, gen, (p.run << 4) | stream), p.key0, p.key1);
+}
+
+// integer in [0, m)
+__device__ __forceinline__ uint32_t below(uint32_t u, uint32_t m) { return __umulhi(u, m); }
+// real in (0,1), binary64: (u + 1/2) 2^-32 (exact)
+__device__ __forceinline__ double unit64(uint32_t u) {
+  return __dmul_rn(__dadd_rn((double)u, 0.5), 0x1p-32);
+}
+// real in (0,1), binary32: ((u >> 9) + 1/2) 2^-23 (exact)
+__device__ __forceinline__ float unit32(uint32_t u) {
+  return __fmul_rn(__fadd_rn(__uint2float_rn(u >> 9), 0.5f), 0x1p-23f);
+}
+
+// order-preserving map of a non-NaN float to uint32 (never 0)
+__device__ __forceinline__ uint32_t fkey(float f) {
+  uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+// order-preserving map of a non-NaN double to uint64
+__device__ __forceinline__ unsigned long long dkey(double f) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(f);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// ---------------------------------------------------------------- lane layout
+// A warp holds one circuit's N x N unitary: lane = (row group g, column j),
+// j = lane & (N-1), g = the next RBL lane bits; each lane keeps ROWS rows of
+// its column in registers: row i = (g << RBR) | r.  The top RBL row bits live
+// in lane bits, the low RBR row bits in register indices.  For n <= 2 the
+// upper lanes are shadows that compute but never write.
+template <int NQ>
+struct Lay {
+  static constexpr int N = 1 << NQ;
+  static constexpr int RBL = (NQ < 5 - NQ) ? NQ : 5 - NQ;
+  static constexpr int RBR = NQ - RBL;
+  static constexpr int ROWS = 1 << RBR;
+  static constexpr int USED = N << RBL;  // lanes that hold data
+};
+
+}  // namespace qe

@@ -1,0 +1,78 @@
+// qe_host.h -- internal launch interface between the C ABI (capi.cu) and the
+// kernel translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qe_dev.cuh"
+
+namespace qe {
+
+struct LaunchCfg {
+  uint32_t num_sms = 1;
+  // resident 256-thread blocks per SM of the circuit kernels, by qubit count
+  uint32_t step32[6] = {1, 1, 1, 1, 1, 1};
+  uint32_t step64[6] = {1, 1, 1, 1, 1, 1};
+};
+
+// persistent grid: at most the resident blocks of the whole GPU, fewer if
+// there are fewer warps of work (8 warps per 256-thread block)
+inline uint32_t grid_for(const LaunchCfg &lc, uint64_t warps, uint32_t per_sm) {
+  uint64_t need = (warps + 7) / 8;
+  uint64_t cap = (uint64_t)lc.num_sms * per_sm;
+  if (need > cap) need = cap;
+  return need ? (uint32_t)need : 1u;
+}
+
+// one ranking job: search `prob` over n circuits whose working-precision
+// fitness is at fit (float or double by the search's precision) and whose
+// cost|work words are at meta; gates at gsrc (rescoring); update_record says
+// whether the best-so-far record and report fields are written.
+struct RankJob {
+  uint32_t prob;
+  uint32_t n;
+  const void *fit;
+  const uint32_t *meta;
+  const uint8_t *gsrc;
+  uint32_t update_record;
+  uint32_t pad;
+};
+
+// k_circuit.cu
+cudaError_t query_circuit_occupancy(LaunchCfg &lc);
+// all searches of a launch have n qubits
+cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs,
+                        const uint32_t *group, const uint32_t *prefix, uint32_t n_group,
+                        uint32_t total, bool canon, const DevGlobal &g, cudaStream_t st);
+cudaError_t launch_sample(const LaunchCfg &lc, const DevProblem *probs, uint32_t prob, uint32_t P,
+                          uint32_t L, uint32_t gen, uint8_t *gate_idx, uint32_t *seg_id,
+                          cudaStream_t st);
+cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *probs, uint32_t prob,
+                        bool canon, const uint8_t *gates, uint32_t n, void *fit, uint32_t *cost,
+                        void *S, const DevGlobal &g, cudaStream_t st);
+cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, const DevProblem *probs,
+                           const uint8_t *gsrc, const DevGlobal &g, cudaStream_t st);
+
+// k_update.cu
+cudaError_t launch_init_state(const DevProblem *probs, uint32_t prob, uint64_t nseg,
+                              cudaStream_t st);
+cudaError_t launch_scatter(const DevProblem *probs, uint32_t prob, uint32_t P, uint32_t L,
+                           const uint32_t *seg_id, const double *fitness, uint32_t *err,
+                           cudaStream_t st);
+// elitism + mutation for the searches group[0..n_group); prefA: P*L prefix,
+// prefB: ceil(P/32) prefix; gen read from *d_gen when d_gen != NULL
+cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const uint32_t *group,
+                          const uint32_t *prefA, const uint32_t *prefB, uint32_t n_group,
+                          uint32_t totalA, uint32_t totalB, const uint32_t *d_gen, uint32_t gen,
+                          const uint32_t *seg_override, const DevGlobal &g, cudaStream_t st);
+
+// k_rank.cu
+// jobs == NULL: one job given by value in `single`
+cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
+                               const RankJob &single, const DevGlobal &g, cudaStream_t st);
+cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
+                             const RankJob &single, const DevGlobal &g, cudaStream_t st);
+cudaError_t launch_finish(const DevGlobal &g, cudaStream_t st);
+cudaError_t launch_reset_counter(const DevGlobal &g, cudaStream_t st);
+
+}  // namespace qe

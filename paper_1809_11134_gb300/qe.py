@@ -1,0 +1,368 @@
+"""Thin ctypes binding of the C ABI in include/qe.h (libqe.so).
+
+Every function marshals arguments and calls the library; all computation runs
+in the library's CUDA kernels.  Device buffers are torch CUDA tensors (their
+data_ptr() is passed), host buffers are numpy arrays.  There is no fallback:
+importing the binding without a built libqe.so raises.
+"""
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqe.so")
+
+QE_OK, QE_EINVAL, QE_ENOMEM, QE_ECUDA, QE_ETIMEOUT, QE_ENUMERIC, QE_ESTATE, QE_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["QE_OK", "QE_EINVAL", "QE_ENOMEM", "QE_ECUDA", "QE_ETIMEOUT", "QE_ENUMERIC",
+                "QE_ESTATE", "QE_EUNSUPPORTED"]
+QE_LIB_NCV, QE_LIB_HT, QE_LIB_IDENTITY = 1, 2, 4
+QE_PREC_FP64, QE_PREC_FP32, QE_PREC_SPLIT_TC = 0, 1, 2
+QE_FIT_TRACE, QE_FIT_PROB = 0, 1
+QE_ENC_QEQEA, QE_ENC_GA = 0, 1
+QE_ERRW_BAD_GATE, QE_ERRW_NONFINITE = 1, 2
+
+# every symbol include/qe.h declares
+EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_host", "qe_compose",
+           "qe_update", "qe_step", "qe_last_generation", "qe_state_bytes", "qe_get_state",
+           "qe_set_state", "qe_generation", "qe_stage_timing", "qe_stage_times",
+           "qe_last_error", "qe_destroy"]
+
+
+class qe_problem(C.Structure):
+    _fields_ = [("n_qubits", C.c_uint32), ("circuit_len", C.c_uint32),
+                ("population", C.c_uint32), ("library", C.c_uint32), ("encoding", C.c_uint32),
+                ("precision", C.c_uint32), ("fitness_kind", C.c_uint32), ("topk", C.c_uint32),
+                ("seed", C.c_uint64), ("p_mutation", C.c_double), ("mutation_range", C.c_double),
+                ("ga_mutation_rate", C.c_double), ("cost_weight", C.c_double),
+                ("target_perm", C.c_uint8 * 32)]
+
+
+class qe_ranked(C.Structure):
+    _fields_ = [("circuit", C.c_uint32), ("cost", C.c_uint32), ("fitness", C.c_double)]
+
+
+class qe_report(C.Structure):
+    _fields_ = [("generation", C.c_uint32), ("best_gen", C.c_uint32),
+                ("best_fitness", C.c_double), ("gen_best_fitness", C.c_double),
+                ("mean_fitness", C.c_double), ("useful_flops", C.c_uint64),
+                ("best_cost", C.c_uint32), ("best_len", C.c_uint32), ("error_word", C.c_uint32),
+                ("reserved", C.c_uint32), ("best_gates", C.c_uint8 * 64)]
+
+
+class QeError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, message))
+
+
+_lib = None
+
+
+def lib():
+    """Load libqe.so (built by __graft_entry__.build() / _build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libqe.so is not built (run __graft_entry__.build()); "
+                              "there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        vp, u32, u64, sz = C.c_void_p, C.c_uint32, C.c_uint64, C.c_size_t
+        L.qe_library_info.argtypes = [u32, u32, C.POINTER(u32), C.POINTER(u32)]
+        L.qe_init.argtypes = [C.POINTER(vp), C.POINTER(qe_problem), u32, vp]
+        L.qe_sample.argtypes = [vp, u32, u32, vp, vp]
+        L.qe_eval.argtypes = [vp, u32, vp, u32, vp, vp, C.POINTER(qe_ranked)]
+        L.qe_eval_host.argtypes = [vp, u32, vp, u32, vp, C.POINTER(qe_ranked)]
+        L.qe_compose.argtypes = [vp, u32, vp, u32, vp]
+        L.qe_update.argtypes = [vp, u32, u32, vp, vp]
+        L.qe_step.argtypes = [vp, u32, C.POINTER(qe_report)]
+        L.qe_last_generation.argtypes = [vp, u32, vp, vp, vp, C.POINTER(qe_ranked)]
+        L.qe_state_bytes.argtypes = [vp, u32, C.POINTER(sz)]
+        L.qe_get_state.argtypes = [vp, u32, vp, sz]
+        L.qe_set_state.argtypes = [vp, u32, vp, sz]
+        L.qe_generation.argtypes = [vp, C.POINTER(u32)]
+        L.qe_stage_timing.argtypes = [vp, C.c_int]
+        L.qe_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
+        L.qe_last_error.argtypes = [vp]
+        L.qe_last_error.restype = C.c_char_p
+        L.qe_destroy.argtypes = [vp]
+        L.qe_destroy.restype = None
+        for name in EXPORTS:
+            if name not in ("qe_last_error", "qe_destroy"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(ctx_ptr, status):
+    if status != QE_OK:
+        msg = lib().qe_last_error(ctx_ptr)
+        raise QeError(status, (msg or b"").decode())
+    return status
+
+
+def to_problem(s) -> qe_problem:
+    """qe_problem from a workloads.Search (or pass a qe_problem through)."""
+    if isinstance(s, qe_problem):
+        return s
+    p = qe_problem()
+    p.n_qubits, p.circuit_len, p.population, p.library = s.n, s.L, s.P, s.library
+    p.encoding = getattr(s, "encoding", QE_ENC_QEQEA)
+    p.precision, p.fitness_kind, p.topk = s.precision, s.fitness_kind, s.topk
+    p.seed = s.seed
+    p.p_mutation, p.mutation_range = s.p_mutation, s.mutation_range
+    p.ga_mutation_rate, p.cost_weight = s.ga_mutation_rate, s.cost_weight
+    for j in range(32):
+        p.target_perm[j] = s.perm[j] if j < len(s.perm) else 0
+    return p
+
+
+def qe_library_info(n_qubits: int, library: int):
+    g, r = C.c_uint32(), C.c_uint32()
+    _check(None, lib().qe_library_info(n_qubits, library, C.byref(g), C.byref(r)))
+    return g.value, r.value
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _need(t, dtype, numel, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() < numel:
+        raise TypeError("%s must be a contiguous %s tensor with >= %d elements" % (name, dtype, numel))
+
+
+class Context:
+    """One qe_ctx: n independent searches sharing every launch."""
+
+    def __init__(self, searches: Sequence, stream=None):
+        self.searches = list(searches)
+        probs = (qe_problem * len(self.searches))(*[to_problem(s) for s in self.searches])
+        self._probs = probs
+        h = C.c_void_p()
+        st = lib().qe_init(C.byref(h), probs, len(self.searches), _stream_handle(stream))
+        if st != QE_OK:
+            raise QeError(st, (lib().qe_last_error(None) or b"").decode())
+        self.h = h
+        self.stream = stream
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def prob(self, i):
+        return self._probs[i]
+
+    # ------------------------------------------------------------ calls
+    def sample(self, prob, gen, gate_idx, seg_id):
+        import torch
+        p = self._probs[prob]
+        n = p.population * p.circuit_len
+        _need(gate_idx, torch.uint8, n, "gate_idx")
+        _need(seg_id, torch.int32, n, "seg_id")
+        _check(self.h, lib().qe_sample(self.h, prob, gen, _ptr(gate_idx), _ptr(seg_id)))
+
+    def eval(self, prob, gate_idx, fitness, n_circuits=None, cost=None, topk=False):
+        import torch
+        p = self._probs[prob]
+        n = gate_idx.shape[0] if n_circuits is None else n_circuits
+        _need(gate_idx, torch.uint8, n * p.circuit_len, "gate_idx")
+        _need(fitness, torch.float64 if p.precision == QE_PREC_FP64 else torch.float32, n,
+              "fitness")
+        if cost is not None:
+            _need(cost, torch.int32, n, "cost")
+        out = None
+        if topk:
+            k = min(max(p.topk, 1), n)
+            out = (qe_ranked * max(k, 1))()
+        _check(self.h, lib().qe_eval(self.h, prob, _ptr(gate_idx), n, _ptr(fitness), _ptr(cost),
+                                     out))
+        if topk:
+            return [(r.circuit, r.cost, r.fitness) for r in out[:k]]
+        return None
+
+    def eval_host(self, prob, gate_idx: np.ndarray, topk=False):
+        p = self._probs[prob]
+        g = np.ascontiguousarray(gate_idx, np.uint8)
+        n = g.shape[0]
+        fit = np.zeros(n, np.float64 if p.precision == QE_PREC_FP64 else np.float32)
+        out = None
+        if topk:
+            k = min(max(p.topk, 1), n)
+            out = (qe_ranked * max(k, 1))()
+        _check(self.h, lib().qe_eval_host(self.h, prob, g.ctypes.data_as(C.c_void_p), n,
+                                          fit.ctypes.data_as(C.c_void_p), out))
+        if topk:
+            return fit, [(r.circuit, r.cost, r.fitness) for r in out[:k]]
+        return fit
+
+    def eval_host_ptr(self, prob, h_gates_ptr, n, h_fit_ptr, topk_buf=None):
+        """qe_eval_host on raw host pointers (pinned buffers, for timing)."""
+        return _check(self.h, lib().qe_eval_host(self.h, prob, C.c_void_p(h_gates_ptr), n,
+                                                 C.c_void_p(h_fit_ptr), topk_buf))
+
+    def compose(self, prob, gate_idx, unitary, n_circuits=None):
+        import torch
+        p = self._probs[prob]
+        n = gate_idx.shape[0] if n_circuits is None else n_circuits
+        N = 1 << p.n_qubits
+        dt = torch.float64 if p.precision == QE_PREC_FP64 else torch.float32
+        _need(unitary, dt, n * N * N * 2, "unitary")
+        _need(gate_idx, torch.uint8, n * p.circuit_len, "gate_idx")
+        _check(self.h, lib().qe_compose(self.h, prob, _ptr(gate_idx), n, _ptr(unitary)))
+
+    def update(self, prob, gen, seg_id, fitness):
+        import torch
+        p = self._probs[prob]
+        _need(seg_id, torch.int32, p.population * p.circuit_len, "seg_id")
+        _need(fitness, torch.float64, p.population, "fitness")
+        _check(self.h, lib().qe_update(self.h, prob, gen, _ptr(seg_id), _ptr(fitness)))
+
+    def step(self, n_gen=1, reports=True):
+        rep = (qe_report * len(self.searches))() if reports else None
+        st = lib().qe_step(self.h, n_gen, rep)
+        if st not in (QE_OK, QE_ENUMERIC):
+            _check(self.h, st)
+        if not reports:
+            return st
+        out = []
+        for r in rep:
+            out.append(dict(generation=r.generation, best_gen=r.best_gen,
+                            best_fitness=r.best_fitness, gen_best_fitness=r.gen_best_fitness,
+                            mean_fitness=r.mean_fitness, useful_flops=r.useful_flops,
+                            best_cost=r.best_cost, best_len=r.best_len, error_word=r.error_word,
+                            best_gates=list(r.best_gates[:r.best_len]), status=st))
+        return out
+
+    def step_raw(self, n_gen, rep_buf):
+        """qe_step into a preallocated qe_report array (for timing)."""
+        return lib().qe_step(self.h, n_gen, rep_buf)
+
+    def last_generation(self, prob):
+        p = self._probs[prob]
+        PL = p.population * p.circuit_len
+        gi = np.zeros(PL, np.uint8)
+        sid = np.zeros(PL, np.uint32)
+        fit = np.zeros(p.population, np.float64)
+        k = max(p.topk, 1)
+        tk = (qe_ranked * k)()
+        _check(self.h, lib().qe_last_generation(self.h, prob, gi.ctypes.data_as(C.c_void_p),
+                                                sid.ctypes.data_as(C.c_void_p),
+                                                fit.ctypes.data_as(C.c_void_p), tk))
+        return dict(gate_idx=gi.reshape(p.population, p.circuit_len),
+                    seg_id=sid.reshape(p.population, p.circuit_len), fitness=fit,
+                    topk=[(r.circuit, r.cost, r.fitness) for r in tk])
+
+    def state_bytes(self, prob):
+        n = C.c_size_t()
+        _check(self.h, lib().qe_state_bytes(self.h, prob, C.byref(n)))
+        return n.value
+
+    def get_state(self, prob):
+        """QEQEA: (cur[S*8] f32, best[S*8] f32, best_f[S] f32); GA: genome [P, L] u8."""
+        nb = self.state_bytes(prob)
+        buf = np.zeros(nb, np.uint8)
+        _check(self.h, lib().qe_get_state(self.h, prob, buf.ctypes.data_as(C.c_void_p), nb))
+        p = self._probs[prob]
+        if p.encoding == QE_ENC_GA:
+            return buf.reshape(p.population, p.circuit_len)
+        S = nb // 68
+        cur = buf[:32 * S].view(np.float32).copy()
+        best = buf[32 * S:64 * S].view(np.float32).copy()
+        bf = buf[64 * S:].view(np.float32).copy()
+        return cur, best, bf
+
+    def set_state(self, prob, cur, best=None, best_f=None):
+        p = self._probs[prob]
+        if p.encoding == QE_ENC_GA:
+            buf = np.ascontiguousarray(cur, np.uint8).ravel()
+        else:
+            buf = np.concatenate([np.ascontiguousarray(cur, np.float32).view(np.uint8).ravel(),
+                                  np.ascontiguousarray(best, np.float32).view(np.uint8).ravel(),
+                                  np.ascontiguousarray(best_f, np.float32).view(np.uint8).ravel()])
+        _check(self.h, lib().qe_set_state(self.h, prob, buf.ctypes.data_as(C.c_void_p), buf.size))
+
+    def stage_timing(self, enable=True):
+        _check(self.h, lib().qe_stage_timing(self.h, 1 if enable else 0))
+
+    def stage_times(self):
+        """ms of the last generation: circuits, select, rescore, sort, update, whole"""
+        ms = (C.c_float * 6)()
+        _check(self.h, lib().qe_stage_times(self.h, ms))
+        return list(ms)
+
+    def generation(self):
+        g = C.c_uint32()
+        _check(self.h, lib().qe_generation(self.h, C.byref(g)))
+        return g.value
+
+
+# ABI-named entry points (same names as include/qe.h)
+def qe_init(searches, stream=None) -> Context:
+    return Context(searches, stream)
+
+
+def qe_sample(ctx: Context, prob, gen, gate_idx, seg_id):
+    return ctx.sample(prob, gen, gate_idx, seg_id)
+
+
+def qe_eval(ctx: Context, prob, gate_idx, fitness, n_circuits=None, cost=None, topk=False):
+    return ctx.eval(prob, gate_idx, fitness, n_circuits, cost, topk)
+
+
+def qe_eval_host(ctx: Context, prob, gate_idx, topk=False):
+    return ctx.eval_host(prob, gate_idx, topk)
+
+
+def qe_compose(ctx: Context, prob, gate_idx, unitary, n_circuits=None):
+    return ctx.compose(prob, gate_idx, unitary, n_circuits)
+
+
+def qe_update(ctx: Context, prob, gen, seg_id, fitness):
+    return ctx.update(prob, gen, seg_id, fitness)
+
+
+def qe_step(ctx: Context, n_gen=1):
+    return ctx.step(n_gen)
+
+
+def qe_last_generation(ctx: Context, prob):
+    return ctx.last_generation(prob)
+
+
+def qe_get_state(ctx: Context, prob):
+    return ctx.get_state(prob)
+
+
+def qe_set_state(ctx: Context, prob, cur, best=None, best_f=None):
+    return ctx.set_state(prob, cur, best, best_f)
+
+
+def qe_destroy(ctx: Context):
+    ctx.close()
