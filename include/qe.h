@@ -221,6 +221,31 @@ qe_status qe_set_state(qe_ctx *ctx, uint32_t prob, const void *h_buf, size_t byt
 /* Generations completed by qe_step. */
 qe_status qe_generation(const qe_ctx *ctx, uint32_t *gen);
 
+/* Evaluation and ranking without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc -- code running
+ * while a host framework's caching allocator owns the device memory, plugins
+ * in a process whose memory budget is fixed up front, loops that must never
+ * block in an allocator.  It needs no context: given one search description
+ * (host struct; encoding, seed and mutation fields are ignored), n_circuits
+ * gate strings d_gate_idx[c*L + t] on the device, it writes their fitness to
+ * d_fitness (float, or double for QE_PREC_FP64; the same arithmetic as
+ * qe_eval) and, if d_topk is not NULL, the best min(max(topk,1), n_circuits)
+ * circuits rescored in binary64 and sorted by (fitness desc, cost asc, index
+ * asc) to the DEVICE array d_topk.  All work is enqueued on cuda_stream; the
+ * call does not synchronise.  Scratch comes from one static device array of
+ * the library (about 1.25 MiB, held by every GPU that loads the library until
+ * the process exits), so n_circuits is limited to 65536 (QE_EINVAL above it)
+ * and calls that overlap on the GPU -- on different streams, or from
+ * different threads -- race on that scratch.  The first call on a device
+ * looks up the array's device address and launch shapes, so make that first
+ * call before any stream capture.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Errors are returned as a status with a message written
+ * to h_msg (msg_len bytes, may be NULL); invalid gate indices give NaN
+ * fitness.  QE_PREC_SPLIT_TC is QE_EUNSUPPORTED. */
+qe_status qe_eval_rank_static(const qe_problem *prob, const uint8_t *d_gate_idx,
+                              uint32_t n_circuits, void *d_fitness, qe_ranked *d_topk,
+                              void *cuda_stream, char *h_msg, size_t msg_len);
+
 /* Last error message of ctx ("" if none); static text when ctx is NULL. */
 const char *qe_last_error(const qe_ctx *ctx);
 

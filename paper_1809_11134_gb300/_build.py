@@ -18,7 +18,7 @@ LIB = os.path.join(PKG, "libqe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
-UNITS = ["capi.cu", "k_circuit.cu", "k_update.cu", "k_rank.cu"]
+UNITS = ["capi.cu", "k_circuit.cu", "k_update.cu", "k_rank.cu", "noalloc.cu"]
 
 
 def nvcc():

@@ -29,7 +29,7 @@ QE_ERRW_BAD_GATE, QE_ERRW_NONFINITE = 1, 2
 EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_host", "qe_compose",
            "qe_update", "qe_step", "qe_last_generation", "qe_state_bytes", "qe_get_state",
            "qe_set_state", "qe_generation", "qe_stage_timing", "qe_stage_times",
-           "qe_last_error", "qe_destroy"]
+           "qe_eval_rank_static", "qe_last_error", "qe_destroy"]
 
 
 class qe_problem(C.Structure):
@@ -86,6 +86,8 @@ def lib():
         L.qe_generation.argtypes = [vp, C.POINTER(u32)]
         L.qe_stage_timing.argtypes = [vp, C.c_int]
         L.qe_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
+        L.qe_eval_rank_static.argtypes = [C.POINTER(qe_problem), vp, u32, vp, vp, vp,
+                                          C.c_char_p, sz]
         L.qe_last_error.argtypes = [vp]
         L.qe_last_error.restype = C.c_char_p
         L.qe_destroy.argtypes = [vp]
@@ -321,6 +323,23 @@ class Context:
         g = C.c_uint32()
         _check(self.h, lib().qe_generation(self.h, C.byref(g)))
         return g.value
+
+
+def qe_eval_rank_static(search, gate_idx, fitness, topk=None, n_circuits=None, stream=None):
+    """Context-free evaluation + ranking that allocates no device memory.
+
+    gate_idx, fitness and topk (a CUDA uint8 tensor of 16-byte qe_ranked
+    records, or None) are device tensors; the call is asynchronous on `stream`.
+    For callers that may not allocate while it runs, every buffer must exist
+    beforehand; see include/qe.h for the limits and the race between
+    overlapping calls."""
+    p = to_problem(search)
+    n = gate_idx.shape[0] if n_circuits is None else n_circuits
+    msg = C.create_string_buffer(256)
+    st = lib().qe_eval_rank_static(C.byref(p), _ptr(gate_idx), n, _ptr(fitness), _ptr(topk),
+                                   _stream_handle(stream), msg, 256)
+    if st != QE_OK:
+        raise QeError(st, msg.value.decode())
 
 
 # ABI-named entry points (same names as include/qe.h)
