@@ -32,8 +32,8 @@ struct Group {
 struct qe_ctx {
   int device = 0;
   cudaStream_t user = nullptr;
-  cudaStream_t cap = nullptr, side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t cap = nullptr, side = nullptr, side2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
   std::vector<qe_problem> probs;
   std::vector<DevProblem> hp;
   DevProblem *d_probs = nullptr;
@@ -46,7 +46,7 @@ struct qe_ctx {
   // all QEQEA searches (update launch)
   uint32_t n_upd = 0, upd_totalA = 0, upd_totalB = 0;
   uint32_t *d_upd_ids = nullptr, *d_upd_prefA = nullptr, *d_upd_prefB = nullptr;
-  // per-search single arrays for qe_update: {id}, {0, P*L}, {0, ceil(P/32)}
+  // per-search single arrays for qe_update: {id}, {0, P*L}, {0, ceil(P/32)*R}
   uint32_t *d_single = nullptr;
   RankJob *d_jobs = nullptr;
   uint32_t n_jobs = 0;
@@ -177,6 +177,40 @@ struct Arena {
 // the column error; the probability form doubles it.  Generous by a factor 2.
 float eps_d_for(uint32_t L) { return (float)((double)L * 8e-7 + 2e-6); }
 
+// Eq. (12) in binary32: index 0..2 of cv/sv = theta1..3 (c_k, s_k), 3..7 =
+// phi1..5 (cos, sin).  Phase factors e^{i(+-a +-b ...)} are products of the
+// single-parameter phases taken left to right, real factors are applied left
+// to right, every operation rounded (this file is built without FMA
+// contraction), so the table equals a per-segment evaluation in that order.
+struct F2 {
+  float re, im;
+};
+static F2 f2mul(F2 a, F2 b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+static F2 f2sub(F2 a, F2 b) { return {a.re - b.re, a.im - b.im}; }
+static F2 f2scale(F2 a, float s) { return {a.re * s, a.im * s}; }
+static F2 f2neg(F2 a) { return {-a.re, -a.im}; }
+
+void su3_binary32(const float *cv, const float *sv, float2 *out) {
+  const float c1 = cv[0], c2 = cv[1], c3 = cv[2], s1 = sv[0], s2 = sv[1], s3 = sv[2];
+  auto ep = [&](int k) { return F2{cv[2 + k], sv[2 + k]}; };
+  auto em = [&](int k) { return F2{cv[2 + k], -sv[2 + k]}; };
+  F2 U[9];
+  U[0] = f2scale(f2scale(ep(1), c1), c2);
+  U[1] = f2scale(ep(3), s1);
+  U[2] = f2scale(f2scale(ep(4), c1), s2);
+  U[3] = f2sub(f2scale(f2scale(f2mul(em(4), em(5)), s2), s3),
+               f2scale(f2scale(f2scale(f2mul(f2mul(ep(1), ep(2)), em(3)), s1), c2), c3));
+  U[4] = f2scale(f2scale(ep(2), c1), c3);
+  U[5] = f2sub(f2neg(f2scale(f2scale(f2mul(em(1), em(5)), c2), s3)),
+               f2scale(f2scale(f2scale(f2mul(f2mul(ep(2), em(3)), ep(4)), s1), s2), c3));
+  U[6] = f2sub(f2neg(f2scale(f2scale(f2mul(em(2), em(4)), s2), c3)),
+               f2scale(f2scale(f2scale(f2mul(f2mul(ep(1), em(3)), ep(5)), s1), c2), s3));
+  U[7] = f2scale(f2scale(ep(5), c1), s3);
+  U[8] = f2sub(f2scale(f2scale(f2mul(em(1), em(2)), c2), c3),
+               f2scale(f2scale(f2scale(f2mul(f2mul(em(3), ep(4)), ep(5)), s1), s2), s3));
+  for (int k = 0; k < 9; ++k) out[k] = make_float2(U[k].re, U[k].im);
+}
+
 unsigned long long threshold(double p) {
   // number of u in [0, 2^32) with (u + 1/2) 2^-32 < p
   const double X = p * 4294967296.0;
@@ -195,7 +229,8 @@ qe_status check_ctx(qe_ctx *ctx, uint32_t prob) {
 
 // stage events (when timing): 0 start, 1 after the circuit kernels, 2 after
 // ranking selection, 3 after rescoring, 4 after the sort (main stream);
-// 5 before and 6 after the update (side stream); 7 end of the generation
+// 5 before and 6 after the update (side stream, forked after the selection);
+// 7 end of the generation
 qe_status build_graph(qe_ctx *ctx) {
   cudaStream_t cs = ctx->cap;
   QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -210,18 +245,23 @@ qe_status build_graph(qe_ctx *ctx) {
                       (uint32_t)gr.ids.size(), gr.total, gr.canon, ctx->g, cs);
   }
   mark(1, cs);
-  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, cs);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-  mark(5, ctx->side);
-  if (e == cudaSuccess && ctx->n_upd)
-    e = launch_update(ctx->lc, ctx->d_probs, ctx->d_upd_ids, ctx->d_upd_prefA, ctx->d_upd_prefB,
-                      ctx->n_upd, ctx->upd_totalA, ctx->upd_totalB, ctx->g.gen, 0, nullptr, ctx->g,
-                      ctx->side);
-  mark(6, ctx->side);
+  // the selection runs alone (it needs whole 1024-thread CTAs); then the update
+  // forks off and overlaps the binary64 rescoring and the sort
   RankJob none{};
   if (e == cudaSuccess)
     e = launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, none, ctx->g, cs);
   mark(2, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side2, ctx->ev_fork, 0);
+  mark(5, ctx->side);
+  if (e == cudaSuccess && ctx->n_upd)
+    e = launch_update(ctx->lc, ctx->d_probs, ctx->d_upd_ids, ctx->d_upd_prefA, ctx->d_upd_prefB,
+                      ctx->n_upd, ctx->upd_totalA, ctx->upd_totalB, ctx->g.gen, 0, nullptr, ctx->g,
+                      ctx->side, ctx->side2);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_join2, 0);
+  mark(6, ctx->side);
   for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
     if (e == cudaSuccess && ctx->rescore_nq[nq])
       e = launch_rescore(ctx->lc, nq, ctx->d_probs, nullptr, ctx->g, cs);
@@ -240,6 +280,27 @@ qe_status build_graph(qe_ctx *ctx) {
   }
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
   ctx->graph = graph;
+  // the ranking chain is the critical path; the update (a parallel branch)
+  // runs at the lowest priority so its blocks never delay the ranking's CTAs
+  {
+    int lo_pri = 0, hi_pri = 0;
+    QE_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri));
+    size_t nn = 0;
+    QE_CUDA(ctx, cudaGraphGetNodes(graph, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    QE_CUDA(ctx, cudaGraphGetNodes(graph, nodes.data(), &nn));
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      QE_CUDA(ctx, cudaGraphNodeGetType(nd, &ty));
+      if (ty != cudaGraphNodeTypeKernel) continue;
+      cudaKernelNodeParams kp;
+      QE_CUDA(ctx, cudaGraphKernelNodeGetParams(nd, &kp));
+      cudaKernelNodeAttrValue v;
+      memset(&v, 0, sizeof v);
+      v.priority = is_update_kernel(kp.func) ? lo_pri : hi_pri;
+      QE_CUDA(ctx, cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &v));
+    }
+  }
   QE_CUDA(ctx, cudaGraphInstantiate(&ctx->gexec, graph, 0));
   return QE_OK;
 }
@@ -272,6 +333,8 @@ void qe_destroy(qe_ctx *ctx) {
     if (ev) cudaEventDestroy(ev);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->side2) cudaStreamDestroy(ctx->side2);
+  if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
   if (ctx->h_recs) cudaFreeHost(ctx->h_recs);
   if (ctx->arena) cudaFree(ctx->arena);
   delete ctx;
@@ -307,6 +370,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
                          prop.name));
   ctx->lc.num_sms = (uint32_t)prop.multiProcessorCount;
   e = query_circuit_occupancy(ctx->lc);
+  if (e == cudaSuccess) e = rank_init();
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "occupancy query"));
 
   // ---- arena layout
@@ -336,6 +400,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     d.key0 = (uint32_t)q.seed;
     d.key1 = (uint32_t)(q.seed >> 32);
     d.eps_d = eps_d_for(d.L);
+    d.pen_per_gate = (float)(q.cost_weight / (double)d.L);
     d.p_mut = q.p_mutation;
     d.cost_weight = q.cost_weight;
     d.ga_rate = q.ga_mutation_rate;
@@ -346,10 +411,8 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     build_ops(d.n, q.library, d.gop);
     const size_t P = d.P, PL = (size_t)d.P * d.L;
     if (q.encoding == QE_ENC_QEQEA) {
-      ar.take(&d.cur, d.nseg * 32);
-      ar.take(&d.best, d.nseg * 32);
-      ar.take(&d.best_f, d.nseg * 4);
-      ar.take(&d.sfkey, d.nseg * 4);
+      ar.take(&d.segs, d.nseg * 64);
+      ar.take(&d.fk, d.nseg * 8);
       ar.take(&d.seg_id, PL * 4);
       ar.take(&d.qubit_tab, (kQ + 1) * sizeof(float2));
     } else {
@@ -372,6 +435,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   ar.take(&ctx->d_probs, n_probs * sizeof(DevProblem));
   ar.take(&ctx->g.th_tab, (kQ + 1) * sizeof(float2));
   ar.take(&ctx->g.ph_tab, (kQ + 1) * sizeof(float2));
+  ar.take(&ctx->g.su3_tab, (size_t)8 * kQ * 9 * sizeof(float2));
   ar.take(&ctx->g.gen, 4);
   ar.take(&ctx->g.err, 4);
   ar.take(&ctx->g.rescore_n, 4);
@@ -442,6 +506,27 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     return bail(cuda_fail(ctx, e, "uploading tables"));
   if ((e = trig((2.0 * pi) / (double)kQ, ctx->g.ph_tab, us)) != cudaSuccess)
     return bail(cuda_fail(ctx, e, "uploading tables"));
+  {
+    std::vector<float2> U((size_t)8 * kQ * 9);
+    for (int j = 0; j < 8; ++j) {
+      const double step = (j < 3 ? pi / 2.0 : 2.0 * pi) / (double)kQ;
+      for (int m = 0; m < kQ; ++m) {
+        float cv[8], sv[8];
+        for (int k = 0; k < 8; ++k) {
+          cv[k] = 1.0f;
+          sv[k] = 0.0f;
+        }
+        const double ang = (double)m * step;
+        cv[j] = (float)std::cos(ang);
+        sv[j] = (float)std::sin(ang);
+        su3_binary32(cv, sv, &U[((size_t)j * kQ + m) * 9]);
+      }
+    }
+    e = cudaMemcpyAsync(ctx->g.su3_tab, U.data(), U.size() * sizeof(float2),
+                        cudaMemcpyHostToDevice, us);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "uploading the SU(3) table"));
+  }
   std::vector<Best> recs(n_probs);
   std::vector<RankJob> jobs(n_probs);
   std::vector<uint32_t> single(n_probs * 5);
@@ -466,7 +551,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     single[5 * i + 1] = 0;
     single[5 * i + 2] = d.P * d.L;
     single[5 * i + 3] = 0;
-    single[5 * i + 4] = (d.P + 31) / 32;
+    single[5 * i + 4] = ((d.P + 31) / 32) * d.R;
   }
   ctx->n_jobs = n_probs;
   std::vector<uint32_t> host_u32;
@@ -493,7 +578,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     std::vector<uint32_t> pa(upd.size() + 1, 0), pb(upd.size() + 1, 0);
     for (size_t k = 0; k < upd.size(); ++k) {
       pa[k + 1] = pa[k] + ctx->hp[upd[k]].P * ctx->hp[upd[k]].L;
-      pb[k + 1] = pb[k] + (ctx->hp[upd[k]].P + 31) / 32;
+      pb[k + 1] = pb[k] + ((ctx->hp[upd[k]].P + 31) / 32) * ctx->hp[upd[k]].R;
     }
     ctx->upd_totalA = pa.back();
     ctx->upd_totalB = pb.back();
@@ -516,6 +601,8 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaMallocHost"));
   e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "creating streams"));
@@ -636,7 +723,7 @@ qe_status qe_update(qe_ctx *ctx, uint32_t prob, uint32_t gen, const uint32_t *d_
   QE_CUDA(ctx, launch_scatter(ctx->d_probs, prob, d.P, d.L, d_seg_id, d_fitness, ctx->g.err, us));
   const uint32_t *s = ctx->d_single + 5 * prob;
   QE_CUDA(ctx, launch_update(ctx->lc, ctx->d_probs, s, s + 1, s + 3, 1, d.P * d.L,
-                             (d.P + 31) / 32, nullptr, gen, d_seg_id, ctx->g, us));
+                             ((d.P + 31) / 32) * d.R, nullptr, gen, d_seg_id, ctx->g, us, us));
   return QE_OK;
 }
 
@@ -768,14 +855,21 @@ static qe_status state_copy(qe_ctx *ctx, uint32_t prob, void *h, size_t bytes, b
   const cudaMemcpyKind kd = out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
   char *hb = (char *)h;
   if (d.enc == QE_ENC_QEQEA) {
+    // the caller's layout is cur[S][8], best[S][8], best_f[S]; on the device
+    // cur and best share a 64-B line and best_f sits beside the fitness key
     const size_t S = d.nseg;
-    void *parts[3] = {d.cur, d.best, d.best_f};
-    const size_t sz[3] = {S * 32, S * 32, S * 4};
-    size_t off = 0;
-    for (int k = 0; k < 3; ++k) {
-      if (out) QE_CUDA(ctx, cudaMemcpyAsync(hb + off, parts[k], sz[k], kd, us));
-      else QE_CUDA(ctx, cudaMemcpyAsync(parts[k], hb + off, sz[k], kd, us));
-      off += sz[k];
+    char *sg = (char *)d.segs, *fk = (char *)d.fk;
+    struct Part {
+      char *dev;
+      size_t dpitch, width, host_off;
+    } parts[3] = {{sg, 64, 32, 0}, {sg + 32, 64, 32, S * 32}, {fk, 8, 4, S * 64}};
+    for (const Part &pt : parts) {
+      if (out)
+        QE_CUDA(ctx, cudaMemcpy2DAsync(hb + pt.host_off, pt.width, pt.dev, pt.dpitch, pt.width, S,
+                                       kd, us));
+      else
+        QE_CUDA(ctx, cudaMemcpy2DAsync(pt.dev, pt.dpitch, hb + pt.host_off, pt.width, pt.width, S,
+                                       kd, us));
     }
   } else {
     if (out) QE_CUDA(ctx, cudaMemcpyAsync(hb, d.gate_idx, need, kd, us));

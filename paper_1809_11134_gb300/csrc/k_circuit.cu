@@ -253,6 +253,27 @@ __device__ __forceinline__ uint32_t op_work(const DevProblem &p, int op) {
   return (o & 1) ? 2 * NN : 4 * NN;          // T: 2N^2, H: 4N^2
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *ptr) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
+// If individual i mutates in this generation, the update will walk all of its
+// R*L segments (their 64-B records and fitness pairs): prefetch them into L2
+// from the circuit kernel, which is instruction-bound, so that the update,
+// which is latency-bound, finds them there.
+__device__ __forceinline__ void prefetch_mutated(const DevProblem &p, uint32_t i, uint32_t gen,
+                                                 int lane) {
+  const uint4 v = draw(p, i, 0, gen, kStMutDecide);
+  if (!((unsigned long long)v.x < p.mut_T)) return;
+  const uint32_t RL = p.R * p.L;
+  for (uint32_t x = lane; x < RL; x += 32) {
+    const uint32_t r = x / p.L, t = x - r * p.L;
+    const uint32_t seg = r * p.LP + i * p.L + t;
+    prefetch_l2(cur_of(p, seg));
+    if ((t & 7) == 0) prefetch_l2(key_of(p, seg));
+  }
+}
+
 // ------------------------------------------------------------------ sampling
 // Sec. IV-D: draw whichIndividual and whichRotationOrInteraction, form the
 // segment index (Eq. (10)), measure the segment's qutrit (and qubit) in binary32.
@@ -261,8 +282,10 @@ __device__ __forceinline__ void sample_slot(const DevProblem &p, uint32_t c, uin
   const uint4 u = draw(p, c, t, gen, kStSample);
   const uint32_t i = below(u.x, p.P), r = below(u.y, p.R);
   const uint32_t seg = r * p.LP + i * p.L + t;
-  const float4 a = __ldg(p.cur + 2 * (size_t)seg);
-  const float4 b = __ldg(p.cur + 2 * (size_t)seg + 1);
+  const float4 a = __ldg(cur_of(p, seg));
+  const float4 b = __ldg(cur_of(p, seg) + 1);
+  // the update reads this segment's best record next: bring it into L2 now
+  prefetch_l2(best_of(p, seg));
   const float p0 = __fadd_rn(__fmul_rn(a.x, a.x), __fmul_rn(a.y, a.y));
   const float p1 = __fadd_rn(__fmul_rn(a.z, a.z), __fmul_rn(a.w, a.w));
   const float p2 = __fadd_rn(__fmul_rn(b.x, b.x), __fmul_rn(b.y, b.y));
@@ -303,13 +326,15 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
     re[r] = (((grp << Ly::RBR) | r) == j) ? R(1) : R(0);
     im[r] = R(0);
   }
-  uint32_t cost = 0, work = 0;
-  for (uint32_t t = 0; t < p.L; ++t) {
+  // gate cost and work of this lane's slots, reduced once (identity ops and
+  // the slots beyond L carry kOpIdentity)
+  const uint32_t cost = __reduce_add_sync(kFull, (ops0 != kOpIdentity) + (ops1 != kOpIdentity));
+  const uint32_t work = __reduce_add_sync(kFull, op_work(p, (int)ops0) + op_work(p, (int)ops1));
+  const uint32_t L = p.L;
+  for (uint32_t t = 0; t < L; ++t) {
     const uint32_t src = t < 32 ? ops0 : ops1;
     const int op = __shfl_sync(kFull, (int)src, (int)(t & 31));
     if (op == kOpIdentity) continue;
-    cost += 1;
-    work += op_work(p, op);
     const R s = (op & kOpNeg) ? R(-1) : R(1);
     dispatch<NQ, R, CANON>(op & 0x7f, re, im, lane, s);
   }
@@ -356,13 +381,15 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
         b = __dadd_rn(b, -xi);
       }
     }
-    const double size = (double)N;
+    // (size - x) / size: size = N is a power of two, so the division is the
+    // exact scaling by 1/N (identical result, no binary64 division sequence)
+    const double size = (double)N, inv = 1.0 / (double)N;
     double d;
     if (p.fit_kind == 1) {
-      d = __ddiv_rn(__dsub_rn(size, a), size);
+      d = __dmul_rn(__dsub_rn(size, a), inv);
     } else {
       const double m = __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
-      d = __ddiv_rn(__dsub_rn(size, m), size);
+      d = __dmul_rn(__dsub_rn(size, m), inv);
     }
     if (d < 0.0) d = 0.0;
     const double f = __dsub_rn(1.0, __dsqrt_rn(d));
@@ -381,12 +408,12 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
       a += __shfl_xor_sync(kFull, a, o);
       b += __shfl_xor_sync(kFull, b, o);
     }
-    const float size = (float)N;
+    const float size = (float)N, inv = 1.f / (float)N;
     float d;
     if (p.fit_kind == 1) {
-      d = (size - a) / size;
+      d = (size - a) * inv;
     } else {
-      d = (size - sqrtf(a * a + b * b)) / size;
+      d = (size - sqrtf(a * a + b * b)) * inv;
     }
     d = fmaxf(d, 0.f);
     const float f = 1.f - sqrtf(d);
@@ -422,7 +449,7 @@ __device__ __forceinline__ uint32_t find_problem(const uint32_t *prefix, uint32_
 // scheduler otherwise interleaves every row pair of a gate and asks for ~190.
 template <int NQ, bool CANON>
 constexpr int min_blocks() {
-  return (NQ == 5 && !CANON) ? 2 : 1;
+  return (NQ == 5 && !CANON) ? 2 : ((NQ <= 3 && !CANON) ? 6 : 1);
 }
 
 template <int NQ, typename R, bool CANON>
@@ -453,6 +480,7 @@ __global__ void __launch_bounds__(256, min_blocks<NQ, CANON>()) k_step(const Dev
       p.seg_id[(size_t)c * p.L + lane + 32] = seg1;
       o1 = op_of(p, gg, bad);
     }
+    prefetch_mutated(p, c, gen, lane);
     CircuitOut out = compose_score<NQ, R, CANON>(p, lane, o0, o1, (R *)nullptr);
     const bool nonfinite = !isfinite(out.F);
     if (lane == 0) {
@@ -463,8 +491,8 @@ __global__ void __launch_bounds__(256, min_blocks<NQ, CANON>()) k_step(const Dev
     }
     if (!nonfinite) {
       const uint32_t key = fkey((float)out.F);
-      if ((uint32_t)lane < p.L) atomicMax(p.sfkey + seg0, key);
-      if ((uint32_t)lane + 32 < p.L) atomicMax(p.sfkey + seg1, key);
+      if ((uint32_t)lane < p.L) atomicMax(key_of(p, seg0), key);
+      if ((uint32_t)lane + 32 < p.L) atomicMax(key_of(p, seg1), key);
     }
   }
 }
@@ -521,7 +549,9 @@ __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ 
   const int lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const uint32_t total = *g.rescore_n;
-  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+  // entries are dealt block-first (entry w -> block w % gridDim) so that a
+  // short queue spreads one binary64 circuit per SM before doubling up
+  for (uint32_t w = blockIdx.x + gridDim.x * (threadIdx.x >> 5); w < total; w += nw) {
     const uint32_t ent = g.rescore_list[w];
     const DevProblem &p = probs[ent >> 20];
     if (p.n != (uint32_t)NQ) continue;

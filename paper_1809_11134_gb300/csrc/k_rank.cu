@@ -8,45 +8,40 @@
 //   top-k; the candidates {F_hi >= tau} are rescored in binary64 (k_rescore in
 //   k_circuit.cu) and sorted by (F desc, cost asc, index asc).  Binary64
 //   searches use the degenerate band F_lo = F_hi = F.
-// One CTA per search does the selection (4-pass radix select of the k-th
-// largest F_lo key) and, in a second launch, the sort (bitonic, in chunks of
-// 2048 so any number of candidates fits in shared memory).
+// One CTA per search does the selection (3-pass radix select over the top 24
+// bits of the F_lo keys) and, in a second launch, the sort (bitonic, in chunks
+// of up to 2048 so any number of candidates fits in shared memory).
 #include "qe_dev.cuh"
 #include "qe_host.h"
 
 namespace qe {
 
 constexpr int kRankThreads = 1024;
+constexpr int kSortThreads = 256;
 constexpr int kSortN = 2048;
+constexpr size_t kSelectSmem = (4096 + 2 * 4096) * sizeof(uint32_t);
+constexpr int kKeyCache = 4096;  // circuits whose keys the selection keeps in shared memory
 
 __device__ __forceinline__ double dkey_inv(unsigned long long k) {
   const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
   return __longlong_as_double((long long)b);
 }
 
-// binary64 fitness interval of circuit c as a pair of float keys
+// binary64 fitness interval of circuit c as a pair of float keys (binary32
+// arithmetic only; the slop covers its rounding)
 __device__ __forceinline__ void bounds(const DevProblem &p, const RankJob &jb, uint32_t c,
-                                       uint32_t &klo, uint32_t &khi) {
-  if (p.prec == 0) {
-    const double F = ((const double *)jb.fit)[c];
-    if (!(F == F)) {
-      klo = khi = 1u;  // NaN ranks last
-      return;
-    }
-    klo = fkey(__double2float_rd(F));
-    khi = fkey(__double2float_ru(F));
-    return;
-  }
-  const float F = ((const float *)jb.fit)[c];
+                                       float F, uint32_t &klo, uint32_t &khi) {
   if (!(F == F)) {
-    klo = khi = 1u;
+    klo = khi = 1u;  // NaN ranks last
     return;
   }
-  float pen = 0.f;
-  if (p.cost_weight != 0.0) {
-    const uint32_t cost = jb.meta[c] & 0xffu;
-    pen = (float)(p.cost_weight * ((double)cost / (double)p.L));
+  if (p.prec == 0) {
+    const double D = ((const double *)jb.fit)[c];
+    klo = fkey(__double2float_rd(D));
+    khi = fkey(__double2float_ru(D));
+    return;
   }
+  const float pen = p.pen_per_gate * (float)(jb.meta[c] & 0xffu);
   const float f = F + pen;
   const float t = 1.f - f;
   const float d = t * t;
@@ -57,6 +52,48 @@ __device__ __forceinline__ void bounds(const DevProblem &p, const RankJob &jb, u
   khi = fkey(fhi - pen + slop);
 }
 
+// suffix scan of the 4096-bin histogram: finds the bin where the count taken
+// from the top first reaches rem; every thread owns 4 consecutive bins
+__device__ __forceinline__ void find_bin(const uint32_t *hist, uint32_t rem, uint32_t *s_wsum,
+                                         uint32_t *s_bin, uint32_t *s_rem) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // thread t owns bins 4095-4t .. 4092-4t (descending)
+  uint32_t h[4], loc = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    h[q] = hist[4095 - 4 * tid - q];
+    loc += h[q];
+  }
+  uint32_t v = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) s_wsum[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = s_wsum[lane], x = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += u;
+    }
+    s_wsum[32 + lane] = x - w;  // exclusive prefix of the warp totals
+  }
+  __syncthreads();
+  uint32_t run = s_wsum[32 + wid] + v - loc;  // count above this thread's first bin
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (run < rem && run + h[q] >= rem) {
+      *s_bin = 4095 - 4 * tid - q;
+      *s_rem = rem - run;
+    }
+    run += h[q];
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *__restrict__ probs,
                                                               const RankJob *__restrict__ jobs,
                                                               RankJob single, DevGlobal g) {
@@ -64,20 +101,45 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *
   const DevProblem &p = probs[jb.prob];
   const uint32_t n = jb.n;
   const uint32_t k = p.k < n ? p.k : n;
-  __shared__ uint32_t hist[256];
+  extern __shared__ uint32_t dyn_smem[];
+  uint32_t *hist = dyn_smem;                // 4096 bins
+  uint32_t *s_lo = dyn_smem + 4096;         // kKeyCache low keys
+  uint32_t *s_hi = s_lo + kKeyCache;        // kKeyCache high keys
+  __shared__ uint32_t s_wsum[64];
   __shared__ uint32_t s_bin, s_rem, s_cnt, s_base;
   __shared__ float s_sum[kRankThreads / 32];
   __shared__ unsigned long long s_work[kRankThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const bool cached = n <= (uint32_t)kKeyCache;
+  for (int b = tid; b < 4096; b += kRankThreads) hist[b] = 0;
+  __syncthreads();
 
-  // mean fitness and useful work (report fields)
-  if (jb.update_record) {
-    float sum = 0.f;
-    unsigned long long work = 0;
-    for (uint32_t c = tid; c < n; c += kRankThreads) {
-      sum += p.prec == 0 ? (float)((const double *)jb.fit)[c] : ((const float *)jb.fit)[c];
-      work += jb.meta[c] >> 8;
+  // pass 1: one read of every fitness: keys (cached in shared memory), the
+  // histogram of the top 12 bits of the low keys, the mean and the work.
+  // Histogram updates are aggregated per warp (__match_any_sync): fitness
+  // values are often discrete, and many lanes hit the same bin.
+  float sum = 0.f;
+  unsigned long long work = 0;
+  for (uint32_t c0 = 0; c0 < n; c0 += kRankThreads) {
+    const uint32_t c = c0 + tid;
+    uint32_t bin = 4096u;
+    if (c < n) {
+      const float F = p.prec == 0 ? (float)((const double *)jb.fit)[c] : ((const float *)jb.fit)[c];
+      const uint32_t meta = jb.meta[c];
+      sum += F;
+      work += meta >> 8;
+      uint32_t lo, hi;
+      bounds(p, jb, c, F, lo, hi);
+      if (cached) {
+        s_lo[c] = lo;
+        s_hi[c] = hi;
+      }
+      bin = lo >> 20;
     }
+    const uint32_t peers = __match_any_sync(kFull, bin);
+    if (bin < 4096u && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+  }
+  if (jb.update_record) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       sum += __shfl_xor_sync(kFull, sum, o);
@@ -87,46 +149,47 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *
       s_sum[wid] = sum;
       s_work[wid] = work;
     }
-    __syncthreads();
-    if (tid == 0) {
-      double tot = 0.0;
-      unsigned long long wt = 0;
-      for (int w = 0; w < kRankThreads / 32; ++w) {
-        tot += (double)s_sum[w];
-        wt += s_work[w];
-      }
-      p.rec->mean_fitness = n ? tot / (double)n : 0.0;
+  }
+  __syncthreads();
+  if (jb.update_record && wid == 0) {
+    double t = (double)s_sum[lane];
+    unsigned long long wt = s_work[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      t += __shfl_xor_sync(kFull, t, o);
+      wt += __shfl_xor_sync(kFull, wt, o);
+    }
+    if (lane == 0) {
+      p.rec->mean_fitness = n ? t / (double)n : 0.0;
       p.rec->useful_flops = wt;
     }
   }
 
-  // radix select: tau = k-th largest low key
-  uint32_t prefix = 0, mask = 0;
-  if (tid == 0) s_rem = k;
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int b = tid; b < 256; b += kRankThreads) hist[b] = 0;
-    __syncthreads();
-    for (uint32_t c = tid; c < n; c += kRankThreads) {
+  // tau = the k-th largest low key with its last 8 bits cleared (top 12 bits,
+  // then the next 12), so tau <= the exact k-th largest and at least k circuits
+  // have F_lo >= tau (a lower tau only adds candidates)
+  find_bin(hist, k, s_wsum, &s_bin, &s_rem);
+  const uint32_t b1 = s_bin, rem = s_rem;
+  for (int b = tid; b < 4096; b += kRankThreads) hist[b] = 0;
+  __syncthreads();
+  for (uint32_t c0 = 0; c0 < n; c0 += kRankThreads) {
+    const uint32_t c = c0 + tid;
+    uint32_t bin = 4096u;
+    if (c < n) {
       uint32_t lo, hi;
-      bounds(p, jb, c, lo, hi);
-      if ((lo & mask) == prefix) atomicAdd(&hist[(lo >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t rem = s_rem, b = 255;
-      for (;; --b) {
-        const uint32_t h = hist[b];
-        if (h >= rem || b == 0) break;
-        rem -= h;
+      if (cached) lo = s_lo[c];
+      else {
+        const float F = p.prec == 0 ? (float)((const double *)jb.fit)[c] : ((const float *)jb.fit)[c];
+        bounds(p, jb, c, F, lo, hi);
       }
-      s_bin = b;
-      s_rem = rem;
+      if ((lo >> 20) == b1) bin = (lo >> 8) & 4095u;
     }
-    __syncthreads();
-    prefix |= s_bin << shift;
-    mask |= 255u << shift;
+    const uint32_t peers = __match_any_sync(kFull, bin);
+    if (bin < 4096u && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
   }
-  const uint32_t tau = prefix;
+  __syncthreads();
+  find_bin(hist, rem, s_wsum, &s_bin, &s_rem);
+  const uint32_t tau = (b1 << 20) | (s_bin << 8);
 
   // candidates: F_hi >= tau
   if (tid == 0) s_cnt = 0;
@@ -136,7 +199,11 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *
     bool take = false;
     if (c < n) {
       uint32_t lo, hi;
-      bounds(p, jb, c, lo, hi);
+      if (cached) hi = s_hi[c];
+      else {
+        const float F = p.prec == 0 ? (float)((const double *)jb.fit)[c] : ((const float *)jb.fit)[c];
+        bounds(p, jb, c, F, lo, hi);
+      }
       take = hi >= tau;
     }
     const uint32_t bal = __ballot_sync(kFull, take);
@@ -165,7 +232,7 @@ __device__ __forceinline__ bool key_less(unsigned long long ah, unsigned long lo
   return ah < bh || (ah == bh && al < bl);
 }
 
-__global__ void __launch_bounds__(kRankThreads) k_rank_sort(const DevProblem *__restrict__ probs,
+__global__ void __launch_bounds__(kSortThreads) k_rank_sort(const DevProblem *__restrict__ probs,
                                                             const RankJob *__restrict__ jobs,
                                                             RankJob single, DevGlobal g) {
   const RankJob jb = jobs ? jobs[blockIdx.x] : single;
@@ -177,29 +244,31 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_sort(const DevProblem *__
   const int tid = threadIdx.x;
   const unsigned long long kMaxKey = ~0ull;
   uint32_t kept = 0, next = 0;
-  // ascending order of (~dkey(F), cost << 32 | c) == (F desc, cost asc, c asc)
+  // ascending order of (~dkey(F), cost << 32 | c) == (F desc, cost asc, c asc);
+  // each round sorts the kept top-k plus the next candidates with a bitonic
+  // network sized to the next power of two of their count
   do {
-    for (uint32_t s = tid; s < (uint32_t)kSortN; s += kRankThreads) {
-      if (s >= kept) {
-        const uint32_t src = next + (s - kept);
-        if (src < M) {
-          const uint32_t c = p.cand[src];
-          const double F = p.cand_f[src];
-          const uint32_t cost = jb.meta[c] & 0xffu;
-          kh[s] = (F == F) ? ~dkey(F) : kMaxKey - 1;
-          kl[s] = ((unsigned long long)cost << 32) | c;
-        } else {
-          kh[s] = kMaxKey;
-          kl[s] = kMaxKey;
-        }
+    const uint32_t added = (M - next) < (uint32_t)(kSortN - kept) ? (M - next) : (kSortN - kept);
+    uint32_t S = 2;
+    while (S < kept + added) S <<= 1;
+    for (uint32_t s = kept + tid; s < S; s += kSortThreads) {
+      const uint32_t src = next + (s - kept);
+      if (s < kept + added) {
+        const uint32_t c = p.cand[src];
+        const double F = p.cand_f[src];
+        const uint32_t cost = jb.meta[c] & 0xffu;
+        kh[s] = (F == F) ? ~dkey(F) : kMaxKey - 1;
+        kl[s] = ((unsigned long long)cost << 32) | c;
+      } else {
+        kh[s] = kMaxKey;
+        kl[s] = kMaxKey;
       }
     }
-    const uint32_t added = (M - next) < (uint32_t)(kSortN - kept) ? (M - next) : (kSortN - kept);
     next += added;
     __syncthreads();
-    for (uint32_t size = 2; size <= (uint32_t)kSortN; size <<= 1) {
+    for (uint32_t size = 2; size <= S; size <<= 1) {
       for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-        for (uint32_t i = tid; i < (uint32_t)kSortN; i += kRankThreads) {
+        for (uint32_t i = tid; i < S; i += kSortThreads) {
           const uint32_t jx = i ^ stride;
           if (jx > i) {
             const bool asc = (i & size) == 0;
@@ -222,7 +291,7 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_sort(const DevProblem *__
     __syncthreads();
   } while (next < M);
 
-  for (uint32_t s = tid; s < kept; s += kRankThreads) {
+  for (uint32_t s = tid; s < kept; s += kSortThreads) {
     Ranked r;
     r.circuit = (uint32_t)(kl[s] & 0xffffffffu);
     r.cost = (uint32_t)(kl[s] >> 32);
@@ -230,23 +299,36 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_sort(const DevProblem *__
                                       : dkey_inv(~kh[s]);
     p.topk_out[s] = r;
   }
-  if (tid == 0 && jb.update_record) {
+  if (jb.update_record && tid < 64) {
+    // best-so-far record: thread 0 decides, 64 threads copy the gates
+    __shared__ int s_improve;
     Best *rec = p.rec;
     const uint32_t gen = *g.gen;
-    rec->generation = gen + 1;
-    rec->error_word |= *g.err;
-    if (kept > 0 && kh[0] < kMaxKey - 1) {
-      const double F = dkey_inv(~kh[0]);
-      const uint32_t c = (uint32_t)(kl[0] & 0xffffffffu);
-      const uint32_t cost = (uint32_t)(kl[0] >> 32);
-      rec->gen_best_fitness = F;
-      if (F > rec->best_fitness || (F == rec->best_fitness && cost < rec->best_cost)) {
-        rec->best_fitness = F;
-        rec->best_cost = cost;
-        rec->best_gen = gen;
-        rec->best_len = p.L;
+    const bool valid = kept > 0 && kh[0] < kMaxKey - 1;
+    const double F = valid ? dkey_inv(~kh[0]) : 0.0;
+    const uint32_t c = (uint32_t)(kl[0] & 0xffffffffu);
+    const uint32_t cost = (uint32_t)(kl[0] >> 32);
+    if (tid == 0) {
+      rec->generation = gen + 1;
+      rec->error_word |= *g.err;
+      s_improve = 0;
+      if (valid) {
+        rec->gen_best_fitness = F;
+        if (F > rec->best_fitness || (F == rec->best_fitness && cost < rec->best_cost)) {
+          rec->best_fitness = F;
+          rec->best_cost = cost;
+          rec->best_gen = gen;
+          rec->best_len = p.L;
+          s_improve = 1;
+        }
+      }
+    }
+    __syncwarp();
+    if (tid < 32) {
+      const int imp = __shfl_sync(kFull, s_improve, 0);
+      if (imp) {
         const uint8_t *gs = jb.gsrc + (size_t)c * p.L;
-        for (uint32_t t = 0; t < 64; ++t) rec->best_gates[t] = t < p.L ? gs[t] : 0;
+        for (uint32_t t = tid; t < 64; t += 32) rec->best_gates[t] = t < p.L ? gs[t] : 0;
       }
     }
   }
@@ -262,15 +344,20 @@ __global__ void k_reset_counter(DevGlobal g) { *g.rescore_n = 0; }
 cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
                                const RankJob &single, const DevGlobal &g, cudaStream_t st) {
   if (!n_jobs) return cudaSuccess;
-  k_rank_select<<<n_jobs, kRankThreads, 0, st>>>(probs, jobs, single, g);
+  k_rank_select<<<n_jobs, kRankThreads, kSelectSmem, st>>>(probs, jobs, single, g);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
                              const RankJob &single, const DevGlobal &g, cudaStream_t st) {
   if (!n_jobs) return cudaSuccess;
-  k_rank_sort<<<n_jobs, kRankThreads, 0, st>>>(probs, jobs, single, g);
+  k_rank_sort<<<n_jobs, kSortThreads, 0, st>>>(probs, jobs, single, g);
   return cudaGetLastError();
+}
+
+cudaError_t rank_init() {
+  return cudaFuncSetAttribute(k_rank_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kSelectSmem);
 }
 
 cudaError_t launch_finish(const DevGlobal &g, cudaStream_t st) {

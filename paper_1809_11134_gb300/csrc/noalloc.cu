@@ -147,6 +147,7 @@ extern "C" qe_status qe_eval_rank_static(const qe_problem *prob, const uint8_t *
         return say(h_msg, msg_len, QE_ECUDA, "cudaGetSymbolAddress of the static scratch failed");
       s.lc.num_sms = (uint32_t)prop.multiProcessorCount;
       e = qe::query_circuit_occupancy(s.lc);
+      if (e == cudaSuccess) e = qe::rank_init();
       if (e != cudaSuccess) return say(h_msg, msg_len, QE_ECUDA, cudaGetErrorString(e));
       s.base = (unsigned char *)addr;
       s.ready = true;
@@ -171,6 +172,7 @@ extern "C" qe_status qe_eval_rank_static(const qe_problem *prob, const uint8_t *
   d.k = q.topk ? q.topk : 1;
   d.cost_weight = q.cost_weight;
   d.eps_d = (float)((double)d.L * 8e-7 + 2e-6);
+  d.pen_per_gate = (float)(q.cost_weight / (double)d.L);
   for (uint32_t j = 0; j < 32; ++j) d.perm[j] = j < N ? q.target_perm[j] : 0;
   memset(d.gop, qe::kOpIdentity, sizeof d.gop);
   ops_of(d.n, q.library, d.gop);

@@ -1,10 +1,13 @@
 // qe_dev.cuh -- device-side data layout and primitives of the QEQEA engine.
 //
 // One search's state lives in a single device arena (see capi.cu):
-//   cur/best   : S segments x 32 B  {q0re,q0im,q1re,q1im,q2re,q2im,b0,b1} as 2 float4
-//   best_f     : S floats (segment's best fitness, binary32)
-//   sfkey      : S uint32 (this generation's segment fitness as an order-preserving
-//                key; 0 = untouched), reset to 0 by the update kernel
+//   segs       : S segments x 64 B = {cur, best}, each 32 B
+//                {q0re,q0im,q1re,q1im,q2re,q2im,b0,b1} as 2 float4, so elitism
+//                touches one 64-B line whichever record it keeps
+//   fk         : S x {best_f (binary32 bits), sfkey} -- the segment's best
+//                fitness and this generation's segment fitness as an
+//                order-preserving key (0 = untouched, reset by the update),
+//                side by side so both arrive in one DRAM burst
 //   gate_idx   : P*L uint8, seg_id: P*L uint32 (the generation's circuits)
 //   fit32/fit64: P (working-precision fitness), meta: P (cost | work << 8)
 // where S = R*P*L and seg = r*L*P + i*L + t (Eq. (10)).
@@ -48,7 +51,7 @@ struct DevProblem {
   uint32_t run, has_qubit, base;                // base = 1 if I is library index 0
   uint32_t key0, key1;
   float eps_d;        // bound on |d32 - d64|, d = (N - |tr|)/N, for the binary32 path
-  float pad0;
+  float pen_per_gate; // cost_weight / L in binary32 (ranking bounds only)
   double p_mut, cost_weight, ga_rate;
   // an individual mutates when its Philox word u < mut_T, i.e. when
   // (u + 1/2) 2^-32 < p_mut (mut_T = ceil(p_mut 2^32 - 1/2), clamped to [0, 2^32])
@@ -57,9 +60,8 @@ struct DevProblem {
   uint8_t perm[32];
   uint8_t gop[80];    // library index -> op byte (see k_circuit.cu), kOpIdentity for I
   // state and per-generation buffers
-  float4 *cur, *best;
-  float *best_f;
-  uint32_t *sfkey;
+  float4 *segs;  // 4 float4 per segment: cur (2), best (2)
+  uint32_t *fk;  // 2 words per segment: best_f bits, sfkey
   uint8_t *gate_idx;
   uint32_t *seg_id;
   float *fit32;
@@ -82,6 +84,7 @@ struct DevProblem {
 struct DevGlobal {
   float2 *th_tab;     // cos/sin of m * (pi/2) / Q
   float2 *ph_tab;     // cos/sin of m * (2 pi) / Q
+  float2 *su3_tab;    // Eq. (12) for parameter j at level m: [8][Q][9] complex
   uint32_t *gen;      // generation counter (graph replays read it)
   uint32_t *err;      // error word
   uint32_t *rescore_list;  // (problem << 20 | slot) pairs to rescore in binary64
@@ -134,6 +137,20 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
 __device__ __forceinline__ unsigned long long dkey(double f) {
   unsigned long long b = (unsigned long long)__double_as_longlong(f);
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// ---------------------------------------------------------------- state access
+__device__ __forceinline__ float4 *cur_of(const DevProblem &p, uint32_t seg) {
+  return p.segs + 4 * (size_t)seg;
+}
+__device__ __forceinline__ float4 *best_of(const DevProblem &p, uint32_t seg) {
+  return p.segs + 4 * (size_t)seg + 2;
+}
+__device__ __forceinline__ float *bestf_of(const DevProblem &p, uint32_t seg) {
+  return reinterpret_cast<float *>(p.fk + 2 * (size_t)seg);
+}
+__device__ __forceinline__ uint32_t *key_of(const DevProblem &p, uint32_t seg) {
+  return p.fk + 2 * (size_t)seg + 1;
 }
 
 // ---------------------------------------------------------------- lane layout

@@ -54,6 +54,7 @@ cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, const DevProblem *p
                            const uint8_t *gsrc, const DevGlobal &g, cudaStream_t st);
 
 // k_update.cu
+bool is_update_kernel(const void *f);  // an update kernel (graph node priorities)
 cudaError_t launch_init_state(const DevProblem *probs, uint32_t prob, uint64_t nseg,
                               cudaStream_t st);
 cudaError_t launch_scatter(const DevProblem *probs, uint32_t prob, uint32_t P, uint32_t L,
@@ -61,12 +62,15 @@ cudaError_t launch_scatter(const DevProblem *probs, uint32_t prob, uint32_t P, u
                            cudaStream_t st);
 // elitism + mutation for the searches group[0..n_group); prefA: P*L prefix,
 // prefB: ceil(P/32) prefix; gen read from *d_gen when d_gen != NULL
+// role A (elitism) on stA, role B (mutation) on stB; the two may run concurrently
 cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const uint32_t *group,
                           const uint32_t *prefA, const uint32_t *prefB, uint32_t n_group,
                           uint32_t totalA, uint32_t totalB, const uint32_t *d_gen, uint32_t gen,
-                          const uint32_t *seg_override, const DevGlobal &g, cudaStream_t st);
+                          const uint32_t *seg_override, const DevGlobal &g, cudaStream_t stA,
+                          cudaStream_t stB);
 
 // k_rank.cu
+cudaError_t rank_init();  // once per device before the first ranking launch
 // jobs == NULL: one job given by value in `single`
 cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
                                const RankJob &single, const DevGlobal &g, cudaStream_t st);

@@ -180,6 +180,7 @@ def test_fp32_exact_on_textbook_circuits(qe, torch):
     (5, NCV | HT, 64, 600, 128),
     (3, NCV | HT, 6, 50, 50),        # k = P
     (2, NCV, 2, 3000, 1),
+    (4, NCV | HT, 12, 20000, 64),   # beyond the selection's shared-memory key cache
 ])
 def test_topk_bit_exact(qe, torch, prec, n, lib, L, P, k):
     rng = np.random.default_rng(P + k)
