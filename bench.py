@@ -217,7 +217,6 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
         dist.barrier()
-    reps = ctx.step(0) if False else None
     value = ws * n_circ * args.steps / (total_ms / 1e3)
     clocks = clk.summary()
 
@@ -281,11 +280,8 @@ def roofline(dom, ms, searches, last, pk):
     sm_max = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
     if dom == "circuits":
-        flops = 0
-        for s, l in zip(searches, last):
-            pass
         # useful flops of the generation (gate-count model), counted exactly
-        flops = sum(r for r in (gen_flops(s, l) for s, l in zip(searches, last)))
+        flops = sum(gen_flops(s, l) for s, l in zip(searches, last))
         ach = flops / (ms / 1e3) / 1e12
         return {"kernel": "k_step (sample + compose + score + scatter)", "bound": "alu",
                 "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
@@ -360,8 +356,10 @@ def end_to_end(qe, ctx_unused, searches, last, steps):
 
 
 def per_config(qe, torch, args):
-    """Eval rate (sample + compose/score + rank) and step rate at n = 3, 4, 5,
-    binary32 vs plain binary64, a few generations each (context only)."""
+    """Circuit-kernel rate (sample + compose + score) and generation rate at
+    n = 3, 4, 5, binary32 vs plain binary64, a few generations each, from the
+    events inside the generation graph (context next to the headline)."""
+    import numpy as np
     from paper_1809_11134_gb300 import workloads as W
     out = {}
     for cfg, gens32, gens64 in ((2, 20, 5), (3, 6, 2), (5, 4, 1)):
@@ -377,13 +375,16 @@ def per_config(qe, torch, args):
                 ctx.step_raw(1, None)
                 times.append(ctx.stage_times())
             ctx.close()
-            import numpy as np
             t = np.array(times).mean(axis=0)
             n = sum(s.P for s in searches)
             res["fp32" if prec else "fp64"] = {
-                "eval_circuits_per_s": n / ((t[0] + t[1] + t[2] + t[3]) / 1e3),
-                "step_circuits_per_s": n / (t[5] / 1e3), "stage_ms": [round(x, 4) for x in t]}
-        res["fp32_over_fp64_eval"] = res["fp32"]["eval_circuits_per_s"] / res["fp64"]["eval_circuits_per_s"]
+                "circuit_kernel_circuits_per_s": n / (t[0] / 1e3),
+                "generation_circuits_per_s": n / (t[5] / 1e3),
+                "circuit_kernel_ms": round(float(t[0]), 4), "generation_ms": round(float(t[5]), 4)}
+        res["fp32_over_fp64_circuit_kernel"] = (res["fp32"]["circuit_kernel_circuits_per_s"] /
+                                                res["fp64"]["circuit_kernel_circuits_per_s"])
+        res["fp32_over_fp64_generation"] = (res["fp32"]["generation_circuits_per_s"] /
+                                            res["fp64"]["generation_circuits_per_s"])
         out["config%d" % cfg] = res
     return out
 

@@ -33,7 +33,7 @@ struct qe_ctx {
   int device = 0;
   cudaStream_t user = nullptr;
   cudaStream_t cap = nullptr, side = nullptr, side2 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_fork2 = nullptr;
   std::vector<qe_problem> probs;
   std::vector<DevProblem> hp;
   DevProblem *d_probs = nullptr;
@@ -56,6 +56,9 @@ struct qe_ctx {
   void *d_stage_fit = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t dgraph = nullptr;      // ranking of the last generation alone (drain)
+  cudaGraphExec_t dexec = nullptr;
+  bool pending_rank = false;         // the last generation is not ranked yet
   // stage timing: events recorded inside the generation graph
   bool timing = false;
   cudaEvent_t tev[8] = {nullptr};
@@ -227,34 +230,70 @@ qe_status check_ctx(qe_ctx *ctx, uint32_t prob) {
   return QE_OK;
 }
 
-// stage events (when timing): 0 start, 1 after the circuit kernels, 2 after
-// ranking selection, 3 after rescoring, 4 after the sort (main stream);
-// 5 before and 6 after the update (side stream, forked after the selection);
-// 7 end of the generation
+// Node priorities: the ranking chain (a latency chain on a few SMs) first,
+// then the circuit kernels, the update last.
+qe_status set_priorities(qe_ctx *ctx, cudaGraph_t graph) {
+  int lo_pri = 0, hi_pri = 0;
+  QE_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri));
+  size_t nn = 0;
+  QE_CUDA(ctx, cudaGraphGetNodes(graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  QE_CUDA(ctx, cudaGraphGetNodes(graph, nodes.data(), &nn));
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    QE_CUDA(ctx, cudaGraphNodeGetType(nd, &ty));
+    if (ty != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp;
+    QE_CUDA(ctx, cudaGraphKernelNodeGetParams(nd, &kp));
+    cudaKernelNodeAttrValue v;
+    memset(&v, 0, sizeof v);
+    // greatest priority: ranking; then the circuit kernels; least: the update
+    const int mid_pri = (lo_pri + hi_pri) / 2;
+    v.priority = is_update_kernel(kp.func) ? lo_pri : (is_circuit_kernel(kp.func) ? mid_pri : hi_pri);
+    QE_CUDA(ctx, cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &v));
+  }
+  return QE_OK;
+}
+
+// the ranking chain of generation *gen - 1 (select -> binary64 rescoring -> sort)
+cudaError_t enqueue_rank_chain(qe_ctx *ctx, cudaStream_t cs) {
+  RankJob none{};
+  cudaError_t e = launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, none, ctx->g, cs);
+  for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
+    if (e == cudaSuccess && ctx->rescore_nq[nq])
+      e = launch_rescore(ctx->lc, nq, ctx->d_probs, nullptr, true, ctx->g, cs);
+  if (e == cudaSuccess)
+    e = launch_rank_sort(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, none, ctx->g, cs);
+  return e;
+}
+
+// One generation, software-pipelined: generation g's circuit kernels and
+// update run on side streams while the main stream ranks generation g - 1
+// (its circuits and fitness sit in the other half of the double buffers).
+// Stage events (when timing): 0 start; 1 after the circuit kernels; 2 after
+// the selection, 3 after the rescoring, 4 after the sort (ranking of g - 1);
+// 5 before and 6 after the update; 7 end of the generation.
 qe_status build_graph(qe_ctx *ctx) {
   cudaStream_t cs = ctx->cap;
   QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   auto mark = [&](int k, cudaStream_t st) {
-    if (e == cudaSuccess && ctx->timing) e = cudaEventRecordWithFlags(ctx->tev[k], st, cudaEventRecordExternal);
+    if (e == cudaSuccess && ctx->timing)
+      e = cudaEventRecordWithFlags(ctx->tev[k], st, cudaEventRecordExternal);
   };
   mark(0, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+  // generation g: circuits, then the two update roles
   for (auto &gr : ctx->groups) {
     if (e == cudaSuccess)
       e = launch_step(ctx->lc, gr.n, ctx->d_probs, gr.d_ids, gr.d_prefix,
-                      (uint32_t)gr.ids.size(), gr.total, gr.canon, ctx->g, cs);
+                      (uint32_t)gr.ids.size(), gr.total, gr.canon, ctx->g, ctx->side);
   }
-  mark(1, cs);
-  // the selection runs alone (it needs whole 1024-thread CTAs); then the update
-  // forks off and overlaps the binary64 rescoring and the sort
-  RankJob none{};
-  if (e == cudaSuccess)
-    e = launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, none, ctx->g, cs);
-  mark(2, cs);
-  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, cs);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side2, ctx->ev_fork, 0);
+  mark(1, ctx->side);
   mark(5, ctx->side);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork2, ctx->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side2, ctx->ev_fork2, 0);
   if (e == cudaSuccess && ctx->n_upd)
     e = launch_update(ctx->lc, ctx->d_probs, ctx->d_upd_ids, ctx->d_upd_prefA, ctx->d_upd_prefB,
                       ctx->n_upd, ctx->upd_totalA, ctx->upd_totalB, ctx->g.gen, 0, nullptr, ctx->g,
@@ -262,11 +301,14 @@ qe_status build_graph(qe_ctx *ctx) {
   if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_join2, 0);
   mark(6, ctx->side);
+  // generation g - 1: ranking
+  if (e == cudaSuccess) e = launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, RankJob{}, ctx->g, cs);
+  mark(2, cs);
   for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
     if (e == cudaSuccess && ctx->rescore_nq[nq])
-      e = launch_rescore(ctx->lc, nq, ctx->d_probs, nullptr, ctx->g, cs);
+      e = launch_rescore(ctx->lc, nq, ctx->d_probs, nullptr, true, ctx->g, cs);
   mark(3, cs);
-  if (e == cudaSuccess) e = launch_rank_sort(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, none, ctx->g, cs);
+  if (e == cudaSuccess) e = launch_rank_sort(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, RankJob{}, ctx->g, cs);
   mark(4, cs);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
@@ -280,28 +322,30 @@ qe_status build_graph(qe_ctx *ctx) {
   }
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
   ctx->graph = graph;
-  // the ranking chain is the critical path; the update (a parallel branch)
-  // runs at the lowest priority so its blocks never delay the ranking's CTAs
-  {
-    int lo_pri = 0, hi_pri = 0;
-    QE_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri));
-    size_t nn = 0;
-    QE_CUDA(ctx, cudaGraphGetNodes(graph, nullptr, &nn));
-    std::vector<cudaGraphNode_t> nodes(nn);
-    QE_CUDA(ctx, cudaGraphGetNodes(graph, nodes.data(), &nn));
-    for (auto nd : nodes) {
-      cudaGraphNodeType ty;
-      QE_CUDA(ctx, cudaGraphNodeGetType(nd, &ty));
-      if (ty != cudaGraphNodeTypeKernel) continue;
-      cudaKernelNodeParams kp;
-      QE_CUDA(ctx, cudaGraphKernelNodeGetParams(nd, &kp));
-      cudaKernelNodeAttrValue v;
-      memset(&v, 0, sizeof v);
-      v.priority = is_update_kernel(kp.func) ? lo_pri : hi_pri;
-      QE_CUDA(ctx, cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &v));
-    }
-  }
+  qe_status st = set_priorities(ctx, graph);
+  if (st != QE_OK) return st;
   QE_CUDA(ctx, cudaGraphInstantiate(&ctx->gexec, graph, 0));
+  // drain graph: the ranking chain alone, then a clean rescore queue
+  QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  e = enqueue_rank_chain(ctx, cs);
+  if (e == cudaSuccess) e = launch_reset_counter(ctx->g, cs);
+  graph = nullptr;
+  e2 = cudaStreamEndCapture(cs, &graph);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(ctx, e, "capturing the ranking graph");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+  ctx->dgraph = graph;
+  QE_CUDA(ctx, cudaGraphInstantiate(&ctx->dexec, graph, 0));
+  return QE_OK;
+}
+
+// rank the last generation now if its ranking is still pending
+qe_status drain(qe_ctx *ctx) {
+  if (!ctx->pending_rank || !ctx->dexec) return QE_OK;
+  QE_CUDA(ctx, cudaGraphLaunch(ctx->dexec, ctx->user));
+  ctx->pending_rank = false;
   return QE_OK;
 }
 
@@ -327,6 +371,8 @@ void qe_destroy(qe_ctx *ctx) {
   if (!ctx) return;
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  if (ctx->dexec) cudaGraphExecDestroy(ctx->dexec);
+  if (ctx->dgraph) cudaGraphDestroy(ctx->dgraph);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   for (auto &ev : ctx->tev)
@@ -335,6 +381,7 @@ void qe_destroy(qe_ctx *ctx) {
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->side2) cudaStreamDestroy(ctx->side2);
   if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
+  if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
   if (ctx->h_recs) cudaFreeHost(ctx->h_recs);
   if (ctx->arena) cudaFree(ctx->arena);
   delete ctx;
@@ -419,10 +466,11 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
       ar.take(&d.genome_next, PL);
       ar.take(&d.ga_cum, P * 8);
     }
-    ar.take(&d.gate_idx, PL);
-    if (q.precision == QE_PREC_FP64) ar.take(&d.fit64, P * 8);
-    else ar.take(&d.fit32, P * 4);
-    ar.take(&d.meta, P * 4);
+    // generation buffers, two of each (generation parity)
+    ar.take(&d.gate_idx, 2 * PL);
+    if (q.precision == QE_PREC_FP64) ar.take(&d.fit64, 2 * P * 8);
+    else ar.take(&d.fit32, 2 * P * 4);
+    ar.take(&d.meta, 2 * P * 4);
     ar.take(&d.cand, P * 4);
     ar.take(&d.cand_f, P * 8);
     ar.take(&d.cand_n, 4);
@@ -439,6 +487,8 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   ar.take(&ctx->g.gen, 4);
   ar.take(&ctx->g.err, 4);
   ar.take(&ctx->g.rescore_n, 4);
+  ar.take(&ctx->g.ranked, 4);
+  ar.take(&ctx->g.rank_active, 4);
   ar.take(&ctx->g.rescore_list, total_P * 4);
   ar.take(&ctx->d_jobs, n_probs * sizeof(RankJob));
   ar.take(&ctx->d_single, n_probs * 5 * 4);
@@ -547,6 +597,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     j.meta = d.meta;
     j.gsrc = d.gate_idx;
     j.update_record = 1;
+    j.pipelined = 1;
     single[5 * i + 0] = i;
     single[5 * i + 1] = 0;
     single[5 * i + 2] = d.P * d.L;
@@ -590,10 +641,12 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.gen, 0, 4, us);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.err, 0, 4, us);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.rescore_n, 0, 4, us);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.ranked, 0, 4, us);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.rank_active, 0, 4, us);
   for (uint32_t i = 0; i < n_probs && e == cudaSuccess; ++i) {
     const DevProblem &d = ctx->hp[i];
     if (d.enc == QE_ENC_QEQEA) e = launch_init_state(ctx->d_probs, i, d.nseg, us);
-    else e = cudaMemsetAsync(d.gate_idx, 0, (size_t)d.P * d.L, us);
+    else e = cudaMemsetAsync(d.gate_idx, 0, 2 * (size_t)d.P * d.L, us);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(us);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "initialising the state"));
@@ -603,6 +656,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "creating streams"));
@@ -636,7 +690,7 @@ static qe_status rank_single(qe_ctx *ctx, uint32_t prob, uint32_t n, const void 
   QE_CUDA(ctx, launch_reset_counter(ctx->g, us));
   QE_CUDA(ctx, launch_rank_select(ctx->d_probs, nullptr, 1, j, ctx->g, us));
   if (d.prec != QE_PREC_FP64)
-    QE_CUDA(ctx, launch_rescore(ctx->lc, d.n, ctx->d_probs, gsrc, ctx->g, us));
+    QE_CUDA(ctx, launch_rescore(ctx->lc, d.n, ctx->d_probs, gsrc, false, ctx->g, us));
   QE_CUDA(ctx, launch_rank_sort(ctx->d_probs, nullptr, 1, j, ctx->g, us));
   QE_CUDA(ctx, launch_reset_counter(ctx->g, us));
   const uint32_t k = d.k < n ? d.k : n;
@@ -669,6 +723,10 @@ qe_status qe_eval(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_
   if (n_circuits > (1u << 24)) return fail(ctx, QE_EINVAL, "n_circuits must be <= 2^24");
   if (h_topk && n_circuits > d.P)
     return fail(ctx, QE_EINVAL, "ranking needs n_circuits <= population");
+  if (h_topk) {
+    st = drain(ctx);  // the ranking scratch and d.meta may still hold a pending ranking
+    if (st != QE_OK) return st;
+  }
   uint32_t *cost = d_cost ? d_cost : (h_topk ? d.meta : nullptr);
   QE_CUDA(ctx, launch_eval(ctx->lc, d.n, ctx->d_probs, prob, d.prec == QE_PREC_FP64, d_gate_idx,
                            n_circuits, d_fitness, cost, nullptr, ctx->g, ctx->user));
@@ -685,6 +743,8 @@ qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
   if (n_circuits > d.P) return fail(ctx, QE_EINVAL, "n_circuits must be <= population");
   const size_t fb = d.prec == QE_PREC_FP64 ? 8 : 4;
   cudaStream_t us = ctx->user;
+  st = drain(ctx);
+  if (st != QE_OK) return st;
   QE_CUDA(ctx, cudaMemcpyAsync(ctx->d_stage_gates, h_gate_idx, (size_t)n_circuits * d.L,
                                cudaMemcpyHostToDevice, us));
   QE_CUDA(ctx, launch_eval(ctx->lc, d.n, ctx->d_probs, prob, d.prec == QE_PREC_FP64,
@@ -737,7 +797,12 @@ qe_status qe_step(qe_ctx *ctx, uint32_t n_gen, qe_report *h_reports) {
   }
   for (uint32_t k = 0; k < n_gen; ++k) QE_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->user));
   ctx->gen += n_gen;
-  if (!h_reports) return QE_OK;  // enqueued only
+  if (n_gen) ctx->pending_rank = true;
+  if (!h_reports) return QE_OK;  // enqueued only; the last generation ranks later
+  {
+    qe_status st = drain(ctx);
+    if (st != QE_OK) return st;
+  }
   const uint32_t np = (uint32_t)ctx->probs.size();
   QE_CUDA(ctx, cudaMemcpyAsync(ctx->h_recs, ctx->d_recs, np * sizeof(Best), cudaMemcpyDeviceToHost,
                                ctx->user));
@@ -771,6 +836,8 @@ qe_status qe_stage_timing(qe_ctx *ctx, int enable) {
   QE_CUDA(ctx, cudaStreamSynchronize(ctx->user));
   if (want && !ctx->tev[0])
     for (auto &ev : ctx->tev) QE_CUDA(ctx, cudaEventCreate(&ev));
+  qe_status dst = drain(ctx);
+  if (dst != QE_OK) return dst;
   if (ctx->gexec) {
     cudaGraphExecDestroy(ctx->gexec);
     ctx->gexec = nullptr;
@@ -778,6 +845,14 @@ qe_status qe_stage_timing(qe_ctx *ctx, int enable) {
   if (ctx->graph) {
     cudaGraphDestroy(ctx->graph);
     ctx->graph = nullptr;
+  }
+  if (ctx->dexec) {
+    cudaGraphExecDestroy(ctx->dexec);
+    ctx->dexec = nullptr;
+  }
+  if (ctx->dgraph) {
+    cudaGraphDestroy(ctx->dgraph);
+    ctx->dgraph = nullptr;
   }
   ctx->timing = want;
   return QE_OK;
@@ -787,7 +862,7 @@ qe_status qe_stage_times(qe_ctx *ctx, float *ms) {
   if (!ctx || !ms) return fail(ctx, QE_EINVAL, "null argument");
   if (!ctx->timing || !ctx->gexec) return fail(ctx, QE_ESTATE, "stage timing is not enabled");
   QE_CUDA(ctx, cudaStreamSynchronize(ctx->user));
-  const int pairs[6][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {5, 6}, {0, 7}};
+  const int pairs[6][2] = {{0, 1}, {0, 2}, {2, 3}, {3, 4}, {5, 6}, {0, 7}};
   for (int k = 0; k < 6; ++k)
     QE_CUDA(ctx, cudaEventElapsedTime(&ms[k], ctx->tev[pairs[k][0]], ctx->tev[pairs[k][1]]));
   return QE_OK;
@@ -805,18 +880,24 @@ qe_status qe_last_generation(qe_ctx *ctx, uint32_t prob, uint8_t *h_gate_idx, ui
   if (st != QE_OK) return st;
   const DevProblem &d = ctx->hp[prob];
   cudaStream_t us = ctx->user;
+  st = drain(ctx);
+  if (st != QE_OK) return st;
   const size_t PL = (size_t)d.P * d.L;
+  const size_t b = ctx->gen ? ((ctx->gen - 1) & 1u) : 0;  // buffer of the last generation
   std::vector<float> f32;
   std::vector<Ranked> tk;
-  if (h_gate_idx) QE_CUDA(ctx, cudaMemcpyAsync(h_gate_idx, d.gate_idx, PL, cudaMemcpyDeviceToHost, us));
+  if (h_gate_idx)
+    QE_CUDA(ctx, cudaMemcpyAsync(h_gate_idx, d.gate_idx + b * PL, PL, cudaMemcpyDeviceToHost, us));
   if (h_seg_id && d.seg_id)
     QE_CUDA(ctx, cudaMemcpyAsync(h_seg_id, d.seg_id, PL * 4, cudaMemcpyDeviceToHost, us));
   if (h_fitness) {
     if (d.prec == QE_PREC_FP64) {
-      QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, d.fit64, (size_t)d.P * 8, cudaMemcpyDeviceToHost, us));
+      QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, d.fit64 + b * d.P, (size_t)d.P * 8,
+                                   cudaMemcpyDeviceToHost, us));
     } else {
       f32.resize(d.P);
-      QE_CUDA(ctx, cudaMemcpyAsync(f32.data(), d.fit32, (size_t)d.P * 4, cudaMemcpyDeviceToHost, us));
+      QE_CUDA(ctx, cudaMemcpyAsync(f32.data(), d.fit32 + b * d.P, (size_t)d.P * 4,
+                                   cudaMemcpyDeviceToHost, us));
     }
   }
   if (h_topk) {

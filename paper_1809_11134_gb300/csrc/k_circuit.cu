@@ -243,6 +243,109 @@ __device__ __forceinline__ void dispatch(int op, R (&re)[Lay<NQ>::ROWS], R (&im)
 }
 #undef QE_CASE
 
+// ------------------------------------------------------------------ 5 qubits: target at bit 0
+// With n = 5 a lane holds a whole column (32 rows, all in registers).  A switch
+// with one case per (kind, control, target) would be ~50 cases of unrolled
+// register updates, more code than the instruction cache holds.  Instead the
+// kernel keeps a map from wires to physical row bits: before each gate the
+// target wire's bit is exchanged with bit 0 (4 static cases of register moves),
+// then the gate acts on bit 0 with its control at any other bit (CNOT, CV:
+// 4 cases each; H, T: 1 each).  Rows are translated through the map only at
+// the end.  Binary32 arithmetic; the binary64 paths keep the direct switch.
+__device__ __forceinline__ void xchg(float &a, float &b) {
+  const float t = a;
+  a = b;
+  b = t;
+}
+
+// exchange physical row bits 0 and B of the column
+template <int B>
+__device__ __forceinline__ void swap_bit0(float (&re)[32], float (&im)[32]) {
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    if ((r & 1) && !((r >> B) & 1)) {
+      const int q = (r ^ 1) | (1 << B);
+      xchg(re[r], re[q]);
+      xchg(im[r], im[q]);
+    }
+  }
+}
+
+// gate of kind K on target bit 0, control at bit CB (-1: none)
+template <int K, int CB>
+__device__ __forceinline__ void gate_bit0(float (&re)[32], float (&im)[32], float s) {
+  using A = Ar<float, false>;
+#pragma unroll
+  for (int r0 = 0; r0 < 32; r0 += 2) {
+    if (CB >= 0 && !((r0 >> CB) & 1)) continue;
+    const int r1 = r0 | 1;
+    if constexpr (K == kCnot) {
+      xchg(re[r0], re[r1]);
+      xchg(im[r0], im[r1]);
+    } else if constexpr (K == kCvx) {
+      A::cvx_pair(re[r0], im[r0], re[r1], im[r1], s);
+    } else if constexpr (K == kHad) {
+      A::had_pair(re[r0], im[r0], re[r1], im[r1]);
+    } else {
+      A::tx(re[r1], im[r1], s);
+    }
+  }
+}
+
+// apply one op: wire bits in pos (3 bits per wire), wire at each bit in inv
+__device__ __forceinline__ void apply5(int op, uint32_t &pos, uint32_t &inv, float (&re)[32],
+                                       float (&im)[32]) {
+  constexpr int NP2 = 2 * 5 * 4;
+  const int o = op & 0x7f;
+  const float s = (op & kOpNeg) ? -1.f : 1.f;
+  int kind, tw, cw = -1;
+  if (o < NP2) {
+    const int pr = o >> 1;
+    cw = pr >> 2;
+    const int tt = pr & 3;
+    tw = tt >= cw ? tt + 1 : tt;
+    kind = (o & 1) ? kCvx : kCnot;
+  } else {
+    tw = (o - NP2) >> 1;
+    kind = (o & 1) ? kTx : kHad;
+  }
+  const int b = (pos >> (3 * tw)) & 7;
+  if (b != 0) {
+    switch (b) {
+      case 1: swap_bit0<1>(re, im); break;
+      case 2: swap_bit0<2>(re, im); break;
+      case 3: swap_bit0<3>(re, im); break;
+      default: swap_bit0<4>(re, im); break;
+    }
+    const int w0 = inv & 7;  // wire now at bit 0
+    pos = (pos & ~(7u << (3 * w0))) | ((uint32_t)b << (3 * w0));
+    pos &= ~(7u << (3 * tw));
+    inv = (inv & ~(7u << (3 * b))) | ((uint32_t)w0 << (3 * b));
+    inv = (inv & ~7u) | (uint32_t)tw;
+  }
+  const int cb = cw < 0 ? 0 : (int)((pos >> (3 * cw)) & 7);
+  switch (kind * 5 + cb) {
+    case kCnot * 5 + 1: gate_bit0<kCnot, 1>(re, im, s); break;
+    case kCnot * 5 + 2: gate_bit0<kCnot, 2>(re, im, s); break;
+    case kCnot * 5 + 3: gate_bit0<kCnot, 3>(re, im, s); break;
+    case kCnot * 5 + 4: gate_bit0<kCnot, 4>(re, im, s); break;
+    case kCvx * 5 + 1: gate_bit0<kCvx, 1>(re, im, s); break;
+    case kCvx * 5 + 2: gate_bit0<kCvx, 2>(re, im, s); break;
+    case kCvx * 5 + 3: gate_bit0<kCvx, 3>(re, im, s); break;
+    case kCvx * 5 + 4: gate_bit0<kCvx, 4>(re, im, s); break;
+    case kHad * 5: gate_bit0<kHad, -1>(re, im, s); break;
+    default: gate_bit0<kTx, -1>(re, im, s); break;
+  }
+}
+
+// physical row of logical row x under the map
+__device__ __forceinline__ int phys_row5(int x, uint32_t pos) {
+  int p = 0;
+#pragma unroll
+  for (int w = 0; w < 5; ++w) p |= ((x >> (4 - w)) & 1) << ((pos >> (3 * w)) & 7);
+  return p;
+}
+
 // real operations of one op on an N x N state (gate-count work model)
 __device__ __forceinline__ uint32_t op_work(const DevProblem &p, int op) {
   if (op == kOpIdentity) return 0;
@@ -331,12 +434,27 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
   const uint32_t cost = __reduce_add_sync(kFull, (ops0 != kOpIdentity) + (ops1 != kOpIdentity));
   const uint32_t work = __reduce_add_sync(kFull, op_work(p, (int)ops0) + op_work(p, (int)ops1));
   const uint32_t L = p.L;
+  // 5-qubit binary32: wire w starts at physical bit 4 - w (pos), bit b holds
+  // wire 4 - b (inv); both stay the identity map elsewhere
+  constexpr bool kMapped = NQ == 5 && !CANON;
+  uint32_t pos = 0, inv = 0;
+  if constexpr (kMapped) {
+#pragma unroll
+    for (int w = 0; w < 5; ++w) {
+      pos |= (uint32_t)(4 - w) << (3 * w);
+      inv |= (uint32_t)w << (3 * (4 - w));
+    }
+  }
   for (uint32_t t = 0; t < L; ++t) {
     const uint32_t src = t < 32 ? ops0 : ops1;
     const int op = __shfl_sync(kFull, (int)src, (int)(t & 31));
     if (op == kOpIdentity) continue;
-    const R s = (op & kOpNeg) ? R(-1) : R(1);
-    dispatch<NQ, R, CANON>(op & 0x7f, re, im, lane, s);
+    if constexpr (kMapped) {
+      apply5(op, pos, inv, re, im);
+    } else {
+      const R s = (op & kOpNeg) ? R(-1) : R(1);
+      dispatch<NQ, R, CANON>(op & 0x7f, re, im, lane, s);
+    }
   }
   CircuitOut out;
   out.cost = cost;
@@ -346,7 +464,14 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
     if (!shadow) {
 #pragma unroll
       for (int r = 0; r < Ly::ROWS; ++r) {
-        const int i = (grp << Ly::RBR) | r;
+        int i = (grp << Ly::RBR) | r;
+        if constexpr (kMapped) {
+          // logical row of physical row r: bit b of r is wire inv[b]
+          int x = 0;
+#pragma unroll
+          for (int b = 0; b < 5; ++b) x |= ((r >> b) & 1) << (4 - (int)((inv >> (3 * b)) & 7));
+          i = x;
+        }
         S_out[2 * (i * N + j)] = re[r];
         S_out[2 * (i * N + j) + 1] = im[r];
       }
@@ -355,7 +480,8 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
   // this lane's S[perm[j]][j], if it holds that row.  Picked by an arithmetic
   // blend (exact: one term has weight 1, the rest weight 0) so that the state
   // array is never indexed dynamically and stays in registers.
-  const int pj = p.perm[j];
+  int pj = p.perm[j];
+  if constexpr (kMapped) pj = phys_row5(pj, pos);
   R vr = R(0), vi = R(0);
   {
     const uint32_t own = (!shadow && (pj >> Ly::RBR) == grp) ? (1u << (pj & (Ly::ROWS - 1))) : 0u;
@@ -369,31 +495,38 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
   const double pen =
       p.cost_weight == 0.0 ? 0.0 : __dmul_rn(p.cost_weight, __ddiv_rn((double)cost, (double)p.L));
   if constexpr (CANON) {
-    // sequential sum over j ascending, every lane runs the same sequence
+    // sequential sum over j ascending, on lane 0 (the values arrive by shuffle;
+    // the binary64 arithmetic runs on one lane only)
     double a = 0.0, b = 0.0;
     for (int jj = 0; jj < N; ++jj) {
       const int owner = ((p.perm[jj] >> Ly::RBR) << NQ) | jj;
       const double xr = __shfl_sync(kFull, vr, owner), xi = __shfl_sync(kFull, vi, owner);
-      if (p.fit_kind == 1) {
-        a = __dadd_rn(a, __dadd_rn(__dmul_rn(xr, xr), __dmul_rn(xi, xi)));
-      } else {
-        a = __dadd_rn(a, xr);
-        b = __dadd_rn(b, -xi);
+      if (lane == 0) {
+        if (p.fit_kind == 1) {
+          a = __dadd_rn(a, __dadd_rn(__dmul_rn(xr, xr), __dmul_rn(xi, xi)));
+        } else {
+          a = __dadd_rn(a, xr);
+          b = __dadd_rn(b, -xi);
+        }
       }
     }
-    // (size - x) / size: size = N is a power of two, so the division is the
-    // exact scaling by 1/N (identical result, no binary64 division sequence)
-    const double size = (double)N, inv = 1.0 / (double)N;
-    double d;
-    if (p.fit_kind == 1) {
-      d = __dmul_rn(__dsub_rn(size, a), inv);
-    } else {
-      const double m = __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
-      d = __dmul_rn(__dsub_rn(size, m), inv);
+    double F = 0.0;
+    if (lane == 0) {
+      // (size - x) / size: size = N is a power of two, so the division is the
+      // exact scaling by 1/N (identical result, no binary64 division sequence)
+      const double size = (double)N, inv = 1.0 / (double)N;
+      double d;
+      if (p.fit_kind == 1) {
+        d = __dmul_rn(__dsub_rn(size, a), inv);
+      } else {
+        const double m = __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
+        d = __dmul_rn(__dsub_rn(size, m), inv);
+      }
+      if (d < 0.0) d = 0.0;
+      const double f = __dsub_rn(1.0, __dsqrt_rn(d));
+      F = __dsub_rn(f, pen);
     }
-    if (d < 0.0) d = 0.0;
-    const double f = __dsub_rn(1.0, __dsqrt_rn(d));
-    out.F = __dsub_rn(f, pen);
+    out.F = __shfl_sync(kFull, F, 0);
   } else {
     float a, b;
     if (p.fit_kind == 1) {
@@ -464,19 +597,21 @@ __global__ void __launch_bounds__(256, min_blocks<NQ, CANON>()) k_step(const Dev
     const uint32_t q = find_problem(prefix, n_group, w);
     const DevProblem &p = probs[group[q]];
     const uint32_t c = w - prefix[q];
+    const uint32_t par = gen & 1u;  // generation buffer
+    uint8_t *gate_idx = p.gate_idx + (size_t)par * p.P * p.L;
     uint32_t o0 = kOpIdentity, o1 = kOpIdentity, seg0 = 0, seg1 = 0;
     bool bad = false;
     if ((uint32_t)lane < p.L) {
       uint32_t gg;
       sample_slot(p, c, lane, gen, gg, seg0);
-      p.gate_idx[(size_t)c * p.L + lane] = (uint8_t)gg;
+      gate_idx[(size_t)c * p.L + lane] = (uint8_t)gg;
       p.seg_id[(size_t)c * p.L + lane] = seg0;
       o0 = op_of(p, gg, bad);
     }
     if ((uint32_t)lane + 32 < p.L) {
       uint32_t gg;
       sample_slot(p, c, lane + 32, gen, gg, seg1);
-      p.gate_idx[(size_t)c * p.L + lane + 32] = (uint8_t)gg;
+      gate_idx[(size_t)c * p.L + lane + 32] = (uint8_t)gg;
       p.seg_id[(size_t)c * p.L + lane + 32] = seg1;
       o1 = op_of(p, gg, bad);
     }
@@ -484,9 +619,9 @@ __global__ void __launch_bounds__(256, min_blocks<NQ, CANON>()) k_step(const Dev
     CircuitOut out = compose_score<NQ, R, CANON>(p, lane, o0, o1, (R *)nullptr);
     const bool nonfinite = !isfinite(out.F);
     if (lane == 0) {
-      if constexpr (CANON) p.fit64[c] = out.F;
-      else p.fit32[c] = (float)out.F;
-      p.meta[c] = out.cost | (out.work << 8);
+      if constexpr (CANON) p.fit64[(size_t)par * p.P + c] = out.F;
+      else p.fit32[(size_t)par * p.P + c] = (float)out.F;
+      p.meta[(size_t)par * p.P + c] = out.cost | (out.work << 8);
       if (nonfinite) atomicOr(g.err, kErrNonFinite);
     }
     if (!nonfinite) {
@@ -545,9 +680,12 @@ __global__ void __launch_bounds__(256, min_blocks<NQ, CANON>()) k_eval(const Dev
 // entries of other widths are skipped.
 template <int NQ>
 __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ probs,
-                                                 const uint8_t *__restrict__ gsrc, DevGlobal g) {
+                                                 const uint8_t *__restrict__ gsrc, int pipelined,
+                                                 DevGlobal g) {
   const int lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  if (pipelined && !*g.rank_active) return;
+  const uint32_t par = pipelined ? ((*g.gen - 1u) & 1u) : 0u;
   const uint32_t total = *g.rescore_n;
   // entries are dealt block-first (entry w -> block w % gridDim) so that a
   // short queue spreads one binary64 circuit per SM before doubling up
@@ -557,7 +695,8 @@ __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ 
     if (p.n != (uint32_t)NQ) continue;
     const uint32_t slot = ent & 0xfffffu;
     const uint32_t c = p.cand[slot];
-    const uint8_t *gates = (gsrc ? gsrc : p.gate_idx) + (size_t)c * p.L;
+    const uint8_t *gates =
+        (gsrc ? gsrc : p.gate_idx + (size_t)par * p.P * p.L) + (size_t)c * p.L;
     bool bad = false;
     uint32_t o0 = kOpIdentity, o1 = kOpIdentity;
     if ((uint32_t)lane < p.L) o0 = op_of(p, gates[lane], bad);
@@ -625,12 +764,22 @@ cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *prob
 }
 
 cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, const DevProblem *probs,
-                           const uint8_t *gsrc, const DevGlobal &g, cudaStream_t st) {
+                           const uint8_t *gsrc, bool pipelined, const DevGlobal &g,
+                           cudaStream_t st) {
   const uint32_t blocks = lc.num_sms * lc.step64[nq];
-#define QE_L(NQ) k_rescore<NQ><<<blocks, 256, 0, st>>>(probs, gsrc, g);
+#define QE_L(NQ) k_rescore<NQ><<<blocks, 256, 0, st>>>(probs, gsrc, pipelined ? 1 : 0, g);
   QE_NQ_SWITCH(nq, QE_L)
 #undef QE_L
   return cudaGetLastError();
+}
+
+bool is_circuit_kernel(const void *f) {
+#define QE_K(NQ)                                                                        \
+  if (f == (const void *)k_step<NQ, float, false> || f == (const void *)k_step<NQ, double, true>) \
+    return true;
+  QE_K(1) QE_K(2) QE_K(3) QE_K(4) QE_K(5)
+#undef QE_K
+  return false;
 }
 
 cudaError_t query_circuit_occupancy(LaunchCfg &lc) {

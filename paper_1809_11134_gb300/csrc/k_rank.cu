@@ -94,11 +94,31 @@ __device__ __forceinline__ void find_bin(const uint32_t *hist, uint32_t rem, uin
   __syncthreads();
 }
 
+// a pipelined job ranks generation gen - 1 from buffer (gen - 1) & 1
+__device__ __forceinline__ RankJob resolve(RankJob jb, const DevProblem &p, uint32_t gen) {
+  if (jb.pipelined) {
+    const size_t b = (gen - 1u) & 1u;
+    jb.fit = (const char *)jb.fit + b * p.P * (p.prec == 0 ? 8 : 4);
+    jb.meta += b * p.P;
+    jb.gsrc += b * p.P * p.L;
+  }
+  return jb;
+}
+
 __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *__restrict__ probs,
                                                               const RankJob *__restrict__ jobs,
                                                               RankJob single, DevGlobal g) {
-  const RankJob jb = jobs ? jobs[blockIdx.x] : single;
+  RankJob jb = jobs ? jobs[blockIdx.x] : single;
   const DevProblem &p = probs[jb.prob];
+  if (jb.pipelined) {
+    // the chain of generation gen - 1 runs once: skip when there is none or
+    // when it was already ranked (drained); every block takes the same decision
+    const uint32_t gen = *g.gen;
+    const bool active = gen > 0 && *g.ranked < gen;
+    if (threadIdx.x == 0) *g.rank_active = active ? 1u : 0u;
+    if (!active) return;
+    jb = resolve(jb, p, gen);
+  }
   const uint32_t n = jb.n;
   const uint32_t k = p.k < n ? p.k : n;
   extern __shared__ uint32_t dyn_smem[];
@@ -232,17 +252,128 @@ __device__ __forceinline__ bool key_less(unsigned long long ah, unsigned long lo
   return ah < bh || (ah == bh && al < bl);
 }
 
+// Best-so-far record and report fields of a ranked generation (one warp):
+// lane 0 decides, the warp copies the gates of an improvement.
+__device__ __forceinline__ void record_best(const DevProblem &p, const RankJob &jb, const DevGlobal &g,
+                                            uint32_t gen, unsigned long long kh0,
+                                            unsigned long long kl0, uint32_t kept, int lane) {
+  const unsigned long long kMaxKey = ~0ull;
+  Best *rec = p.rec;
+  const bool valid = kept > 0 && kh0 < kMaxKey - 1;
+  const double F = valid ? dkey_inv(~kh0) : 0.0;
+  const uint32_t c = (uint32_t)(kl0 & 0xffffffffu);
+  const uint32_t cost = (uint32_t)(kl0 >> 32);
+  int improve = 0;
+  if (lane == 0) {
+    rec->generation = gen + 1;
+    rec->error_word |= *g.err;
+    if (jb.pipelined) *g.ranked = gen + 1;
+    if (valid) {
+      rec->gen_best_fitness = F;
+      if (F > rec->best_fitness || (F == rec->best_fitness && cost < rec->best_cost)) {
+        rec->best_fitness = F;
+        rec->best_cost = cost;
+        rec->best_gen = gen;
+        rec->best_len = p.L;
+        improve = 1;
+      }
+    }
+  }
+  improve = __shfl_sync(kFull, improve, 0);
+  if (improve) {
+    const uint8_t *gs = jb.gsrc + (size_t)c * p.L;
+    for (uint32_t t = lane; t < 64; t += 32) rec->best_gates[t] = t < p.L ? gs[t] : 0;
+  }
+}
+
+// compare-exchange of two 128-bit keys held as (hi, lo) pairs
+__device__ __forceinline__ void keep_side(unsigned long long &h, unsigned long long &l,
+                                          unsigned long long ph, unsigned long long pl,
+                                          bool keep_min) {
+  const bool pless = key_less(ph, pl, h, l);
+  if (keep_min == pless) {
+    h = ph;
+    l = pl;
+  }
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_rank_sort(const DevProblem *__restrict__ probs,
                                                             const RankJob *__restrict__ jobs,
                                                             RankJob single, DevGlobal g) {
-  const RankJob jb = jobs ? jobs[blockIdx.x] : single;
+  RankJob jb = jobs ? jobs[blockIdx.x] : single;
   const DevProblem &p = probs[jb.prob];
+  uint32_t gen = 0;
+  if (jb.pipelined) {
+    if (!*g.rank_active) return;
+    gen = *g.gen - 1u;  // the generation being ranked
+    jb = resolve(jb, p, gen + 1u);
+  } else if (jb.update_record) {
+    gen = *g.gen;
+  }
   const uint32_t n = jb.n;
   const uint32_t k = p.k < n ? p.k : n;
   const uint32_t M = *p.cand_n;
   __shared__ unsigned long long kh[kSortN], kl[kSortN];
   const int tid = threadIdx.x;
   const unsigned long long kMaxKey = ~0ull;
+  if (M <= 64) {
+    // one warp: 64 keys, two per lane (index lane and lane + 32), bitonic by
+    // shuffles; no block barriers
+    if (tid >= 32) return;
+    const int lane = tid;
+    unsigned long long h[2], l[2];
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl) {
+      const uint32_t i = lane + 32 * sl;
+      h[sl] = kMaxKey;
+      l[sl] = kMaxKey;
+      if (i < M) {
+        const uint32_t c = p.cand[i];
+        const double F = p.cand_f[i];
+        h[sl] = (F == F) ? ~dkey(F) : kMaxKey - 1;
+        l[sl] = ((unsigned long long)(jb.meta[c] & 0xffu) << 32) | c;
+      }
+    }
+#pragma unroll
+    for (uint32_t size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        if (stride == 32) {  // partner is the lane's other key
+          const bool asc = true;
+          const unsigned long long h0 = h[0], l0 = l[0];
+          keep_side(h[0], l[0], h[1], l[1], asc);
+          keep_side(h[1], l[1], h0, l0, !asc);
+        } else {
+#pragma unroll
+          for (int sl = 0; sl < 2; ++sl) {
+            const uint32_t i = lane + 32 * sl;
+            const unsigned long long ph = __shfl_xor_sync(kFull, h[sl], stride);
+            const unsigned long long pl = __shfl_xor_sync(kFull, l[sl], stride);
+            const bool asc = (i & size) == 0, lower = (i & stride) == 0;
+            keep_side(h[sl], l[sl], ph, pl, lower == asc);
+          }
+        }
+      }
+    }
+    const uint32_t kept = M < k ? M : k;
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl) {
+      const uint32_t i = lane + 32 * sl;
+      if (i < kept) {
+        Ranked rr;
+        rr.circuit = (uint32_t)(l[sl] & 0xffffffffu);
+        rr.cost = (uint32_t)(l[sl] >> 32);
+        rr.fitness = (h[sl] >= kMaxKey - 1) ? __longlong_as_double(0x7ff8000000000000ll)
+                                           : dkey_inv(~h[sl]);
+        p.topk_out[i] = rr;
+      }
+    }
+    if (jb.update_record) {
+      const unsigned long long h0 = __shfl_sync(kFull, h[0], 0), l0 = __shfl_sync(kFull, l[0], 0);
+      record_best(p, jb, g, gen, h0, l0, kept, lane);
+    }
+    return;
+  }
   uint32_t kept = 0, next = 0;
   // ascending order of (~dkey(F), cost << 32 | c) == (F desc, cost asc, c asc);
   // each round sorts the kept top-k plus the next candidates with a bitonic
@@ -299,39 +430,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rank_sort(const DevProblem *__
                                       : dkey_inv(~kh[s]);
     p.topk_out[s] = r;
   }
-  if (jb.update_record && tid < 64) {
-    // best-so-far record: thread 0 decides, 64 threads copy the gates
-    __shared__ int s_improve;
-    Best *rec = p.rec;
-    const uint32_t gen = *g.gen;
-    const bool valid = kept > 0 && kh[0] < kMaxKey - 1;
-    const double F = valid ? dkey_inv(~kh[0]) : 0.0;
-    const uint32_t c = (uint32_t)(kl[0] & 0xffffffffu);
-    const uint32_t cost = (uint32_t)(kl[0] >> 32);
-    if (tid == 0) {
-      rec->generation = gen + 1;
-      rec->error_word |= *g.err;
-      s_improve = 0;
-      if (valid) {
-        rec->gen_best_fitness = F;
-        if (F > rec->best_fitness || (F == rec->best_fitness && cost < rec->best_cost)) {
-          rec->best_fitness = F;
-          rec->best_cost = cost;
-          rec->best_gen = gen;
-          rec->best_len = p.L;
-          s_improve = 1;
-        }
-      }
-    }
-    __syncwarp();
-    if (tid < 32) {
-      const int imp = __shfl_sync(kFull, s_improve, 0);
-      if (imp) {
-        const uint8_t *gs = jb.gsrc + (size_t)c * p.L;
-        for (uint32_t t = tid; t < 64; t += 32) rec->best_gates[t] = t < p.L ? gs[t] : 0;
-      }
-    }
-  }
+  if (jb.update_record && tid < 32) record_best(p, jb, g, gen, kh[0], kl[0], kept, tid);
 }
 
 __global__ void k_finish(DevGlobal g) {

@@ -207,7 +207,8 @@ extern "C" qe_status qe_eval_rank_static(const qe_problem *prob, const uint8_t *
     j.gsrc = d_gate_idx;
     j.update_record = 0;
     if (e == cudaSuccess) e = qe::launch_rank_select(probs, nullptr, 1, j, g, st);
-    if (e == cudaSuccess && !canon) e = qe::launch_rescore(slot.lc, d.n, probs, d_gate_idx, g, st);
+    if (e == cudaSuccess && !canon)
+      e = qe::launch_rescore(slot.lc, d.n, probs, d_gate_idx, false, g, st);
     if (e == cudaSuccess) e = qe::launch_rank_sort(probs, nullptr, 1, j, g, st);
   }
   if (e != cudaSuccess) return say(h_msg, msg_len, QE_ECUDA, cudaGetErrorString(e));

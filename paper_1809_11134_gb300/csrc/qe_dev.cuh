@@ -8,8 +8,10 @@
 //                fitness and this generation's segment fitness as an
 //                order-preserving key (0 = untouched, reset by the update),
 //                side by side so both arrive in one DRAM burst
-//   gate_idx   : P*L uint8, seg_id: P*L uint32 (the generation's circuits)
-//   fit32/fit64: P (working-precision fitness), meta: P (cost | work << 8)
+//   gate_idx   : 2 x P*L uint8 (the generation's circuits, double-buffered by
+//                generation parity so a generation's ranking can overlap the
+//                next generation), seg_id: P*L uint32
+//   fit32/fit64: 2 x P (working-precision fitness), meta: 2 x P (cost | work << 8)
 // where S = R*P*L and seg = r*L*P + i*L + t (Eq. (10)).
 #pragma once
 #include <cuda_runtime.h>
@@ -89,6 +91,8 @@ struct DevGlobal {
   uint32_t *err;      // error word
   uint32_t *rescore_list;  // (problem << 20 | slot) pairs to rescore in binary64
   uint32_t *rescore_n;
+  uint32_t *ranked;       // generations whose ranking is done (pipelined ranking)
+  uint32_t *rank_active;  // 1 while a pipelined ranking chain has work to do
 };
 
 // ---------------------------------------------------------------- Philox4x32-10

@@ -28,6 +28,9 @@ inline uint32_t grid_for(const LaunchCfg &lc, uint64_t warps, uint32_t per_sm) {
 // fitness is at fit (float or double by the search's precision) and whose
 // cost|work words are at meta; gates at gsrc (rescoring); update_record says
 // whether the best-so-far record and report fields are written.
+// pipelined: the buffers are the search's double-buffered generation buffers
+// and the job ranks generation *gen - 1 (buffer (gen-1) & 1); the chain is
+// skipped when that generation is already ranked (or gen == 0).
 struct RankJob {
   uint32_t prob;
   uint32_t n;
@@ -35,11 +38,12 @@ struct RankJob {
   const uint32_t *meta;
   const uint8_t *gsrc;
   uint32_t update_record;
-  uint32_t pad;
+  uint32_t pipelined;
 };
 
 // k_circuit.cu
 cudaError_t query_circuit_occupancy(LaunchCfg &lc);
+bool is_circuit_kernel(const void *f);  // a generation circuit kernel (graph node priorities)
 // all searches of a launch have n qubits
 cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs,
                         const uint32_t *group, const uint32_t *prefix, uint32_t n_group,
@@ -50,8 +54,12 @@ cudaError_t launch_sample(const LaunchCfg &lc, const DevProblem *probs, uint32_t
 cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *probs, uint32_t prob,
                         bool canon, const uint8_t *gates, uint32_t n, void *fit, uint32_t *cost,
                         void *S, const DevGlobal &g, cudaStream_t st);
+// gsrc == NULL: each candidate's search's own generation buffer; pipelined:
+// that buffer is the one of generation *gen - 1, and nothing runs unless the
+// chain is active
 cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, const DevProblem *probs,
-                           const uint8_t *gsrc, const DevGlobal &g, cudaStream_t st);
+                           const uint8_t *gsrc, bool pipelined, const DevGlobal &g,
+                           cudaStream_t st);
 
 // k_update.cu
 bool is_update_kernel(const void *f);  // an update kernel (graph node priorities)

@@ -286,6 +286,30 @@ def test_step_trajectory_fp64_bit_exact(qe, torch, cfg, P, gens):
             assert state_equal(bf, ref[run][3])
 
 
+@pytest.mark.parametrize("calls", [[5, 0], [3, 2], [1, 1, 1, 1]])
+def test_pipelined_generations_fp64_bit_exact(qe, torch, calls):
+    """Generations enqueued without reports rank the previous generation while
+    the next one runs; the reports after draining equal the oracle's."""
+    searches = W.config(2, precision=W.PREC_FP64, P=200)
+    gens = sum(calls)
+    ref = _oracle_run(searches, gens)
+    with qe.Context(searches) as ctx:
+        for n in calls[:-1]:
+            ctx.step_raw(n, None)
+        reps = ctx.step(calls[-1])
+        for run, s in enumerate(searches):
+            gi, sid, F, tk, bfit, bcost, bgates = ref[run][0][gens - 1]
+            last = ctx.last_generation(run)
+            assert np.array_equal(last["gate_idx"], gi) and np.array_equal(last["fitness"], F)
+            assert [t[0] for t in last["topk"]] == list(tk[:s.topk])
+            r = reps[run]
+            assert r["generation"] == gens
+            assert r["best_fitness"] == bfit and r["best_cost"] == bcost
+            assert bytes(r["best_gates"]) == bgates[:s.L]
+            c, b, bf = ctx.get_state(run)
+            assert state_equal(c, ref[run][1]) and state_equal(bf, ref[run][3])
+
+
 def test_step_fp32_each_stage_matches(qe, torch):
     """binary32 generations: the sample is bit-exact for the state the step
     started from, fitness within its bound, the rescored top-k bit-exact, and
