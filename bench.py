@@ -27,6 +27,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "candidate circuits evaluated/sec at n=3/4/5 qubits, FP32 batched vs FP64 plain"
+WORKLOADS = {
+    1: "3-qubit QEQEA: Toffoli, 19-gate NCV+I library, L=5, P=64, seed 0, binary64",
+    2: "3-qubit QEQEA: Toffoli + Fredkin + Peres targets, 28-gate NCV+H/T/T^dag+I library, L=16, "
+       "P=4096 each, Philox seed 1, binary32 compose with binary64 top-32 rescoring",
+    3: "4-qubit QEQEA: C3NOT, 48-gate NCV+H/T/T^dag library, L=32, P=65536, binary32 with "
+       "binary64 top-64",
+    4: "1024 uneven QEQEA searches, n in {3,4,5}, L in [8,64], P in [256,4096], random "
+       "permutation targets, binary32 with binary64 top-32",
+    5: "5-qubit QEQEA: C4NOT, 75-gate NCV+H/T/T^dag library, L=64, P=262144, binary32 with "
+       "binary64 top-128",
+}
 UNIT = "circuits/s"
 
 
@@ -179,7 +190,7 @@ def run_ours(args):
     from paper_1809_11134_gb300 import qe
     from paper_1809_11134_gb300 import workloads as W
 
-    searches = W.config(2)
+    searches = W.config(args.config, P=args.population)
     if rank:
         for s in searches:
             s.seed = s.seed + 1000 * rank  # independent replica per rank
@@ -233,12 +244,14 @@ def run_ours(args):
     names = ["circuits", "rank_select", "rescore", "rank_sort", "update", "generation"]
     stage = dict(zip(names, st_mean))
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel: the circuit kernel (sample +
+    # compose + score + scatter), the largest kernel of a generation in the ncu
+    # launch list (profiles/launches_3qubit_bench.md); its time is the event
+    # interval around it inside the generation graph
     pk = peaks()
-    hbm = pk.get("hbm_gbs")
-    dom = max(names[:5], key=lambda n: stage[n])
     last = [ctx.last_generation(r) for r in range(len(searches))]
-    roof = roofline(dom, stage[dom], searches, last, pk)
+    roof = roofline("circuits", stage["circuits"], searches, last, pk,
+                    traffic=TRAFFIC.get((args.config, args.population)))
 
     # ---- end to end through the public API with host buffers
     e2e = end_to_end(qe, ctx, searches, last, args.steps)
@@ -251,16 +264,16 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "3-qubit QEQEA: Toffoli + Fredkin + Peres targets, 28-gate "
-                                   "NCV+H/T/T^dag+I library, L=16, P=4096 each, Philox seed 1, "
-                                   "binary32 compose with binary64 top-32 rescoring; one step = "
-                                   "one generation of the three searches",
+            "config": {"workload": WORKLOADS.get(args.config, "benchmark search set %d" % args.config)
+                                   + ("" if args.population is None else " (P capped at %d)" % args.population)
+                                   + "; one step = one generation, ranked binary64 top-k pipelined "
+                                     "one generation behind",
                        "circuits_per_step": n_circ, "parallelism": "replica per GPU",
                        "l2": "flushed (256 MB write) before every timed step",
                        "stage_ms": {k: round(v, 5) for k, v in stage.items()}},
             "roofline": roof,
             "e2e": e2e,
-            "gpu_launches": (len(set((s.n, s.precision == 0) for s in searches)) + 5) * args.steps,
+            "gpu_launches": launches_per_generation(searches) * args.steps,
             "clocks": clocks,
             "wall_s": wall,
         }
@@ -274,7 +287,13 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def roofline(dom, ms, searches, last, pk):
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_step launch from an
+# ncu capture of this workload (profiles/k_step_3qubit_bench.md); cold L2 (ncu
+# flushes caches between replays), so it includes the update's L2 prefetch
+TRAFFIC = {(2, None): 41.325e6}
+
+
+def roofline(dom, ms, searches, last, pk, traffic=None):
     """Achieved algorithmic rate of the dominant kernel against its roofline."""
     hbm = pk.get("hbm_gbs")
     sm_max = pk.get("sm_max_mhz", 2070.0)
@@ -285,7 +304,8 @@ def roofline(dom, ms, searches, last, pk):
         ach = flops / (ms / 1e3) / 1e12
         return {"kernel": "k_step (sample + compose + score + scatter)", "bound": "alu",
                 "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max}
+                "traffic": traffic, "algorithmic_flops": flops, "ms": ms,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % sm_max}
     if dom == "update":
         b = update_bytes(searches, last)
         ach = b / (ms / 1e3) / 1e9
@@ -298,6 +318,15 @@ def roofline(dom, ms, searches, last, pk):
     return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": ach / hbm if hbm else None, "traffic": None,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+
+
+def launches_per_generation(searches):
+    """Kernel nodes of one generation graph: one circuit kernel per (width,
+    arithmetic) group, the two update kernels, selection, one rescoring kernel
+    per width with binary32 searches, sort, finish."""
+    groups = len(set((s.n, s.precision == 0) for s in searches))
+    widths = len(set(s.n for s in searches if s.precision != 0))
+    return groups + 2 + 1 + widths + 1 + 1
 
 
 def gen_flops(s, last):
@@ -399,6 +428,10 @@ def main():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-population", type=int, default=512)
+    ap.add_argument("--config", type=int, default=2,
+                    help="benchmark search set 1-5 (2 = the 3-qubit headline workload)")
+    ap.add_argument("--population", type=int, default=None,
+                    help="cap P (for profiling smaller cases of a configuration)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
