@@ -184,7 +184,12 @@ qe_status qe_update(qe_ctx *ctx, uint32_t prob, uint32_t gen, const uint32_t *d_
 
 /* Run n_gen whole generations of every search (sample -> compose/score ->
  * rank with binary64 rescoring -> update, or the GA's eval -> rank -> select /
- * cross / mutate), replayed as one CUDA graph per generation.  With h_reports
+ * cross / mutate), replayed as one CUDA graph per generation.  GA breeding
+ * (Sec. V-B comparison): stochastic universal sampling on the weights
+ * floor(clamp(F, 0, 1) 2^32) of the working-precision fitness, one-point
+ * crossover of children (2m, 2m+1), per-gene replacement with probability
+ * ga_mutation_rate, and child 0 = the best circuit by (working-precision F
+ * desc, cost asc, index asc).  With h_reports
  * (n_probs entries) the call then copies one qe_report per search, synchronises
  * and returns QE_ENUMERIC if any search's error_word is set; with h_reports ==
  * NULL it only enqueues the generations on the stream and returns. */
@@ -211,7 +216,9 @@ qe_status qe_last_generation(qe_ctx *ctx, uint32_t prob, uint8_t *h_gate_idx, ui
  *   QEQEA: cur[S][8] float, best[S][8] float, best_f[S] float, S = R*P*L, with
  *          the 8 floats of a segment {q0.re, q0.im, q1.re, q1.im, q2.re, q2.im,
  *          b0, b1} (qutrit amplitudes, then qubit amplitudes);
- *   GA:    genome[P][L] uint8. */
+ *   GA:    genome[P][L] uint8, the population the next qe_step generation
+ *          evaluates (gene values below the library size; qe_set_state returns
+ *          QE_EINVAL for any other value). */
 qe_status qe_state_bytes(const qe_ctx *ctx, uint32_t prob, size_t *bytes);
 /* Copy the state out to / in from host memory of exactly qe_state_bytes bytes.
  * Synchronises. */

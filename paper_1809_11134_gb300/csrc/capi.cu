@@ -41,11 +41,14 @@ struct qe_ctx {
   LaunchCfg lc;
   void *arena = nullptr;
   size_t arena_bytes = 0;
-  std::vector<Group> groups;  // QEQEA circuit launches, one per (arithmetic, qubit count)
+  std::vector<Group> groups;  // circuit launches, one per (arithmetic, qubit count)
   bool rescore_nq[QE_MAX_QUBITS + 1] = {false};  // widths with binary32 searches
   // all QEQEA searches (update launch)
   uint32_t n_upd = 0, upd_totalA = 0, upd_totalB = 0;
   uint32_t *d_upd_ids = nullptr, *d_upd_prefA = nullptr, *d_upd_prefB = nullptr;
+  // all GA searches (breeding launches): ids and prefix sums of ceil(P/2) pairs
+  uint32_t n_ga = 0, ga_pairs = 0;
+  uint32_t *d_ga_ids = nullptr, *d_ga_prefix = nullptr;
   // per-search single arrays for qe_update: {id}, {0, P*L}, {0, ceil(P/32)*R}
   uint32_t *d_single = nullptr;
   RankJob *d_jobs = nullptr;
@@ -291,6 +294,8 @@ qe_status build_graph(qe_ctx *ctx) {
                       (uint32_t)gr.ids.size(), gr.total, gr.canon, ctx->g, ctx->side);
   }
   mark(1, ctx->side);
+  if (e == cudaSuccess && ctx->n_ga)
+    e = launch_ga_prep(ctx->d_probs, ctx->d_ga_ids, ctx->n_ga, ctx->g, ctx->side);
   mark(5, ctx->side);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork2, ctx->side);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side2, ctx->ev_fork2, 0);
@@ -312,6 +317,11 @@ qe_status build_graph(qe_ctx *ctx) {
   mark(4, cs);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
+  // GA breeding of generation g + 1 overwrites the buffer generation g - 1's
+  // ranking has just read
+  if (e == cudaSuccess && ctx->n_ga)
+    e = launch_ga_next(ctx->lc, ctx->d_probs, ctx->d_ga_ids, ctx->d_ga_prefix, ctx->n_ga,
+                       ctx->ga_pairs, ctx->g, cs);
   if (e == cudaSuccess) e = launch_finish(ctx->g, cs);
   mark(7, cs);
   cudaGraph_t graph = nullptr;
@@ -452,6 +462,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     d.cost_weight = q.cost_weight;
     d.ga_rate = q.ga_mutation_rate;
     d.mut_T = threshold(q.p_mutation);
+    d.ga_T = threshold(q.ga_mutation_rate);
     d.nseg = (uint64_t)d.R * d.L * d.P;
     for (uint32_t j = 0; j < 32; ++j) d.perm[j] = j < d.N ? q.target_perm[j] : 0;
     memset(d.gop, kOpIdentity, sizeof d.gop);
@@ -463,8 +474,8 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
       ar.take(&d.seg_id, PL * 4);
       ar.take(&d.qubit_tab, (kQ + 1) * sizeof(float2));
     } else {
-      ar.take(&d.genome_next, PL);
       ar.take(&d.ga_cum, P * 8);
+      ar.take(&d.ga_info, 16);
     }
     // generation buffers, two of each (generation parity)
     ar.take(&d.gate_idx, 2 * PL);
@@ -494,15 +505,15 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   ar.take(&ctx->d_single, n_probs * 5 * 4);
   ar.take(&ctx->d_stage_gates, max_PL);
   ar.take(&ctx->d_stage_fit, max_P * 8);
-  // groups: QEQEA searches by (arithmetic, qubit count), widest first
-  std::vector<uint32_t> upd;
+  // groups: searches by (arithmetic, qubit count), widest first
+  std::vector<uint32_t> upd, ga;
   for (int k = 0; k < 2; ++k)
     for (uint32_t nq = QE_MAX_QUBITS; nq >= 1; --nq) {
       Group gr;
       gr.canon = k == 1;
       gr.n = nq;
       for (uint32_t i = 0; i < n_probs; ++i) {
-        if (probs[i].encoding != QE_ENC_QEQEA || probs[i].n_qubits != nq) continue;
+        if (probs[i].n_qubits != nq) continue;
         if ((probs[i].precision == QE_PREC_FP64) != gr.canon) continue;
         gr.ids.push_back(i);
       }
@@ -510,6 +521,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     }
   for (uint32_t i = 0; i < n_probs; ++i) {
     if (probs[i].encoding == QE_ENC_QEQEA) upd.push_back(i);
+    else ga.push_back(i);
     if (probs[i].precision != QE_PREC_FP64) ctx->rescore_nq[probs[i].n_qubits] = true;
   }
   for (auto &gr : ctx->groups) {
@@ -520,6 +532,9 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   ar.take(&ctx->d_upd_ids, (upd.size() + 1) * 4);
   ar.take(&ctx->d_upd_prefA, (upd.size() + 1) * 4);
   ar.take(&ctx->d_upd_prefB, (upd.size() + 1) * 4);
+  ctx->n_ga = (uint32_t)ga.size();
+  ar.take(&ctx->d_ga_ids, (ga.size() + 1) * 4);
+  ar.take(&ctx->d_ga_prefix, (ga.size() + 1) * 4);
 
   size_t free_b = 0, total_b = 0;
   e = cudaMemGetInfo(&free_b, &total_b);
@@ -638,6 +653,14 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     if (e == cudaSuccess) e = put(ctx->d_upd_prefB, pb);
     if (e == cudaSuccess) e = cudaStreamSynchronize(us);
   }
+  {
+    std::vector<uint32_t> pg(ga.size() + 1, 0);
+    for (size_t k = 0; k < ga.size(); ++k) pg[k + 1] = pg[k] + (ctx->hp[ga[k]].P + 1) / 2;
+    ctx->ga_pairs = pg.back();
+    if (e == cudaSuccess) e = put(ctx->d_ga_ids, ga);
+    if (e == cudaSuccess) e = put(ctx->d_ga_prefix, pg);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.gen, 0, 4, us);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.err, 0, 4, us);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.rescore_n, 0, 4, us);
@@ -646,7 +669,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   for (uint32_t i = 0; i < n_probs && e == cudaSuccess; ++i) {
     const DevProblem &d = ctx->hp[i];
     if (d.enc == QE_ENC_QEQEA) e = launch_init_state(ctx->d_probs, i, d.nseg, us);
-    else e = cudaMemsetAsync(d.gate_idx, 0, 2 * (size_t)d.P * d.L, us);
+    else e = launch_ga_init(ctx->d_probs, i, d.P, d.L, us);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(us);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "initialising the state"));
@@ -790,7 +813,6 @@ qe_status qe_update(qe_ctx *ctx, uint32_t prob, uint32_t gen, const uint32_t *d_
 qe_status qe_step(qe_ctx *ctx, uint32_t n_gen, qe_report *h_reports) {
   if (!ctx) return fail(nullptr, QE_EINVAL, "null context");
   if (ctx->poisoned) return fail(ctx, QE_ESTATE, "context is poisoned by an earlier CUDA error");
-  if (ctx->groups.empty()) return fail(ctx, QE_EUNSUPPORTED, "no QEQEA search in this context");
   if (!ctx->gexec) {
     qe_status st = build_graph(ctx);
     if (st != QE_OK) return st;
@@ -953,8 +975,14 @@ static qe_status state_copy(qe_ctx *ctx, uint32_t prob, void *h, size_t bytes, b
                                        kd, us));
     }
   } else {
-    if (out) QE_CUDA(ctx, cudaMemcpyAsync(hb, d.gate_idx, need, kd, us));
-    else QE_CUDA(ctx, cudaMemcpyAsync(d.gate_idx, hb, need, kd, us));
+    // the genome the next generation evaluates
+    uint8_t *genome = d.gate_idx + (size_t)(ctx->gen & 1u) * need;
+    if (!out)
+      for (size_t e = 0; e < need; ++e)
+        if (((const uint8_t *)hb)[e] >= d.G)
+          return fail(ctx, QE_EINVAL, "genome holds a gate index outside the library");
+    if (out) QE_CUDA(ctx, cudaMemcpyAsync(hb, genome, need, kd, us));
+    else QE_CUDA(ctx, cudaMemcpyAsync(genome, hb, need, kd, us));
   }
   QE_CUDA(ctx, cudaStreamSynchronize(us));
   return QE_OK;

@@ -601,21 +601,28 @@ __global__ void __launch_bounds__(256, min_blocks<NQ, CANON>()) k_step(const Dev
     uint8_t *gate_idx = p.gate_idx + (size_t)par * p.P * p.L;
     uint32_t o0 = kOpIdentity, o1 = kOpIdentity, seg0 = 0, seg1 = 0;
     bool bad = false;
-    if ((uint32_t)lane < p.L) {
-      uint32_t gg;
-      sample_slot(p, c, lane, gen, gg, seg0);
-      gate_idx[(size_t)c * p.L + lane] = (uint8_t)gg;
-      p.seg_id[(size_t)c * p.L + lane] = seg0;
-      o0 = op_of(p, gg, bad);
+    const bool qeqea = p.enc == kEncQeqea;
+    if (qeqea) {
+      if ((uint32_t)lane < p.L) {
+        uint32_t gg;
+        sample_slot(p, c, lane, gen, gg, seg0);
+        gate_idx[(size_t)c * p.L + lane] = (uint8_t)gg;
+        p.seg_id[(size_t)c * p.L + lane] = seg0;
+        o0 = op_of(p, gg, bad);
+      }
+      if ((uint32_t)lane + 32 < p.L) {
+        uint32_t gg;
+        sample_slot(p, c, lane + 32, gen, gg, seg1);
+        gate_idx[(size_t)c * p.L + lane + 32] = (uint8_t)gg;
+        p.seg_id[(size_t)c * p.L + lane + 32] = seg1;
+        o1 = op_of(p, gg, bad);
+      }
+      prefetch_mutated(p, c, gen, lane);
+    } else {
+      // GA: this generation's genome, bred by the previous generation (k_ga_next)
+      if ((uint32_t)lane < p.L) o0 = op_of(p, gate_idx[(size_t)c * p.L + lane], bad);
+      if ((uint32_t)lane + 32 < p.L) o1 = op_of(p, gate_idx[(size_t)c * p.L + lane + 32], bad);
     }
-    if ((uint32_t)lane + 32 < p.L) {
-      uint32_t gg;
-      sample_slot(p, c, lane + 32, gen, gg, seg1);
-      gate_idx[(size_t)c * p.L + lane + 32] = (uint8_t)gg;
-      p.seg_id[(size_t)c * p.L + lane + 32] = seg1;
-      o1 = op_of(p, gg, bad);
-    }
-    prefetch_mutated(p, c, gen, lane);
     CircuitOut out = compose_score<NQ, R, CANON>(p, lane, o0, o1, (R *)nullptr);
     const bool nonfinite = !isfinite(out.F);
     if (lane == 0) {
@@ -624,7 +631,7 @@ __global__ void __launch_bounds__(256, min_blocks<NQ, CANON>()) k_step(const Dev
       p.meta[(size_t)par * p.P + c] = out.cost | (out.work << 8);
       if (nonfinite) atomicOr(g.err, kErrNonFinite);
     }
-    if (!nonfinite) {
+    if (!nonfinite && qeqea) {
       const uint32_t key = fkey((float)out.F);
       if ((uint32_t)lane < p.L) atomicMax(key_of(p, seg0), key);
       if ((uint32_t)lane + 32 < p.L) atomicMax(key_of(p, seg1), key);

@@ -1,0 +1,238 @@
+// k_ga.cu -- the classical GA of the paper's comparison (Sec. V-B) on the same
+// evaluation path: integer gate-string genomes, stochastic universal sampling,
+// one-point crossover, per-gene mutation, elitism.
+//
+// Per generation g (genome in gate_idx buffer g & 1, already evaluated into
+// fit/meta buffer g & 1 by the circuit kernel without sampling):
+//   k_ga_prep  one CTA per search: SUS weights floor(clamp(F,0,1) 2^32) and
+//              their inclusive prefix sums (integers, so exact in any order),
+//              the total W, and the elite = best by (F desc, cost asc, index asc)
+//              in the working precision;
+//   k_ga_next  one warp per pair of children: parents by SUS (pointer
+//              s + m floor(W/P), parent = first c with cum[c] > pointer),
+//              one-point crossover at 1 + below(u, L-1), per-gene mutation,
+//              child 0 = the elite; written to gate_idx buffer (g+1) & 1.
+// Philox streams as the oracle: (0, 0, g) for the SUS offset, (pair, 1, g) for
+// the cut, (child, 2 + t, g) for gene t's mutation, all with stream 4; the
+// initial genome draws (c, t, 0) with stream 5.
+#include "qe_dev.cuh"
+#include "qe_host.h"
+
+namespace qe {
+
+constexpr int kGaThreads = 1024;
+
+__device__ __forceinline__ uint32_t find_ga(const uint32_t *prefix, uint32_t n, uint32_t x) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(prefix + mid) <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double ga_fitness(const DevProblem &p, uint32_t par, uint32_t c) {
+  return p.prec == 0 ? p.fit64[(size_t)par * p.P + c] : (double)p.fit32[(size_t)par * p.P + c];
+}
+
+// SUS weight: max(F, 0) clamped to 1 as a 32-bit fixed-point integer
+__device__ __forceinline__ unsigned long long sus_weight(double F) {
+  if (!(F > 0.0)) return 0ull;
+  const double x = F < 1.0 ? F : 1.0;
+  return (unsigned long long)floor(__dmul_rn(x, 4294967296.0));
+}
+
+// a before b in the ranking key (F desc, cost asc, index asc); NaN last
+__device__ __forceinline__ bool ga_better(double Fa, uint32_t ca, uint32_t ia, double Fb,
+                                          uint32_t cb, uint32_t ib) {
+  const bool na = !(Fa == Fa), nb = !(Fb == Fb);
+  if (na != nb) return nb;
+  if (!na && Fa != Fb) return Fa > Fb;
+  if (ca != cb) return ca < cb;
+  return ia < ib;
+}
+
+// keep the better of (F, cost, idx) and lane l ^ o's candidate
+__device__ __forceinline__ void elite_shfl(double &F, uint32_t &cost, uint32_t &idx, int o) {
+  const double oF = __shfl_xor_sync(kFull, F, o);
+  const uint32_t oc = __shfl_xor_sync(kFull, cost, o), oi = __shfl_xor_sync(kFull, idx, o);
+  if (oi != 0xffffffffu && (idx == 0xffffffffu || ga_better(oF, oc, oi, F, cost, idx))) {
+    F = oF;
+    cost = oc;
+    idx = oi;
+  }
+}
+
+// One CTA per GA search, tiles of kGaThreads circuits: each thread weighs one
+// circuit, a block scan gives the tile's prefix sums, a running carry the rest.
+__global__ void __launch_bounds__(kGaThreads) k_ga_prep(const DevProblem *__restrict__ probs,
+                                                        const uint32_t *__restrict__ ids,
+                                                        DevGlobal g) {
+  const DevProblem &p = probs[ids[blockIdx.x]];
+  const uint32_t par = *g.gen & 1u;
+  const uint32_t P = p.P, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  __shared__ unsigned long long s_sum[kGaThreads / 32], s_tot;
+  __shared__ double s_F[kGaThreads / 32];
+  __shared__ uint32_t s_cost[kGaThreads / 32], s_idx[kGaThreads / 32];
+  double bF = 0.0;
+  uint32_t bcost = 0xffffffffu, bidx = 0xffffffffu;
+  unsigned long long carry = 0;
+  for (uint32_t base = 0; base < P; base += kGaThreads) {
+    const uint32_t c = base + tid;
+    unsigned long long w = 0;
+    if (c < P) {
+      const double F = ga_fitness(p, par, c);
+      w = sus_weight(F);
+      const uint32_t cost = p.meta[(size_t)par * P + c] & 0xffu;
+      if (bidx == 0xffffffffu || ga_better(F, cost, c, bF, bcost, bidx)) {
+        bF = F;
+        bcost = cost;
+        bidx = c;
+      }
+    }
+    unsigned long long v = w;  // warp inclusive scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(kFull, v, o);
+      if (lane >= (uint32_t)o) v += u;
+    }
+    if (lane == 31) s_sum[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      const unsigned long long x0 = s_sum[lane];
+      unsigned long long x = x0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(kFull, x, o);
+        if (lane >= (uint32_t)o) x += u;
+      }
+      s_sum[lane] = x - x0;  // exclusive prefix of the warp totals
+      if (lane == 31) s_tot = x;
+    }
+    __syncthreads();
+    if (c < P) p.ga_cum[c] = carry + s_sum[wid] + v;
+    carry += s_tot;
+  }
+  // the elite: warp reduction, then across warps
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) elite_shfl(bF, bcost, bidx, o);
+  if (lane == 0) {
+    s_F[wid] = bF;
+    s_cost[wid] = bcost;
+    s_idx[wid] = bidx;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    double F = s_F[lane];
+    uint32_t cost = s_cost[lane], idx = s_idx[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) elite_shfl(F, cost, idx, o);
+    if (lane == 0) {
+      p.ga_info[0] = carry;  // W
+      p.ga_info[1] = idx;    // elite
+    }
+  }
+}
+
+// first c in [0, P) with cum[c] > ptr (P - 1 if none)
+__device__ __forceinline__ uint32_t sus_parent(const unsigned long long *cum, uint32_t P,
+                                               unsigned long long ptr) {
+  uint32_t lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (cum[mid] > ptr) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_ga_next(const DevProblem *__restrict__ probs,
+                                                 const uint32_t *__restrict__ ids,
+                                                 const uint32_t *__restrict__ prefix,
+                                                 uint32_t n_ga, uint32_t total_pairs, DevGlobal g) {
+  const uint32_t gen = *g.gen;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total_pairs; w += nw) {
+    const uint32_t q = find_ga(prefix, n_ga, w);
+    const DevProblem &p = probs[ids[q]];
+    const uint32_t pair = w - prefix[q];
+    const uint32_t P = p.P, L = p.L;
+    const uint8_t *src = p.gate_idx + (size_t)(gen & 1u) * P * L;
+    uint8_t *dst = p.gate_idx + (size_t)((gen + 1u) & 1u) * P * L;
+    const uint32_t m0 = 2 * pair, m1 = m0 + 1;
+    const unsigned long long W = p.ga_info[0];
+    const uint32_t elite = (uint32_t)p.ga_info[1];
+    const unsigned long long D = W / P;
+    uint32_t a = m0, b = m1 < P ? m1 : m0;
+    if (D > 0) {
+      const uint4 u = draw(p, 0, 0, gen, kStGa);
+      const unsigned long long r64 = ((unsigned long long)u.y << 32) | u.x;
+      const unsigned long long s0 = __umul64hi(r64, D);
+      a = sus_parent(p.ga_cum, P, s0 + (unsigned long long)m0 * D);
+      if (m1 < P) b = sus_parent(p.ga_cum, P, s0 + (unsigned long long)m1 * D);
+    }
+    uint32_t cut = L;
+    if (m1 < P && L > 1) cut = 1 + below(draw(p, pair, 1, gen, kStGa).x, L - 1);
+    for (uint32_t t = lane; t < L; t += 32) {
+      const uint8_t ga = src[(size_t)a * L + t], gb = src[(size_t)b * L + t];
+      // child m0
+      uint8_t x = t < cut ? ga : gb;
+      if (m0 == 0) {
+        x = src[(size_t)elite * L + t];
+      } else {
+        const uint4 v = draw(p, m0, 2 + t, gen, kStGa);
+        if ((unsigned long long)v.x < p.ga_T) x = (uint8_t)below(v.y, p.G);
+      }
+      dst[(size_t)m0 * L + t] = x;
+      if (m1 < P) {
+        uint8_t y = t < cut ? gb : ga;
+        const uint4 v = draw(p, m1, 2 + t, gen, kStGa);
+        if ((unsigned long long)v.x < p.ga_T) y = (uint8_t)below(v.y, p.G);
+        dst[(size_t)m1 * L + t] = y;
+      }
+    }
+  }
+}
+
+// initial genome: gene (c, t) = below(u, G) with Philox (c, t, 0, stream 5)
+__global__ void __launch_bounds__(256) k_ga_init(const DevProblem *__restrict__ probs,
+                                                 uint32_t prob) {
+  const DevProblem &p = probs[prob];
+  const size_t n = (size_t)p.P * p.L;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t c = (uint32_t)(e / p.L), t = (uint32_t)(e % p.L);
+    p.gate_idx[e] = (uint8_t)below(draw(p, c, t, 0, kStGaInit).x, p.G);
+  }
+}
+
+cudaError_t launch_ga_init(const DevProblem *probs, uint32_t prob, uint32_t P, uint32_t L,
+                           cudaStream_t st) {
+  uint64_t blocks = ((uint64_t)P * L + 255) / 256;
+  if (blocks > 65536) blocks = 65536;
+  if (!blocks) blocks = 1;
+  k_ga_init<<<(uint32_t)blocks, 256, 0, st>>>(probs, prob);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ga_prep(const DevProblem *probs, const uint32_t *ids, uint32_t n_ga,
+                           const DevGlobal &g, cudaStream_t st) {
+  if (!n_ga) return cudaSuccess;
+  k_ga_prep<<<n_ga, kGaThreads, 0, st>>>(probs, ids, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ga_next(const LaunchCfg &lc, const DevProblem *probs, const uint32_t *ids,
+                           const uint32_t *prefix, uint32_t n_ga, uint32_t total_pairs,
+                           const DevGlobal &g, cudaStream_t st) {
+  if (!n_ga || !total_pairs) return cudaSuccess;
+  uint64_t blocks = ((uint64_t)total_pairs + 7) / 8;
+  const uint64_t cap = (uint64_t)lc.num_sms * 8;
+  if (blocks > cap) blocks = cap;
+  k_ga_next<<<(uint32_t)blocks, 256, 0, st>>>(probs, ids, prefix, n_ga, total_pairs, g);
+  return cudaGetLastError();
+}
+
+}  // namespace qe

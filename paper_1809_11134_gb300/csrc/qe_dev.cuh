@@ -10,7 +10,9 @@
 //                side by side so both arrive in one DRAM burst
 //   gate_idx   : 2 x P*L uint8 (the generation's circuits, double-buffered by
 //                generation parity so a generation's ranking can overlap the
-//                next generation), seg_id: P*L uint32
+//                next generation; a GA search keeps its genome here),
+//                seg_id: P*L uint32 (QEQEA only)
+//   ga_cum     : P uint64 SUS prefix sums (GA only)
 //   fit32/fit64: 2 x P (working-precision fitness), meta: 2 x P (cost | work << 8)
 // where S = R*P*L and seg = r*L*P + i*L + t (Eq. (10)).
 #pragma once
@@ -29,6 +31,9 @@ constexpr float kH32 = 0x1.6a09e6p-1f;
 
 // Philox4x32-10 counter words: (a, b, gen, run << 4 | stream)
 enum Stream : uint32_t { kStSample = 0, kStMutDecide = 1, kStMutSeg = 2, kStGa = 4, kStGaInit = 5 };
+
+// encodings (mirror QE_ENC_*)
+constexpr uint32_t kEncQeqea = 0u, kEncGa = 1u;
 
 // device error word bits (mirrors QE_ERRW_*)
 constexpr uint32_t kErrBadGate = 1u, kErrNonFinite = 2u;
@@ -58,6 +63,8 @@ struct DevProblem {
   // an individual mutates when its Philox word u < mut_T, i.e. when
   // (u + 1/2) 2^-32 < p_mut (mut_T = ceil(p_mut 2^32 - 1/2), clamped to [0, 2^32])
   unsigned long long mut_T;
+  // GA: a gene mutates when its Philox word u < ga_T (same rule with ga_rate)
+  unsigned long long ga_T;
   uint64_t nseg;
   uint8_t perm[32];
   uint8_t gop[80];    // library index -> op byte (see k_circuit.cu), kOpIdentity for I
@@ -77,9 +84,9 @@ struct DevProblem {
   Best *rec;
   // mutation table: cos/sin of m * mutation_range / Q, m = 0..Q
   float2 *qubit_tab;
-  // GA buffers
-  uint8_t *genome_next;
+  // GA buffers: SUS prefix sums of the weights, and {W, elite}
   unsigned long long *ga_cum;
+  unsigned long long *ga_info;
 };
 
 // context-wide device pointers

@@ -85,6 +85,17 @@ cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uin
 cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
                              const RankJob &single, const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_finish(const DevGlobal &g, cudaStream_t st);
+
+// GA (k_ga.cu): initial genome of one search into gate_idx buffer 0; per
+// generation the SUS prefix sums and elite of the searches in ids, then the
+// next genome (one warp per pair of children; prefix = pair-count prefix sums)
+cudaError_t launch_ga_init(const DevProblem *probs, uint32_t prob, uint32_t P, uint32_t L,
+                           cudaStream_t st);
+cudaError_t launch_ga_prep(const DevProblem *probs, const uint32_t *ids, uint32_t n_ga,
+                           const DevGlobal &g, cudaStream_t st);
+cudaError_t launch_ga_next(const LaunchCfg &lc, const DevProblem *probs, const uint32_t *ids,
+                           const uint32_t *prefix, uint32_t n_ga, uint32_t total_pairs,
+                           const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_reset_counter(const DevGlobal &g, cudaStream_t st);
 
 }  // namespace qe

@@ -112,7 +112,7 @@ def to_problem(s) -> qe_problem:
         return s
     p = qe_problem()
     p.n_qubits, p.circuit_len, p.population, p.library = s.n, s.L, s.P, s.library
-    p.encoding = getattr(s, "encoding", QE_ENC_QEQEA)
+    p.encoding = s.encoding
     p.precision, p.fitness_kind, p.topk = s.precision, s.fitness_kind, s.topk
     p.seed = s.seed
     p.p_mutation, p.mutation_range = s.p_mutation, s.mutation_range

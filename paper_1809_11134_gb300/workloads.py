@@ -16,6 +16,7 @@ import numpy as np
 LIB_NCV, LIB_HT, LIB_IDENTITY = 1, 2, 4
 PREC_FP64, PREC_FP32, PREC_SPLIT_TC = 0, 1, 2
 FIT_TRACE, FIT_PROB = 0, 1
+ENC_QEQEA, ENC_GA = 0, 1
 
 
 def _bit(x, n, w):
@@ -79,9 +80,11 @@ class Search:
     ga_mutation_rate: float = 0.02
     cost_weight: float = 0.0
     name: str = field(default="")
+    encoding: int = ENC_QEQEA
 
 
-def config(k: int, precision: int = None, P: int = None, seed: int = None) -> List[Search]:
+def config(k: int, precision: int = None, P: int = None, seed: int = None,
+           encoding: int = None) -> List[Search]:
     """The five benchmark searches (3-5 qubit permutation targets).
 
     1: 3-qubit Toffoli, NCV + identity (19 gates), L=5, P=64, FP64, seed 0
@@ -91,6 +94,9 @@ def config(k: int, precision: int = None, P: int = None, seed: int = None) -> Li
     4: 1024 uneven searches, n in {3,4,5}, L in [8,64], P in [256,4096],
        uniform random permutation targets (seed 2), top-32
     5: 5-qubit C4NOT, NCV + H/T/T^dag (75 gates), L=64, P=262144, top-128
+
+    encoding=ENC_GA turns every search into the classical GA on the same
+    shapes (integer genomes, per-gene mutation rate 0.02).
     """
     full = LIB_NCV | LIB_HT
     if k == 1:
@@ -123,6 +129,8 @@ def config(k: int, precision: int = None, P: int = None, seed: int = None) -> Li
             x.P = min(x.P, P)
         if seed is not None:
             x.seed = seed
+        if encoding is not None:
+            x.encoding = encoding
     return s
 
 

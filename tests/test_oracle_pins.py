@@ -529,9 +529,82 @@ def test_ga_sus_equal_weights_selects_everyone_once():
     out = oracle.ga_next(p, G, 3, 0.0, genome, F, cost)
     # no mutation: every gene of every child comes from a parent; with equal
     # weights SUS picks each parent exactly once, so each value appears L times
-    vals, cnt = np.unique(out[1:].ravel(), return_counts=True)
     assert out[0].tolist() == genome[0].tolist()  # elitism: ties -> lowest index
-    assert cnt.sum() == (P - 1) * L
+    # parent m = m, so children (2m, 2m+1) hold genomes 2m and 2m+1 split at one
+    # cut: L genes of each value, and column 0 (before every cut) is the parent
+    for m in range(2, P, 2):
+        pair = out[m:m + 2].ravel()
+        assert sorted(pair.tolist()) == [m] * L + [m + 1] * L
+        assert out[m, 0] == m and out[m + 1, 0] == m + 1
+
+
+def test_ga_sus_counts_are_within_one_of_expectation():
+    """Stochastic universal sampling (Baker 1987): with pointer spacing
+    D = floor(W / P), parent c is drawn floor(w_c / D) or ceil(w_c / D) times
+    (one fewer at most for the last weighted circuit, whose interval reaches
+    past the last pointer), pointers ascend so parents come in index order,
+    and the weights clamp F to [0, 1] (F <= 0 is never drawn)."""
+    P, L, G = 200, 3, 19
+    rng = np.random.default_rng(11)
+    for gen in range(5):
+        p = oracle.make_problem(3, L, P, NCV | ID, W.cknot(3), seed=gen)
+        genome = np.repeat(np.arange(P, dtype=np.uint8)[:, None], L, axis=1)
+        F = rng.uniform(-0.3, 1.3, P)
+        F[:3] = [-1.0, 2.0, 0.0]
+        cost = np.zeros(P, np.uint32)
+        out = oracle.ga_next(p, G, gen, 0.0, genome, F, cost)
+        assert out[0].tolist() == genome[1].tolist()  # elite: F = 2.0
+        parents = out[1:, 0].astype(np.int64)  # column 0 precedes every cut
+        assert np.all(np.diff(parents) >= 0)
+        w = [int(np.floor(min(max(f, 0.0), 1.0) * 2.0**32)) for f in F]
+        assert w[1] == 2**32 and w[0] == w[2] == 0
+        D = sum(w) // P
+        cum = np.cumsum(w)
+        last = max(c for c in range(P) if w[c])
+        cnt = np.bincount(parents, minlength=P)
+        assert all(cnt[c] == 0 for c in range(P) if w[c] == 0)
+
+        def ok(counts):
+            for c in range(P):
+                lo = w[c] // D - (1 if c == last else 0)
+                hi = -(-w[c] // D)
+                if not (lo <= counts[c] <= hi):
+                    return False
+            return True
+
+        # child 0's SUS parent (overwritten by the elite) is the first c with
+        # cum[c] > s, s in [0, D): one of the circuits whose interval starts below D
+        cands = [c for c in range(P) if w[c] and (c == 0 or cum[c - 1] < D)]
+        assert any(ok(cnt + np.eye(P, dtype=np.int64)[c]) for c in cands)
+
+
+def test_ga_sus_pointer_on_a_boundary_takes_the_next_circuit():
+    """Weights of 1 each (F = 2^-32): W = P, D = 1, the offset s = floor(r D / 2^64)
+    is 0, pointer m = m sits on the boundary cum[m-1] = m, and SUS, which picks
+    the circuit whose half-open interval [cum[c-1], cum[c]) holds the pointer,
+    draws parent m for child m."""
+    P, L, G = 40, 2, 19
+    p = oracle.make_problem(3, L, P, NCV | ID, W.cknot(3), seed=4)
+    genome = np.repeat(np.arange(P, dtype=np.uint8)[:, None], L, axis=1)
+    F = np.full(P, 2.0**-32)
+    out = oracle.ga_next(p, G, 0, 0.0, genome, F, np.zeros(P, np.uint32))
+    assert out[1:, 0].tolist() == list(range(1, P))
+
+
+def test_ga_sus_offset_is_uniform():
+    """Weights (0.1, 0.4, 0.1, 0.4) of W = 2^32 with P = 4: pointers s, s + 1/4,
+    s + 1/2, s + 3/4 (units of W), so child 2's parent is circuit 2 exactly when
+    s < 0.1 W, with probability 0.4 over a uniform s in [0, W/4)."""
+    P, L, G = 4, 2, 19
+    p = oracle.make_problem(3, L, P, NCV | ID, W.cknot(3), seed=8)
+    genome = np.repeat(np.arange(P, dtype=np.uint8)[:, None], L, axis=1)
+    F = np.array([0.1, 0.4, 0.1, 0.4])
+    hits, n = 0, 600
+    for gen in range(n):
+        out = oracle.ga_next(p, G, gen, 0.0, genome, F, np.zeros(P, np.uint32))
+        assert out[1, 0] == 1 and out[3, 0] == 3
+        hits += out[2, 0] == 2
+    assert abs(hits / n - 0.4) < 4 * np.sqrt(0.24 / n)
 
 
 def test_ga_crossover_is_one_point_and_mutation_rate():
