@@ -203,6 +203,9 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             flush.zero_()
 
+    # launch plan picked by timing real generations (results do not depend on it)
+    tune_ms = ctx.autotune(3)
+    plan = ctx.launch_plan()
     for _ in range(args.warmup):
         ctx.step(1)
     # ---- timed region: K generations, L2 flushed before each
@@ -250,7 +253,11 @@ def run_ours(args):
     # interval around it inside the generation graph
     pk = peaks()
     last = [ctx.last_generation(r) for r in range(len(searches))]
-    roof = roofline("circuits", stage["circuits"], searches, last, pk,
+    # useful flops of one more generation, counted by the library from the
+    # sampled gates (qe_report.useful_flops); the gate mix drifts slowly
+    reps = ctx.step(1)
+    flops = sum(r["useful_flops"] for r in reps)
+    roof = roofline("circuits", stage["circuits"], flops, searches, pk,
                     traffic=TRAFFIC.get((args.config, args.population)))
 
     # ---- end to end through the public API with host buffers
@@ -270,6 +277,7 @@ def run_ours(args):
                                      "one generation behind",
                        "circuits_per_step": n_circ, "parallelism": "replica per GPU",
                        "l2": "flushed (256 MB write) before every timed step",
+                       "launch_plan": plan, "autotune_ms_per_plan": [round(m, 5) for m in tune_ms],
                        "stage_ms": {k: round(v, 5) for k, v in stage.items()}},
             "roofline": roof,
             "e2e": e2e,
@@ -293,21 +301,20 @@ def run_ours(args):
 TRAFFIC = {(2, None): 41.325e6}
 
 
-def roofline(dom, ms, searches, last, pk, traffic=None):
+def roofline(dom, ms, flops, searches, pk, traffic=None):
     """Achieved algorithmic rate of the dominant kernel against its roofline."""
     hbm = pk.get("hbm_gbs")
     sm_max = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
     if dom == "circuits":
-        # useful flops of the generation (gate-count model), counted exactly
-        flops = sum(gen_flops(s, l) for s, l in zip(searches, last))
+        # useful flops of a generation (gate-count model)
         ach = flops / (ms / 1e3) / 1e12
         return {"kernel": "k_step (sample + compose + score + scatter)", "bound": "alu",
                 "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
                 "traffic": traffic, "algorithmic_flops": flops, "ms": ms,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % sm_max}
     if dom == "update":
-        b = update_bytes(searches, last)
+        b = flops  # algorithmic bytes of the update (update_bytes)
         ach = b / (ms / 1e3) / 1e9
         return {"kernel": "k_update (elitism + mutation)", "bound": "hbm", "achieved": ach,
                 "peak": hbm, "unit": "GB/s", "frac": ach / hbm if hbm else None, "traffic": None,
@@ -327,12 +334,6 @@ def launches_per_generation(searches):
     groups = len(set((s.n, s.precision == 0) for s in searches))
     widths = len(set(s.n for s in searches if s.precision != 0))
     return groups + 2 + 1 + widths + 1 + 1
-
-
-def gen_flops(s, last):
-    import oracle
-    g = last["gate_idx"]
-    return sum(oracle.useful_flops(s.n, s.library, row) for row in g)
 
 
 def update_bytes(searches, last):
@@ -384,44 +385,101 @@ def end_to_end(qe, ctx_unused, searches, last, steps):
             "call": "qe_eval_host (binary32 eval + binary64 top-k) per search, pinned host buffers"}
 
 
-def per_config(qe, torch, args):
-    """Circuit-kernel rate (sample + compose + score) and generation rate at
-    n = 3, 4, 5, binary32 vs plain binary64, a few generations each, from the
-    events inside the generation graph (context next to the headline)."""
+def _stage_rates(qe, torch, searches, gens):
+    """Mean stage times of `gens` generations after one warm-up generation
+    (binary32 searches first pick their launch plan with the autotuner)."""
     import numpy as np
+    from paper_1809_11134_gb300 import workloads as W
+    stream = torch.cuda.Stream()
+    ctx = qe.Context(searches, stream=stream)
+    if searches[0].precision != W.PREC_FP64:
+        ctx.autotune(2)
+    ctx.step(1)
+    ctx.stage_timing(True)
+    times = []
+    for _ in range(gens):
+        ctx.step_raw(1, None)
+        times.append(ctx.stage_times())
+    ctx.stage_timing(False)
+    reps = ctx.step(1)
+    t = np.array(times).mean(axis=0)
+    n = sum(s.P for s in searches)
+    flops = sum(r["useful_flops"] for r in reps)
+    res = {"circuit_kernel_circuits_per_s": n / (t[0] / 1e3),
+           "generation_circuits_per_s": n / (t[5] / 1e3),
+           "circuit_kernel_ms": round(float(t[0]), 4), "generation_ms": round(float(t[5]), 4),
+           "circuit_kernel_useful_tflops": flops / (t[0] / 1e3) / 1e12,
+           "launch_plan": ctx.launch_plan()}
+    return ctx, res
+
+
+def _fp32_error(qe, torch, ctx32, searches, n_unitary=256):
+    """Max |F32 - F64| over the last binary32 generation's circuits and max
+    elementwise |U32 - U64| over the first n_unitary of them; the binary64
+    values come from the library's binary64 path, which the parity tests hold
+    bit-exact with the oracle."""
+    import numpy as np
+    from paper_1809_11134_gb300 import workloads as W
+    s64 = [W.Search(**{**s.__dict__, "precision": W.PREC_FP64}) for s in searches]
+    ctx64 = qe.Context(s64)
+    f_err, u_err = 0.0, 0.0
+    for r, s in enumerate(searches):
+        last = ctx32.last_generation(r)
+        g = torch.from_numpy(np.ascontiguousarray(last["gate_idx"])).cuda()
+        f64 = torch.zeros(s.P, dtype=torch.float64, device="cuda")
+        ctx64.eval(r, g, f64)
+        f_err = max(f_err, float(np.abs(last["fitness"] - f64.cpu().numpy()).max()))
+        m = min(n_unitary, s.P)
+        N = 1 << s.n
+        u32 = torch.zeros(m * N * N * 2, dtype=torch.float32, device="cuda")
+        u64 = torch.zeros(m * N * N * 2, dtype=torch.float64, device="cuda")
+        ctx32.compose(r, g[:m], u32, n_circuits=m)
+        ctx64.compose(r, g[:m], u64, n_circuits=m)
+        u_err = max(u_err, float((u32.double() - u64).abs().max().item()))
+    ctx64.close()
+    return f_err, u_err
+
+
+def per_config(qe, torch, args):
+    """Per benchmark search set: circuit-kernel rate (sample + compose + score)
+    and generation rate, binary32 vs plain binary64, from the events inside the
+    generation graph, with the binary32 path's largest error against binary64;
+    the 1024 uneven searches (binary32); and the GA run of the 5-qubit search on
+    the same evaluation (context next to the headline)."""
     from paper_1809_11134_gb300 import workloads as W
     out = {}
     for cfg, gens32, gens64 in ((2, 20, 5), (3, 6, 2), (5, 4, 1)):
         res = {}
         for prec, gens in ((W.PREC_FP32, gens32), (W.PREC_FP64, gens64)):
             searches = W.config(cfg, precision=prec)
-            stream = torch.cuda.Stream()
-            ctx = qe.Context(searches, stream=stream)
-            ctx.step(1)
-            ctx.stage_timing(True)
-            times = []
-            for _ in range(gens):
-                ctx.step_raw(1, None)
-                times.append(ctx.stage_times())
+            ctx, r = _stage_rates(qe, torch, searches, gens)
+            if prec == W.PREC_FP32:
+                r["max_abs_fitness_err_vs_fp64"], r["max_abs_unitary_err_vs_fp64"] = \
+                    _fp32_error(qe, torch, ctx, searches)
             ctx.close()
-            t = np.array(times).mean(axis=0)
-            n = sum(s.P for s in searches)
-            res["fp32" if prec else "fp64"] = {
-                "circuit_kernel_circuits_per_s": n / (t[0] / 1e3),
-                "generation_circuits_per_s": n / (t[5] / 1e3),
-                "circuit_kernel_ms": round(float(t[0]), 4), "generation_ms": round(float(t[5]), 4)}
+            res["fp32" if prec else "fp64"] = r
         res["fp32_over_fp64_circuit_kernel"] = (res["fp32"]["circuit_kernel_circuits_per_s"] /
                                                 res["fp64"]["circuit_kernel_circuits_per_s"])
         res["fp32_over_fp64_generation"] = (res["fp32"]["generation_circuits_per_s"] /
                                             res["fp64"]["generation_circuits_per_s"])
         out["config%d" % cfg] = res
+    searches = W.config(4)
+    ctx, r = _stage_rates(qe, torch, searches, 3)
+    ctx.close()
+    r["searches"] = len(searches)
+    r["circuits_per_generation"] = sum(s.P for s in searches)
+    out["config4"] = {"fp32": r}
+    searches = W.config(5, encoding=W.ENC_GA)
+    ctx, r = _stage_rates(qe, torch, searches, 4)
+    ctx.close()
+    out["config5_ga"] = {"fp32": r}
     return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")

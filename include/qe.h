@@ -195,6 +195,24 @@ qe_status qe_update(qe_ctx *ctx, uint32_t prob, uint32_t gen, const uint32_t *d_
  * NULL it only enqueues the generations on the stream and returns. */
 qe_status qe_step(qe_ctx *ctx, uint32_t n_gen, qe_report *h_reports);
 
+/* Launch-plan autotuner.  A generation graph can be launched in several ways
+ * that give bit-identical results: with or without a launch-completion edge
+ * that lets the previous generation's ranking selection start before the
+ * circuit kernels fill the GPU, and with the circuit kernels' persistent grid
+ * at the resident block count, one block per SM less (room for the ranking
+ * chain), or one warp per circuit in a single wave.  qe_autotune runs
+ * 1 + gens_per_plan (1..64) generations of every search with each plan (up to
+ * six), times the last gens_per_plan on the stream with CUDA events, and keeps
+ * the fastest for every later qe_step.  These are real generations: they
+ * advance the searches exactly as qe_step would (qe_generation counts them).
+ * With n_plans != NULL, h_ms receives up to *n_plans mean generation times (ms,
+ * in plan order: with the edge, then without; grids in the order above) and
+ * *n_plans the number of plans tried.  Synchronises.  QE_ESTATE while stage
+ * timing is on. */
+qe_status qe_autotune(qe_ctx *ctx, uint32_t gens_per_plan, float *h_ms, uint32_t *n_plans);
+/* The launch plan in use, as text (NUL-terminated, truncated to len). */
+qe_status qe_launch_plan(const qe_ctx *ctx, char *h_buf, size_t len);
+
 /* Stage timing.  qe_stage_timing(ctx, 1) rebuilds the generation graph with
  * CUDA events recorded between its kernels (on the stream each kernel runs
  * on); qe_stage_times then gives, for the last generation run, ms[0] circuit

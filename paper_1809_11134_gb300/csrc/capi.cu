@@ -29,6 +29,13 @@ struct Group {
 
 }  // namespace
 
+// How a generation graph is launched; results do not depend on it.
+struct Plan {
+  bool select_first = true;  // launch-completion edge: ranking selection -> circuits
+  uint32_t grid_mode = 0;    // circuit kernels: 0 resident blocks, 1 one block less per SM,
+                             // 2 one warp per circuit in a single launch wave
+};
+
 struct qe_ctx {
   int device = 0;
   cudaStream_t user = nullptr;
@@ -59,6 +66,10 @@ struct qe_ctx {
   void *d_stage_fit = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // launch plan of the generation graph (qe_autotune picks it by timing)
+  Plan plan;
+  bool tuned = false;
+  std::string plan_text;
   cudaGraph_t dgraph = nullptr;      // ranking of the last generation alone (drain)
   cudaGraphExec_t dexec = nullptr;
   bool pending_rank = false;         // the last generation is not ranked yet
@@ -258,6 +269,62 @@ qe_status set_priorities(qe_ctx *ctx, cudaGraph_t graph) {
   return QE_OK;
 }
 
+// Let the first circuit kernel of a generation start only once every block of
+// the previous generation's selection kernel is resident (a launch-completion
+// edge: the circuit kernel does not wait for the selection to finish).  Without
+// it the circuit kernel's persistent grid fills every SM first and the ranking
+// chain, the longer of the two concurrent paths, starts only as its blocks
+// retire.  Skipped when the selection has more blocks than the GPU holds at
+// once (many searches), where waiting for all of them to start would delay the
+// circuits instead.
+qe_status add_select_first_edge(qe_ctx *ctx, cudaGraph_t graph) {
+  if (ctx->n_jobs > 2 * ctx->lc.num_sms) return QE_OK;  // see above
+  size_t nn = 0;
+  QE_CUDA(ctx, cudaGraphGetNodes(graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  QE_CUDA(ctx, cudaGraphGetNodes(graph, nodes.data(), &nn));
+  auto circuit_node = [&](cudaGraphNode_t nd, bool &yes) -> qe_status {
+    cudaGraphNodeType ty;
+    QE_CUDA(ctx, cudaGraphNodeGetType(nd, &ty));
+    yes = false;
+    if (ty != cudaGraphNodeTypeKernel) return QE_OK;
+    cudaKernelNodeParams kp;
+    QE_CUDA(ctx, cudaGraphKernelNodeGetParams(nd, &kp));
+    yes = is_circuit_kernel(kp.func);
+    return QE_OK;
+  };
+  cudaGraphNode_t sel = nullptr, first = nullptr;
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    QE_CUDA(ctx, cudaGraphNodeGetType(nd, &ty));
+    if (ty != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp;
+    QE_CUDA(ctx, cudaGraphKernelNodeGetParams(nd, &kp));
+    if (is_select_kernel(kp.func)) sel = nd;
+    if (!is_circuit_kernel(kp.func)) continue;
+    // the group launched first: no circuit kernel before it
+    size_t nd_deps = 0;
+    QE_CUDA(ctx, cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &nd_deps));
+    std::vector<cudaGraphNode_t> deps(nd_deps);
+    if (nd_deps) QE_CUDA(ctx, cudaGraphNodeGetDependencies(nd, deps.data(), nullptr, &nd_deps));
+    bool after_circuit = false;
+    for (auto dp : deps) {
+      bool yes = false;
+      qe_status st = circuit_node(dp, yes);
+      if (st != QE_OK) return st;
+      after_circuit = after_circuit || yes;
+    }
+    if (!after_circuit) first = nd;
+  }
+  if (!sel || !first) return QE_OK;
+  cudaGraphEdgeData ed;
+  memset(&ed, 0, sizeof ed);
+  ed.from_port = cudaGraphKernelNodePortLaunchCompletion;
+  ed.type = cudaGraphDependencyTypeProgrammatic;
+  QE_CUDA(ctx, cudaGraphAddDependencies(graph, &sel, &first, &ed, 1));
+  return QE_OK;
+}
+
 // the ranking chain of generation *gen - 1 (select -> binary64 rescoring -> sort)
 cudaError_t enqueue_rank_chain(qe_ctx *ctx, cudaStream_t cs) {
   RankJob none{};
@@ -276,8 +343,11 @@ cudaError_t enqueue_rank_chain(qe_ctx *ctx, cudaStream_t cs) {
 // Stage events (when timing): 0 start; 1 after the circuit kernels; 2 after
 // the selection, 3 after the rescoring, 4 after the sort (ranking of g - 1);
 // 5 before and 6 after the update; 7 end of the generation.
-qe_status build_graph(qe_ctx *ctx) {
+qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
+                          cudaGraphExec_t *out_exec) {
   cudaStream_t cs = ctx->cap;
+  LaunchCfg lc = ctx->lc;
+  lc.grid_mode = plan.grid_mode;
   QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   auto mark = [&](int k, cudaStream_t st) {
@@ -290,7 +360,7 @@ qe_status build_graph(qe_ctx *ctx) {
   // generation g: circuits, then the two update roles
   for (auto &gr : ctx->groups) {
     if (e == cudaSuccess)
-      e = launch_step(ctx->lc, gr.n, ctx->d_probs, gr.d_ids, gr.d_prefix,
+      e = launch_step(lc, gr.n, ctx->d_probs, gr.d_ids, gr.d_prefix,
                       (uint32_t)gr.ids.size(), gr.total, gr.canon, ctx->g, ctx->side);
   }
   mark(1, ctx->side);
@@ -331,16 +401,42 @@ qe_status build_graph(qe_ctx *ctx) {
     return cuda_fail(ctx, e, "capturing the generation graph");
   }
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
-  ctx->graph = graph;
   qe_status st = set_priorities(ctx, graph);
+  if (st == QE_OK && plan.select_first) st = add_select_first_edge(ctx, graph);
+  if (st != QE_OK) {
+    cudaGraphDestroy(graph);
+    return st;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiateWithFlags(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return cuda_fail(ctx, e, "cudaGraphInstantiateWithFlags");
+  }
+  *out_graph = graph;
+  *out_exec = exec;
+  return QE_OK;
+}
+
+std::string plan_string(const Plan &p) {
+  static const char *modes[3] = {"resident blocks", "resident blocks - 1 per SM",
+                                 "one warp per circuit"};
+  return std::string("selection before circuits: ") + (p.select_first ? "yes" : "no") +
+         "; circuit grid: " + modes[p.grid_mode < 3 ? p.grid_mode : 0];
+}
+
+qe_status build_graph(qe_ctx *ctx) {
+  qe_status st = build_gen_graph(ctx, ctx->plan, &ctx->graph, &ctx->gexec);
   if (st != QE_OK) return st;
-  QE_CUDA(ctx, cudaGraphInstantiate(&ctx->gexec, graph, 0));
+  if (ctx->plan_text.empty()) ctx->plan_text = plan_string(ctx->plan) + " (default)";
+  if (ctx->dexec) return QE_OK;
   // drain graph: the ranking chain alone, then a clean rescore queue
+  cudaStream_t cs = ctx->cap;
   QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  e = enqueue_rank_chain(ctx, cs);
+  cudaError_t e = enqueue_rank_chain(ctx, cs);
   if (e == cudaSuccess) e = launch_reset_counter(ctx->g, cs);
-  graph = nullptr;
-  e2 = cudaStreamEndCapture(cs, &graph);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
   if (e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     return cuda_fail(ctx, e, "capturing the ranking graph");
@@ -847,6 +943,104 @@ qe_status qe_step(qe_ctx *ctx, uint32_t n_gen, qe_report *h_reports) {
     memcpy(r.best_gates, b.best_gates, 64);
   }
   if (errw) return fail(ctx, QE_ENUMERIC, "a search reported an invalid gate or non-finite fitness");
+  return QE_OK;
+}
+
+qe_status qe_autotune(qe_ctx *ctx, uint32_t gens_per_plan, float *h_ms, uint32_t *n_plans) {
+  if (!ctx) return fail(nullptr, QE_EINVAL, "null context");
+  if (ctx->poisoned) return fail(ctx, QE_ESTATE, "context is poisoned by an earlier CUDA error");
+  if (ctx->timing) return fail(ctx, QE_ESTATE, "qe_autotune needs stage timing off");
+  if (gens_per_plan < 1 || gens_per_plan > 64)
+    return fail(ctx, QE_EINVAL, "gens_per_plan must be 1..64");
+  if (!ctx->gexec) {
+    qe_status st = build_graph(ctx);  // also the drain graph
+    if (st != QE_OK) return st;
+  }
+  // candidate plans: with and without the selection-first edge, three grids
+  // (the middle one only where some circuit kernel keeps several blocks per SM)
+  bool several = false;
+  for (auto &gr : ctx->groups)
+    several = several || (gr.canon ? ctx->lc.step64[gr.n] : ctx->lc.step32[gr.n]) > 1;
+  std::vector<Plan> cands;
+  for (int sf = 1; sf >= 0; --sf)
+    for (uint32_t gm = 0; gm < 3; ++gm) {
+      if (gm == 1 && !several) continue;
+      Plan p;
+      p.select_first = sf == 1;
+      p.grid_mode = gm;
+      cands.push_back(p);
+    }
+  const size_t C = cands.size();
+  std::vector<cudaGraph_t> graphs(C, nullptr);
+  std::vector<cudaGraphExec_t> execs(C, nullptr);
+  std::vector<cudaEvent_t> ev(2 * C, nullptr);
+  auto cleanup = [&](size_t keep) {
+    for (size_t i = 0; i < C; ++i) {
+      if (i == keep) continue;
+      if (execs[i]) cudaGraphExecDestroy(execs[i]);
+      if (graphs[i]) cudaGraphDestroy(graphs[i]);
+    }
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  qe_status st = QE_OK;
+  cudaError_t e = cudaSuccess;
+  uint32_t launched = 0;
+  // every candidate runs real generations: one to settle, then gens_per_plan timed
+  for (size_t i = 0; i < C && st == QE_OK && e == cudaSuccess; ++i) {
+    st = build_gen_graph(ctx, cands[i], &graphs[i], &execs[i]);
+    if (st != QE_OK) break;
+    e = cudaEventCreate(&ev[2 * i]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[2 * i + 1]);
+    if (e == cudaSuccess) e = cudaGraphLaunch(execs[i], ctx->user);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i], ctx->user);
+    for (uint32_t k = 0; k < gens_per_plan && e == cudaSuccess; ++k)
+      e = cudaGraphLaunch(execs[i], ctx->user);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i + 1], ctx->user);
+    if (e == cudaSuccess) launched += 1 + gens_per_plan;
+  }
+  if (e == cudaSuccess && st == QE_OK) e = cudaStreamSynchronize(ctx->user);
+  ctx->gen += launched;
+  if (launched) ctx->pending_rank = true;
+  if (st != QE_OK || e != cudaSuccess) {
+    cleanup(C);
+    return st != QE_OK ? st : cuda_fail(ctx, e, "autotuning the generation graph");
+  }
+  std::vector<float> ms(C, 0.f);
+  size_t best = 0;
+  for (size_t i = 0; i < C; ++i) {
+    e = cudaEventElapsedTime(&ms[i], ev[2 * i], ev[2 * i + 1]);
+    if (e != cudaSuccess) {
+      cleanup(C);
+      return cuda_fail(ctx, e, "cudaEventElapsedTime");
+    }
+    ms[i] /= (float)gens_per_plan;
+    if (ms[i] < ms[best]) best = i;
+  }
+  cleanup(best);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->graph = graphs[best];
+  ctx->gexec = execs[best];
+  ctx->plan = cands[best];
+  ctx->tuned = true;
+  char b[96];
+  snprintf(b, sizeof b, " (autotuned: %.4f ms per generation; %zu plans tried)", ms[best], C);
+  ctx->plan_text = plan_string(ctx->plan) + b;
+  if (n_plans) {
+    const uint32_t cap = *n_plans;
+    if (h_ms)
+      for (size_t i = 0; i < C && i < cap; ++i) h_ms[i] = ms[i];
+    *n_plans = (uint32_t)C;
+  }
+  return QE_OK;
+}
+
+qe_status qe_launch_plan(const qe_ctx *ctx, char *h_buf, size_t len) {
+  if (!ctx || !h_buf || !len) return QE_EINVAL;
+  const std::string t = ctx->plan_text.empty() ? plan_string(ctx->plan) + " (default)"
+                                               : ctx->plan_text;
+  snprintf(h_buf, len, "%s", t.c_str());
   return QE_OK;
 }
 

@@ -728,7 +728,9 @@ cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs
                         const uint32_t *group, const uint32_t *prefix, uint32_t n_group,
                         uint32_t total, bool canon, const DevGlobal &g, cudaStream_t st) {
   if (total == 0) return cudaSuccess;
-  const uint32_t per = canon ? lc.step64[n] : lc.step32[n];
+  uint32_t per = canon ? lc.step64[n] : lc.step32[n];
+  if (lc.grid_mode == 1 && per > 1) per -= 1;
+  if (lc.grid_mode == 2) per = 0xffffu;  // every circuit's warp in one launch
   const uint32_t blocks = grid_for(lc, total, per);
 #define QE_L(NQ)                                                                               \
   if (canon)                                                                                   \

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *
   uint32_t *s_hi = s_lo + kKeyCache;        // kKeyCache high keys
   __shared__ uint32_t s_wsum[64];
   __shared__ uint32_t s_bin, s_rem, s_cnt, s_base;
-  __shared__ float s_sum[kRankThreads / 32];
+  __shared__ double s_sum[kRankThreads / 32];
   __shared__ unsigned long long s_work[kRankThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const bool cached = n <= (uint32_t)kKeyCache;
@@ -138,15 +138,16 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *
   // histogram of the top 12 bits of the low keys, the mean and the work.
   // Histogram updates are aggregated per warp (__match_any_sync): fitness
   // values are often discrete, and many lanes hit the same bin.
-  float sum = 0.f;
+  double sum = 0.0;  // mean fitness: binary64 sum of the working-precision values
   unsigned long long work = 0;
   for (uint32_t c0 = 0; c0 < n; c0 += kRankThreads) {
     const uint32_t c = c0 + tid;
     uint32_t bin = 4096u;
     if (c < n) {
-      const float F = p.prec == 0 ? (float)((const double *)jb.fit)[c] : ((const float *)jb.fit)[c];
+      const double Fw = p.prec == 0 ? ((const double *)jb.fit)[c] : (double)((const float *)jb.fit)[c];
+      const float F = (float)Fw;
       const uint32_t meta = jb.meta[c];
-      sum += F;
+      sum += Fw;
       work += meta >> 8;
       uint32_t lo, hi;
       bounds(p, jb, c, F, lo, hi);
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *
   }
   __syncthreads();
   if (jb.update_record && wid == 0) {
-    double t = (double)s_sum[lane];
+    double t = s_sum[lane];
     unsigned long long wt = s_work[lane];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -453,6 +454,8 @@ cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint3
   k_rank_sort<<<n_jobs, kSortThreads, 0, st>>>(probs, jobs, single, g);
   return cudaGetLastError();
 }
+
+bool is_select_kernel(const void *f) { return f == (const void *)k_rank_select; }
 
 cudaError_t rank_init() {
   return cudaFuncSetAttribute(k_rank_select, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -13,6 +13,9 @@ struct LaunchCfg {
   // resident 256-thread blocks per SM of the circuit kernels, by qubit count
   uint32_t step32[6] = {1, 1, 1, 1, 1, 1};
   uint32_t step64[6] = {1, 1, 1, 1, 1, 1};
+  // generation circuit kernels: 0 = resident blocks, 1 = one block less per SM
+  // (room for a concurrent ranking chain), 2 = one warp per circuit, one wave
+  uint32_t grid_mode = 0;
 };
 
 // persistent grid: at most the resident blocks of the whole GPU, fewer if
@@ -80,6 +83,7 @@ cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const ui
 // k_rank.cu
 cudaError_t rank_init();  // once per device before the first ranking launch
 // jobs == NULL: one job given by value in `single`
+bool is_select_kernel(const void *f);  // the ranking's selection kernel (graph edges)
 cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
                                const RankJob &single, const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,

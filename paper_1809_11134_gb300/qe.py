@@ -28,7 +28,8 @@ QE_ERRW_BAD_GATE, QE_ERRW_NONFINITE = 1, 2
 # every symbol include/qe.h declares
 EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_host", "qe_compose",
            "qe_update", "qe_step", "qe_last_generation", "qe_state_bytes", "qe_get_state",
-           "qe_set_state", "qe_generation", "qe_stage_timing", "qe_stage_times",
+           "qe_set_state", "qe_generation", "qe_autotune", "qe_launch_plan", "qe_stage_timing",
+           "qe_stage_times",
            "qe_eval_rank_static", "qe_last_error", "qe_destroy"]
 
 
@@ -84,6 +85,8 @@ def lib():
         L.qe_get_state.argtypes = [vp, u32, vp, sz]
         L.qe_set_state.argtypes = [vp, u32, vp, sz]
         L.qe_generation.argtypes = [vp, C.POINTER(u32)]
+        L.qe_autotune.argtypes = [vp, u32, C.POINTER(C.c_float), C.POINTER(u32)]
+        L.qe_launch_plan.argtypes = [vp, C.c_char_p, sz]
         L.qe_stage_timing.argtypes = [vp, C.c_int]
         L.qe_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
         L.qe_eval_rank_static.argtypes = [C.POINTER(qe_problem), vp, u32, vp, vp, vp,
@@ -309,6 +312,19 @@ class Context:
                                   np.ascontiguousarray(best, np.float32).view(np.uint8).ravel(),
                                   np.ascontiguousarray(best_f, np.float32).view(np.uint8).ravel()])
         _check(self.h, lib().qe_set_state(self.h, prob, buf.ctypes.data_as(C.c_void_p), buf.size))
+
+    def autotune(self, gens_per_plan=2):
+        """qe_autotune: time every launch plan on real generations, keep the
+        fastest; returns the mean generation time (ms) of each plan tried."""
+        ms = (C.c_float * 8)()
+        n = C.c_uint32(8)
+        _check(self.h, lib().qe_autotune(self.h, gens_per_plan, ms, C.byref(n)))
+        return list(ms[:n.value])
+
+    def launch_plan(self):
+        b = C.create_string_buffer(256)
+        _check(self.h, lib().qe_launch_plan(self.h, b, 256))
+        return b.value.decode()
 
     def stage_timing(self, enable=True):
         _check(self.h, lib().qe_stage_timing(self.h, 1 if enable else 0))

@@ -256,7 +256,8 @@ def _oracle_run(searches, gens):
         hist = []
         for gen in range(gens):
             gi, sid, F, cost, tk = oracle.step(p, cur, best, bf, gen, max(s.topk, 1), rep)
-            hist.append((gi, sid, F, tk, rep.best_fitness, rep.best_cost, bytes(rep.best_gates)))
+            hist.append((gi, sid, F, tk, rep.best_fitness, rep.best_cost, bytes(rep.best_gates),
+                         rep.useful_flops, rep.mean_fitness))
         out.append((hist, cur, best, bf))
     return out
 
@@ -269,7 +270,7 @@ def test_step_trajectory_fp64_bit_exact(qe, torch, cfg, P, gens):
         for gen in range(gens):
             reps = ctx.step(1)
             for run, s in enumerate(searches):
-                gi, sid, F, tk, bfit, bcost, bgates = ref[run][0][gen]
+                gi, sid, F, tk, bfit, bcost, bgates, flops, mean = ref[run][0][gen]
                 last = ctx.last_generation(run)
                 assert np.array_equal(last["gate_idx"], gi)
                 assert np.array_equal(last["seg_id"], sid)
@@ -280,6 +281,8 @@ def test_step_trajectory_fp64_bit_exact(qe, torch, cfg, P, gens):
                 assert r["generation"] == gen + 1
                 assert r["best_fitness"] == bfit and r["best_cost"] == bcost
                 assert bytes(r["best_gates"]) == bgates[:s.L]
+                assert r["useful_flops"] == flops
+                assert abs(r["mean_fitness"] - mean) <= 1e-12
         for run in range(len(searches)):
             c, b, bf = ctx.get_state(run)
             assert state_equal(c, ref[run][1]) and state_equal(b, ref[run][2])
@@ -298,7 +301,7 @@ def test_pipelined_generations_fp64_bit_exact(qe, torch, calls):
             ctx.step_raw(n, None)
         reps = ctx.step(calls[-1])
         for run, s in enumerate(searches):
-            gi, sid, F, tk, bfit, bcost, bgates = ref[run][0][gens - 1]
+            gi, sid, F, tk, bfit, bcost, bgates, flops, mean = ref[run][0][gens - 1]
             last = ctx.last_generation(run)
             assert np.array_equal(last["gate_idx"], gi) and np.array_equal(last["fitness"], F)
             assert [t[0] for t in last["topk"]] == list(tk[:s.topk])
