@@ -175,6 +175,32 @@ def cpu_baseline(seconds=10.0):
                       "dense binary64 compose/score, full sort, update; %.1f s" % (gen, dt)}
 
 
+def replica_searches(W, config, population, rank):
+    """The searches one rank runs: the benchmark set, seeds offset by rank so
+    that every GPU runs an independent replica (weak scaling, no data-path
+    collective)."""
+    searches = W.config(config, P=population)
+    for s in searches:
+        s.seed = s.seed + 1000 * rank
+    return searches
+
+
+def max_over_ranks(total_ms, ws, device):
+    """The timed region's length is the slowest rank's (all_reduce MAX)."""
+    if ws <= 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(n_circ_per_rank, steps, ws, total_ms):
+    """Candidate circuits of all ranks per second of the slowest rank."""
+    return ws * n_circ_per_rank * steps / (total_ms / 1e3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -190,10 +216,7 @@ def run_ours(args):
     from paper_1809_11134_gb300 import qe
     from paper_1809_11134_gb300 import workloads as W
 
-    searches = W.config(args.config, P=args.population)
-    if rank:
-        for s in searches:
-            s.seed = s.seed + 1000 * rank  # independent replica per rank
+    searches = replica_searches(W, args.config, args.population, rank)
     n_circ = sum(s.P for s in searches)
     stream = torch.cuda.Stream()
     ctx = qe.Context(searches, stream=stream)
@@ -225,13 +248,10 @@ def run_ours(args):
         wall = time.perf_counter() - t0
     torch.cuda.synchronize()
     step_ms = [starts[k].elapsed_time(ends[k]) for k in range(args.steps)]
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), ws, "cuda")
     if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    value = ws * n_circ * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(n_circ, args.steps, ws, total_ms)
     clocks = clk.summary()
 
     # ---- per-stage times inside the generation graph (events between kernels)
@@ -252,6 +272,7 @@ def run_ours(args):
     # launch list (profiles/launches_3qubit_bench.md); its time is the event
     # interval around it inside the generation graph
     pk = peaks()
+    alu32, alu64 = qe.measure_alu_peaks()
     last = [ctx.last_generation(r) for r in range(len(searches))]
     # useful flops of one more generation, counted by the library from the
     # sampled gates (qe_report.useful_flops); the gate mix drifts slowly
@@ -259,6 +280,19 @@ def run_ours(args):
     flops = sum(r["useful_flops"] for r in reps)
     roof = roofline("circuits", stage["circuits"], flops, searches, pk,
                     traffic=TRAFFIC.get((args.config, args.population)))
+    ub = update_bytes(searches, last)
+    kernels = [
+        {"kernel": "k_step (sample + compose + score + scatter)", "bound": "alu",
+         "achieved_tflops": roof["achieved"], "frac_of_derived_fp32": roof["frac"],
+         "frac_of_measured_fp32": roof["achieved"] / alu32},
+        {"kernel": "k_update_elite + k_update_mutate", "bound": "hbm",
+         "achieved_gbs": ub / (stage["update"] / 1e3) / 1e9,
+         "frac_of_measured_hbm": ub / (stage["update"] / 1e3) / 1e9 / pk["hbm_gbs"]
+         if pk.get("hbm_gbs") else None, "algorithmic_bytes": ub},
+        {"kernel": "k_rank_select", "bound": "hbm",
+         "achieved_gbs": n_circ * 8 / (stage["rank_select"] / 1e3) / 1e9,
+         "note": "reads each fitness and cost word once; one CTA per search, latency-bound"},
+    ]
 
     # ---- end to end through the public API with host buffers
     e2e = end_to_end(qe, ctx, searches, last, args.steps)
@@ -280,6 +314,9 @@ def run_ours(args):
                        "launch_plan": plan, "autotune_ms_per_plan": [round(m, 5) for m in tune_ms],
                        "stage_ms": {k: round(v, 5) for k, v in stage.items()}},
             "roofline": roof,
+            "kernel_rooflines": kernels,
+            "alu_peaks_measured_tflops": {"fp32": alu32, "fp64": alu64,
+                                          "how": "qe_measure_alu_peaks: FMA chains on every SM"},
             "e2e": e2e,
             "gpu_launches": launches_per_generation(searches) * args.steps,
             "clocks": clocks,
@@ -405,11 +442,22 @@ def _stage_rates(qe, torch, searches, gens):
     t = np.array(times).mean(axis=0)
     n = sum(s.P for s in searches)
     flops = sum(r["useful_flops"] for r in reps)
+    pk = peaks()
+    fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     res = {"circuit_kernel_circuits_per_s": n / (t[0] / 1e3),
            "generation_circuits_per_s": n / (t[5] / 1e3),
            "circuit_kernel_ms": round(float(t[0]), 4), "generation_ms": round(float(t[5]), 4),
            "circuit_kernel_useful_tflops": flops / (t[0] / 1e3) / 1e12,
            "launch_plan": ctx.launch_plan()}
+    if searches[0].precision != W.PREC_FP64:
+        res["circuit_kernel_alu_frac"] = res["circuit_kernel_useful_tflops"] / fp32_peak
+        if searches[0].encoding == W.ENC_QEQEA:
+            last = [ctx.last_generation(r) for r in range(len(searches))]
+            ub = update_bytes(searches, last)
+            res["update_ms"] = round(float(t[4]), 4)
+            res["update_algorithmic_gbs"] = ub / (t[4] / 1e3) / 1e9
+            res["update_hbm_frac"] = res["update_algorithmic_gbs"] / pk["hbm_gbs"] \
+                if pk.get("hbm_gbs") else None
     return ctx, res
 
 

@@ -195,6 +195,13 @@ qe_status qe_update(qe_ctx *ctx, uint32_t prob, uint32_t gen, const uint32_t *d_
  * NULL it only enqueues the generations on the stream and returns. */
 qe_status qe_step(qe_ctx *ctx, uint32_t n_gen, qe_report *h_reports);
 
+/* FMA throughput of the current GPU in binary32 and binary64 (TFLOP/s, an FMA
+ * counted as two flops), measured with independent FMA chains on every SM.
+ * Not part of the method: the denominators of the arithmetic rooflines of the
+ * circuit and rescoring kernels.  Allocates and frees a small device buffer;
+ * synchronises. */
+qe_status qe_measure_alu_peaks(double *fp32_tflops, double *fp64_tflops);
+
 /* Launch-plan autotuner.  A generation graph can be launched in several ways
  * that give bit-identical results: with or without a launch-completion edge
  * that lets the previous generation's ranking selection start before the

@@ -19,7 +19,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
-UNITS = ["capi.cu", "k_circuit.cu", "k_update.cu", "k_rank.cu", "k_ga.cu", "noalloc.cu"]
+UNITS = ["capi.cu", "k_circuit.cu", "k_update.cu", "k_rank.cu", "k_ga.cu", "noalloc.cu",
+         "probe.cu"]
 
 
 def nvcc():

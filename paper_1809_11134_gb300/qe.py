@@ -29,7 +29,7 @@ QE_ERRW_BAD_GATE, QE_ERRW_NONFINITE = 1, 2
 EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_host", "qe_compose",
            "qe_update", "qe_step", "qe_last_generation", "qe_state_bytes", "qe_get_state",
            "qe_set_state", "qe_generation", "qe_autotune", "qe_launch_plan", "qe_stage_timing",
-           "qe_stage_times",
+           "qe_stage_times", "qe_measure_alu_peaks",
            "qe_eval_rank_static", "qe_last_error", "qe_destroy"]
 
 
@@ -88,6 +88,7 @@ def lib():
         L.qe_autotune.argtypes = [vp, u32, C.POINTER(C.c_float), C.POINTER(u32)]
         L.qe_launch_plan.argtypes = [vp, C.c_char_p, sz]
         L.qe_stage_timing.argtypes = [vp, C.c_int]
+        L.qe_measure_alu_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.qe_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
         L.qe_eval_rank_static.argtypes = [C.POINTER(qe_problem), vp, u32, vp, vp, vp,
                                           C.c_char_p, sz]
@@ -339,6 +340,13 @@ class Context:
         g = C.c_uint32()
         _check(self.h, lib().qe_generation(self.h, C.byref(g)))
         return g.value
+
+
+def measure_alu_peaks():
+    """(binary32, binary64) FMA throughput of the current GPU, TFLOP/s."""
+    a, b = C.c_double(), C.c_double()
+    _check(None, lib().qe_measure_alu_peaks(C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def qe_eval_rank_static(search, gate_idx, fitness, topk=None, n_circuits=None, stream=None):
