@@ -69,7 +69,12 @@ typedef enum {
 /* arithmetic of the composition */
 #define QE_PREC_FP64 0u     /* binary64, fixed operation order: bit-identical to the oracle */
 #define QE_PREC_FP32 1u     /* binary32 in registers, binary64 rescoring of the top-k */
-#define QE_PREC_SPLIT_TC 2u /* hi/lo split binary32 products on tensor cores, binary64 rescoring */
+/* hi/lo split products on tensor cores: reserved, QE_EUNSUPPORTED.  A gate
+ * here updates O(N^2) amplitudes in registers; as a dense product on tensor
+ * cores it would be O(N^3) work with three split products per gate, whose
+ * ceiling at full tensor throughput is at or below the register form's
+ * measured rate, with a larger rounding error. */
+#define QE_PREC_SPLIT_TC 2u
 
 /* fitness kind (Sec. IV-E) */
 #define QE_FIT_TRACE 0u /* Eq. (11): 1 - sqrt((N - |tr(S^dag T)|)/N) */

@@ -167,7 +167,9 @@ qe_status validate(const qe_problem &p, uint32_t idx) {
     seen[v] = true;
   }
   if (p.precision == QE_PREC_SPLIT_TC) {
-    snprintf(b, sizeof b, "problem %u: QE_PREC_SPLIT_TC is not available in this build", idx);
+    snprintf(b, sizeof b,
+             "problem %u: QE_PREC_SPLIT_TC is not provided (gates are applied in registers; "
+             "use QE_PREC_FP32)", idx);
     return fail(nullptr, QE_EUNSUPPORTED, b);
   }
   return QE_OK;
