@@ -580,13 +580,22 @@ __device__ __forceinline__ uint32_t find_problem(const uint32_t *prefix, uint32_
 // minimum resident 256-thread blocks per SM: the 5-qubit binary32 kernel is
 // capped at 128 registers (its 64 state registers plus temporaries); the
 // scheduler otherwise interleaves every row pair of a gate and asks for ~190.
+//
+// The 5-qubit binary32 kernel runs 128-thread blocks, at least three per SM,
+// so each thread may use 168 registers: its 64 state registers and the gate
+// temporaries then fit without spilling (with 256-thread blocks the same
+// occupancy allows 128 registers and spills ~220 B per thread).
+template <int NQ, bool CANON>
+constexpr int block_threads() {
+  return (NQ == 5 && !CANON) ? 128 : 256;
+}
 template <int NQ, bool CANON>
 constexpr int min_blocks() {
-  return (NQ == 5 && !CANON) ? 2 : ((NQ <= 3 && !CANON) ? 6 : 1);
+  return (NQ == 5 && !CANON) ? 3 : ((NQ <= 3 && !CANON) ? 6 : 1);
 }
 
 template <int NQ, typename R, bool CANON>
-__global__ void __launch_bounds__(256, min_blocks<NQ, CANON>()) k_step(const DevProblem *__restrict__ probs,
+__global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CANON>()) k_step(const DevProblem *__restrict__ probs,
                                               const uint32_t *__restrict__ group,
                                               const uint32_t *__restrict__ prefix,
                                               uint32_t n_group, uint32_t total, DevGlobal g) {
@@ -657,7 +666,7 @@ __global__ void __launch_bounds__(256) k_sample(const DevProblem *__restrict__ p
 
 // Fitness (and optionally the unitaries) of caller-provided gate strings.
 template <int NQ, typename R, bool CANON>
-__global__ void __launch_bounds__(256, min_blocks<NQ, CANON>()) k_eval(const DevProblem *__restrict__ probs, uint32_t prob,
+__global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CANON>()) k_eval(const DevProblem *__restrict__ probs, uint32_t prob,
                                               const uint8_t *__restrict__ gates, uint32_t n,
                                               R *fit, uint32_t *cost, R *S, DevGlobal g) {
   const DevProblem &p = probs[prob];
@@ -731,12 +740,16 @@ cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs
   uint32_t per = canon ? lc.step64[n] : lc.step32[n];
   if (lc.grid_mode == 1 && per > 1) per -= 1;
   if (lc.grid_mode == 2) per = 0xffffu;  // every circuit's warp in one launch
-  const uint32_t blocks = grid_for(lc, total, per);
-#define QE_L(NQ)                                                                               \
-  if (canon)                                                                                   \
-    k_step<NQ, double, true><<<blocks, 256, 0, st>>>(probs, group, prefix, n_group, total, g); \
-  else                                                                                         \
-    k_step<NQ, float, false><<<blocks, 256, 0, st>>>(probs, group, prefix, n_group, total, g);
+#define QE_L(NQ)                                                                          \
+  if (canon) {                                                                            \
+    constexpr int bt = block_threads<NQ, true>();                                         \
+    k_step<NQ, double, true><<<grid_for(lc, total, per, bt / 32), bt, 0, st>>>(          \
+        probs, group, prefix, n_group, total, g);                                         \
+  } else {                                                                                \
+    constexpr int bt = block_threads<NQ, false>();                                        \
+    k_step<NQ, float, false><<<grid_for(lc, total, per, bt / 32), bt, 0, st>>>(          \
+        probs, group, prefix, n_group, total, g);                                         \
+  }
   QE_NQ_SWITCH(n, QE_L)
 #undef QE_L
   return cudaGetLastError();
@@ -759,14 +772,16 @@ cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *prob
                         void *S, const DevGlobal &g, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const uint32_t per = canon ? lc.step64[nq] : lc.step32[nq];
-  const uint32_t blocks = grid_for(lc, n, per);
-#define QE_L(NQ)                                                                      \
-  if (canon)                                                                          \
-    k_eval<NQ, double, true><<<blocks, 256, 0, st>>>(probs, prob, gates, n, (double *)fit, \
-                                                     cost, (double *)S, g);           \
-  else                                                                                \
-    k_eval<NQ, float, false><<<blocks, 256, 0, st>>>(probs, prob, gates, n, (float *)fit,  \
-                                                     cost, (float *)S, g);
+#define QE_L(NQ)                                                                           \
+  if (canon) {                                                                             \
+    constexpr int bt = block_threads<NQ, true>();                                          \
+    k_eval<NQ, double, true><<<grid_for(lc, n, per, bt / 32), bt, 0, st>>>(               \
+        probs, prob, gates, n, (double *)fit, cost, (double *)S, g);                       \
+  } else {                                                                                 \
+    constexpr int bt = block_threads<NQ, false>();                                         \
+    k_eval<NQ, float, false><<<grid_for(lc, n, per, bt / 32), bt, 0, st>>>(                \
+        probs, prob, gates, n, (float *)fit, cost, (float *)S, g);                         \
+  }
   QE_NQ_SWITCH(nq, QE_L)
 #undef QE_L
   return cudaGetLastError();
@@ -796,10 +811,12 @@ cudaError_t query_circuit_occupancy(LaunchCfg &lc) {
   int b = 0;
 #define QE_Q(NQ)                                                                            \
   if (e == cudaSuccess)                                                                     \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, float, false>, 256, 0); \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, float, false>,         \
+                                                      block_threads<NQ, false>(), 0);       \
   lc.step32[NQ] = b > 0 ? b : 1;                                                            \
   if (e == cudaSuccess)                                                                     \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, double, true>, 256, 0); \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, double, true>,         \
+                                                      block_threads<NQ, true>(), 0);        \
   lc.step64[NQ] = b > 0 ? b : 1;
   QE_Q(1) QE_Q(2) QE_Q(3) QE_Q(4) QE_Q(5)
 #undef QE_Q

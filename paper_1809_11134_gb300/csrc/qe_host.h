@@ -19,9 +19,9 @@ struct LaunchCfg {
 };
 
 // persistent grid: at most the resident blocks of the whole GPU, fewer if
-// there are fewer warps of work (8 warps per 256-thread block)
-inline uint32_t grid_for(const LaunchCfg &lc, uint64_t warps, uint32_t per_sm) {
-  uint64_t need = (warps + 7) / 8;
+// there are fewer warps of work (wpb warps per block)
+inline uint32_t grid_for(const LaunchCfg &lc, uint64_t warps, uint32_t per_sm, uint32_t wpb = 8) {
+  uint64_t need = (warps + wpb - 1) / wpb;
   uint64_t cap = (uint64_t)lc.num_sms * per_sm;
   if (need > cap) need = cap;
   return need ? (uint32_t)need : 1u;
