@@ -212,14 +212,17 @@ qe_status qe_measure_alu_peaks(double *fp32_tflops, double *fp64_tflops);
  * that lets the previous generation's ranking selection start before the
  * circuit kernels fill the GPU, and with the circuit kernels' persistent grid
  * at the resident block count, one block per SM less (room for the ranking
- * chain), or one warp per circuit in a single wave.  qe_autotune runs
- * 1 + gens_per_plan (1..64) generations of every search with each plan (up to
- * six), times the last gens_per_plan on the stream with CUDA events, and keeps
- * the fastest for every later qe_step.  These are real generations: they
+ * chain), or one warp per circuit in a single wave, and, when searches of
+ * several qubit counts share the context, with their circuit kernels one after
+ * the other or on parallel streams.  qe_autotune runs 1 + gens_per_plan
+ * (1..64) generations of every search with each plan (up to twelve), times the
+ * last gens_per_plan on the stream with CUDA events, and keeps the fastest for
+ * every later qe_step.  These are real generations: they
  * advance the searches exactly as qe_step would (qe_generation counts them).
  * With n_plans != NULL, h_ms receives up to *n_plans mean generation times (ms,
- * in plan order: with the edge, then without; grids in the order above) and
- * *n_plans the number of plans tried.  Synchronises.  QE_ESTATE while stage
+ * in plan order: sequential widths, then parallel; within each, with the edge,
+ * then without; grids in the order above) and *n_plans the number of plans
+ * tried.  Synchronises.  QE_ESTATE while stage
  * timing is on. */
 qe_status qe_autotune(qe_ctx *ctx, uint32_t gens_per_plan, float *h_ms, uint32_t *n_plans);
 /* The launch plan in use, as text (NUL-terminated, truncated to len). */

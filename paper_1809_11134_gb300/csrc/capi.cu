@@ -34,12 +34,16 @@ struct Plan {
   bool select_first = true;  // launch-completion edge: ranking selection -> circuits
   uint32_t grid_mode = 0;    // circuit kernels: 0 resident blocks, 1 one block less per SM,
                              // 2 one warp per circuit in a single launch wave
+  bool concurrent = false;   // circuit kernels of different widths on parallel streams
 };
 
 struct qe_ctx {
   int device = 0;
   cudaStream_t user = nullptr;
   cudaStream_t cap = nullptr, side = nullptr, side2 = nullptr;
+  std::vector<cudaStream_t> gstreams;  // extra streams for concurrent circuit kernels
+  std::vector<cudaEvent_t> gjoin;
+  cudaEvent_t gfork = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_fork2 = nullptr;
   std::vector<qe_problem> probs;
   std::vector<DevProblem> hp;
@@ -271,7 +275,7 @@ qe_status set_priorities(qe_ctx *ctx, cudaGraph_t graph) {
   return QE_OK;
 }
 
-// Let the first circuit kernel of a generation start only once every block of
+// Let the first circuit kernel(s) of a generation start only once every block of
 // the previous generation's selection kernel is resident (a launch-completion
 // edge: the circuit kernel does not wait for the selection to finish).  Without
 // it the circuit kernel's persistent grid fills every SM first and the ranking
@@ -295,7 +299,8 @@ qe_status add_select_first_edge(qe_ctx *ctx, cudaGraph_t graph) {
     yes = is_circuit_kernel(kp.func);
     return QE_OK;
   };
-  cudaGraphNode_t sel = nullptr, first = nullptr;
+  cudaGraphNode_t sel = nullptr;
+  std::vector<cudaGraphNode_t> firsts;
   for (auto nd : nodes) {
     cudaGraphNodeType ty;
     QE_CUDA(ctx, cudaGraphNodeGetType(nd, &ty));
@@ -304,7 +309,7 @@ qe_status add_select_first_edge(qe_ctx *ctx, cudaGraph_t graph) {
     QE_CUDA(ctx, cudaGraphKernelNodeGetParams(nd, &kp));
     if (is_select_kernel(kp.func)) sel = nd;
     if (!is_circuit_kernel(kp.func)) continue;
-    // the group launched first: no circuit kernel before it
+    // a group launched first: no circuit kernel before it
     size_t nd_deps = 0;
     QE_CUDA(ctx, cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &nd_deps));
     std::vector<cudaGraphNode_t> deps(nd_deps);
@@ -316,14 +321,14 @@ qe_status add_select_first_edge(qe_ctx *ctx, cudaGraph_t graph) {
       if (st != QE_OK) return st;
       after_circuit = after_circuit || yes;
     }
-    if (!after_circuit) first = nd;
+    if (!after_circuit) firsts.push_back(nd);
   }
-  if (!sel || !first) return QE_OK;
+  if (!sel) return QE_OK;
   cudaGraphEdgeData ed;
   memset(&ed, 0, sizeof ed);
   ed.from_port = cudaGraphKernelNodePortLaunchCompletion;
   ed.type = cudaGraphDependencyTypeProgrammatic;
-  QE_CUDA(ctx, cudaGraphAddDependencies(graph, &sel, &first, &ed, 1));
+  for (auto f : firsts) QE_CUDA(ctx, cudaGraphAddDependencies(graph, &sel, &f, &ed, 1));
   return QE_OK;
 }
 
@@ -360,11 +365,19 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
   if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
   // generation g: circuits, then the two update roles
-  for (auto &gr : ctx->groups) {
+  const bool conc = plan.concurrent && ctx->groups.size() > 1;
+  if (conc && e == cudaSuccess) e = cudaEventRecord(ctx->gfork, ctx->side);
+  for (size_t k = 0; k < ctx->groups.size(); ++k) {
+    const Group &gr = ctx->groups[k];
+    cudaStream_t gs = (conc && k > 0) ? ctx->gstreams[k - 1] : ctx->side;
+    if (conc && k > 0 && e == cudaSuccess) e = cudaStreamWaitEvent(gs, ctx->gfork, 0);
     if (e == cudaSuccess)
       e = launch_step(lc, gr.n, ctx->d_probs, gr.d_ids, gr.d_prefix,
-                      (uint32_t)gr.ids.size(), gr.total, gr.canon, ctx->g, ctx->side);
+                      (uint32_t)gr.ids.size(), gr.total, gr.canon, ctx->g, gs);
+    if (conc && k > 0 && e == cudaSuccess) e = cudaEventRecord(ctx->gjoin[k - 1], gs);
   }
+  for (size_t k = 1; conc && k < ctx->groups.size(); ++k)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->gjoin[k - 1], 0);
   mark(1, ctx->side);
   if (e == cudaSuccess && ctx->n_ga)
     e = launch_ga_prep(ctx->d_probs, ctx->d_ga_ids, ctx->n_ga, ctx->g, ctx->side);
@@ -424,7 +437,8 @@ std::string plan_string(const Plan &p) {
   static const char *modes[3] = {"resident blocks", "resident blocks - 1 per SM",
                                  "one warp per circuit"};
   return std::string("selection before circuits: ") + (p.select_first ? "yes" : "no") +
-         "; circuit grid: " + modes[p.grid_mode < 3 ? p.grid_mode : 0];
+         "; circuit grid: " + modes[p.grid_mode < 3 ? p.grid_mode : 0] +
+         (p.concurrent ? "; widths on parallel streams" : "");
 }
 
 qe_status build_graph(qe_ctx *ctx) {
@@ -490,6 +504,9 @@ void qe_destroy(qe_ctx *ctx) {
   if (ctx->side2) cudaStreamDestroy(ctx->side2);
   if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
   if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
+  if (ctx->gfork) cudaEventDestroy(ctx->gfork);
+  for (auto v : ctx->gjoin) cudaEventDestroy(v);
+  for (auto st : ctx->gstreams) cudaStreamDestroy(st);
   if (ctx->h_recs) cudaFreeHost(ctx->h_recs);
   if (ctx->arena) cudaFree(ctx->arena);
   delete ctx;
@@ -780,6 +797,15 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->gfork, cudaEventDisableTiming);
+  for (size_t k = 1; k < ctx->groups.size() && e == cudaSuccess; ++k) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t v = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) ctx->gstreams.push_back(s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+    if (e == cudaSuccess) ctx->gjoin.push_back(v);
+  }
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "creating streams"));
   *out = ctx;
   return QE_OK;
@@ -964,14 +990,17 @@ qe_status qe_autotune(qe_ctx *ctx, uint32_t gens_per_plan, float *h_ms, uint32_t
   for (auto &gr : ctx->groups)
     several = several || (gr.canon ? ctx->lc.step64[gr.n] : ctx->lc.step32[gr.n]) > 1;
   std::vector<Plan> cands;
-  for (int sf = 1; sf >= 0; --sf)
-    for (uint32_t gm = 0; gm < 3; ++gm) {
-      if (gm == 1 && !several) continue;
-      Plan p;
-      p.select_first = sf == 1;
-      p.grid_mode = gm;
-      cands.push_back(p);
-    }
+  const int n_conc = ctx->groups.size() > 1 ? 2 : 1;
+  for (int cc = 0; cc < n_conc; ++cc)
+    for (int sf = 1; sf >= 0; --sf)
+      for (uint32_t gm = 0; gm < 3; ++gm) {
+        if (gm == 1 && !several) continue;
+        Plan p;
+        p.select_first = sf == 1;
+        p.grid_mode = gm;
+        p.concurrent = cc == 1;
+        cands.push_back(p);
+      }
   const size_t C = cands.size();
   std::vector<cudaGraph_t> graphs(C, nullptr);
   std::vector<cudaGraphExec_t> execs(C, nullptr);

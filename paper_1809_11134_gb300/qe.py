@@ -317,8 +317,8 @@ class Context:
     def autotune(self, gens_per_plan=2):
         """qe_autotune: time every launch plan on real generations, keep the
         fastest; returns the mean generation time (ms) of each plan tried."""
-        ms = (C.c_float * 8)()
-        n = C.c_uint32(8)
+        ms = (C.c_float * 16)()
+        n = C.c_uint32(16)
         _check(self.h, lib().qe_autotune(self.h, gens_per_plan, ms, C.byref(n)))
         return list(ms[:n.value])
 
