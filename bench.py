@@ -28,15 +28,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "candidate circuits evaluated/sec at n=3/4/5 qubits, FP32 batched vs FP64 plain"
 WORKLOADS = {
-    1: "3-qubit QEQEA: Toffoli, 19-gate NCV+I library, L=5, P=64, seed 0, binary64",
+    1: "3-qubit QEQEA: Toffoli, 19-gate NCV+I library, L=5, P=64, seed 0",
     2: "3-qubit QEQEA: Toffoli + Fredkin + Peres targets, 28-gate NCV+H/T/T^dag+I library, L=16, "
-       "P=4096 each, Philox seed 1, binary32 compose with binary64 top-32 rescoring",
-    3: "4-qubit QEQEA: C3NOT, 48-gate NCV+H/T/T^dag library, L=32, P=65536, binary32 with "
-       "binary64 top-64",
+       "P=4096 each, Philox seed 1, top-32 per generation",
+    3: "4-qubit QEQEA: C3NOT, 48-gate NCV+H/T/T^dag library, L=32, P=65536, top-64",
     4: "1024 uneven QEQEA searches, n in {3,4,5}, L in [8,64], P in [256,4096], random "
-       "permutation targets, binary32 with binary64 top-32",
-    5: "5-qubit QEQEA: C4NOT, 75-gate NCV+H/T/T^dag library, L=64, P=262144, binary32 with "
-       "binary64 top-128",
+       "permutation targets, top-32",
+    5: "5-qubit QEQEA: C4NOT, 75-gate NCV+H/T/T^dag library, L=64, P=262144, top-128",
 }
 UNIT = "circuits/s"
 
@@ -117,8 +115,8 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    searches = W.config(2)
-    P = args.ref_population
+    searches = W.config(args.config, P=args.population)
+    P = min(args.ref_population, min(s.P for s in searches))
     probs = [oracle.make_problem(s.n, s.L, P, s.library, s.perm, seed=s.seed, run=r)
              for r, s in enumerate(searches)]
     states = [oracle.init_state(p) for p in probs]
@@ -141,11 +139,12 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "3-qubit Toffoli/Fredkin/Peres search, 28-gate library, L=16, "
-                               "P=%d per step (sample of P=4096)" % P, "l2": "host"},
+        "config": {"workload": workload_name(args), "circuits_per_step": P,
+                   "parallelism": "one host thread", "l2": "host memory"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "one generation of one of the three searches at P=%d per step "
-                                   "(sample, dense Kronecker compose, score, sort, update)" % P},
+                         "sample": "each step: one generation of one of the searches with its "
+                                   "population capped at P=%d (sample, dense Kronecker compose, "
+                                   "score, sort, update)" % P},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -173,6 +172,12 @@ def cpu_baseline(seconds=10.0):
     return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d whole generations of the Toffoli search (P=4096, L=16): sample, "
                       "dense binary64 compose/score, full sort, update; %.1f s" % (gen, dt)}
+
+
+def workload_name(args):
+    return (WORKLOADS.get(args.config, "benchmark search set %d" % args.config)
+            + ("" if args.population is None else " (P capped at %d)" % args.population)
+            + "; one step = one generation")
 
 
 def replica_searches(W, config, population, rank):
@@ -305,10 +310,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS.get(args.config, "benchmark search set %d" % args.config)
-                                   + ("" if args.population is None else " (P capped at %d)" % args.population)
-                                   + "; one step = one generation, ranked binary64 top-k pipelined "
-                                     "one generation behind",
+            "config": {"workload": workload_name(args),
+                       "arithmetic": "binary32 composition and scoring, top-k rescored in "
+                                     "binary64 and ranked one generation behind (pipelined)",
                        "circuits_per_step": n_circ, "parallelism": "replica per GPU",
                        "l2": "flushed (256 MB write) before every timed step",
                        "launch_plan": plan, "autotune_ms_per_plan": [round(m, 5) for m in tune_ms],
