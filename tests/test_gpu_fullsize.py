@@ -204,3 +204,53 @@ def test_5qubit_full_size_ga(qe, torch):
         nxt = oracle.ga_next(p, _G(s), 0, s.ga_mutation_rate, g0, last["fitness"], cost_all)
         assert np.array_equal(ctx.get_state(0), nxt)
 
+
+
+def test_maximum_sizes(qe, torch):
+    """The largest search the ABI accepts: n = 5, L = 64, P = 2^20 (R*P*L =
+    1.68e9 segments, 107 GB of encoding state), top-1024; plus 4096 searches
+    in one context.  Checked on sampled outputs: the slot structure of the
+    sample, binary32 fitness of a random subset, and the top-1024 (binary64
+    values of a sample of its entries, ranking order, no sampled outsider above
+    the last entry)."""
+    s = W.Search(5, 64, 1 << 20, W.LIB_NCV | W.LIB_HT, W.cknot(5), seed=21, topk=1024)
+    p = oracle_problem(s, 0)
+    rng = np.random.default_rng(21)
+    with qe.Context([s]) as ctx:
+        ctx.step_raw(1, None)
+        last = ctx.last_generation(0)
+    sid = last["seg_id"].astype(np.int64)
+    LP = s.L * s.P
+    assert np.all(sid // LP < oracle.num_regions(s.n, s.library))
+    assert np.array_equal(sid % s.L, np.broadcast_to(np.arange(s.L), sid.shape))
+    sub = rng.choice(s.P, 100, replace=False)
+    F, C = oracle.eval_circuits(p, last["gate_idx"][sub])
+    assert_fp32_fitness(last["fitness"][sub], F, s, C)
+    tk = last["topk"]
+    assert len(tk) == 1024
+    keys = [(-t[2], t[1], t[0]) for t in tk]
+    assert keys == sorted(keys)
+    pick = np.sort(rng.choice(1024, 64, replace=False))
+    idx = np.array([tk[j][0] for j in pick], np.int64)
+    Fk, Ck = oracle.eval_circuits(p, last["gate_idx"][idx])
+    assert [tk[j][2] for j in pick] == list(Fk) and [tk[j][1] for j in pick] == list(Ck)
+    others = np.setdiff1d(rng.choice(s.P, 100, replace=False), [t[0] for t in tk])
+    Fo, Co = oracle.eval_circuits(p, last["gate_idx"][others])
+    for f, c, i in zip(Fo, Co, others):
+        assert (-f, c, i) > keys[-1]
+    many = [W.Search(3, 4, 8, W.LIB_NCV | W.LIB_IDENTITY, W.cknot(3), seed=5, topk=2,
+                     precision=W.PREC_FP64) for _ in range(4096)]
+    with qe.Context(many) as ctx:
+        reps = ctx.step(2)
+    assert len(reps) == 4096 and all(r["generation"] == 2 for r in reps)
+    for run in (0, 1234, 4095):
+        ref = oracle_problem(many[run], run)
+        cur, best, bf = oracle.init_state(ref)
+        bfit = -np.inf
+        for gen in range(2):
+            gi, sid = oracle.sample(ref, cur, gen)
+            Fg, Cg = oracle.eval_circuits(ref, gi)
+            b = oracle.topk(Fg, Cg, 1)[0]
+            bfit = max(bfit, Fg[b])
+            oracle.update(ref, cur, best, bf, gen, sid, Fg)
+        assert reps[run]["best_fitness"] == bfit
