@@ -588,6 +588,8 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
       ar.take(&d.fk, d.nseg * 8);
       ar.take(&d.seg_id, PL * 4);
       ar.take(&d.qubit_tab, (kQ + 1) * sizeof(float2));
+      ar.take(&d.mut_list, 2 * P * 4);
+      ar.take(&d.mut_cnt, 2 * 4);
     } else {
       ar.take(&d.ga_cum, P * 8);
       ar.take(&d.ga_info, 16);
@@ -783,7 +785,10 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.rank_active, 0, 4, us);
   for (uint32_t i = 0; i < n_probs && e == cudaSuccess; ++i) {
     const DevProblem &d = ctx->hp[i];
-    if (d.enc == QE_ENC_QEQEA) e = launch_init_state(ctx->d_probs, i, d.nseg, us);
+    if (d.enc == QE_ENC_QEQEA) {
+      e = launch_init_state(ctx->d_probs, i, d.nseg, us);
+      if (e == cudaSuccess) e = cudaMemsetAsync(d.mut_cnt, 0, 2 * 4, us);
+    }
     else e = launch_ga_init(ctx->d_probs, i, d.P, d.L, us);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(us);

@@ -367,7 +367,11 @@ __device__ __forceinline__ void prefetch_l2(const void *ptr) {
 __device__ __forceinline__ void prefetch_mutated(const DevProblem &p, uint32_t i, uint32_t gen,
                                                  int lane) {
   const uint4 v = draw(p, i, 0, gen, kStMutDecide);
+  if (lane == 0 && i == 0) p.mut_cnt[(gen + 1u) & 1u] = 0u;  // the next generation's list
   if (!((unsigned long long)v.x < p.mut_T)) return;
+  // list the individual for the update's mutation role (any order: the
+  // individuals' segments are disjoint)
+  if (lane == 0) p.mut_list[(size_t)(gen & 1u) * p.P + atomicAdd(p.mut_cnt + (gen & 1u), 1u)] = i;
   const uint32_t RL = p.R * p.L;
   for (uint32_t x = lane; x < RL; x += 32) {
     const uint32_t r = x / p.L, t = x - r * p.L;

@@ -5,9 +5,11 @@
 //  role A (k_update_elite), one thread per (circuit, slot): if the segment's
 //    individual is not mutated this generation, the first thread to take the
 //    segment's fitness key (atomicExch to 0) applies elitism to it;
-//  role B (k_update_mutate), one warp per (32 individuals, region): for each
-//    individual that mutates, the warp walks its L segments of that region,
-//    applies elitism where the segment was used, then mutates it.
+//  role B, for each segment of an individual that mutates: elitism where the
+//    segment was used, then mutation.  Inside the generation graph
+//    (k_update_mutate_list) one thread per segment of the individuals the
+//    circuit kernel listed; for qe_update or contexts with many searches
+//    (k_update_mutate) one warp per (32 individuals, region).
 // A segment belongs to exactly one role, so no segment is touched twice.
 // All mutation arithmetic is binary32 with _rn intrinsics in the order the
 // oracle fixes (no contraction), so the state stays bit-identical to it; the
@@ -17,6 +19,10 @@
 #include "qe_host.h"
 
 namespace qe {
+
+// contexts with at most this many QEQEA searches use the listed mutation role;
+// every block of that kernel walks the searches one after another
+constexpr uint32_t kListMaxSearches = 64;
 
 struct fc {
   float re, im;
@@ -142,7 +148,49 @@ __global__ void __launch_bounds__(256, 8) k_update_elite(const DevProblem *__res
   }
 }
 
-// role B: individuals that mutate; one warp per (32 individuals, region)
+// one segment of a mutating individual: elitism if it was used this
+// generation (its fitness key is set), then mutation
+__device__ __forceinline__ void mutate_segment(const DevProblem &p, const DevGlobal &g,
+                                               uint32_t seg, uint32_t gen) {
+  const uint2 fkv = *reinterpret_cast<const uint2 *>(p.fk + 2 * (size_t)seg);
+  const uint32_t key = fkv.y;
+  float bf = __uint_as_float(fkv.x);
+  const float4 *line = cur_of(p, seg);
+  float4 c0 = line[0], c1 = line[1];
+  if (key) {
+    const float4 b0 = line[2], b1 = line[3];
+    *key_of(p, seg) = 0u;
+    const float sf = fkey_inv(key);
+    elitism(p, seg, sf, bf, c0, c1, b0, b1);
+    if (sf > bf) bf = sf;
+  }
+  mutate(p, g, seg, gen, bf, c0, c1);
+}
+
+// role B, inside the generation graph: the segments of the individuals the
+// circuit kernel listed, one thread per segment (the list has no order; each
+// segment is independent), searches one after another
+__global__ void __launch_bounds__(256) k_update_mutate_list(const DevProblem *__restrict__ probs,
+                                                            const uint32_t *__restrict__ group,
+                                                            uint32_t n_group,
+                                                            const uint32_t *d_gen, DevGlobal g) {
+  const uint32_t gen = *d_gen, par = gen & 1u;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t q = 0; q < n_group; ++q) {
+    const DevProblem &p = probs[group[q]];
+    const uint32_t RL = p.R * p.L;
+    const uint32_t total = p.mut_cnt[par] * RL;
+    const uint32_t *list = p.mut_list + (size_t)par * p.P;
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
+      const uint32_t e = x / RL, rem = x - e * RL;
+      const uint32_t r = rem / p.L, t = rem - r * p.L;
+      mutate_segment(p, g, r * p.LP + list[e] * p.L + t, gen);
+    }
+  }
+}
+
+// role B for qe_update (no circuit kernel has listed the individuals): one
+// warp per (32 individuals, region), the decision drawn here
 __global__ void __launch_bounds__(256) k_update_mutate(const DevProblem *__restrict__ probs,
                                                        const uint32_t *__restrict__ group,
                                                        const uint32_t *__restrict__ prefB,
@@ -166,20 +214,7 @@ __global__ void __launch_bounds__(256) k_update_mutate(const DevProblem *__restr
     for (uint32_t x = lane; x < items; x += 32) {
       const uint32_t b = x / p.L, t = x - b * p.L;
       const uint32_t ii = i0 + __fns(bal, 0, (int)b + 1);
-      const uint32_t seg = r * p.LP + ii * p.L + t;
-      const uint2 fkv = *reinterpret_cast<const uint2 *>(p.fk + 2 * (size_t)seg);
-      const uint32_t key = fkv.y;
-      float bf = __uint_as_float(fkv.x);
-      const float4 *line = cur_of(p, seg);
-      float4 c0 = line[0], c1 = line[1];
-      if (key) {
-        const float4 b0 = line[2], b1 = line[3];
-        *key_of(p, seg) = 0u;
-        const float sf = fkey_inv(key);
-        elitism(p, seg, sf, bf, c0, c1, b0, b1);
-        if (sf > bf) bf = sf;
-      }
-      mutate(p, g, seg, gen, bf, c0, c1);
+      mutate_segment(p, g, r * p.LP + ii * p.L + t, gen);
     }
   }
 }
@@ -221,7 +256,8 @@ __global__ void __launch_bounds__(256) k_init_state(const DevProblem *__restrict
 }
 
 bool is_update_kernel(const void *f) {
-  return f == (const void *)k_update_elite || f == (const void *)k_update_mutate;
+  return f == (const void *)k_update_elite || f == (const void *)k_update_mutate ||
+         f == (const void *)k_update_mutate_list;
 }
 
 cudaError_t launch_init_state(const DevProblem *probs, uint32_t prob, uint64_t nseg,
@@ -262,8 +298,13 @@ cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const ui
                                                 seg_override);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_update_mutate<<<(uint32_t)bB, 256, 0, stB>>>(probs, group, prefB, n_group, totalB, d_gen, gen,
-                                                 g);
+  if (d_gen && n_group <= kListMaxSearches) {
+    // generation graph: the circuit kernel listed the mutating individuals
+    k_update_mutate_list<<<lc.num_sms * 8, 256, 0, stB>>>(probs, group, n_group, d_gen, g);
+  } else {
+    k_update_mutate<<<(uint32_t)bB, 256, 0, stB>>>(probs, group, prefB, n_group, totalB, d_gen,
+                                                   gen, g);
+  }
   return cudaGetLastError();
 }
 

@@ -12,6 +12,7 @@
 //                generation parity so a generation's ranking can overlap the
 //                next generation; a GA search keeps its genome here),
 //                seg_id: P*L uint32 (QEQEA only)
+//   mut_list   : 2 x P individual ids, mut_cnt: 2 counters (QEQEA only)
 //   ga_cum     : P uint64 SUS prefix sums (GA only)
 //   fit32/fit64: 2 x P (working-precision fitness), meta: 2 x P (cost | work << 8)
 // where S = R*P*L and seg = r*L*P + i*L + t (Eq. (10)).
@@ -84,6 +85,11 @@ struct DevProblem {
   Best *rec;
   // mutation table: cos/sin of m * mutation_range / Q, m = 0..Q
   float2 *qubit_tab;
+  // individuals that mutate this generation, listed by the circuit kernel:
+  // 2 x P entries and 2 counters, by generation parity (the circuit kernel of
+  // generation g appends to half g & 1 and clears the counter of the other)
+  uint32_t *mut_list;
+  uint32_t *mut_cnt;
   // GA buffers: SUS prefix sums of the weights, and {W, elite}
   unsigned long long *ga_cum;
   unsigned long long *ga_info;
