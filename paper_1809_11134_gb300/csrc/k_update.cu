@@ -4,7 +4,8 @@
 // Two kernels, which may run concurrently, split the update of every search:
 //  role A (k_update_elite), one thread per (circuit, slot): if the segment's
 //    individual is not mutated this generation, the first thread to take the
-//    segment's fitness key (atomicExch to 0) applies elitism to it;
+//    segment's fitness key (a 64-bit atomicAnd that clears it) applies
+//    elitism to it;
 //  role B, for each segment of an individual that mutates: elitism where the
 //    segment was used, then mutation.  Inside the generation graph
 //    (k_update_mutate_list) one thread per segment of the individuals the
@@ -142,8 +143,12 @@ __global__ void __launch_bounds__(256, 8) k_update_elite(const DevProblem *__res
     const float4 *line = cur_of(p, seg);
     float4 c0 = line[0], c1 = line[1];
     const float4 b0 = line[2], b1 = line[3];
-    const float bf = *bestf_of(p, seg);
-    const uint32_t key = atomicExch(key_of(p, seg), 0u);
+    // best fitness and fitness key in one 64-bit atomic that clears the key
+    // (low word: best_f bits, high word: key); one slot per segment sees it set
+    const unsigned long long pr =
+        atomicAnd(reinterpret_cast<unsigned long long *>(p.fk + 2 * (size_t)seg), 0xffffffffull);
+    const float bf = __uint_as_float((uint32_t)pr);
+    const uint32_t key = (uint32_t)(pr >> 32);
     if (key) elitism(p, seg, fkey_inv(key), bf, c0, c1, b0, b1);
   }
 }
