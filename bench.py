@@ -336,10 +336,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_step launch from an
-# ncu capture of this workload (profiles/k_step_3qubit_bench.md); cold L2 (ncu
-# flushes caches between replays), so it includes the update's L2 prefetch
-TRAFFIC = {(2, None): 41.325e6}
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_step launch (a timed
+# step, right after the L2 flush) from an ncu capture of this workload
+# (profiles/k_step_3qubit_bench.md): the reads include the update's L2
+# prefetch, the writes mostly the flush buffer's dirty lines evicted meanwhile
+TRAFFIC = {(2, None): 80.661e6}
 
 
 def roofline(dom, ms, flops, searches, pk, traffic=None):
