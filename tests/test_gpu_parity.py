@@ -377,3 +377,45 @@ def test_degenerate_searches(qe, torch):
         for run in range(len(searches)):
             c, b, bf = ctx.get_state(run)
             assert state_equal(c, ref[run][1]) and state_equal(bf, ref[run][3])
+
+
+@pytest.mark.parametrize("kind,lam", [(W.FIT_PROB, 0.0), (W.FIT_TRACE, 0.2), (W.FIT_PROB, 0.1)])
+def test_step_fitness_kinds_and_cost(qe, torch, kind, lam):
+    """Whole generations with the probability reading of the fitness and with
+    the gate-cost penalty: binary64 trajectories bit-exact (ranking, record,
+    state), and binary32 generations with their top-k bit-exact."""
+    s64 = [W.Search(3, 12, 300, NCV | HT | ID, W.peres(), seed=31, precision=W.PREC_FP64,
+                    topk=9, fitness_kind=kind, cost_weight=lam),
+           W.Search(4, 10, 120, NCV | HT, W.cknot(4), seed=32, precision=W.PREC_FP64,
+                    topk=5, fitness_kind=kind, cost_weight=lam)]
+    ref = _oracle_run(s64, 6)
+    with qe.Context(s64) as ctx:
+        for gen in range(6):
+            reps = ctx.step(1)
+            for run, s in enumerate(s64):
+                gi, sid, F, tk, bfit, bcost, bgates, flops, mean = ref[run][0][gen]
+                last = ctx.last_generation(run)
+                assert np.array_equal(last["gate_idx"], gi) and np.array_equal(last["fitness"], F)
+                assert [t[0] for t in last["topk"]] == list(tk[:s.topk])
+                assert reps[run]["best_fitness"] == bfit and reps[run]["best_cost"] == bcost
+        for run in range(len(s64)):
+            c, b, bf = ctx.get_state(run)
+            assert state_equal(c, ref[run][1]) and state_equal(bf, ref[run][3])
+    s32 = [W.Search(3, 16, 700, NCV | HT | ID, W.fredkin(), seed=33, topk=16, fitness_kind=kind,
+                    cost_weight=lam),
+           W.Search(5, 20, 90, NCV | HT, W.cknot(5), seed=34, topk=6, fitness_kind=kind,
+                    cost_weight=lam)]
+    probs = [oracle_problem(s, r) for r, s in enumerate(s32)]
+    with qe.Context(s32) as ctx:
+        for gen in range(3):
+            before = [ctx.get_state(r) for r in range(len(s32))]
+            ctx.step_raw(1, None)
+            for run, s in enumerate(s32):
+                last = ctx.last_generation(run)
+                gi, _ = oracle.sample(probs[run], before[run][0].copy(), gen)
+                assert np.array_equal(last["gate_idx"], gi)
+                F, C = oracle.eval_circuits(probs[run], gi)
+                assert_fp32_fitness(last["fitness"], F, s, C)
+                order = oracle.topk(F, C, s.topk)
+                assert [t[0] for t in last["topk"]] == list(order)
+                assert [t[2] for t in last["topk"]] == list(F[order])
