@@ -11,8 +11,8 @@ import numpy as np
 
 from . import build as _build
 
-LIB_NCV, LIB_HT, LIB_IDENTITY = 1, 2, 4
-I, CNOT, CV, CVDG, H, T, TDG = range(7)
+LIB_NCV, LIB_HT, LIB_IDENTITY, LIB_ISING = 1, 2, 4, 8
+I, CNOT, CV, CVDG, H, T, TDG, RX, RY, RZ, J = range(11)
 FIT_TRACE, FIT_PROB = 0, 1
 Q = 4096
 
@@ -60,6 +60,15 @@ def lib():
         L.oracle_num_segments.argtypes = [C.POINTER(Problem)]
         L.oracle_num_segments.restype = C.c_uint64
         L.oracle_gate_matrix.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _f64p, _f64p]
+        L.oracle_half_angle.argtypes = [C.c_float, C.c_float, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]
+        L.oracle_gate_matrix_amp.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_float,
+                                             C.c_float, _f64p, _f64p]
+        L.oracle_compose_amp.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p, _f32p, _f64p,
+                                         _f64p]
+        L.oracle_eval_amp.argtypes = [C.POINTER(Problem), _u8p, _f32p, C.c_uint32, _f64p, _u32p]
+        L.oracle_sample_amp.argtypes = [C.POINTER(Problem), _f32p, C.c_uint32, _u8p, _u32p,
+                                        _f32p]
         L.oracle_compose.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p, _f64p, _f64p]
         L.oracle_score.argtypes = [C.c_uint32, _f64p, _f64p, _u8p, C.c_uint32]
         L.oracle_score.restype = C.c_double
@@ -140,12 +149,31 @@ def gate_matrix(n, library, g):
     return (re + 1j * im).reshape(N, N)
 
 
-def compose(n, library, gates):
+def half_angle(b0, b1):
+    c, s = C.c_double(), C.c_double()
+    lib().oracle_half_angle(b0, b1, C.byref(c), C.byref(s))
+    return c.value, s.value
+
+
+def gate_matrix_amp(n, library, g, b0, b1):
+    N = 1 << n
+    re = np.zeros(N * N)
+    im = np.zeros(N * N)
+    lib().oracle_gate_matrix_amp(n, library, g, b0, b1, re, im)
+    return (re + 1j * im).reshape(N, N)
+
+
+def compose(n, library, gates, amps=None):
+    """amps: the slots' qubit amplitudes, shape [L, 2] float32 (Ising library)"""
     N = 1 << n
     g = np.ascontiguousarray(gates, np.uint8)
     re = np.zeros(N * N)
     im = np.zeros(N * N)
-    lib().oracle_compose(n, library, len(g), g, re, im)
+    if amps is None:
+        lib().oracle_compose(n, library, len(g), g, re, im)
+    else:
+        a = np.ascontiguousarray(amps, np.float32).ravel()
+        lib().oracle_compose_amp(n, library, len(g), g, a, re, im)
     return re.reshape(N, N), im.reshape(N, N)
 
 
@@ -166,12 +194,18 @@ def useful_flops(n, library, gates):
     return lib().oracle_useful_flops(n, library, len(g), g)
 
 
-def eval_circuits(p, gates):
+def eval_circuits(p, gates, amps=None):
+    """amps: [n, L, 2] float32 slot amplitudes (Ising library), else None"""
     g = np.ascontiguousarray(gates, np.uint8).reshape(-1, p.L)
     nc = g.shape[0]
     F = np.zeros(max(nc, 1))
     cost_ = np.zeros(max(nc, 1), np.uint32)
-    lib().oracle_eval(C.byref(p), g.ravel() if nc else np.zeros(1, np.uint8), nc, F, cost_)
+    gp = g.ravel() if nc else np.zeros(1, np.uint8)
+    if amps is None:
+        lib().oracle_eval(C.byref(p), gp, nc, F, cost_)
+    else:
+        a = np.ascontiguousarray(amps, np.float32).ravel()
+        lib().oracle_eval_amp(C.byref(p), gp, a if nc else np.zeros(2, np.float32), nc, F, cost_)
     return F[:nc], cost_[:nc]
 
 
@@ -184,11 +218,15 @@ def init_state(p):
     return cur[:8 * S], best[:8 * S], bf[:S]
 
 
-def sample(p, cur, gen):
+def sample(p, cur, gen, with_amps=False):
     gi = np.zeros(p.P * p.L, np.uint8)
     sid = np.zeros(p.P * p.L, np.uint32)
-    lib().oracle_sample(C.byref(p), np.ascontiguousarray(cur, np.float32), gen, gi, sid)
-    return gi.reshape(p.P, p.L), sid.reshape(p.P, p.L)
+    if not with_amps:
+        lib().oracle_sample(C.byref(p), np.ascontiguousarray(cur, np.float32), gen, gi, sid)
+        return gi.reshape(p.P, p.L), sid.reshape(p.P, p.L)
+    amps = np.zeros(2 * p.P * p.L, np.float32)
+    lib().oracle_sample_amp(C.byref(p), np.ascontiguousarray(cur, np.float32), gen, gi, sid, amps)
+    return gi.reshape(p.P, p.L), sid.reshape(p.P, p.L), amps.reshape(p.P, p.L, 2)
 
 
 def update(p, cur, best, best_f, gen, seg_id, fitness):

@@ -71,7 +71,11 @@ enum { ST_SAMPLE = 0, ST_MUT_DECIDE = 1, ST_MUT_SEG = 2, ST_GA = 4, ST_GA_INIT =
 /* ======================================================================
  * Library and population geometry.
  * ====================================================================== */
+/* Ising library: the n wires, then the n(n-1)/2 pairs i < j */
+static int is_ising(uint32_t library) { return library == ORC_LIB_ISING; }
+
 uint32_t oracle_num_regions(uint32_t n, uint32_t library) {
+  if (is_ising(library)) return n + n * (n - 1) / 2;
   uint32_t r = 0;
   if (library & ORC_LIB_NCV) r += n * (n - 1);
   if (library & ORC_LIB_HT) r += n;
@@ -79,6 +83,7 @@ uint32_t oracle_num_regions(uint32_t n, uint32_t library) {
 }
 
 uint32_t oracle_num_gates(uint32_t n, uint32_t library) {
+  if (is_ising(library)) return 3 * n + n * (n - 1) / 2;
   return ((library & ORC_LIB_IDENTITY) ? 1u : 0u) + 3u * oracle_num_regions(n, library);
 }
 
@@ -88,6 +93,26 @@ int oracle_gate_desc(uint32_t n, uint32_t library, uint32_t g, int *kind, int *c
   uint32_t code = g;
   *ctrl = -1;
   *tgt = -1;
+  if (is_ising(library)) {
+    if (g < 3 * n) {
+      *tgt = (int)(g / 3);
+      *kind = (g % 3 == 0) ? ORC_RX : (g % 3 == 1) ? ORC_RY : ORC_RZ;
+      return 0;
+    }
+    /* pair number g - 3n in lexicographic order of (i, j), i < j */
+    uint32_t q = g - 3 * n;
+    for (uint32_t i = 0; i < n; ++i)
+      for (uint32_t j = i + 1; j < n; ++j) {
+        if (q == 0) {
+          *ctrl = (int)i;
+          *tgt = (int)j;
+          *kind = ORC_J;
+          return 0;
+        }
+        --q;
+      }
+    return -1;
+  }
   if (library & ORC_LIB_IDENTITY) {
     if (g == 0) {
       *kind = ORC_I;
@@ -111,7 +136,7 @@ int oracle_gate_desc(uint32_t n, uint32_t library, uint32_t g, int *kind, int *c
 }
 
 uint32_t oracle_region_gate(uint32_t n, uint32_t library, uint32_t r, uint32_t k) {
-  (void)n;
+  if (is_ising(library)) return r < n ? 3 * r + k : 3 * n + (r - n);
   return ((library & ORC_LIB_IDENTITY) ? 1u : 0u) + 3u * r + k;
 }
 
@@ -146,8 +171,20 @@ static cplx cadd(cplx a, cplx b) {
   return r;
 }
 
-/* 2x2 single-qubit operator acting on the target wire */
-static void gate_2x2(int kind, cplx u[2][2]) {
+/* cos(theta/2), sin(theta/2) of the angle of the amplitudes (b0, b1) =
+   (cos theta, sin theta), theta in [0, 2 pi): sin(theta/2) >= 0, and
+   cos(theta/2) < 0 exactly when theta > pi, i.e. b1 < 0 */
+void oracle_half_angle(float b0, float b1, double *c, double *s) {
+  double a = (1.0 + (double)b0) * 0.5, b = (1.0 - (double)b0) * 0.5;
+  if (a < 0.0) a = 0.0;
+  if (b < 0.0) b = 0.0;
+  *c = (b1 < 0.0f) ? -sqrt(a) : sqrt(a);
+  *s = sqrt(b);
+}
+
+/* 2x2 single-qubit operator acting on the target wire; (c, s) = cos/sin of
+   theta/2 for the rotations of Eqs. (3)-(5) */
+static void gate_2x2(int kind, double c, double s, cplx u[2][2]) {
   const double h = ORC_H_COEF;
   cplx z = {0.0, 0.0}, one = {1.0, 0.0};
   u[0][0] = one;
@@ -185,6 +222,22 @@ static void gate_2x2(int kind, cplx u[2][2]) {
     case ORC_TDG:
       u[1][1] = (cplx){h, -h};
       break;
+    case ORC_RX: /* Eq. (3): [[c, -i s], [-i s, c]] */
+      u[0][0] = (cplx){c, 0.0};
+      u[0][1] = (cplx){0.0, -s};
+      u[1][0] = (cplx){0.0, -s};
+      u[1][1] = (cplx){c, 0.0};
+      break;
+    case ORC_RY: /* Eq. (4): [[c, -s], [s, c]] */
+      u[0][0] = (cplx){c, 0.0};
+      u[0][1] = (cplx){-s, 0.0};
+      u[1][0] = (cplx){s, 0.0};
+      u[1][1] = (cplx){c, 0.0};
+      break;
+    case ORC_RZ: /* Eq. (5): diag(e^{-i theta/2}, e^{i theta/2}) */
+      u[0][0] = (cplx){c, -s};
+      u[1][1] = (cplx){c, s};
+      break;
     default:
       break;
   }
@@ -218,13 +271,23 @@ static void kron_chain(uint32_t n, cplx (*M)[2][2], cplx *out) {
   free(b);
 }
 
-static void dense_gate(uint32_t n, int kind, int ctrl, int tgt, cplx *G) {
+static void dense_gate(uint32_t n, int kind, int ctrl, int tgt, double c, double s, cplx *G) {
   uint32_t N = 1u << n;
   cplx id[2][2] = {{{1.0, 0.0}, {0.0, 0.0}}, {{0.0, 0.0}, {1.0, 0.0}}};
   cplx u[2][2];
-  gate_2x2(kind, u);
+  gate_2x2(kind, c, s, u);
   cplx (*M)[2][2] = malloc(sizeof(cplx[2][2]) * n);
-  if (kind == ORC_I) {
+  if (kind == ORC_J) {
+    /* interaction template: the +-1 diagonal D = z_i z_j, then the term-wise
+       exponent exp(-i theta/2 D) = c - i D s on the diagonal */
+    for (uint32_t e = 0; e < N * N; ++e) G[e] = (cplx){0.0, 0.0};
+    for (uint32_t b = 0; b < N; ++b) {
+      int zi = ((b >> (n - 1 - (uint32_t)ctrl)) & 1u) ? -1 : 1;
+      int zj = ((b >> (n - 1 - (uint32_t)tgt)) & 1u) ? -1 : 1;
+      double d = (double)(zi * zj);
+      G[b * N + b] = (cplx){c, -d * s};
+    }
+  } else if (kind == ORC_I) {
     for (uint32_t w = 0; w < n; ++w) memcpy(M[w], id, sizeof id);
     kron_chain(n, M, G);
   } else if (ctrl < 0) {
@@ -248,7 +311,24 @@ static void dense_gate(uint32_t n, int kind, int ctrl, int tgt, cplx *G) {
   free(M);
 }
 
+/* cos/sin of theta/2 of slot t (Ising), NaN without amplitudes */
+static void slot_angle(uint32_t library, const float *amps, uint32_t t, double *c, double *s) {
+  if (!is_ising(library)) {
+    *c = 1.0;
+    *s = 0.0;
+  } else if (!amps) {
+    *c = *s = NAN;
+  } else {
+    oracle_half_angle(amps[2 * t], amps[2 * t + 1], c, s);
+  }
+}
+
 void oracle_gate_matrix(uint32_t n, uint32_t library, uint32_t g, double *re, double *im) {
+  oracle_gate_matrix_amp(n, library, g, NAN, NAN, re, im);
+}
+
+void oracle_gate_matrix_amp(uint32_t n, uint32_t library, uint32_t g, float b0, float b1,
+                            double *re, double *im) {
   uint32_t N = 1u << n;
   int kind, ctrl, tgt;
   cplx *G = (cplx *)malloc(sizeof(cplx) * N * N);
@@ -257,7 +337,10 @@ void oracle_gate_matrix(uint32_t n, uint32_t library, uint32_t g, double *re, do
     free(G);
     return;
   }
-  dense_gate(n, kind, ctrl, tgt, G);
+  const float ab[2] = {b0, b1};
+  double c, s;
+  slot_angle(library, (b0 == b0) ? ab : NULL, 0, &c, &s);
+  dense_gate(n, kind, ctrl, tgt, c, s, G);
   for (uint32_t e = 0; e < N * N; ++e) {
     re[e] = G[e].re;
     im[e] = G[e].im;
@@ -275,7 +358,8 @@ static void matmul(uint32_t N, const cplx *A, const cplx *B, cplx *C) {
     }
 }
 
-static void compose_c(uint32_t n, uint32_t library, uint32_t L, const uint8_t *gates, cplx *S) {
+static void compose_c(uint32_t n, uint32_t library, uint32_t L, const uint8_t *gates,
+                      const float *amps, cplx *S) {
   uint32_t N = 1u << n;
   cplx *G = (cplx *)malloc(sizeof(cplx) * N * N);
   cplx *T = (cplx *)malloc(sizeof(cplx) * N * N);
@@ -287,7 +371,9 @@ static void compose_c(uint32_t n, uint32_t library, uint32_t L, const uint8_t *g
       for (uint32_t e = 0; e < N * N; ++e) S[e] = (cplx){NAN, NAN};
       break;
     }
-    dense_gate(n, kind, ctrl, tgt, G);
+    double c, s;
+    slot_angle(library, amps, t, &c, &s);
+    dense_gate(n, kind, ctrl, tgt, c, s, G);
     matmul(N, G, S, T); /* S <- G_t S */
     memcpy(S, T, sizeof(cplx) * N * N);
   }
@@ -297,9 +383,14 @@ static void compose_c(uint32_t n, uint32_t library, uint32_t L, const uint8_t *g
 
 void oracle_compose(uint32_t n, uint32_t library, uint32_t L, const uint8_t *gates, double *S_re,
                     double *S_im) {
+  oracle_compose_amp(n, library, L, gates, NULL, S_re, S_im);
+}
+
+void oracle_compose_amp(uint32_t n, uint32_t library, uint32_t L, const uint8_t *gates,
+                        const float *amps, double *S_re, double *S_im) {
   uint32_t N = 1u << n;
   cplx *S = (cplx *)malloc(sizeof(cplx) * N * N);
-  compose_c(n, library, L, gates, S);
+  compose_c(n, library, L, gates, amps, S);
   for (uint32_t e = 0; e < N * N; ++e) {
     S_re[e] = S[e].re;
     S_im[e] = S[e].im;
@@ -373,6 +464,12 @@ uint64_t oracle_useful_flops(uint32_t n, uint32_t library, uint32_t L, const uin
       case ORC_TDG:
         total += 2 * NN;
         break;
+      case ORC_RX: /* every amplitude: two real-by-complex products and a sum */
+      case ORC_RY:
+      case ORC_RZ: /* every amplitude: one complex product */
+      case ORC_J:
+        total += 6 * NN;
+        break;
       default:
         break;
     }
@@ -382,11 +479,16 @@ uint64_t oracle_useful_flops(uint32_t n, uint32_t library, uint32_t L, const uin
 
 void oracle_eval(const oracle_problem *p, const uint8_t *gates, uint32_t n_circuits, double *F,
                  uint32_t *cost) {
+  oracle_eval_amp(p, gates, NULL, n_circuits, F, cost);
+}
+
+void oracle_eval_amp(const oracle_problem *p, const uint8_t *gates, const float *amps,
+                     uint32_t n_circuits, double *F, uint32_t *cost) {
   uint32_t N = 1u << p->n;
   cplx *S = (cplx *)malloc(sizeof(cplx) * N * N);
   for (uint32_t c = 0; c < n_circuits; ++c) {
     const uint8_t *g = gates + (uint64_t)c * p->L;
-    compose_c(p->n, p->library, p->L, g, S);
+    compose_c(p->n, p->library, p->L, g, amps ? amps + (uint64_t)c * 2 * p->L : NULL, S);
     double f = score_c(p->n, S, p->perm, p->fitness_kind);
     uint32_t k = oracle_cost(p->n, p->library, p->L, g);
     double pen = p->cost_weight * ((double)k / (double)p->L);
@@ -428,8 +530,15 @@ void oracle_init_state(const oracle_problem *p, float *cur, float *best, float *
  * ====================================================================== */
 void oracle_sample(const oracle_problem *p, const float *cur, uint32_t gen, uint8_t *gate_idx,
                    uint32_t *seg_id) {
+  oracle_sample_amp(p, cur, gen, gate_idx, seg_id, NULL);
+}
+
+void oracle_sample_amp(const oracle_problem *p, const float *cur, uint32_t gen, uint8_t *gate_idx,
+                       uint32_t *seg_id, float *amps) {
   uint32_t R = oracle_num_regions(p->n, p->library);
-  int has_qubit = (p->library & ORC_LIB_IDENTITY) != 0;
+  /* discrete libraries with the identity: the qubit decides "gate present";
+     Ising: the qubit holds the angle and is not measured */
+  int has_qubit = (p->library & ORC_LIB_IDENTITY) != 0 && !is_ising(p->library);
   for (uint32_t c = 0; c < p->P; ++c)
     for (uint32_t t = 0; t < p->L; ++t) {
       uint32_t u[4];
@@ -457,6 +566,10 @@ void oracle_sample(const oracle_problem *p, const float *cur, uint32_t gen, uint
       }
       gate_idx[(uint64_t)c * p->L + t] = (uint8_t)g;
       seg_id[(uint64_t)c * p->L + t] = (uint32_t)seg;
+      if (amps) {
+        amps[2 * ((uint64_t)c * p->L + t)] = q[6];
+        amps[2 * ((uint64_t)c * p->L + t) + 1] = q[7];
+      }
     }
 }
 
@@ -654,7 +767,9 @@ void oracle_update(const oracle_problem *p, float *cur, float *best, float *best
                    const uint32_t *seg_id, const double *fitness) {
   uint64_t S = oracle_num_segments(p);
   uint32_t R = oracle_num_regions(p->n, p->library);
-  int has_qubit = (p->library & ORC_LIB_IDENTITY) != 0;
+  /* the qubit exists with the identity (gate present) and in the Ising
+     library (the angle); either may be mutated */
+  int has_qubit = (p->library & (ORC_LIB_IDENTITY | ORC_LIB_ISING)) != 0;
   float *sf = (float *)malloc(sizeof(float) * (S ? S : 1));
   uint8_t *touched = (uint8_t *)calloc(S ? S : 1, 1);
   /* segment fitness: a segment takes the fitness of the circuit that used it
@@ -730,8 +845,11 @@ void oracle_topk(const double *F, const uint32_t *cost, uint32_t n, uint32_t k, 
 void oracle_step(const oracle_problem *p, float *cur, float *best, float *best_f, uint32_t gen,
                  uint32_t topk, uint8_t *gate_idx, uint32_t *seg_id, double *F, uint32_t *cost,
                  uint32_t *topk_idx, oracle_report *rep) {
-  oracle_sample(p, cur, gen, gate_idx, seg_id);
-  oracle_eval(p, gate_idx, p->P, F, cost);
+  float *amps = NULL;
+  if (is_ising(p->library)) amps = (float *)malloc(sizeof(float) * 2 * (uint64_t)p->P * p->L);
+  oracle_sample_amp(p, cur, gen, gate_idx, seg_id, amps);
+  oracle_eval_amp(p, gate_idx, amps, p->P, F, cost);
+  free(amps);
   uint32_t k = topk ? topk : 1;
   uint32_t *tk = topk_idx;
   uint32_t local[1];

@@ -23,7 +23,17 @@
  *   - regions: one per ordered pair (qutrit picks CNOT/CV/CV^dag), then one per
  *     wire when H/T/T^dag are in the library (qutrit picks H/T/T^dag);
  *   - with the identity in the library every segment also carries a qubit
- *     whose outcome 1 means "gate present".
+ *     whose outcome 1 means "gate present";
+ *   - Ising library: regions = the n wires (the qutrit picks the axis x/y/z of
+ *     a rotation on that wire, Sec. IV-A) then the n(n-1)/2 wire pairs i < j
+ *     in lexicographic order (an interaction template); library index
+ *     3w + k = R_{x,y,z}(theta) on wire w, then 3n + pair = J on that pair;
+ *     the angle theta of a slot is the angle of the sampled segment's qubit
+ *     amplitudes (b0, b1) = (cos theta, sin theta), theta in [0, 2 pi), and
+ *     the gates take cos(theta/2) = sgn(b1) sqrt((1 + b0)/2),
+ *     sin(theta/2) = sqrt((1 - b0)/2) (sgn(b1) = -1 iff b1 < 0), binary64;
+ *     J(theta) = exp(-i theta/2 D) with D the +-1 template diagonal
+ *     z_i z_j (z = +1 for bit 0, -1 for bit 1).
  *
  * Measurement and mutation arithmetic is binary32 (the state's precision),
  * each operation rounded in the written order; the decision "x < cdf" is thus
@@ -50,6 +60,7 @@ extern "C" {
 #define ORC_LIB_NCV 1u
 #define ORC_LIB_HT 2u
 #define ORC_LIB_IDENTITY 4u
+#define ORC_LIB_ISING 8u /* the paper's own library (Sec. III, IV-A): alone, never mixed */
 
 /* gate kinds */
 #define ORC_I 0
@@ -59,6 +70,10 @@ extern "C" {
 #define ORC_H 4
 #define ORC_T 5
 #define ORC_TDG 6
+#define ORC_RX 7 /* Eq. (3) */
+#define ORC_RY 8 /* Eq. (4) */
+#define ORC_RZ 9 /* Eq. (5) */
+#define ORC_J 10 /* interaction template J_ij (Sec. III, IV-A) */
 
 /* fitness kinds */
 #define ORC_FIT_TRACE 0 /* Eq. (11) as printed: |tr(S^dag T)| */
@@ -93,7 +108,18 @@ uint32_t oracle_region_gate(uint32_t n, uint32_t library, uint32_t r, uint32_t k
 uint64_t oracle_segment_index(uint64_t r, uint64_t i, uint64_t t, uint64_t L, uint64_t P);
 uint64_t oracle_num_segments(const oracle_problem *p);
 
+/* ---- Ising angles: cos/sin of theta/2 from a slot's qubit amplitudes ---- */
+void oracle_half_angle(float b0, float b1, double *c, double *s);
+
 /* ---- gates, composition, score (Sec. III, IV-C, IV-E) ---- */
+/* The *_amp forms take, for the Ising library, the sampled qubit amplitudes
+   (b0, b1) of every slot (amps[2t], amps[2t+1]); the other libraries ignore
+   them (amps may be NULL).  The forms without amps are the discrete-library
+   calls (an Ising gate without an angle yields NaN). */
+void oracle_gate_matrix_amp(uint32_t n, uint32_t library, uint32_t g, float b0, float b1,
+                            double *re, double *im);
+void oracle_compose_amp(uint32_t n, uint32_t library, uint32_t L, const uint8_t *gates,
+                        const float *amps, double *S_re, double *S_im);
 /* dense N x N complex matrix of library gate g, row-major, re/im planes */
 void oracle_gate_matrix(uint32_t n, uint32_t library, uint32_t g, double *re, double *im);
 /* S = G_{L-1} ... G_0 for one circuit */
@@ -106,6 +132,9 @@ uint32_t oracle_cost(uint32_t n, uint32_t library, uint32_t L, const uint8_t *ga
 /* F[c] = f(S_c) - lambda*cost_c/L for n_circuits circuits gates[c*L + t] */
 void oracle_eval(const oracle_problem *p, const uint8_t *gates, uint32_t n_circuits, double *F,
                  uint32_t *cost);
+/* the same with each circuit's slot amplitudes at amps + c*2L */
+void oracle_eval_amp(const oracle_problem *p, const uint8_t *gates, const float *amps,
+                     uint32_t n_circuits, double *F, uint32_t *cost);
 /* useful real ops of one circuit (gate-count model, see design notes) */
 uint64_t oracle_useful_flops(uint32_t n, uint32_t library, uint32_t L, const uint8_t *gates);
 
@@ -115,6 +144,9 @@ void oracle_init_state(const oracle_problem *p, float *cur, float *best, float *
 /* ---- circuit construction by measurement (Sec. IV-D, Eq. (10)) ---- */
 void oracle_sample(const oracle_problem *p, const float *cur, uint32_t gen, uint8_t *gate_idx,
                    uint32_t *seg_id);
+/* the same, also writing every slot's qubit amplitudes (2 floats per slot) to amps */
+void oracle_sample_amp(const oracle_problem *p, const float *cur, uint32_t gen, uint8_t *gate_idx,
+                       uint32_t *seg_id, float *amps);
 
 /* ---- segment fitness, elitism, adaptive mutation (Sec. IV-E1, IV-F) ---- */
 void oracle_update(const oracle_problem *p, float *cur, float *best, float *best_f, uint32_t gen,
