@@ -65,6 +65,19 @@ typedef enum {
 #define QE_LIB_NCV 1u
 #define QE_LIB_HT 2u
 #define QE_LIB_IDENTITY 4u
+/* The paper's own library (Sec. III Eqs. (3)-(5), Sec. IV-A), used alone:
+ * regions = the n wires (the qutrit picks the rotation axis x/y/z on that
+ * wire), then the n(n-1)/2 wire pairs i < j in lexicographic order (an
+ * interaction template J_ij).  Library index 3w + k is R_{x,y,z} on wire w,
+ * 3n + q is J on pair q: G = 3n + n(n-1)/2.  A slot's angle theta is the angle
+ * of the sampled segment's qubit amplitudes (b0, b1) = (cos theta,
+ * sin theta), theta in [0, 2 pi) (the qubit is not measured), and the gates
+ * use cos(theta/2) = sgn(b1) sqrt((1 + b0)/2), sin(theta/2) = sqrt((1 - b0)/2)
+ * (sgn(b1) = -1 iff b1 < 0); J(theta) = exp(-i theta/2 Z_i Z_j).  The qubit
+ * mutation turns theta by +-(1 - f) mutationRange (Sec. IV-F).  QEQEA
+ * encoding only; circuits given by the caller carry their angles as such
+ * amplitude pairs (qe_eval_amp, qe_compose_amp). */
+#define QE_LIB_ISING 8u
 
 /* arithmetic of the composition */
 #define QE_PREC_FP64 0u     /* binary64, fixed operation order: bit-identical to the oracle */
@@ -180,6 +193,16 @@ qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
 qe_status qe_compose(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_t n_circuits,
                      void *d_unitary);
 
+/* qe_eval / qe_compose for the Ising library: d_amps[2*(c*L + t) + {0,1}] are
+ * the qubit amplitudes (b0, b1) = (cos theta, sin theta) that give slot t of
+ * circuit c its angle (see QE_LIB_ISING); float, caller-owned DEVICE memory.
+ * For the other libraries d_amps is ignored.  qe_eval, qe_eval_host and
+ * qe_compose return QE_EINVAL for an Ising search. */
+qe_status qe_eval_amp(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, const float *d_amps,
+                      uint32_t n_circuits, void *d_fitness, uint32_t *d_cost, qe_ranked *h_topk);
+qe_status qe_compose_amp(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx,
+                         const float *d_amps, uint32_t n_circuits, void *d_unitary);
+
 /* Segment fitness, elitism and adaptive mutation (Sec. IV-E1, IV-F) of search
  * prob at generation gen, given the d_seg_id[P*L] of that generation's
  * circuits and their d_fitness[P] (double).  A pure function of (state, seed,
@@ -271,7 +294,8 @@ qe_status qe_generation(const qe_ctx *ctx, uint32_t *gen);
  * d_fitness (float, or double for QE_PREC_FP64; the same arithmetic as
  * qe_eval) and, if d_topk is not NULL, the best min(max(topk,1), n_circuits)
  * circuits rescored in binary64 and sorted by (fitness desc, cost asc, index
- * asc) to the DEVICE array d_topk.  All work is enqueued on cuda_stream; the
+ * asc) to the DEVICE array d_topk.  Discrete libraries only (QE_LIB_ISING is
+ * QE_EINVAL here).  All work is enqueued on cuda_stream; the
  * call does not synchronise.  Scratch comes from one static device array of
  * the library (about 1.25 MiB, held by every GPU that loads the library until
  * the process exits), so n_circuits is limited to 65536 (QE_EINVAL above it)

@@ -21,6 +21,7 @@ thread_local std::string g_init_error;
 
 struct Group {
   bool canon = false;
+  bool ising = false;  // the Ising library (slots carry angles)
   uint32_t n = 0;  // qubit count of every search in the group
   std::vector<uint32_t> ids;
   uint32_t *d_ids = nullptr, *d_prefix = nullptr;
@@ -53,7 +54,8 @@ struct qe_ctx {
   void *arena = nullptr;
   size_t arena_bytes = 0;
   std::vector<Group> groups;  // circuit launches, one per (arithmetic, qubit count)
-  bool rescore_nq[QE_MAX_QUBITS + 1] = {false};  // widths with binary32 searches
+  // widths with binary32 searches: bit 0 discrete libraries, bit 1 Ising
+  uint8_t rescore_nq[QE_MAX_QUBITS + 1] = {0};
   // all QEQEA searches (update launch)
   uint32_t n_upd = 0, upd_totalA = 0, upd_totalB = 0;
   uint32_t *d_upd_ids = nullptr, *d_upd_prefA = nullptr, *d_upd_prefB = nullptr;
@@ -106,6 +108,7 @@ qe_status cuda_fail(qe_ctx *ctx, cudaError_t e, const char *what) {
   } while (0)
 
 uint32_t regions(uint32_t n, uint32_t lib) {
+  if (lib == QE_LIB_ISING) return n + n * (n - 1) / 2;
   uint32_t r = 0;
   if (lib & QE_LIB_NCV) r += n * (n - 1);
   if (lib & QE_LIB_HT) r += n;
@@ -113,12 +116,19 @@ uint32_t regions(uint32_t n, uint32_t lib) {
 }
 
 uint32_t gates(uint32_t n, uint32_t lib) {
+  if (lib == QE_LIB_ISING) return 3u * n + n * (n - 1) / 2;
   return ((lib & QE_LIB_IDENTITY) ? 1u : 0u) + 3u * regions(n, lib);
 }
 
 // op byte of every library index (see k_circuit.cu for the op numbering)
 void build_ops(uint32_t n, uint32_t lib, uint8_t *gop) {
   uint32_t g = 0;
+  if (lib == QE_LIB_ISING) {
+    for (uint32_t w = 0; w < n; ++w)
+      for (uint32_t k = 0; k < 3; ++k) gop[g++] = (uint8_t)(kOpIsingRot + 3 * w + k);
+    for (uint32_t q = 0; q < n * (n - 1) / 2; ++q) gop[g++] = (uint8_t)(kOpIsingJ + q);
+    return;
+  }
   if (lib & QE_LIB_IDENTITY) gop[g++] = kOpIdentity;
   if (lib & QE_LIB_NCV)
     for (uint32_t c = 0; c < n; ++c)
@@ -148,7 +158,10 @@ qe_status validate(const qe_problem &p, uint32_t idx) {
   if (p.n_qubits < 1 || p.n_qubits > QE_MAX_QUBITS) return bad("n_qubits must be 1..5");
   if (p.circuit_len < 1 || p.circuit_len > QE_MAX_LEN) return bad("circuit_len must be 1..64");
   if (p.population < 1 || p.population > QE_MAX_POP) return bad("population must be 1..2^20");
-  if (p.library & ~(QE_LIB_NCV | QE_LIB_HT | QE_LIB_IDENTITY)) return bad("unknown library bits");
+  if (p.library & ~(QE_LIB_NCV | QE_LIB_HT | QE_LIB_IDENTITY | QE_LIB_ISING))
+    return bad("unknown library bits");
+  if ((p.library & QE_LIB_ISING) && p.library != QE_LIB_ISING)
+    return bad("QE_LIB_ISING is used alone");
   const uint32_t R = regions(p.n_qubits, p.library);
   if (R == 0) return bad("library has no gates for this n_qubits");
   if (p.encoding > QE_ENC_GA) return bad("unknown encoding");
@@ -169,6 +182,10 @@ qe_status validate(const qe_problem &p, uint32_t idx) {
     const uint32_t v = p.target_perm[j];
     if (v >= N || seen[v]) return bad("target_perm is not a permutation of 0..2^n-1");
     seen[v] = true;
+  }
+  if (p.library == QE_LIB_ISING && p.encoding == QE_ENC_GA) {
+    snprintf(b, sizeof b, "problem %u: the GA runs on the discrete libraries only", idx);
+    return fail(nullptr, QE_EUNSUPPORTED, b);
   }
   if (p.precision == QE_PREC_SPLIT_TC) {
     snprintf(b, sizeof b,
@@ -337,8 +354,9 @@ cudaError_t enqueue_rank_chain(qe_ctx *ctx, cudaStream_t cs) {
   RankJob none{};
   cudaError_t e = launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, none, ctx->g, cs);
   for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
-    if (e == cudaSuccess && ctx->rescore_nq[nq])
-      e = launch_rescore(ctx->lc, nq, ctx->d_probs, nullptr, true, ctx->g, cs);
+    for (int is = 0; is < 2; ++is)
+      if (e == cudaSuccess && ((ctx->rescore_nq[nq] >> is) & 1))
+        e = launch_rescore(ctx->lc, nq, is == 1, ctx->d_probs, nullptr, nullptr, true, ctx->g, cs);
   if (e == cudaSuccess)
     e = launch_rank_sort(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, none, ctx->g, cs);
   return e;
@@ -373,7 +391,7 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
     if (conc && k > 0 && e == cudaSuccess) e = cudaStreamWaitEvent(gs, ctx->gfork, 0);
     if (e == cudaSuccess)
       e = launch_step(lc, gr.n, ctx->d_probs, gr.d_ids, gr.d_prefix,
-                      (uint32_t)gr.ids.size(), gr.total, gr.canon, ctx->g, gs);
+                      (uint32_t)gr.ids.size(), gr.total, gr.canon, gr.ising, ctx->g, gs);
     if (conc && k > 0 && e == cudaSuccess) e = cudaEventRecord(ctx->gjoin[k - 1], gs);
   }
   for (size_t k = 1; conc && k < ctx->groups.size(); ++k)
@@ -395,8 +413,9 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
   if (e == cudaSuccess) e = launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, RankJob{}, ctx->g, cs);
   mark(2, cs);
   for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
-    if (e == cudaSuccess && ctx->rescore_nq[nq])
-      e = launch_rescore(ctx->lc, nq, ctx->d_probs, nullptr, true, ctx->g, cs);
+    for (int is = 0; is < 2; ++is)
+      if (e == cudaSuccess && ((ctx->rescore_nq[nq] >> is) & 1))
+        e = launch_rescore(ctx->lc, nq, is == 1, ctx->d_probs, nullptr, nullptr, true, ctx->g, cs);
   mark(3, cs);
   if (e == cudaSuccess) e = launch_rank_sort(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, RankJob{}, ctx->g, cs);
   mark(4, cs);
@@ -478,7 +497,8 @@ extern "C" {
 qe_status qe_library_info(uint32_t n_qubits, uint32_t library, uint32_t *n_gates,
                           uint32_t *n_regions) {
   if (n_qubits < 1 || n_qubits > QE_MAX_QUBITS) return QE_EINVAL;
-  if (library & ~(QE_LIB_NCV | QE_LIB_HT | QE_LIB_IDENTITY)) return QE_EINVAL;
+  if (library & ~(QE_LIB_NCV | QE_LIB_HT | QE_LIB_IDENTITY | QE_LIB_ISING)) return QE_EINVAL;
+  if ((library & QE_LIB_ISING) && library != QE_LIB_ISING) return QE_EINVAL;
   if (n_gates) *n_gates = gates(n_qubits, library);
   if (n_regions) *n_regions = regions(n_qubits, library);
   return QE_OK;
@@ -567,8 +587,12 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     d.topk = q.topk;
     d.k = q.topk ? q.topk : 1;
     d.run = i;
-    d.has_qubit = (q.library & QE_LIB_IDENTITY) ? 1u : 0u;
-    d.base = d.has_qubit;
+    // the qubit exists with the identity (gate present, measured) and in the
+    // Ising library (the angle, not measured); either may be mutated
+    d.has_qubit = (q.library & (QE_LIB_IDENTITY | QE_LIB_ISING)) ? 1u : 0u;
+    d.measure_qubit = (q.library & QE_LIB_IDENTITY) ? 1u : 0u;
+    d.ising = q.library == QE_LIB_ISING ? 1u : 0u;
+    d.base = d.measure_qubit;
     d.key0 = (uint32_t)q.seed;
     d.key1 = (uint32_t)(q.seed >> 32);
     d.eps_d = eps_d_for(d.L);
@@ -590,6 +614,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
       ar.take(&d.qubit_tab, (kQ + 1) * sizeof(float2));
       ar.take(&d.mut_list, 2 * P * 4);
       ar.take(&d.mut_cnt, 2 * 4);
+      if (d.ising) ar.take(&d.amps, 2 * PL * sizeof(float2));
     } else {
       ar.take(&d.ga_cum, P * 8);
       ar.take(&d.ga_info, 16);
@@ -622,24 +647,28 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   ar.take(&ctx->d_single, n_probs * 5 * 4);
   ar.take(&ctx->d_stage_gates, max_PL);
   ar.take(&ctx->d_stage_fit, max_P * 8);
-  // groups: searches by (arithmetic, qubit count), widest first
+  // groups: searches by (arithmetic, library kind, qubit count), widest first
   std::vector<uint32_t> upd, ga;
   for (int k = 0; k < 2; ++k)
-    for (uint32_t nq = QE_MAX_QUBITS; nq >= 1; --nq) {
-      Group gr;
-      gr.canon = k == 1;
-      gr.n = nq;
-      for (uint32_t i = 0; i < n_probs; ++i) {
-        if (probs[i].n_qubits != nq) continue;
-        if ((probs[i].precision == QE_PREC_FP64) != gr.canon) continue;
-        gr.ids.push_back(i);
+    for (int is = 0; is < 2; ++is)
+      for (uint32_t nq = QE_MAX_QUBITS; nq >= 1; --nq) {
+        Group gr;
+        gr.canon = k == 1;
+        gr.ising = is == 1;
+        gr.n = nq;
+        for (uint32_t i = 0; i < n_probs; ++i) {
+          if (probs[i].n_qubits != nq) continue;
+          if ((probs[i].precision == QE_PREC_FP64) != gr.canon) continue;
+          if ((probs[i].library == QE_LIB_ISING) != gr.ising) continue;
+          gr.ids.push_back(i);
+        }
+        if (!gr.ids.empty()) ctx->groups.push_back(gr);
       }
-      if (!gr.ids.empty()) ctx->groups.push_back(gr);
-    }
   for (uint32_t i = 0; i < n_probs; ++i) {
     if (probs[i].encoding == QE_ENC_QEQEA) upd.push_back(i);
     else ga.push_back(i);
-    if (probs[i].precision != QE_PREC_FP64) ctx->rescore_nq[probs[i].n_qubits] = true;
+    if (probs[i].precision != QE_PREC_FP64)
+      ctx->rescore_nq[probs[i].n_qubits] |= probs[i].library == QE_LIB_ISING ? 2 : 1;
   }
   for (auto &gr : ctx->groups) {
     ar.take(&gr.d_ids, gr.ids.size() * 4);
@@ -829,7 +858,8 @@ qe_status qe_sample(qe_ctx *ctx, uint32_t prob, uint32_t gen, uint8_t *d_gate_id
 }
 
 static qe_status rank_single(qe_ctx *ctx, uint32_t prob, uint32_t n, const void *fit,
-                             const uint32_t *meta, const uint8_t *gsrc, qe_ranked *h_topk) {
+                             const uint32_t *meta, const uint8_t *gsrc, const float2 *asrc,
+                             qe_ranked *h_topk) {
   const DevProblem &d = ctx->hp[prob];
   RankJob j{};
   j.prob = prob;
@@ -842,7 +872,8 @@ static qe_status rank_single(qe_ctx *ctx, uint32_t prob, uint32_t n, const void 
   QE_CUDA(ctx, launch_reset_counter(ctx->g, us));
   QE_CUDA(ctx, launch_rank_select(ctx->d_probs, nullptr, 1, j, ctx->g, us));
   if (d.prec != QE_PREC_FP64)
-    QE_CUDA(ctx, launch_rescore(ctx->lc, d.n, ctx->d_probs, gsrc, false, ctx->g, us));
+    QE_CUDA(ctx, launch_rescore(ctx->lc, d.n, d.ising != 0, ctx->d_probs, gsrc, asrc, false,
+                                ctx->g, us));
   QE_CUDA(ctx, launch_rank_sort(ctx->d_probs, nullptr, 1, j, ctx->g, us));
   QE_CUDA(ctx, launch_reset_counter(ctx->g, us));
   const uint32_t k = d.k < n ? d.k : n;
@@ -866,12 +897,15 @@ static qe_status rank_single(qe_ctx *ctx, uint32_t prob, uint32_t n, const void 
   return QE_OK;
 }
 
-qe_status qe_eval(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_t n_circuits,
-                  void *d_fitness, uint32_t *d_cost, qe_ranked *h_topk) {
+static qe_status eval_impl(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx,
+                           const float2 *d_amps, uint32_t n_circuits, void *d_fitness,
+                           uint32_t *d_cost, qe_ranked *h_topk) {
   qe_status st = check_ctx(ctx, prob);
   if (st != QE_OK) return st;
   const DevProblem &d = ctx->hp[prob];
   if (!d_fitness || (n_circuits && !d_gate_idx)) return fail(ctx, QE_EINVAL, "null buffer");
+  if (d.ising && n_circuits && !d_amps)
+    return fail(ctx, QE_EINVAL, "Ising circuits need their angles (qe_eval_amp)");
   if (n_circuits > (1u << 24)) return fail(ctx, QE_EINVAL, "n_circuits must be <= 2^24");
   if (h_topk && n_circuits > d.P)
     return fail(ctx, QE_EINVAL, "ranking needs n_circuits <= population");
@@ -880,10 +914,22 @@ qe_status qe_eval(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_
     if (st != QE_OK) return st;
   }
   uint32_t *cost = d_cost ? d_cost : (h_topk ? d.meta : nullptr);
+  const float2 *amps = d.ising ? d_amps : nullptr;
   QE_CUDA(ctx, launch_eval(ctx->lc, d.n, ctx->d_probs, prob, d.prec == QE_PREC_FP64, d_gate_idx,
-                           n_circuits, d_fitness, cost, nullptr, ctx->g, ctx->user));
+                           amps, n_circuits, d_fitness, cost, nullptr, ctx->g, ctx->user));
   if (!h_topk || n_circuits == 0) return QE_OK;
-  return rank_single(ctx, prob, n_circuits, d_fitness, cost, d_gate_idx, h_topk);
+  return rank_single(ctx, prob, n_circuits, d_fitness, cost, d_gate_idx, amps, h_topk);
+}
+
+qe_status qe_eval(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_t n_circuits,
+                  void *d_fitness, uint32_t *d_cost, qe_ranked *h_topk) {
+  return eval_impl(ctx, prob, d_gate_idx, nullptr, n_circuits, d_fitness, d_cost, h_topk);
+}
+
+qe_status qe_eval_amp(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, const float *d_amps,
+                      uint32_t n_circuits, void *d_fitness, uint32_t *d_cost, qe_ranked *h_topk) {
+  return eval_impl(ctx, prob, d_gate_idx, (const float2 *)d_amps, n_circuits, d_fitness, d_cost,
+                   h_topk);
 }
 
 qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
@@ -893,6 +939,7 @@ qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
   const DevProblem &d = ctx->hp[prob];
   if (!h_fitness || (n_circuits && !h_gate_idx)) return fail(ctx, QE_EINVAL, "null buffer");
   if (n_circuits > d.P) return fail(ctx, QE_EINVAL, "n_circuits must be <= population");
+  if (d.ising) return fail(ctx, QE_EINVAL, "Ising circuits need their angles (qe_eval_amp)");
   const size_t fb = d.prec == QE_PREC_FP64 ? 8 : 4;
   cudaStream_t us = ctx->user;
   st = drain(ctx);
@@ -900,10 +947,11 @@ qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
   QE_CUDA(ctx, cudaMemcpyAsync(ctx->d_stage_gates, h_gate_idx, (size_t)n_circuits * d.L,
                                cudaMemcpyHostToDevice, us));
   QE_CUDA(ctx, launch_eval(ctx->lc, d.n, ctx->d_probs, prob, d.prec == QE_PREC_FP64,
-                           ctx->d_stage_gates, n_circuits, ctx->d_stage_fit, d.meta, nullptr,
-                           ctx->g, us));
+                           ctx->d_stage_gates, nullptr, n_circuits, ctx->d_stage_fit, d.meta,
+                           nullptr, ctx->g, us));
   if (h_topk && n_circuits) {
-    st = rank_single(ctx, prob, n_circuits, ctx->d_stage_fit, d.meta, ctx->d_stage_gates, h_topk);
+    st = rank_single(ctx, prob, n_circuits, ctx->d_stage_fit, d.meta, ctx->d_stage_gates, nullptr,
+                     h_topk);
     if (st != QE_OK && st != QE_ENUMERIC) return st;
   }
   QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, ctx->d_stage_fit, n_circuits * fb,
@@ -912,16 +960,29 @@ qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
   return st;
 }
 
-qe_status qe_compose(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_t n_circuits,
-                     void *d_unitary) {
+static qe_status compose_impl(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx,
+                              const float2 *d_amps, uint32_t n_circuits, void *d_unitary) {
   qe_status st = check_ctx(ctx, prob);
   if (st != QE_OK) return st;
   const DevProblem &d = ctx->hp[prob];
   if (!d_unitary || (n_circuits && !d_gate_idx)) return fail(ctx, QE_EINVAL, "null buffer");
   if (n_circuits > (1u << 20)) return fail(ctx, QE_EINVAL, "n_circuits must be <= 2^20");
+  if (d.ising && n_circuits && !d_amps)
+    return fail(ctx, QE_EINVAL, "Ising circuits need their angles (qe_compose_amp)");
   QE_CUDA(ctx, launch_eval(ctx->lc, d.n, ctx->d_probs, prob, d.prec == QE_PREC_FP64, d_gate_idx,
-                           n_circuits, nullptr, nullptr, d_unitary, ctx->g, ctx->user));
+                           d.ising ? d_amps : nullptr, n_circuits, nullptr, nullptr, d_unitary,
+                           ctx->g, ctx->user));
   return QE_OK;
+}
+
+qe_status qe_compose(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_t n_circuits,
+                     void *d_unitary) {
+  return compose_impl(ctx, prob, d_gate_idx, nullptr, n_circuits, d_unitary);
+}
+
+qe_status qe_compose_amp(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx,
+                         const float *d_amps, uint32_t n_circuits, void *d_unitary) {
+  return compose_impl(ctx, prob, d_gate_idx, (const float2 *)d_amps, n_circuits, d_unitary);
 }
 
 qe_status qe_update(qe_ctx *ctx, uint32_t prob, uint32_t gen, const uint32_t *d_seg_id,

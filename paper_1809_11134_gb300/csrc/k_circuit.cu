@@ -24,7 +24,7 @@
 
 namespace qe {
 
-enum Kind { kCnot = 0, kCvx = 1, kHad = 2, kTx = 3 };
+enum Kind { kCnot = 0, kCvx = 1, kHad = 2, kTx = 3, kRx = 4, kRy = 5, kRz = 6, kJzz = 7 };
 
 // ------------------------------------------------------------------ arithmetic
 template <typename R, bool CANON>
@@ -67,6 +67,26 @@ struct Ar<float, false> {
     const float r = yr, i = yi;
     yr = kH32 * fmaf(-s, i, r);
     yi = kH32 * fmaf(s, r, i);
+  }
+  // Ising rotations (Eqs. (3)-(5)) with c = cos(theta/2), s = sin(theta/2):
+  // the new value of row m given the partner row p; up = this row's target bit
+  static __device__ __forceinline__ void rx_lane(float &mr, float &mi, float pr, float pi,
+                                                 float c, float s) {
+    const float r = mr, i = mi;  // c m - i s p
+    mr = fmaf(s, pi, c * r);
+    mi = fmaf(-s, pr, c * i);
+  }
+  static __device__ __forceinline__ void ry_lane(float &mr, float &mi, float pr, float pi,
+                                                 bool up, float c, float s) {
+    const float t = up ? s : -s;  // row 0: c m - s p; row 1: s p + c m
+    mr = fmaf(t, pr, c * mr);
+    mi = fmaf(t, pi, c * mi);
+  }
+  // m <- (c - i d s) m, d = +-1 (R_z: d = +1 on target bit 0; J: d = z_i z_j)
+  static __device__ __forceinline__ void phase(float &mr, float &mi, float c, float ds) {
+    const float r = mr, i = mi;
+    mr = fmaf(ds, i, c * r);
+    mi = fmaf(-ds, r, c * i);
   }
 };
 
@@ -115,6 +135,30 @@ struct Ar<double, true> {
     const double hr = __dmul_rn(kH64, yr), hi = __dmul_rn(kH64, yi);
     yr = __fma_rn(-s, hi, hr);
     yi = __fma_rn(s, hr, hi);
+  }
+  // Ising rotations, the dense product's two nonzero terms per row: each
+  // complex product (a.re b.re - a.im b.im, a.re b.im + a.im b.re) has one
+  // zero coefficient part, so it is one rounded product per component; the
+  // row sum adds the two terms (order-free: two addends)
+  static __device__ __forceinline__ void rx_lane(double &mr, double &mi, double pr, double pi,
+                                                 double c, double s) {
+    // c m + (-i s) p = (c mr + s pi, c mi - s pr)
+    const double r = mr, i = mi;
+    mr = __dadd_rn(__dmul_rn(c, r), __dmul_rn(s, pi));
+    mi = __dadd_rn(__dmul_rn(c, i), __dmul_rn(-s, pr));
+  }
+  static __device__ __forceinline__ void ry_lane(double &mr, double &mi, double pr, double pi,
+                                                 bool up, double c, double s) {
+    // row 0: c m + (-s) p; row 1: s p + c m
+    const double t = up ? s : -s;
+    mr = __dadd_rn(__dmul_rn(c, mr), __dmul_rn(t, pr));
+    mi = __dadd_rn(__dmul_rn(c, mi), __dmul_rn(t, pi));
+  }
+  // m <- (c, -d s) m, one term: (c mr - (-d s) mi, c mi + (-d s) mr)
+  static __device__ __forceinline__ void phase(double &mr, double &mi, double c, double ds) {
+    const double gi = -ds, r = mr, i = mi;
+    mr = __dsub_rn(__dmul_rn(c, r), __dmul_rn(gi, i));
+    mi = __dadd_rn(__dmul_rn(c, i), __dmul_rn(gi, r));
   }
 };
 
@@ -201,6 +245,75 @@ __device__ __forceinline__ void apply_gate(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<N
   }
 }
 
+// Ising gate of kind R_x / R_y / R_z on wire TW, or the interaction template on
+// wires (WI, TW); c = cos(theta/2), s = sin(theta/2) of the slot
+template <int NQ, typename R, bool CANON, int KIND, int WI, int TW>
+__device__ __forceinline__ void apply_ising(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>::ROWS],
+                                            int lane, R c, R s) {
+  using Ly = Lay<NQ>;
+  using A = Ar<R, CANON>;
+  constexpr int tb = NQ - 1 - TW;  // row bit of wire TW
+  constexpr bool T_REG = tb < Ly::RBR;
+  if constexpr (KIND == kRz || KIND == kJzz) {
+    // diagonal: row i takes (c - i d s), d = +1 where the wire's bit is 0 (R_z),
+    // d = z_i z_j (J)
+    constexpr int ib = KIND == kJzz ? NQ - 1 - WI : 0;
+    constexpr bool I_REG = ib < Ly::RBR;
+    int lt = 0, li = 0;
+    if constexpr (!T_REG) lt = (lane >> (NQ + tb - Ly::RBR)) & 1;
+    if constexpr (KIND == kJzz && !I_REG) li = (lane >> (NQ + ib - Ly::RBR)) & 1;
+#pragma unroll
+    for (int r = 0; r < Ly::ROWS; ++r) {
+      const int bt = T_REG ? ((r >> tb) & 1) : lt;
+      int odd = bt;
+      if constexpr (KIND == kJzz) odd ^= I_REG ? ((r >> ib) & 1) : li;
+      A::phase(re[r], im[r], c, odd ? -s : s);
+    }
+  } else if constexpr (T_REG) {
+#pragma unroll
+    for (int r0 = 0; r0 < Ly::ROWS; ++r0) {
+      if ((r0 >> tb) & 1) continue;
+      const int r1 = r0 | (1 << tb);
+      R xr = re[r0], xi = im[r0], yr = re[r1], yi = im[r1];
+      if constexpr (KIND == kRx) {
+        A::rx_lane(re[r0], im[r0], yr, yi, c, s);
+        A::rx_lane(re[r1], im[r1], xr, xi, c, s);
+      } else {
+        A::ry_lane(re[r0], im[r0], yr, yi, false, c, s);
+        A::ry_lane(re[r1], im[r1], xr, xi, true, c, s);
+      }
+    }
+  } else {
+    constexpr int tl = NQ + tb - Ly::RBR;  // lane bit of the target
+    const bool up = (lane >> tl) & 1;
+#pragma unroll
+    for (int r = 0; r < Ly::ROWS; ++r) {
+      const R pr = __shfl_xor_sync(kFull, re[r], 1 << tl);
+      const R pi = __shfl_xor_sync(kFull, im[r], 1 << tl);
+      if constexpr (KIND == kRx) A::rx_lane(re[r], im[r], pr, pi, c, s);
+      else A::ry_lane(re[r], im[r], pr, pi, up, c, s);
+    }
+  }
+}
+
+// wires of interaction template q (pairs i < j, lexicographic)
+constexpr int jpair_i(int nq, int q) {
+  int i = 0;
+  while (i < nq && q >= nq - 1 - i) {
+    q -= nq - 1 - i;
+    ++i;
+  }
+  return i;
+}
+constexpr int jpair_j(int nq, int q) {
+  int i = 0;
+  while (i < nq && q >= nq - 1 - i) {
+    q -= nq - 1 - i;
+    ++i;
+  }
+  return i + 1 + q;
+}
+
 constexpr int pair_ctrl(int nq, int pr) { return nq > 1 ? pr / (nq - 1) : 0; }
 constexpr int pair_tgt(int nq, int pr) {
   return nq > 1 ? ((pr % (nq - 1)) >= pair_ctrl(nq, pr) ? (pr % (nq - 1)) + 1 : (pr % (nq - 1)))
@@ -209,9 +322,15 @@ constexpr int pair_tgt(int nq, int pr) {
 
 template <int NQ, typename R, bool CANON, int OP>
 __device__ __forceinline__ void apply_op(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>::ROWS], int lane,
-                                         R s) {
+                                         R s, R ic, R is) {
   constexpr int NP = NQ * (NQ - 1);
-  if constexpr (OP < 2 * NP) {
+  if constexpr (OP >= kOpIsingJ) {
+    constexpr int q = OP - kOpIsingJ;
+    apply_ising<NQ, R, CANON, kJzz, jpair_i(NQ, q), jpair_j(NQ, q)>(re, im, lane, ic, is);
+  } else if constexpr (OP >= kOpIsingRot) {
+    constexpr int w = (OP - kOpIsingRot) / 3, k = (OP - kOpIsingRot) % 3;
+    apply_ising<NQ, R, CANON, k == 0 ? kRx : (k == 1 ? kRy : kRz), 0, w>(re, im, lane, ic, is);
+  } else if constexpr (OP < 2 * NP) {
     constexpr int pr = OP >> 1;
     apply_gate<NQ, R, CANON, (OP & 1) ? kCvx : kCnot, pair_ctrl(NQ, pr), pair_tgt(NQ, pr)>(
         re, im, lane, s);
@@ -221,14 +340,27 @@ __device__ __forceinline__ void apply_op(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>
   }
 }
 
+// a kernel compiles either the discrete ops or the Ising ops (ISING)
 #define QE_CASE(k)                                                      \
   case k:                                                               \
-    if constexpr ((k) < 2 * NQ * NQ) apply_op<NQ, R, CANON, (k)>(re, im, lane, s); \
+    if constexpr (!ISING && (k) < 2 * NQ * NQ)                          \
+      apply_op<NQ, R, CANON, (k)>(re, im, lane, s, ic, is);             \
+    break;
+// Ising rotations exist for wires < NQ, templates for pairs < NQ (NQ - 1) / 2
+#define QE_ICASE(k)                                                     \
+  case kOpIsingRot + (k):                                               \
+    if constexpr (ISING && (k) < 3 * NQ)                                \
+      apply_op<NQ, R, CANON, kOpIsingRot + (k)>(re, im, lane, s, ic, is); \
+    break;
+#define QE_JCASE(k)                                                     \
+  case kOpIsingJ + (k):                                                 \
+    if constexpr (ISING && (k) < NQ * (NQ - 1) / 2)                     \
+      apply_op<NQ, R, CANON, kOpIsingJ + (k)>(re, im, lane, s, ic, is); \
     break;
 
-template <int NQ, typename R, bool CANON>
+template <int NQ, typename R, bool CANON, bool ISING>
 __device__ __forceinline__ void dispatch(int op, R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>::ROWS],
-                                         int lane, R s) {
+                                         int lane, R s, R ic, R is) {
   switch (op) {
     QE_CASE(0) QE_CASE(1) QE_CASE(2) QE_CASE(3) QE_CASE(4) QE_CASE(5) QE_CASE(6) QE_CASE(7)
     QE_CASE(8) QE_CASE(9) QE_CASE(10) QE_CASE(11) QE_CASE(12) QE_CASE(13) QE_CASE(14)
@@ -237,11 +369,18 @@ __device__ __forceinline__ void dispatch(int op, R (&re)[Lay<NQ>::ROWS], R (&im)
     QE_CASE(29) QE_CASE(30) QE_CASE(31) QE_CASE(32) QE_CASE(33) QE_CASE(34) QE_CASE(35)
     QE_CASE(36) QE_CASE(37) QE_CASE(38) QE_CASE(39) QE_CASE(40) QE_CASE(41) QE_CASE(42)
     QE_CASE(43) QE_CASE(44) QE_CASE(45) QE_CASE(46) QE_CASE(47) QE_CASE(48) QE_CASE(49)
+    QE_ICASE(0) QE_ICASE(1) QE_ICASE(2) QE_ICASE(3) QE_ICASE(4) QE_ICASE(5) QE_ICASE(6)
+    QE_ICASE(7) QE_ICASE(8) QE_ICASE(9) QE_ICASE(10) QE_ICASE(11) QE_ICASE(12) QE_ICASE(13)
+    QE_ICASE(14)
+    QE_JCASE(0) QE_JCASE(1) QE_JCASE(2) QE_JCASE(3) QE_JCASE(4) QE_JCASE(5) QE_JCASE(6)
+    QE_JCASE(7) QE_JCASE(8) QE_JCASE(9)
     default:
       break;
   }
 }
 #undef QE_CASE
+#undef QE_ICASE
+#undef QE_JCASE
 
 // ------------------------------------------------------------------ 5 qubits: target at bit 0
 // With n = 5 a lane holds a whole column (32 rows, all in registers).  A switch
@@ -271,15 +410,36 @@ __device__ __forceinline__ void swap_bit0(float (&re)[32], float (&im)[32]) {
   }
 }
 
-// gate of kind K on target bit 0, control at bit CB (-1: none)
+// gate of kind K on target bit 0, control at bit CB (-1: none); for the
+// interaction template CB is the bit of its other wire.  ic/is: cos/sin of
+// theta/2 (Ising kinds)
 template <int K, int CB>
-__device__ __forceinline__ void gate_bit0(float (&re)[32], float (&im)[32], float s) {
+__device__ __forceinline__ void gate_bit0(float (&re)[32], float (&im)[32], float s, float ic,
+                                          float is) {
   using A = Ar<float, false>;
+  if constexpr (K == kRz || K == kJzz) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      int odd = r & 1;
+      if constexpr (K == kJzz) odd ^= (r >> CB) & 1;
+      A::phase(re[r], im[r], ic, odd ? -is : is);
+    }
+    return;
+  }
 #pragma unroll
   for (int r0 = 0; r0 < 32; r0 += 2) {
-    if (CB >= 0 && !((r0 >> CB) & 1)) continue;
+    if (K != kRx && K != kRy && CB >= 0 && !((r0 >> CB) & 1)) continue;
     const int r1 = r0 | 1;
-    if constexpr (K == kCnot) {
+    if constexpr (K == kRx || K == kRy) {
+      const float xr = re[r0], xi = im[r0], yr = re[r1], yi = im[r1];
+      if constexpr (K == kRx) {
+        A::rx_lane(re[r0], im[r0], yr, yi, ic, is);
+        A::rx_lane(re[r1], im[r1], xr, xi, ic, is);
+      } else {
+        A::ry_lane(re[r0], im[r0], yr, yi, false, ic, is);
+        A::ry_lane(re[r1], im[r1], xr, xi, true, ic, is);
+      }
+    } else if constexpr (K == kCnot) {
       xchg(re[r0], re[r1]);
       xchg(im[r0], im[r1]);
     } else if constexpr (K == kCvx) {
@@ -293,13 +453,27 @@ __device__ __forceinline__ void gate_bit0(float (&re)[32], float (&im)[32], floa
 }
 
 // apply one op: wire bits in pos (3 bits per wire), wire at each bit in inv
+template <bool ISING>
 __device__ __forceinline__ void apply5(int op, uint32_t &pos, uint32_t &inv, float (&re)[32],
-                                       float (&im)[32]) {
+                                       float (&im)[32], float ic, float is) {
   constexpr int NP2 = 2 * 5 * 4;
   const int o = op & 0x7f;
   const float s = (op & kOpNeg) ? -1.f : 1.f;
   int kind, tw, cw = -1;
-  if (o < NP2) {
+  if (ISING && o >= kOpIsingJ) {
+    // template on wires (i, j): j goes to bit 0, i is the "control" bit
+    int q = o - kOpIsingJ, i = 0;
+    while (q >= 4 - i) {
+      q -= 4 - i;
+      ++i;
+    }
+    cw = i;
+    tw = i + 1 + q;
+    kind = kJzz;
+  } else if (ISING) {
+    tw = (o - kOpIsingRot) / 3;
+    kind = kRx + (o - kOpIsingRot) % 3;
+  } else if (o < NP2) {
     const int pr = o >> 1;
     cw = pr >> 2;
     const int tt = pr & 3;
@@ -324,17 +498,29 @@ __device__ __forceinline__ void apply5(int op, uint32_t &pos, uint32_t &inv, flo
     inv = (inv & ~7u) | (uint32_t)tw;
   }
   const int cb = cw < 0 ? 0 : (int)((pos >> (3 * cw)) & 7);
+  if constexpr (ISING) {
+    switch (kind * 5 + cb) {
+      case kRx * 5: gate_bit0<kRx, -1>(re, im, s, ic, is); break;
+      case kRy * 5: gate_bit0<kRy, -1>(re, im, s, ic, is); break;
+      case kRz * 5: gate_bit0<kRz, -1>(re, im, s, ic, is); break;
+      case kJzz * 5 + 1: gate_bit0<kJzz, 1>(re, im, s, ic, is); break;
+      case kJzz * 5 + 2: gate_bit0<kJzz, 2>(re, im, s, ic, is); break;
+      case kJzz * 5 + 3: gate_bit0<kJzz, 3>(re, im, s, ic, is); break;
+      default: gate_bit0<kJzz, 4>(re, im, s, ic, is); break;
+    }
+    return;
+  }
   switch (kind * 5 + cb) {
-    case kCnot * 5 + 1: gate_bit0<kCnot, 1>(re, im, s); break;
-    case kCnot * 5 + 2: gate_bit0<kCnot, 2>(re, im, s); break;
-    case kCnot * 5 + 3: gate_bit0<kCnot, 3>(re, im, s); break;
-    case kCnot * 5 + 4: gate_bit0<kCnot, 4>(re, im, s); break;
-    case kCvx * 5 + 1: gate_bit0<kCvx, 1>(re, im, s); break;
-    case kCvx * 5 + 2: gate_bit0<kCvx, 2>(re, im, s); break;
-    case kCvx * 5 + 3: gate_bit0<kCvx, 3>(re, im, s); break;
-    case kCvx * 5 + 4: gate_bit0<kCvx, 4>(re, im, s); break;
-    case kHad * 5: gate_bit0<kHad, -1>(re, im, s); break;
-    default: gate_bit0<kTx, -1>(re, im, s); break;
+    case kCnot * 5 + 1: gate_bit0<kCnot, 1>(re, im, s, ic, is); break;
+    case kCnot * 5 + 2: gate_bit0<kCnot, 2>(re, im, s, ic, is); break;
+    case kCnot * 5 + 3: gate_bit0<kCnot, 3>(re, im, s, ic, is); break;
+    case kCnot * 5 + 4: gate_bit0<kCnot, 4>(re, im, s, ic, is); break;
+    case kCvx * 5 + 1: gate_bit0<kCvx, 1>(re, im, s, ic, is); break;
+    case kCvx * 5 + 2: gate_bit0<kCvx, 2>(re, im, s, ic, is); break;
+    case kCvx * 5 + 3: gate_bit0<kCvx, 3>(re, im, s, ic, is); break;
+    case kCvx * 5 + 4: gate_bit0<kCvx, 4>(re, im, s, ic, is); break;
+    case kHad * 5: gate_bit0<kHad, -1>(re, im, s, ic, is); break;
+    default: gate_bit0<kTx, -1>(re, im, s, ic, is); break;
   }
 }
 
@@ -351,6 +537,7 @@ __device__ __forceinline__ uint32_t op_work(const DevProblem &p, int op) {
   if (op == kOpIdentity) return 0;
   const int o = op & 0x7f;
   const uint32_t NN = p.N * p.N;
+  if (o >= kOpIsingRot) return 6 * NN;  // R_x/R_y/R_z/J: six real ops per amplitude
   const int np2 = 2 * (int)(p.n * (p.n - 1));
   if (o < np2) return (o & 1) ? 4 * NN : 0;  // CV: 4N^2, CNOT: 0
   return (o & 1) ? 2 * NN : 4 * NN;          // T: 2N^2, H: 4N^2
@@ -384,8 +571,10 @@ __device__ __forceinline__ void prefetch_mutated(const DevProblem &p, uint32_t i
 // ------------------------------------------------------------------ sampling
 // Sec. IV-D: draw whichIndividual and whichRotationOrInteraction, form the
 // segment index (Eq. (10)), measure the segment's qutrit (and qubit) in binary32.
+template <bool ISING>
 __device__ __forceinline__ void sample_slot(const DevProblem &p, uint32_t c, uint32_t t,
-                                            uint32_t gen, uint32_t &g_out, uint32_t &seg_out) {
+                                            uint32_t gen, uint32_t &g_out, uint32_t &seg_out,
+                                            float2 &amp_out) {
   const uint4 u = draw(p, c, t, gen, kStSample);
   const uint32_t i = below(u.x, p.P), r = below(u.y, p.R);
   const uint32_t seg = r * p.LP + i * p.L + t;
@@ -401,13 +590,36 @@ __device__ __forceinline__ void sample_slot(const DevProblem &p, uint32_t c, uin
   const float x = __fmul_rn(unit32(u.z), s);
   const uint32_t k = (x < p0) ? 0u : ((x < p01) ? 1u : 2u);
   uint32_t g = p.base + 3u * r + k;
-  if (p.has_qubit) {
+  if constexpr (ISING) {
+    if (r >= p.n) g = 3u * p.n + (r - p.n);  // the interaction template of that pair
+    amp_out = make_float2(b.z, b.w);         // the slot's angle; the qubit is not measured
+  } else if (p.measure_qubit) {
     const float B0 = __fmul_rn(b.z, b.z), B1 = __fmul_rn(b.w, b.w);
     const float y = __fmul_rn(unit32(u.w), __fadd_rn(B0, B1));
     if (y < B0) g = 0;
   }
   g_out = g;
   seg_out = seg;
+}
+
+// cos(theta/2), sin(theta/2) of a slot's amplitudes (b0, b1) = (cos theta,
+// sin theta), theta in [0, 2 pi): sgn(b1) sqrt((1 + b0)/2), sqrt((1 - b0)/2);
+// binary64 with every operation rounded (so it equals the oracle's), binary32
+// otherwise
+__device__ __forceinline__ void half_angle(float b0, float b1, double &c, double &s) {
+  double a = __dmul_rn(__dadd_rn(1.0, (double)b0), 0.5);
+  double b = __dmul_rn(__dsub_rn(1.0, (double)b0), 0.5);
+  if (a < 0.0) a = 0.0;
+  if (b < 0.0) b = 0.0;
+  c = __dsqrt_rn(a);
+  if (b1 < 0.f) c = -c;
+  s = __dsqrt_rn(b);
+}
+__device__ __forceinline__ void half_angle(float b0, float b1, float &c, float &s) {
+  const float a = fmaxf(0.f, (1.f + b0) * 0.5f), b = fmaxf(0.f, (1.f - b0) * 0.5f);
+  c = sqrtf(a);
+  if (b1 < 0.f) c = -c;
+  s = sqrtf(b);
 }
 
 // ------------------------------------------------------------------ one circuit
@@ -419,9 +631,11 @@ struct CircuitOut {
 };
 
 // ops0/ops1: this lane's op bytes for slots lane and lane + 32
-template <int NQ, typename R, bool CANON>
+// ic0/is0, ic1/is1: cos/sin of theta/2 of this lane's slots (Ising)
+template <int NQ, typename R, bool CANON, bool ISING = false>
 __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lane, uint32_t ops0,
-                                                    uint32_t ops1, R *S_out) {
+                                                    uint32_t ops1, R *S_out, R ic0 = R(1),
+                                                    R is0 = R(0), R ic1 = R(1), R is1 = R(0)) {
   using Ly = Lay<NQ>;
   constexpr int N = Ly::N;
   const int j = lane & (N - 1);
@@ -453,11 +667,16 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
     const uint32_t src = t < 32 ? ops0 : ops1;
     const int op = __shfl_sync(kFull, (int)src, (int)(t & 31));
     if (op == kOpIdentity) continue;
+    R ic = R(1), is = R(0);
+    if constexpr (ISING) {
+      ic = __shfl_sync(kFull, t < 32 ? ic0 : ic1, (int)(t & 31));
+      is = __shfl_sync(kFull, t < 32 ? is0 : is1, (int)(t & 31));
+    }
     if constexpr (kMapped) {
-      apply5(op, pos, inv, re, im);
+      apply5<ISING>(op, pos, inv, re, im, ic, is);
     } else {
       const R s = (op & kOpNeg) ? R(-1) : R(1);
-      dispatch<NQ, R, CANON>(op & 0x7f, re, im, lane, s);
+      dispatch<NQ, R, CANON, ISING>(op & 0x7f, re, im, lane, s, ic, is);
     }
   }
   CircuitOut out;
@@ -598,7 +817,7 @@ constexpr int min_blocks() {
   return (NQ == 5 && !CANON) ? 3 : ((NQ <= 3 && !CANON) ? 6 : 1);
 }
 
-template <int NQ, typename R, bool CANON>
+template <int NQ, typename R, bool CANON, bool ISING>
 __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CANON>()) k_step(const DevProblem *__restrict__ probs,
                                               const uint32_t *__restrict__ group,
                                               const uint32_t *__restrict__ prefix,
@@ -615,19 +834,23 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
     uint32_t o0 = kOpIdentity, o1 = kOpIdentity, seg0 = 0, seg1 = 0;
     bool bad = false;
     const bool qeqea = p.enc == kEncQeqea;
+    float2 a0 = make_float2(1.f, 0.f), a1 = a0;  // Ising: the slots' angles
     if (qeqea) {
+      float2 *amps = ISING ? p.amps + (size_t)par * p.P * p.L + (size_t)c * p.L : nullptr;
       if ((uint32_t)lane < p.L) {
         uint32_t gg;
-        sample_slot(p, c, lane, gen, gg, seg0);
+        sample_slot<ISING>(p, c, lane, gen, gg, seg0, a0);
         gate_idx[(size_t)c * p.L + lane] = (uint8_t)gg;
         p.seg_id[(size_t)c * p.L + lane] = seg0;
+        if constexpr (ISING) amps[lane] = a0;
         o0 = op_of(p, gg, bad);
       }
       if ((uint32_t)lane + 32 < p.L) {
         uint32_t gg;
-        sample_slot(p, c, lane + 32, gen, gg, seg1);
+        sample_slot<ISING>(p, c, lane + 32, gen, gg, seg1, a1);
         gate_idx[(size_t)c * p.L + lane + 32] = (uint8_t)gg;
         p.seg_id[(size_t)c * p.L + lane + 32] = seg1;
+        if constexpr (ISING) amps[lane + 32] = a1;
         o1 = op_of(p, gg, bad);
       }
       prefetch_mutated(p, c, gen, lane);
@@ -636,7 +859,13 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
       if ((uint32_t)lane < p.L) o0 = op_of(p, gate_idx[(size_t)c * p.L + lane], bad);
       if ((uint32_t)lane + 32 < p.L) o1 = op_of(p, gate_idx[(size_t)c * p.L + lane + 32], bad);
     }
-    CircuitOut out = compose_score<NQ, R, CANON>(p, lane, o0, o1, (R *)nullptr);
+    R ic0 = R(1), is0 = R(0), ic1 = R(1), is1 = R(0);
+    if constexpr (ISING) {
+      half_angle(a0.x, a0.y, ic0, is0);
+      half_angle(a1.x, a1.y, ic1, is1);
+    }
+    CircuitOut out =
+        compose_score<NQ, R, CANON, ISING>(p, lane, o0, o1, (R *)nullptr, ic0, is0, ic1, is1);
     const bool nonfinite = !isfinite(out.F);
     if (lane == 0) {
       if constexpr (CANON) p.fit64[(size_t)par * p.P + c] = out.F;
@@ -662,16 +891,20 @@ __global__ void __launch_bounds__(256) k_sample(const DevProblem *__restrict__ p
        e += (size_t)gridDim.x * blockDim.x) {
     const uint32_t c = (uint32_t)(e / p.L), t = (uint32_t)(e % p.L);
     uint32_t gg, seg;
-    sample_slot(p, c, t, gen, gg, seg);
+    float2 amp;
+    if (p.ising) sample_slot<true>(p, c, t, gen, gg, seg, amp);
+    else sample_slot<false>(p, c, t, gen, gg, seg, amp);
     gate_idx[e] = (uint8_t)gg;
     seg_id[e] = seg;
   }
 }
 
-// Fitness (and optionally the unitaries) of caller-provided gate strings.
-template <int NQ, typename R, bool CANON>
+// Fitness (and optionally the unitaries) of caller-provided gate strings
+// (Ising: with every slot's angle as qubit amplitudes in amps).
+template <int NQ, typename R, bool CANON, bool ISING>
 __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CANON>()) k_eval(const DevProblem *__restrict__ probs, uint32_t prob,
-                                              const uint8_t *__restrict__ gates, uint32_t n,
+                                              const uint8_t *__restrict__ gates,
+                                              const float2 *__restrict__ amps, uint32_t n,
                                               R *fit, uint32_t *cost, R *S, DevGlobal g) {
   const DevProblem &p = probs[prob];
   const int lane = threadIdx.x & 31;
@@ -683,7 +916,19 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
     if ((uint32_t)lane < p.L) o0 = op_of(p, gates[(size_t)c * p.L + lane], bad);
     if ((uint32_t)lane + 32 < p.L) o1 = op_of(p, gates[(size_t)c * p.L + lane + 32], bad);
     const bool anybad = __any_sync(kFull, bad);
-    CircuitOut out = compose_score<NQ, R, CANON>(p, lane, o0, o1, S ? S + NN2 * c : (R *)nullptr);
+    R ic0 = R(1), is0 = R(0), ic1 = R(1), is1 = R(0);
+    if constexpr (ISING) {
+      if ((uint32_t)lane < p.L) {
+        const float2 a = amps[(size_t)c * p.L + lane];
+        half_angle(a.x, a.y, ic0, is0);
+      }
+      if ((uint32_t)lane + 32 < p.L) {
+        const float2 a = amps[(size_t)c * p.L + lane + 32];
+        half_angle(a.x, a.y, ic1, is1);
+      }
+    }
+    CircuitOut out = compose_score<NQ, R, CANON, ISING>(
+        p, lane, o0, o1, S ? S + NN2 * c : (R *)nullptr, ic0, is0, ic1, is1);
     if (lane == 0) {
       double F = anybad ? __longlong_as_double(0x7ff8000000000000ll) : out.F;
       if (fit) fit[c] = (R)F;
@@ -695,12 +940,13 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
 }
 
 // Binary64 rescoring of ranking candidates: list entries are problem << 20 | slot,
-// the circuit is cand[slot] of that problem, gates come from gsrc (NULL = the
-// problem's own generation buffer).  One launch per qubit count present;
-// entries of other widths are skipped.
-template <int NQ>
+// the circuit is cand[slot] of that problem, gates (and Ising angles) come from
+// gsrc/asrc (NULL = the problem's own generation buffers).  One launch per
+// (qubit count, library kind) present; other entries are skipped.
+template <int NQ, bool ISING>
 __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ probs,
-                                                 const uint8_t *__restrict__ gsrc, int pipelined,
+                                                 const uint8_t *__restrict__ gsrc,
+                                                 const float2 *__restrict__ asrc, int pipelined,
                                                  DevGlobal g) {
   const int lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -712,7 +958,7 @@ __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ 
   for (uint32_t w = blockIdx.x + gridDim.x * (threadIdx.x >> 5); w < total; w += nw) {
     const uint32_t ent = g.rescore_list[w];
     const DevProblem &p = probs[ent >> 20];
-    if (p.n != (uint32_t)NQ) continue;
+    if (p.n != (uint32_t)NQ || (p.ising != 0) != ISING) continue;
     const uint32_t slot = ent & 0xfffffu;
     const uint32_t c = p.cand[slot];
     const uint8_t *gates =
@@ -722,7 +968,15 @@ __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ 
     if ((uint32_t)lane < p.L) o0 = op_of(p, gates[lane], bad);
     if ((uint32_t)lane + 32 < p.L) o1 = op_of(p, gates[lane + 32], bad);
     const bool anybad = __any_sync(kFull, bad);
-    CircuitOut out = compose_score<NQ, double, true>(p, lane, o0, o1, (double *)nullptr);
+    double ic0 = 1.0, is0 = 0.0, ic1 = 1.0, is1 = 0.0;
+    if constexpr (ISING) {
+      const float2 *am =
+          (asrc ? asrc : p.amps + (size_t)par * p.P * p.L) + (size_t)c * p.L;
+      if ((uint32_t)lane < p.L) half_angle(am[lane].x, am[lane].y, ic0, is0);
+      if ((uint32_t)lane + 32 < p.L) half_angle(am[lane + 32].x, am[lane + 32].y, ic1, is1);
+    }
+    CircuitOut out = compose_score<NQ, double, true, ISING>(p, lane, o0, o1, (double *)nullptr,
+                                                            ic0, is0, ic1, is1);
     if (lane == 0) p.cand_f[slot] = anybad ? __longlong_as_double(0x7ff8000000000000ll) : out.F;
   }
 }
@@ -739,23 +993,27 @@ __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ 
 
 cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs,
                         const uint32_t *group, const uint32_t *prefix, uint32_t n_group,
-                        uint32_t total, bool canon, const DevGlobal &g, cudaStream_t st) {
+                        uint32_t total, bool canon, bool ising, const DevGlobal &g,
+                        cudaStream_t st) {
   if (total == 0) return cudaSuccess;
   uint32_t per = canon ? lc.step64[n] : lc.step32[n];
   if (lc.grid_mode == 1 && per > 1) per -= 1;
   if (lc.grid_mode == 2) per = 0xffffu;  // every circuit's warp in one launch
+#define QE_LK(NQ, R, C, I)                                                                \
+  {                                                                                       \
+    constexpr int bt = block_threads<NQ, C>();                                            \
+    k_step<NQ, R, C, I><<<grid_for(lc, total, per, bt / 32), bt, 0, st>>>(               \
+        probs, group, prefix, n_group, total, g);                                         \
+  }
 #define QE_L(NQ)                                                                          \
   if (canon) {                                                                            \
-    constexpr int bt = block_threads<NQ, true>();                                         \
-    k_step<NQ, double, true><<<grid_for(lc, total, per, bt / 32), bt, 0, st>>>(          \
-        probs, group, prefix, n_group, total, g);                                         \
+    if (ising) QE_LK(NQ, double, true, true) else QE_LK(NQ, double, true, false)          \
   } else {                                                                                \
-    constexpr int bt = block_threads<NQ, false>();                                        \
-    k_step<NQ, float, false><<<grid_for(lc, total, per, bt / 32), bt, 0, st>>>(          \
-        probs, group, prefix, n_group, total, g);                                         \
+    if (ising) QE_LK(NQ, float, false, true) else QE_LK(NQ, float, false, false)          \
   }
   QE_NQ_SWITCH(n, QE_L)
 #undef QE_L
+#undef QE_LK
   return cudaGetLastError();
 }
 
@@ -772,38 +1030,50 @@ cudaError_t launch_sample(const LaunchCfg &lc, const DevProblem *probs, uint32_t
 }
 
 cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *probs, uint32_t prob,
-                        bool canon, const uint8_t *gates, uint32_t n, void *fit, uint32_t *cost,
-                        void *S, const DevGlobal &g, cudaStream_t st) {
+                        bool canon, const uint8_t *gates, const float2 *amps, uint32_t n,
+                        void *fit, uint32_t *cost, void *S, const DevGlobal &g,
+                        cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const uint32_t per = canon ? lc.step64[nq] : lc.step32[nq];
+  const bool ising = amps != nullptr;
+#define QE_LK(NQ, R, C, I)                                                                 \
+  {                                                                                        \
+    constexpr int bt = block_threads<NQ, C>();                                             \
+    k_eval<NQ, R, C, I><<<grid_for(lc, n, per, bt / 32), bt, 0, st>>>(                    \
+        probs, prob, gates, amps, n, (R *)fit, cost, (R *)S, g);                           \
+  }
 #define QE_L(NQ)                                                                           \
   if (canon) {                                                                             \
-    constexpr int bt = block_threads<NQ, true>();                                          \
-    k_eval<NQ, double, true><<<grid_for(lc, n, per, bt / 32), bt, 0, st>>>(               \
-        probs, prob, gates, n, (double *)fit, cost, (double *)S, g);                       \
+    if (ising) QE_LK(NQ, double, true, true) else QE_LK(NQ, double, true, false)           \
   } else {                                                                                 \
-    constexpr int bt = block_threads<NQ, false>();                                         \
-    k_eval<NQ, float, false><<<grid_for(lc, n, per, bt / 32), bt, 0, st>>>(                \
-        probs, prob, gates, n, (float *)fit, cost, (float *)S, g);                         \
+    if (ising) QE_LK(NQ, float, false, true) else QE_LK(NQ, float, false, false)           \
   }
   QE_NQ_SWITCH(nq, QE_L)
 #undef QE_L
+#undef QE_LK
   return cudaGetLastError();
 }
 
-cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, const DevProblem *probs,
-                           const uint8_t *gsrc, bool pipelined, const DevGlobal &g,
-                           cudaStream_t st) {
+cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, bool ising, const DevProblem *probs,
+                           const uint8_t *gsrc, const float2 *asrc, bool pipelined,
+                           const DevGlobal &g, cudaStream_t st) {
   const uint32_t blocks = lc.num_sms * lc.step64[nq];
-#define QE_L(NQ) k_rescore<NQ><<<blocks, 256, 0, st>>>(probs, gsrc, pipelined ? 1 : 0, g);
+#define QE_L(NQ)                                                                           \
+  if (ising)                                                                               \
+    k_rescore<NQ, true><<<blocks, 256, 0, st>>>(probs, gsrc, asrc, pipelined ? 1 : 0, g);  \
+  else                                                                                     \
+    k_rescore<NQ, false><<<blocks, 256, 0, st>>>(probs, gsrc, asrc, pipelined ? 1 : 0, g);
   QE_NQ_SWITCH(nq, QE_L)
 #undef QE_L
   return cudaGetLastError();
 }
 
 bool is_circuit_kernel(const void *f) {
-#define QE_K(NQ)                                                                        \
-  if (f == (const void *)k_step<NQ, float, false> || f == (const void *)k_step<NQ, double, true>) \
+#define QE_K(NQ)                                                                          \
+  if (f == (const void *)k_step<NQ, float, false, false> ||                               \
+      f == (const void *)k_step<NQ, double, true, false> ||                               \
+      f == (const void *)k_step<NQ, float, false, true> ||                                \
+      f == (const void *)k_step<NQ, double, true, true>)                                  \
     return true;
   QE_K(1) QE_K(2) QE_K(3) QE_K(4) QE_K(5)
 #undef QE_K
@@ -815,11 +1085,11 @@ cudaError_t query_circuit_occupancy(LaunchCfg &lc) {
   int b = 0;
 #define QE_Q(NQ)                                                                            \
   if (e == cudaSuccess)                                                                     \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, float, false>,         \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, float, false, false>,  \
                                                       block_threads<NQ, false>(), 0);       \
   lc.step32[NQ] = b > 0 ? b : 1;                                                            \
   if (e == cudaSuccess)                                                                     \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, double, true>,         \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, double, true, false>,  \
                                                       block_threads<NQ, true>(), 0);        \
   lc.step64[NQ] = b > 0 ? b : 1;
   QE_Q(1) QE_Q(2) QE_Q(3) QE_Q(4) QE_Q(5)

@@ -196,8 +196,8 @@ extern "C" qe_status qe_eval_rank_static(const qe_problem *prob, const uint8_t *
   k_static_setup<<<1, 1, 0, st>>>(d);
   e = cudaGetLastError();
   if (e == cudaSuccess)
-    e = qe::launch_eval(slot.lc, d.n, probs, 0, canon, d_gate_idx, n_circuits, d_fitness, d.meta,
-                        nullptr, g, st);
+    e = qe::launch_eval(slot.lc, d.n, probs, 0, canon, d_gate_idx, nullptr, n_circuits,
+                        d_fitness, d.meta, nullptr, g, st);
   if (d_topk) {
     qe::RankJob j{};
     j.prob = 0;
@@ -208,7 +208,7 @@ extern "C" qe_status qe_eval_rank_static(const qe_problem *prob, const uint8_t *
     j.update_record = 0;
     if (e == cudaSuccess) e = qe::launch_rank_select(probs, nullptr, 1, j, g, st);
     if (e == cudaSuccess && !canon)
-      e = qe::launch_rescore(slot.lc, d.n, probs, d_gate_idx, false, g, st);
+      e = qe::launch_rescore(slot.lc, d.n, false, probs, d_gate_idx, nullptr, false, g, st);
     if (e == cudaSuccess) e = qe::launch_rank_sort(probs, nullptr, 1, j, g, st);
   }
   if (e != cudaSuccess) return say(h_msg, msg_len, QE_ECUDA, cudaGetErrorString(e));

@@ -13,6 +13,7 @@
 //                next generation; a GA search keeps its genome here),
 //                seg_id: P*L uint32 (QEQEA only)
 //   mut_list   : 2 x P individual ids, mut_cnt: 2 counters (QEQEA only)
+//   amps       : 2 x P*L float2 slot angles as qubit amplitudes (Ising only)
 //   ga_cum     : P uint64 SUS prefix sums (GA only)
 //   fit32/fit64: 2 x P (working-precision fitness), meta: 2 x P (cost | work << 8)
 // where S = R*P*L and seg = r*L*P + i*L + t (Eq. (10)).
@@ -26,6 +27,9 @@ constexpr int kQ = 4096;            // mutation magnitude quantisation
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint8_t kOpIdentity = 0xff;
 constexpr uint8_t kOpNeg = 0x80;    // sign bit of the op byte: sigma = -1 (CV^dag, T^dag)
+// Ising ops (no sign bit): kOpIsingRot + 3w + k = R_{x,y,z} on wire w (k = 0, 1, 2),
+// kOpIsingJ + q = the interaction template on wire pair q (lexicographic i < j)
+constexpr uint8_t kOpIsingRot = 64, kOpIsingJ = 80;
 // 1/sqrt(2) rounded to binary64 and to binary32
 constexpr double kH64 = 0x1.6a09e667f3bcdp-1;
 constexpr float kH32 = 0x1.6a09e6p-1f;
@@ -57,6 +61,8 @@ struct DevProblem {
   uint32_t n, N, L, P, R, G, LP;
   uint32_t lib, prec, fit_kind, enc, topk, k;  // k = max(topk, 1)
   uint32_t run, has_qubit, base;                // base = 1 if I is library index 0
+  uint32_t measure_qubit;  // the qubit decides "gate present" (identity in the library)
+  uint32_t ising;          // the Ising library: every slot carries an angle
   uint32_t key0, key1;
   float eps_d;        // bound on |d32 - d64|, d = (N - |tr|)/N, for the binary32 path
   float pen_per_gate; // cost_weight / L in binary32 (ranking bounds only)
@@ -85,6 +91,9 @@ struct DevProblem {
   Best *rec;
   // mutation table: cos/sin of m * mutation_range / Q, m = 0..Q
   float2 *qubit_tab;
+  // Ising: each slot's qubit amplitudes (b0, b1) as sampled (its angle), 2 x P*L,
+  // double-buffered by generation parity like gate_idx
+  float2 *amps;
   // individuals that mutate this generation, listed by the circuit kernel:
   // 2 x P entries and 2 counters, by generation parity (the circuit kernel of
   // generation g appends to half g & 1 and clears the counter of the other)

@@ -50,19 +50,22 @@ bool is_circuit_kernel(const void *f);  // a generation circuit kernel (graph no
 // all searches of a launch have n qubits
 cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs,
                         const uint32_t *group, const uint32_t *prefix, uint32_t n_group,
-                        uint32_t total, bool canon, const DevGlobal &g, cudaStream_t st);
+                        uint32_t total, bool canon, bool ising, const DevGlobal &g,
+                        cudaStream_t st);
 cudaError_t launch_sample(const LaunchCfg &lc, const DevProblem *probs, uint32_t prob, uint32_t P,
                           uint32_t L, uint32_t gen, uint8_t *gate_idx, uint32_t *seg_id,
                           cudaStream_t st);
+// amps: the slots' angles as qubit amplitudes (Ising searches), else NULL
 cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *probs, uint32_t prob,
-                        bool canon, const uint8_t *gates, uint32_t n, void *fit, uint32_t *cost,
-                        void *S, const DevGlobal &g, cudaStream_t st);
+                        bool canon, const uint8_t *gates, const float2 *amps, uint32_t n,
+                        void *fit, uint32_t *cost, void *S, const DevGlobal &g,
+                        cudaStream_t st);
 // gsrc == NULL: each candidate's search's own generation buffer; pipelined:
 // that buffer is the one of generation *gen - 1, and nothing runs unless the
 // chain is active
-cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, const DevProblem *probs,
-                           const uint8_t *gsrc, bool pipelined, const DevGlobal &g,
-                           cudaStream_t st);
+cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, bool ising, const DevProblem *probs,
+                           const uint8_t *gsrc, const float2 *asrc, bool pipelined,
+                           const DevGlobal &g, cudaStream_t st);
 
 // k_update.cu
 bool is_update_kernel(const void *f);  // an update kernel (graph node priorities)

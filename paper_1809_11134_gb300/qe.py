@@ -19,14 +19,15 @@ LIB_PATH = os.path.join(_HERE, "libqe.so")
 QE_OK, QE_EINVAL, QE_ENOMEM, QE_ECUDA, QE_ETIMEOUT, QE_ENUMERIC, QE_ESTATE, QE_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["QE_OK", "QE_EINVAL", "QE_ENOMEM", "QE_ECUDA", "QE_ETIMEOUT", "QE_ENUMERIC",
                 "QE_ESTATE", "QE_EUNSUPPORTED"]
-QE_LIB_NCV, QE_LIB_HT, QE_LIB_IDENTITY = 1, 2, 4
+QE_LIB_NCV, QE_LIB_HT, QE_LIB_IDENTITY, QE_LIB_ISING = 1, 2, 4, 8
 QE_PREC_FP64, QE_PREC_FP32, QE_PREC_SPLIT_TC = 0, 1, 2
 QE_FIT_TRACE, QE_FIT_PROB = 0, 1
 QE_ENC_QEQEA, QE_ENC_GA = 0, 1
 QE_ERRW_BAD_GATE, QE_ERRW_NONFINITE = 1, 2
 
 # every symbol include/qe.h declares
-EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_host", "qe_compose",
+EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_amp", "qe_eval_host",
+           "qe_compose", "qe_compose_amp",
            "qe_update", "qe_step", "qe_last_generation", "qe_state_bytes", "qe_get_state",
            "qe_set_state", "qe_generation", "qe_autotune", "qe_launch_plan", "qe_stage_timing",
            "qe_stage_times", "qe_measure_alu_peaks",
@@ -78,6 +79,8 @@ def lib():
         L.qe_eval.argtypes = [vp, u32, vp, u32, vp, vp, C.POINTER(qe_ranked)]
         L.qe_eval_host.argtypes = [vp, u32, vp, u32, vp, C.POINTER(qe_ranked)]
         L.qe_compose.argtypes = [vp, u32, vp, u32, vp]
+        L.qe_eval_amp.argtypes = [vp, u32, vp, vp, u32, vp, vp, C.POINTER(qe_ranked)]
+        L.qe_compose_amp.argtypes = [vp, u32, vp, vp, u32, vp]
         L.qe_update.argtypes = [vp, u32, u32, vp, vp]
         L.qe_step.argtypes = [vp, u32, C.POINTER(qe_report)]
         L.qe_last_generation.argtypes = [vp, u32, vp, vp, vp, C.POINTER(qe_ranked)]
@@ -194,11 +197,15 @@ class Context:
         _need(seg_id, torch.int32, n, "seg_id")
         _check(self.h, lib().qe_sample(self.h, prob, gen, _ptr(gate_idx), _ptr(seg_id)))
 
-    def eval(self, prob, gate_idx, fitness, n_circuits=None, cost=None, topk=False):
+    def eval(self, prob, gate_idx, fitness, n_circuits=None, cost=None, topk=False, amps=None):
+        """amps: Ising searches, float32 [n, L, 2] device tensor of the slots' qubit
+        amplitudes (their angles): calls qe_eval_amp"""
         import torch
         p = self._probs[prob]
         n = gate_idx.shape[0] if n_circuits is None else n_circuits
         _need(gate_idx, torch.uint8, n * p.circuit_len, "gate_idx")
+        if amps is not None:
+            _need(amps, torch.float32, n * p.circuit_len * 2, "amps")
         _need(fitness, torch.float64 if p.precision == QE_PREC_FP64 else torch.float32, n,
               "fitness")
         if cost is not None:
@@ -207,8 +214,12 @@ class Context:
         if topk:
             k = min(max(p.topk, 1), n)
             out = (qe_ranked * max(k, 1))()
-        _check(self.h, lib().qe_eval(self.h, prob, _ptr(gate_idx), n, _ptr(fitness), _ptr(cost),
-                                     out))
+        if amps is None:
+            _check(self.h, lib().qe_eval(self.h, prob, _ptr(gate_idx), n, _ptr(fitness),
+                                         _ptr(cost), out))
+        else:
+            _check(self.h, lib().qe_eval_amp(self.h, prob, _ptr(gate_idx), _ptr(amps), n,
+                                             _ptr(fitness), _ptr(cost), out))
         if topk:
             return [(r.circuit, r.cost, r.fitness) for r in out[:k]]
         return None
@@ -233,7 +244,7 @@ class Context:
         return _check(self.h, lib().qe_eval_host(self.h, prob, C.c_void_p(h_gates_ptr), n,
                                                  C.c_void_p(h_fit_ptr), topk_buf))
 
-    def compose(self, prob, gate_idx, unitary, n_circuits=None):
+    def compose(self, prob, gate_idx, unitary, n_circuits=None, amps=None):
         import torch
         p = self._probs[prob]
         n = gate_idx.shape[0] if n_circuits is None else n_circuits
@@ -241,7 +252,12 @@ class Context:
         dt = torch.float64 if p.precision == QE_PREC_FP64 else torch.float32
         _need(unitary, dt, n * N * N * 2, "unitary")
         _need(gate_idx, torch.uint8, n * p.circuit_len, "gate_idx")
-        _check(self.h, lib().qe_compose(self.h, prob, _ptr(gate_idx), n, _ptr(unitary)))
+        if amps is None:
+            _check(self.h, lib().qe_compose(self.h, prob, _ptr(gate_idx), n, _ptr(unitary)))
+        else:
+            _need(amps, torch.float32, n * p.circuit_len * 2, "amps")
+            _check(self.h, lib().qe_compose_amp(self.h, prob, _ptr(gate_idx), _ptr(amps), n,
+                                                _ptr(unitary)))
 
     def update(self, prob, gen, seg_id, fitness):
         import torch

@@ -13,7 +13,7 @@ from typing import List
 
 import numpy as np
 
-LIB_NCV, LIB_HT, LIB_IDENTITY = 1, 2, 4
+LIB_NCV, LIB_HT, LIB_IDENTITY, LIB_ISING = 1, 2, 4, 8
 PREC_FP64, PREC_FP32, PREC_SPLIT_TC = 0, 1, 2
 FIT_TRACE, FIT_PROB = 0, 1
 ENC_QEQEA, ENC_GA = 0, 1

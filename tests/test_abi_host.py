@@ -61,7 +61,7 @@ def test_library_info_matches_oracle(qe):
 
 BAD = [
     dict(n=0), dict(n=6), dict(L=0), dict(L=65), dict(P=0), dict(P=(1 << 20) + 1),
-    dict(library=8), dict(library=1, n=1), dict(topk=1025), dict(topk=5000, P=4096),
+    dict(library=16), dict(library=8 | 1), dict(library=1, n=1), dict(topk=1025), dict(topk=5000, P=4096),
     dict(p_mutation=1.5), dict(p_mutation=float("nan")), dict(mutation_range=float("inf")),
     dict(perm=[0, 0, 1, 2, 3, 4, 5, 6]), dict(perm=[8, 1, 2, 3, 4, 5, 6, 7]),
     dict(precision=3), dict(fitness_kind=2), dict(encoding=2), dict(cost_weight=float("nan")),
@@ -111,3 +111,18 @@ def test_struct_layouts(qe):
     assert C.sizeof(qe.qe_problem) == 104
     assert C.sizeof(qe.qe_ranked) == 16
     assert C.sizeof(qe.qe_report) == 120
+
+
+def test_ising_library_geometry_and_refusals(qe):
+    """QE_LIB_ISING: n rotation regions plus n(n-1)/2 templates, 3n + n(n-1)/2 gates
+    (the oracle's numbers); the GA on it is refused as unsupported, without a GPU."""
+    import oracle
+    for n in range(1, 6):
+        g, r = qe.qe_library_info(n, qe.QE_LIB_ISING)
+        assert (g, r) == (oracle.num_gates(n, oracle.LIB_ISING),
+                          oracle.num_regions(n, oracle.LIB_ISING))
+    s = W.Search(3, 8, 64, W.LIB_ISING, W.cknot(3), encoding=W.ENC_GA)
+    probs = (qe.qe_problem * 1)(qe.to_problem(s))
+    h = C.c_void_p()
+    assert qe.lib().qe_init(C.byref(h), probs, 1, None) == qe.QE_EUNSUPPORTED
+    assert b"GA" in qe.lib().qe_last_error(None)
