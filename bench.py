@@ -389,7 +389,10 @@ def update_bytes(searches, last):
     for s, l in zip(searches, last):
         sid = l["seg_id"]
         used = len(np.unique(sid))
-        R = (s.n * (s.n - 1) if s.library & 1 else 0) + (s.n if s.library & 2 else 0)
+        if s.library == 8:  # Ising: the wires, then the wire pairs
+            R = s.n + s.n * (s.n - 1) // 2
+        else:
+            R = (s.n * (s.n - 1) if s.library & 1 else 0) + (s.n if s.library & 2 else 0)
         mutated = s.p_mutation * s.P * R * s.L
         total += sid.size * 8 + used * (32 + 32 + 4) + mutated * (32 + 32 + 4 + 4)
     return total
@@ -497,8 +500,9 @@ def per_config(qe, torch, args):
     """Per benchmark search set: circuit-kernel rate (sample + compose + score)
     and generation rate, binary32 vs plain binary64, from the events inside the
     generation graph, with the binary32 path's largest error against binary64;
-    the 1024 uneven searches (binary32); and the GA run of the 5-qubit search on
-    the same evaluation (context next to the headline)."""
+    the 1024 uneven searches (binary32); the GA run of the 5-qubit search on
+    the same evaluation; and the 3- and 5-qubit shapes on the paper's Ising gate
+    set (context next to the headline)."""
     from paper_1809_11134_gb300 import workloads as W
     out = {}
     for cfg, gens32, gens64 in ((2, 20, 5), (3, 6, 2), (5, 4, 1)):
@@ -526,6 +530,18 @@ def per_config(qe, torch, args):
     ctx, r = _stage_rates(qe, torch, searches, 4)
     ctx.close()
     out["config5_ga"] = {"fp32": r}
+    # the same shapes on the paper's Ising gate set (rotations and templates)
+    for cfg, precs in ((2, (W.PREC_FP32, W.PREC_FP64)), (5, (W.PREC_FP32,))):
+        res = {}
+        for prec in precs:
+            searches = W.config(cfg, precision=prec, library=W.LIB_ISING)
+            ctx, r = _stage_rates(qe, torch, searches, 10 if cfg == 2 else 3)
+            ctx.close()
+            res["fp32" if prec else "fp64"] = r
+        if "fp64" in res:
+            res["fp32_over_fp64_generation"] = (res["fp32"]["generation_circuits_per_s"] /
+                                                res["fp64"]["generation_circuits_per_s"])
+        out["config%d_ising" % cfg] = res
     return out
 
 

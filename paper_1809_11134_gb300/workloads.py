@@ -84,7 +84,7 @@ class Search:
 
 
 def config(k: int, precision: int = None, P: int = None, seed: int = None,
-           encoding: int = None) -> List[Search]:
+           encoding: int = None, library: int = None) -> List[Search]:
     """The five benchmark searches (3-5 qubit permutation targets).
 
     1: 3-qubit Toffoli, NCV + identity (19 gates), L=5, P=64, FP64, seed 0
@@ -96,7 +96,8 @@ def config(k: int, precision: int = None, P: int = None, seed: int = None,
     5: 5-qubit C4NOT, NCV + H/T/T^dag (75 gates), L=64, P=262144, top-128
 
     encoding=ENC_GA turns every search into the classical GA on the same
-    shapes (integer genomes, per-gene mutation rate 0.02).
+    shapes (integer genomes, per-gene mutation rate 0.02); library=LIB_ISING
+    runs the same shapes on the paper's Ising gate set.
     """
     full = LIB_NCV | LIB_HT
     if k == 1:
@@ -131,6 +132,8 @@ def config(k: int, precision: int = None, P: int = None, seed: int = None,
             x.seed = seed
         if encoding is not None:
             x.encoding = encoding
+        if library is not None:
+            x.library = library
     return s
 
 
