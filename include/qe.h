@@ -146,6 +146,8 @@ typedef struct {
   uint32_t error_word;      /* QE_ERRW_* bits seen so far */
   uint32_t reserved;
   uint8_t best_gates[64];   /* gate indices of the best circuit, best_len of them */
+  float best_amps[128];     /* Ising: its slots' angles as qubit amplitudes (b0, b1) per
+                               slot; zero for the other libraries */
 } qe_report;
 
 /* Library geometry without a context: number of gate types and of regions

@@ -34,7 +34,7 @@ class Report(C.Structure):
                 ("best_fitness", C.c_double), ("gen_best_fitness", C.c_double),
                 ("mean_fitness", C.c_double), ("useful_flops", C.c_uint64),
                 ("best_cost", C.c_uint32), ("best_gen", C.c_uint32),
-                ("best_gates", C.c_uint8 * 64)]
+                ("best_gates", C.c_uint8 * 64), ("best_amps", C.c_float * 128)]
 
 
 _lib = None

@@ -849,7 +849,6 @@ void oracle_step(const oracle_problem *p, float *cur, float *best, float *best_f
   if (is_ising(p->library)) amps = (float *)malloc(sizeof(float) * 2 * (uint64_t)p->P * p->L);
   oracle_sample_amp(p, cur, gen, gate_idx, seg_id, amps);
   oracle_eval_amp(p, gate_idx, amps, p->P, F, cost);
-  free(amps);
   uint32_t k = topk ? topk : 1;
   uint32_t *tk = topk_idx;
   uint32_t local[1];
@@ -873,7 +872,10 @@ void oracle_step(const oracle_problem *p, float *cur, float *best, float *best_f
     rep->best_gen = gen;
     memset(rep->best_gates, 0, sizeof rep->best_gates);
     memcpy(rep->best_gates, gate_idx + (uint64_t)b * p->L, p->L);
+    memset(rep->best_amps, 0, sizeof rep->best_amps);
+    if (amps) memcpy(rep->best_amps, amps + (uint64_t)b * 2 * p->L, sizeof(float) * 2 * p->L);
   }
+  free(amps);
   oracle_update(p, cur, best, best_f, gen, seg_id, F);
 }
 

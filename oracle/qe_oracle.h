@@ -173,6 +173,7 @@ typedef struct {
   uint32_t best_cost;
   uint32_t best_gen;     /* generation in which best_fitness was found */
   uint8_t best_gates[64];
+  float best_amps[128]; /* Ising: the best circuit's slot amplitudes */
 } oracle_report;
 
 void oracle_step(const oracle_problem *p, float *cur, float *best, float *best_f, uint32_t gen,

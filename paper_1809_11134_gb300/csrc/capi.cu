@@ -757,6 +757,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     j.fit = d.prec == QE_PREC_FP64 ? (const void *)d.fit64 : (const void *)d.fit32;
     j.meta = d.meta;
     j.gsrc = d.gate_idx;
+    j.asrc = d.amps;
     j.update_record = 1;
     j.pipelined = 1;
     single[5 * i + 0] = i;
@@ -867,6 +868,7 @@ static qe_status rank_single(qe_ctx *ctx, uint32_t prob, uint32_t n, const void 
   j.fit = fit;
   j.meta = meta;
   j.gsrc = gsrc;
+  j.asrc = asrc;
   j.update_record = 0;
   cudaStream_t us = ctx->user;
   QE_CUDA(ctx, launch_reset_counter(ctx->g, us));
@@ -1035,6 +1037,7 @@ qe_status qe_step(qe_ctx *ctx, uint32_t n_gen, qe_report *h_reports) {
     r.error_word = b.error_word;
     r.reserved = 0;
     memcpy(r.best_gates, b.best_gates, 64);
+    memcpy(r.best_amps, b.best_amps, sizeof r.best_amps);
   }
   if (errw) return fail(ctx, QE_ENUMERIC, "a search reported an invalid gate or non-finite fitness");
   return QE_OK;

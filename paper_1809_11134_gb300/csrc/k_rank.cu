@@ -101,6 +101,7 @@ __device__ __forceinline__ RankJob resolve(RankJob jb, const DevProblem &p, uint
     jb.fit = (const char *)jb.fit + b * p.P * (p.prec == 0 ? 8 : 4);
     jb.meta += b * p.P;
     jb.gsrc += b * p.P * p.L;
+    if (jb.asrc) jb.asrc += b * p.P * p.L;
   }
   return jb;
 }
@@ -284,6 +285,11 @@ __device__ __forceinline__ void record_best(const DevProblem &p, const RankJob &
   if (improve) {
     const uint8_t *gs = jb.gsrc + (size_t)c * p.L;
     for (uint32_t t = lane; t < 64; t += 32) rec->best_gates[t] = t < p.L ? gs[t] : 0;
+    if (p.ising && jb.asrc) {
+      const float2 *as = jb.asrc + (size_t)c * p.L;
+      for (uint32_t t = lane; t < 64; t += 32)
+        rec->best_amps[t] = t < p.L ? as[t] : make_float2(0.f, 0.f);
+    }
   }
 }
 

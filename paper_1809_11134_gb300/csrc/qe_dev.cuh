@@ -55,6 +55,7 @@ struct Best {
   unsigned long long useful_flops;
   uint32_t best_cost, best_len, error_word, reserved;
   uint8_t best_gates[64];
+  float2 best_amps[64];  // Ising: the best circuit's slot angles
 };
 
 struct DevProblem {

@@ -40,6 +40,7 @@ struct RankJob {
   const void *fit;
   const uint32_t *meta;
   const uint8_t *gsrc;
+  const float2 *asrc;  // Ising: the circuits' slot angles (NULL otherwise)
   uint32_t update_record;
   uint32_t pipelined;
 };

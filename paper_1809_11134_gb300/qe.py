@@ -52,7 +52,8 @@ class qe_report(C.Structure):
                 ("best_fitness", C.c_double), ("gen_best_fitness", C.c_double),
                 ("mean_fitness", C.c_double), ("useful_flops", C.c_uint64),
                 ("best_cost", C.c_uint32), ("best_len", C.c_uint32), ("error_word", C.c_uint32),
-                ("reserved", C.c_uint32), ("best_gates", C.c_uint8 * 64)]
+                ("reserved", C.c_uint32), ("best_gates", C.c_uint8 * 64),
+                ("best_amps", C.c_float * 128)]
 
 
 class QeError(RuntimeError):
@@ -279,7 +280,8 @@ class Context:
                             best_fitness=r.best_fitness, gen_best_fitness=r.gen_best_fitness,
                             mean_fitness=r.mean_fitness, useful_flops=r.useful_flops,
                             best_cost=r.best_cost, best_len=r.best_len, error_word=r.error_word,
-                            best_gates=list(r.best_gates[:r.best_len]), status=st))
+                            best_gates=list(r.best_gates[:r.best_len]),
+                            best_amps=list(r.best_amps[:2 * r.best_len]), status=st))
         return out
 
     def step_raw(self, n_gen, rep_buf):

@@ -110,7 +110,7 @@ def test_null_context_calls_are_rejected(qe):
 def test_struct_layouts(qe):
     assert C.sizeof(qe.qe_problem) == 104
     assert C.sizeof(qe.qe_ranked) == 16
-    assert C.sizeof(qe.qe_report) == 120
+    assert C.sizeof(qe.qe_report) == 120 + 512
 
 
 def test_ising_library_geometry_and_refusals(qe):

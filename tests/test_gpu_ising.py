@@ -121,7 +121,8 @@ def _oracle_run(searches, gens):
         hist = []
         for gen in range(gens):
             gi, sid, F, cost, tk = oracle.step(p, cur, best, bf, gen, max(s.topk, 1), rep)
-            hist.append((gi, sid, F, tk, rep.best_fitness, rep.best_cost, bytes(rep.best_gates)))
+            hist.append((gi, sid, F, tk, rep.best_fitness, rep.best_cost, bytes(rep.best_gates),
+                         list(rep.best_amps[:2 * s.L])))
         out.append((hist, cur, best, bf))
     return out
 
@@ -140,7 +141,7 @@ def test_step_trajectory_fp64_bit_exact(qe, torch):
         for gen in range(gens):
             reps = ctx.step(1)
             for run, s in enumerate(searches):
-                gi, sid, F, tk, bfit, bcost, bgates = ref[run][0][gen]
+                gi, sid, F, tk, bfit, bcost, bgates, bamps = ref[run][0][gen]
                 last = ctx.last_generation(run)
                 assert np.array_equal(last["gate_idx"], gi), (gen, run)
                 assert np.array_equal(last["seg_id"], sid)
@@ -148,6 +149,7 @@ def test_step_trajectory_fp64_bit_exact(qe, torch):
                 assert [t[0] for t in last["topk"]] == list(tk[:s.topk])
                 assert reps[run]["best_fitness"] == bfit and reps[run]["best_cost"] == bcost
                 assert bytes(reps[run]["best_gates"][:s.L]) == bgates[:s.L]
+                assert reps[run]["best_amps"] == bamps  # the best circuit's angles
         for run in range(len(searches)):
             c, b, bf = ctx.get_state(run)
             assert state_equal(c, ref[run][1]) and state_equal(b, ref[run][2])
