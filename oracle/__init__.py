@@ -89,6 +89,9 @@ def lib():
                                   C.c_uint32, _u8p, _u32p, _f64p, _u32p, _u32p,
                                   C.POINTER(Report)]
         L.oracle_ga_init.argtypes = [C.POINTER(Problem), C.c_uint32, _u8p]
+        L.oracle_ga_init_amp.argtypes = [C.POINTER(Problem), C.c_uint32, _u8p, _f32p]
+        L.oracle_ga_next_amp.argtypes = [C.POINTER(Problem), C.c_uint32, C.c_uint32, C.c_double,
+                                         _u8p, _f32p, _f64p, _u32p, _u8p, _f32p]
         L.oracle_ga_next.argtypes = [C.POINTER(Problem), C.c_uint32, C.c_uint32, C.c_double,
                                      _u8p, _f64p, _u32p, _u8p]
         _lib = L
@@ -288,6 +291,24 @@ def ga_init(p, G):
     g = np.zeros(p.P * p.L, np.uint8)
     lib().oracle_ga_init(C.byref(p), G, g)
     return g.reshape(p.P, p.L)
+
+
+def ga_init_amp(p, G):
+    g = np.zeros(p.P * p.L, np.uint8)
+    a = np.zeros(2 * p.P * p.L, np.float32)
+    lib().oracle_ga_init_amp(C.byref(p), G, g, a)
+    return g.reshape(p.P, p.L), a.reshape(p.P, p.L, 2)
+
+
+def ga_next_amp(p, G, gen, rate, genome, amps, F, cost_):
+    out = np.zeros(p.P * p.L, np.uint8)
+    oa = np.zeros(2 * p.P * p.L, np.float32)
+    lib().oracle_ga_next_amp(C.byref(p), G, gen, rate,
+                             np.ascontiguousarray(genome, np.uint8).ravel(),
+                             np.ascontiguousarray(amps, np.float32).ravel(),
+                             np.ascontiguousarray(F, np.float64),
+                             np.ascontiguousarray(cost_, np.uint32), out, oa)
+    return out.reshape(p.P, p.L), oa.reshape(p.P, p.L, 2)
 
 
 def ga_next(p, G, gen, rate, genome, F, cost_):

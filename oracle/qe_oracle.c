@@ -968,3 +968,106 @@ void oracle_ga_next(const oracle_problem *p, uint32_t G, uint32_t gen, double ga
   free(cum);
   free(parent);
 }
+
+/* ======================================================================
+ * The paper's GA comparator on the Ising library (Sec. V-B): genes are
+ * (gate, angle) pairs, the angle kept as qubit amplitudes like the QEQEA
+ * slots; selection as above (SUS), two-point crossover, and a real-valued
+ * mutation of the angle besides the replacement of whole genes.
+ * ====================================================================== */
+void oracle_ga_init_amp(const oracle_problem *p, uint32_t G, uint8_t *genome, float *amps) {
+  for (uint32_t c = 0; c < p->P; ++c)
+    for (uint32_t t = 0; t < p->L; ++t) {
+      uint32_t u[4];
+      uint64_t e = (uint64_t)c * p->L + t;
+      draw(p, c, t, 0, ST_GA_INIT, u);
+      genome[e] = (uint8_t)below(u[0], G);
+      trig_f32((2.0 * ORC_PI) / (double)ORC_Q, below(u[1], ORC_Q), &amps[2 * e], &amps[2 * e + 1]);
+    }
+}
+
+void oracle_ga_next_amp(const oracle_problem *p, uint32_t G, uint32_t gen, double ga_rate,
+                        const uint8_t *genome, const float *amps, const double *F,
+                        const uint32_t *cost, uint8_t *out, float *out_amps) {
+  uint32_t P = p->P, L = p->L;
+  uint64_t *cum = (uint64_t *)malloc(sizeof(uint64_t) * P);
+  uint64_t W = 0;
+  for (uint32_t c = 0; c < P; ++c) {
+    W += sus_weight(F[c]);
+    cum[c] = W;
+  }
+  uint32_t *parent = (uint32_t *)malloc(sizeof(uint32_t) * P);
+  uint32_t u[4];
+  draw(p, 0, 0, gen, ST_GA, u);
+  uint64_t D = W / P;
+  if (D > 0) {
+    uint64_t r64 = ((uint64_t)u[1] << 32) | u[0];
+    uint64_t s0 = (uint64_t)(((unsigned __int128)r64 * D) >> 64);
+    uint32_t c = 0;
+    for (uint32_t m = 0; m < P; ++m) {
+      uint64_t ptr = s0 + (uint64_t)m * D;
+      while (c + 1 < P && !(cum[c] > ptr)) ++c;
+      parent[m] = c;
+    }
+  } else {
+    for (uint32_t m = 0; m < P; ++m) parent[m] = m;
+  }
+  /* two-point crossover: the genes in [lo, hi) come from the other parent */
+  for (uint32_t m = 0; m < P; m += 2) {
+    uint64_t a = (uint64_t)parent[m] * L, oa = (uint64_t)m * L;
+    if (m + 1 >= P) {
+      memcpy(out + oa, genome + a, L);
+      memcpy(out_amps + 2 * oa, amps + 2 * a, 2 * L * sizeof(float));
+      break;
+    }
+    uint64_t b = (uint64_t)parent[m + 1] * L, ob = (uint64_t)(m + 1) * L;
+    uint32_t lo = L, hi = L;
+    if (L > 1) {
+      uint32_t v[4];
+      draw(p, m / 2, 1, gen, ST_GA, v);
+      uint32_t x = 1 + below(v[0], L - 1), y = 1 + below(v[1], L - 1);
+      lo = x < y ? x : y;
+      hi = x < y ? y : x;
+    }
+    for (uint32_t t = 0; t < L; ++t) {
+      int swap = t >= lo && t < hi;
+      uint64_t sa = swap ? b : a, sb = swap ? a : b;
+      out[oa + t] = genome[sa + t];
+      out[ob + t] = genome[sb + t];
+      out_amps[2 * (oa + t)] = amps[2 * (sa + t)];
+      out_amps[2 * (oa + t) + 1] = amps[2 * (sa + t) + 1];
+      out_amps[2 * (ob + t)] = amps[2 * (sb + t)];
+      out_amps[2 * (ob + t) + 1] = amps[2 * (sb + t) + 1];
+    }
+  }
+  /* per-gene mutation: a fresh gene, or the angle turned by +-m range/Q */
+  for (uint32_t c = 0; c < P; ++c)
+    for (uint32_t t = 0; t < L; ++t) {
+      uint32_t v[4];
+      uint64_t e = (uint64_t)c * L + t;
+      draw(p, c, 2 + t, gen, ST_GA, v);
+      if (unit(v[0]) < ga_rate) {
+        out[e] = (uint8_t)below(v[1], G);
+        trig_f32((2.0 * ORC_PI) / (double)ORC_Q, below(v[2], ORC_Q), &out_amps[2 * e],
+                 &out_amps[2 * e + 1]);
+      } else if (unit(v[3]) < ga_rate) {
+        float cs, sn;
+        trig_f32(p->mutation_range / (double)ORC_Q, below(v[2], ORC_Q + 1), &cs, &sn);
+        if (v[1] & 1u) sn = -sn;
+        float R[2][2] = {{cs, -sn}, {sn, cs}};
+        float b[2] = {out_amps[2 * e], out_amps[2 * e + 1]};
+        for (int r = 0; r < 2; ++r) {
+          float acc = 0.0f;
+          for (int k = 0; k < 2; ++k) acc = acc + R[r][k] * b[k];
+          out_amps[2 * e + r] = acc;
+        }
+      }
+    }
+  /* elitism: the best genome of the parent generation, angles included */
+  uint32_t bidx;
+  oracle_topk(F, cost, P, 1, &bidx);
+  memcpy(out, genome + (uint64_t)bidx * L, L);
+  memcpy(out_amps, amps + 2 * (uint64_t)bidx * L, 2 * L * sizeof(float));
+  free(cum);
+  free(parent);
+}

@@ -185,6 +185,15 @@ void oracle_ga_init(const oracle_problem *p, uint32_t G, uint8_t *genome);
 /* one generation: SUS selection on F, one-point crossover, per-gene mutation, elitism */
 void oracle_ga_next(const oracle_problem *p, uint32_t G, uint32_t gen, double ga_rate,
                     const uint8_t *genome, const double *F, const uint32_t *cost, uint8_t *out);
+/* the paper's own GA comparator on the Ising library (Sec. V-B): every gene is
+   a gate and its angle (qubit amplitudes, 2 floats); angles start uniform on
+   multiples of 2 pi / Q; two-point crossover; per gene, with probability
+   ga_rate a fresh gate and angle, else with probability ga_rate the angle
+   turned by +-m mutationRange / Q, m uniform in [0, Q] */
+void oracle_ga_init_amp(const oracle_problem *p, uint32_t G, uint8_t *genome, float *amps);
+void oracle_ga_next_amp(const oracle_problem *p, uint32_t G, uint32_t gen, double ga_rate,
+                        const uint8_t *genome, const float *amps, const double *F,
+                        const uint32_t *cost, uint8_t *out, float *out_amps);
 
 #ifdef __cplusplus
 }

@@ -180,3 +180,84 @@ def test_mutation_turns_the_angle():
     step = p.mutation_range / oracle.Q
     m = np.abs(d[moved]) / step
     assert np.abs(m - np.round(m)).max() < 1e-3
+
+
+# ---------------------------------------------------------------- the paper's GA on Ising genes
+def _ga_problem(P=400, L=12, n=3, seed=3, rng_=0.3):
+    return oracle.make_problem(n, L, P, ISING, W.cknot(n), seed=seed, mutation_range=rng_)
+
+
+def test_ising_ga_init_is_uniform_on_the_angle_lattice():
+    p = _ga_problem(P=2000, L=10)
+    G = oracle.num_gates(3, ISING)
+    g, a = oracle.ga_init_amp(p, G)
+    from scipy.stats import chisquare
+    assert chisquare(np.bincount(g.ravel(), minlength=G)).pvalue > 1e-3
+    step = 2 * np.pi / oracle.Q
+    th = np.mod(np.arctan2(a[..., 1].astype(np.float64), a[..., 0]), 2 * np.pi)
+    m = np.round(th / step).astype(np.int64) % oracle.Q
+    assert np.array_equal(a[..., 0], np.cos(m * step).astype(np.float32))
+    assert np.array_equal(a[..., 1], np.sin(m * step).astype(np.float32))
+    assert chisquare(np.bincount(m.ravel() * 8 // oracle.Q, minlength=8)).pvalue > 1e-3
+
+
+def test_ising_ga_two_point_crossover_moves_genes_with_their_angles():
+    p = _ga_problem()
+    G = oracle.num_gates(3, ISING)
+    rng = np.random.default_rng(1)
+    g = rng.integers(0, G, (p.P, p.L)).astype(np.uint8)
+    a = np.stack([np.cos(t := rng.uniform(0, 6.28, (p.P, p.L))), np.sin(t)], -1).astype(np.float32)
+    F = rng.uniform(0, 1, p.P)
+    out, oa = oracle.ga_next_amp(p, G, 0, 0.0, g, a, F, np.zeros(p.P, np.uint32))
+    rows = {(bytes(g[c]), a[c].tobytes()): c for c in range(p.P)}
+    seen_two = 0
+    for m in range(2, 200, 2):
+        x, y = out[m], out[m + 1]
+        xa, ya = oa[m], oa[m + 1]
+        ok = False
+        for lo in range(1, p.L + 1):
+            for hi in range(lo, p.L + 1):
+                inner = slice(lo, hi)
+                A = x.copy(); B = y.copy(); Aa = xa.copy(); Ba = ya.copy()
+                A[inner], B[inner] = y[inner], x[inner]
+                Aa[inner], Ba[inner] = ya[inner], xa[inner]
+                if (bytes(A), Aa.tobytes()) in rows and (bytes(B), Ba.tobytes()) in rows:
+                    ok = True
+                    seen_two += hi < p.L and lo < hi
+                    break
+            if ok:
+                break
+        assert ok, m
+    assert seen_two > 50  # genuinely two cuts, not one
+
+
+def test_ising_ga_mutation_rates_and_angle_steps():
+    p = _ga_problem(P=1500, L=16)
+    G = oracle.num_gates(3, ISING)
+    g, a = oracle.ga_init_amp(p, G)
+    F = np.full(p.P, 0.5)
+    cost = np.zeros(p.P, np.uint32)
+    base, base_a = oracle.ga_next_amp(p, G, 4, 0.0, g, a, F, cost)
+    rate = 0.1
+    mut, mut_a = oracle.ga_next_amp(p, G, 4, rate, g, a, F, cost)
+    gchg = (mut[1:] != base[1:]) | np.any(mut_a[1:] != base_a[1:], -1)
+    assert abs(gchg.mean() - (rate + (1 - rate) * rate)) < 0.01
+    # the angle-only mutations turn the amplitudes by a multiple of range/Q
+    same_gate = mut[1:] == base[1:]
+    turned = same_gate & np.any(mut_a[1:] != base_a[1:], -1)
+    z0 = base_a[1:][turned, 0] + 1j * base_a[1:][turned, 1]
+    z1 = mut_a[1:][turned, 0] + 1j * mut_a[1:][turned, 1]
+    d = np.angle(z1 / z0)
+    step = p.mutation_range / oracle.Q
+    # all but the fresh genes that drew the same gate again (about rate/G of the genes)
+    k = np.abs(d) / step
+    small = (np.abs(d) <= p.mutation_range + 1e-6) & (np.abs(k - np.round(k)) < 1e-2)
+    assert small.mean() > 1 - 2 * rate / G / ((1 - rate) * rate)
+    assert out_elite_ok(p, G, g, a)
+
+
+def out_elite_ok(p, G, g, a):
+    F = np.linspace(0, 1, p.P)[::-1].copy()
+    F[0] = 0.2  # the best is circuit 1
+    out, oa = oracle.ga_next_amp(p, G, 1, 0.5, g, a, F, np.zeros(p.P, np.uint32))
+    return np.array_equal(out[0], g[1]) and np.array_equal(oa[0], a[1])
