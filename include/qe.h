@@ -276,7 +276,9 @@ qe_status qe_last_generation(qe_ctx *ctx, uint32_t prob, uint8_t *h_gate_idx, ui
  *          b0, b1} (qutrit amplitudes, then qubit amplitudes);
  *   GA:    genome[P][L] uint8, the population the next qe_step generation
  *          evaluates (gene values below the library size; qe_set_state returns
- *          QE_EINVAL for any other value). */
+ *          QE_EINVAL for any other value); on QE_LIB_ISING followed by
+ *          angle[P][L][2] float, each gene's angle as the qubit amplitudes
+ *          (cos t, sin t). */
 qe_status qe_state_bytes(const qe_ctx *ctx, uint32_t prob, size_t *bytes);
 /* Copy the state out to / in from host memory of exactly qe_state_bytes bytes.
  * Synchronises. */

@@ -183,10 +183,6 @@ qe_status validate(const qe_problem &p, uint32_t idx) {
     if (v >= N || seen[v]) return bad("target_perm is not a permutation of 0..2^n-1");
     seen[v] = true;
   }
-  if (p.library == QE_LIB_ISING && p.encoding == QE_ENC_GA) {
-    snprintf(b, sizeof b, "problem %u: the GA runs on the discrete libraries only", idx);
-    return fail(nullptr, QE_EUNSUPPORTED, b);
-  }
   if (p.precision == QE_PREC_SPLIT_TC) {
     snprintf(b, sizeof b,
              "problem %u: QE_PREC_SPLIT_TC is not provided (gates are applied in registers; "
@@ -614,11 +610,14 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
       ar.take(&d.qubit_tab, (kQ + 1) * sizeof(float2));
       ar.take(&d.mut_list, 2 * P * 4);
       ar.take(&d.mut_cnt, 2 * 4);
-      if (d.ising) ar.take(&d.amps, 2 * PL * sizeof(float2));
     } else {
       ar.take(&d.ga_cum, P * 8);
       ar.take(&d.ga_info, 16);
+      // the Ising GA turns genes' angles with the same table as the qubit mutation
+      if (d.ising) ar.take(&d.qubit_tab, (kQ + 1) * sizeof(float2));
     }
+    // Ising: the slots' angles (QEQEA: as sampled; GA: the genomes' angles)
+    if (d.ising) ar.take(&d.amps, 2 * PL * sizeof(float2));
     // generation buffers, two of each (generation parity)
     ar.take(&d.gate_idx, 2 * PL);
     if (q.precision == QE_PREC_FP64) ar.take(&d.fit64, 2 * P * 8);
@@ -819,7 +818,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
       e = launch_init_state(ctx->d_probs, i, d.nseg, us);
       if (e == cudaSuccess) e = cudaMemsetAsync(d.mut_cnt, 0, 2 * 4, us);
     }
-    else e = launch_ga_init(ctx->d_probs, i, d.P, d.L, us);
+    else e = launch_ga_init(ctx->d_probs, i, d.P, d.L, ctx->g, us);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(us);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "initialising the state"));
@@ -1237,7 +1236,7 @@ qe_status qe_state_bytes(const qe_ctx *ctx, uint32_t prob, size_t *bytes) {
   if (!ctx || !bytes || prob >= ctx->probs.size()) return QE_EINVAL;
   const DevProblem &d = ctx->hp[prob];
   if (d.enc == QE_ENC_QEQEA) *bytes = (size_t)d.nseg * (32 + 32 + 4);
-  else *bytes = (size_t)d.P * d.L;
+  else *bytes = (size_t)d.P * d.L * (d.ising ? 1 + 8 : 1);  // genes (+ Ising angles)
   return QE_OK;
 }
 
@@ -1269,14 +1268,21 @@ static qe_status state_copy(qe_ctx *ctx, uint32_t prob, void *h, size_t bytes, b
                                        kd, us));
     }
   } else {
-    // the genome the next generation evaluates
-    uint8_t *genome = d.gate_idx + (size_t)(ctx->gen & 1u) * need;
+    // the genome the next generation evaluates: the genes, then (Ising) their
+    // angles as qubit amplitudes, two floats a gene
+    const size_t PL = (size_t)d.P * d.L;
+    uint8_t *genome = d.gate_idx + (size_t)(ctx->gen & 1u) * PL;
     if (!out)
-      for (size_t e = 0; e < need; ++e)
+      for (size_t e = 0; e < PL; ++e)
         if (((const uint8_t *)hb)[e] >= d.G)
           return fail(ctx, QE_EINVAL, "genome holds a gate index outside the library");
-    if (out) QE_CUDA(ctx, cudaMemcpyAsync(hb, genome, need, kd, us));
-    else QE_CUDA(ctx, cudaMemcpyAsync(genome, hb, need, kd, us));
+    if (out) QE_CUDA(ctx, cudaMemcpyAsync(hb, genome, PL, kd, us));
+    else QE_CUDA(ctx, cudaMemcpyAsync(genome, hb, PL, kd, us));
+    if (d.ising) {
+      float2 *am = d.amps + (size_t)(ctx->gen & 1u) * PL;
+      if (out) QE_CUDA(ctx, cudaMemcpyAsync(hb + PL, am, PL * sizeof(float2), kd, us));
+      else QE_CUDA(ctx, cudaMemcpyAsync(am, hb + PL, PL * sizeof(float2), kd, us));
+    }
   }
   QE_CUDA(ctx, cudaStreamSynchronize(us));
   return QE_OK;

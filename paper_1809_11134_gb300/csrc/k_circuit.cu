@@ -858,6 +858,11 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
       // GA: this generation's genome, bred by the previous generation (k_ga_next)
       if ((uint32_t)lane < p.L) o0 = op_of(p, gate_idx[(size_t)c * p.L + lane], bad);
       if ((uint32_t)lane + 32 < p.L) o1 = op_of(p, gate_idx[(size_t)c * p.L + lane + 32], bad);
+      if constexpr (ISING) {  // and the genes' angles
+        const float2 *amps = p.amps + (size_t)par * p.P * p.L + (size_t)c * p.L;
+        if ((uint32_t)lane < p.L) a0 = amps[lane];
+        if ((uint32_t)lane + 32 < p.L) a1 = amps[lane + 32];
+      }
     }
     R ic0 = R(1), is0 = R(0), ic1 = R(1), is1 = R(0);
     if constexpr (ISING) {

@@ -1,6 +1,9 @@
 // k_ga.cu -- the classical GA of the paper's comparison (Sec. V-B) on the same
 // evaluation path: integer gate-string genomes, stochastic universal sampling,
-// one-point crossover, per-gene mutation, elitism.
+// one-point crossover, per-gene mutation, elitism.  On the Ising library the
+// genes are (gate, angle) pairs bred as the paper's comparator does (Sec. V-B):
+// angles start on the 2 pi / Q lattice, crossover takes two points, and a gene
+// not drawn fresh may have its angle turned by a multiple of range / Q.
 //
 // Per generation g (genome in gate_idx buffer g & 1, already evaluated into
 // fit/meta buffer g & 1 by the circuit kernel without sampling):
@@ -10,8 +13,10 @@
 //              in the working precision;
 //   k_ga_next  one warp per pair of children: parents by SUS (pointer
 //              s + m floor(W/P), parent = first c with cum[c] > pointer),
-//              one-point crossover at 1 + below(u, L-1), per-gene mutation,
-//              child 0 = the elite; written to gate_idx buffer (g+1) & 1.
+//              one-point crossover at 1 + below(u, L-1) (Ising: genes in
+//              [min, max) of two such points swapped), per-gene mutation,
+//              child 0 = the elite; written to gate_idx buffer (g+1) & 1
+//              (Ising angles: amps buffer (g+1) & 1).
 // Philox streams as the oracle: (0, 0, g) for the SUS offset, (pair, 1, g) for
 // the cut, (child, 2 + t, g) for gene t's mutation, all with stream 4; the
 // initial genome draws (c, t, 0) with stream 5.
@@ -135,6 +140,24 @@ __global__ void __launch_bounds__(kGaThreads) k_ga_prep(const DevProblem *__rest
   }
 }
 
+// Per-gene mutation: word x decides a fresh gene (gate from y; Ising: its
+// angle from z on the 2 pi / Q lattice); for an Ising gene kept, word w decides
+// a turn of its angle by +-m range / Q (m from z, the sign from y's low bit),
+// rotated in binary32 in the order of the encoding's qubit mutation
+__device__ __forceinline__ void ga_mutate(const DevProblem &p, const DevGlobal &g, const uint4 v,
+                                          bool ising, uint8_t &gene, float2 &amp) {
+  if ((unsigned long long)v.x < p.ga_T) {
+    gene = (uint8_t)below(v.y, p.G);
+    if (ising) amp = g.ph_tab[below(v.z, kQ)];
+  } else if (ising && (unsigned long long)v.w < p.ga_T) {
+    const float2 cs = p.qubit_tab[below(v.z, kQ + 1)];
+    const float c = cs.x, s = (v.y & 1u) ? -cs.y : cs.y;
+    const float b0 = amp.x, b1 = amp.y;
+    amp.x = __fadd_rn(__fadd_rn(0.f, __fmul_rn(c, b0)), __fmul_rn(-s, b1));
+    amp.y = __fadd_rn(__fadd_rn(0.f, __fmul_rn(s, b0)), __fmul_rn(c, b1));
+  }
+}
+
 // first c in [0, P) with cum[c] > ptr (P - 1 if none)
 __device__ __forceinline__ uint32_t sus_parent(const unsigned long long *cum, uint32_t P,
                                                unsigned long long ptr) {
@@ -161,6 +184,10 @@ __global__ void __launch_bounds__(256) k_ga_next(const DevProblem *__restrict__ 
     const uint32_t P = p.P, L = p.L;
     const uint8_t *src = p.gate_idx + (size_t)(gen & 1u) * P * L;
     uint8_t *dst = p.gate_idx + (size_t)((gen + 1u) & 1u) * P * L;
+    // Ising genes also carry angles, bred with them
+    const bool ising = p.ising != 0;
+    const float2 *asrc = ising ? p.amps + (size_t)(gen & 1u) * P * L : nullptr;
+    float2 *adst = ising ? p.amps + (size_t)((gen + 1u) & 1u) * P * L : nullptr;
     const uint32_t m0 = 2 * pair, m1 = m0 + 1;
     const unsigned long long W = p.ga_info[0];
     const uint32_t elite = (uint32_t)p.ga_info[1];
@@ -173,47 +200,65 @@ __global__ void __launch_bounds__(256) k_ga_next(const DevProblem *__restrict__ 
       a = sus_parent(p.ga_cum, P, s0 + (unsigned long long)m0 * D);
       if (m1 < P) b = sus_parent(p.ga_cum, P, s0 + (unsigned long long)m1 * D);
     }
-    uint32_t cut = L;
-    if (m1 < P && L > 1) cut = 1 + below(draw(p, pair, 1, gen, kStGa).x, L - 1);
+    // gene t of child m0 comes from parent b for t in [lo, hi), else from a
+    uint32_t lo = L, hi = L;
+    if (m1 < P && L > 1) {
+      const uint4 v = draw(p, pair, 1, gen, kStGa);
+      const uint32_t x = 1 + below(v.x, L - 1);
+      if (ising) {  // two points
+        const uint32_t y = 1 + below(v.y, L - 1);
+        lo = x < y ? x : y;
+        hi = x < y ? y : x;
+      } else {  // one point: the tail from x on
+        lo = x;
+      }
+    }
     for (uint32_t t = lane; t < L; t += 32) {
-      const uint8_t ga = src[(size_t)a * L + t], gb = src[(size_t)b * L + t];
+      const bool sw = t >= lo && t < hi;
+      const size_t ea = (size_t)(sw ? b : a) * L + t, eb = (size_t)(sw ? a : b) * L + t;
       // child m0
-      uint8_t x = t < cut ? ga : gb;
+      uint8_t x = src[ea];
+      float2 ax = ising ? asrc[ea] : make_float2(0.f, 0.f);
       if (m0 == 0) {
         x = src[(size_t)elite * L + t];
+        if (ising) ax = asrc[(size_t)elite * L + t];
       } else {
-        const uint4 v = draw(p, m0, 2 + t, gen, kStGa);
-        if ((unsigned long long)v.x < p.ga_T) x = (uint8_t)below(v.y, p.G);
+        ga_mutate(p, g, draw(p, m0, 2 + t, gen, kStGa), ising, x, ax);
       }
       dst[(size_t)m0 * L + t] = x;
+      if (ising) adst[(size_t)m0 * L + t] = ax;
       if (m1 < P) {
-        uint8_t y = t < cut ? gb : ga;
-        const uint4 v = draw(p, m1, 2 + t, gen, kStGa);
-        if ((unsigned long long)v.x < p.ga_T) y = (uint8_t)below(v.y, p.G);
+        uint8_t y = src[eb];
+        float2 ay = ising ? asrc[eb] : make_float2(0.f, 0.f);
+        ga_mutate(p, g, draw(p, m1, 2 + t, gen, kStGa), ising, y, ay);
         dst[(size_t)m1 * L + t] = y;
+        if (ising) adst[(size_t)m1 * L + t] = ay;
       }
     }
   }
 }
 
-// initial genome: gene (c, t) = below(u, G) with Philox (c, t, 0, stream 5)
+// initial genome: gene (c, t) = below(u.x, G) with Philox (c, t, 0, stream 5);
+// an Ising gene's angle from u.y on the 2 pi / Q lattice
 __global__ void __launch_bounds__(256) k_ga_init(const DevProblem *__restrict__ probs,
-                                                 uint32_t prob) {
+                                                 uint32_t prob, DevGlobal g) {
   const DevProblem &p = probs[prob];
   const size_t n = (size_t)p.P * p.L;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x) {
     const uint32_t c = (uint32_t)(e / p.L), t = (uint32_t)(e % p.L);
-    p.gate_idx[e] = (uint8_t)below(draw(p, c, t, 0, kStGaInit).x, p.G);
+    const uint4 u = draw(p, c, t, 0, kStGaInit);
+    p.gate_idx[e] = (uint8_t)below(u.x, p.G);
+    if (p.ising) p.amps[e] = g.ph_tab[below(u.y, kQ)];
   }
 }
 
 cudaError_t launch_ga_init(const DevProblem *probs, uint32_t prob, uint32_t P, uint32_t L,
-                           cudaStream_t st) {
+                           const DevGlobal &g, cudaStream_t st) {
   uint64_t blocks = ((uint64_t)P * L + 255) / 256;
   if (blocks > 65536) blocks = 65536;
   if (!blocks) blocks = 1;
-  k_ga_init<<<(uint32_t)blocks, 256, 0, st>>>(probs, prob);
+  k_ga_init<<<(uint32_t)blocks, 256, 0, st>>>(probs, prob, g);
   return cudaGetLastError();
 }
 

@@ -98,7 +98,7 @@ cudaError_t launch_finish(const DevGlobal &g, cudaStream_t st);
 // generation the SUS prefix sums and elite of the searches in ids, then the
 // next genome (one warp per pair of children; prefix = pair-count prefix sums)
 cudaError_t launch_ga_init(const DevProblem *probs, uint32_t prob, uint32_t P, uint32_t L,
-                           cudaStream_t st);
+                           const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_ga_prep(const DevProblem *probs, const uint32_t *ids, uint32_t n_ga,
                            const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_ga_next(const LaunchCfg &lc, const DevProblem *probs, const uint32_t *ids,

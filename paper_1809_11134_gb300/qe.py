@@ -309,13 +309,18 @@ class Context:
         return n.value
 
     def get_state(self, prob):
-        """QEQEA: (cur[S*8] f32, best[S*8] f32, best_f[S] f32); GA: genome [P, L] u8."""
+        """QEQEA: (cur[S*8] f32, best[S*8] f32, best_f[S] f32); GA: genome [P, L] u8,
+        on the Ising library (genome, angles [P, L, 2] f32)."""
         nb = self.state_bytes(prob)
         buf = np.zeros(nb, np.uint8)
         _check(self.h, lib().qe_get_state(self.h, prob, buf.ctypes.data_as(C.c_void_p), nb))
         p = self._probs[prob]
         if p.encoding == QE_ENC_GA:
-            return buf.reshape(p.population, p.circuit_len)
+            PL = p.population * p.circuit_len
+            genome = buf[:PL].reshape(p.population, p.circuit_len).copy()
+            if p.library == QE_LIB_ISING:
+                return genome, buf[PL:].view(np.float32).reshape(p.population, p.circuit_len, 2)
+            return genome
         S = nb // 68
         cur = buf[:32 * S].view(np.float32).copy()
         best = buf[32 * S:64 * S].view(np.float32).copy()
@@ -323,9 +328,13 @@ class Context:
         return cur, best, bf
 
     def set_state(self, prob, cur, best=None, best_f=None):
+        """QEQEA: set_state(prob, cur, best, best_f); GA: set_state(prob, genome),
+        on the Ising library set_state(prob, genome, angles)."""
         p = self._probs[prob]
         if p.encoding == QE_ENC_GA:
             buf = np.ascontiguousarray(cur, np.uint8).ravel()
+            if p.library == QE_LIB_ISING:
+                buf = np.concatenate([buf, np.ascontiguousarray(best, np.float32).view(np.uint8).ravel()])
         else:
             buf = np.concatenate([np.ascontiguousarray(cur, np.float32).view(np.uint8).ravel(),
                                   np.ascontiguousarray(best, np.float32).view(np.uint8).ravel(),

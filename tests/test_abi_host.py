@@ -113,16 +113,21 @@ def test_struct_layouts(qe):
     assert C.sizeof(qe.qe_report) == 120 + 512
 
 
-def test_ising_library_geometry_and_refusals(qe):
+def test_ising_library_geometry_and_acceptance(qe, monkeypatch):
     """QE_LIB_ISING: n rotation regions plus n(n-1)/2 templates, 3n + n(n-1)/2 gates
-    (the oracle's numbers); the GA on it is refused as unsupported, without a GPU."""
+    (the oracle's numbers); both encodings pass validation (they reach the
+    allocation, failed here on purpose), mixing it with a discrete library does not."""
     import oracle
     for n in range(1, 6):
         g, r = qe.qe_library_info(n, qe.QE_LIB_ISING)
         assert (g, r) == (oracle.num_gates(n, oracle.LIB_ISING),
                           oracle.num_regions(n, oracle.LIB_ISING))
-    s = W.Search(3, 8, 64, W.LIB_ISING, W.cknot(3), encoding=W.ENC_GA)
+    monkeypatch.setenv("QE_FAULT_ALLOC", "1")
+    for enc in (W.ENC_QEQEA, W.ENC_GA):
+        s = W.Search(3, 8, 64, W.LIB_ISING, W.cknot(3), encoding=enc)
+        probs = (qe.qe_problem * 1)(qe.to_problem(s))
+        h = C.c_void_p()
+        assert qe.lib().qe_init(C.byref(h), probs, 1, None) == qe.QE_ENOMEM
+    s = W.Search(3, 8, 64, W.LIB_ISING | W.LIB_NCV, W.cknot(3), encoding=W.ENC_GA)
     probs = (qe.qe_problem * 1)(qe.to_problem(s))
-    h = C.c_void_p()
-    assert qe.lib().qe_init(C.byref(h), probs, 1, None) == qe.QE_EUNSUPPORTED
-    assert b"GA" in qe.lib().qe_last_error(None)
+    assert qe.lib().qe_init(C.byref(C.c_void_p()), probs, 1, None) == qe.QE_EINVAL
