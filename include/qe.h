@@ -58,7 +58,8 @@ typedef enum {
   QE_ETIMEOUT = 4,     /* a bounded device wait expired; context poisoned */
   QE_ENUMERIC = 5,     /* device saw an invalid gate index or a non-finite fitness */
   QE_ESTATE = 6,       /* context poisoned, or call invalid for this problem */
-  QE_EUNSUPPORTED = 7  /* valid request not implemented by this build / device */
+  QE_EUNSUPPORTED = 7, /* valid request not implemented by this build / device */
+  QE_EIO = 8           /* a checkpoint file could not be opened, read or written */
 } qe_status;
 
 /* gate library bits */
@@ -74,9 +75,10 @@ typedef enum {
  * sin theta), theta in [0, 2 pi) (the qubit is not measured), and the gates
  * use cos(theta/2) = sgn(b1) sqrt((1 + b0)/2), sin(theta/2) = sqrt((1 - b0)/2)
  * (sgn(b1) = -1 iff b1 < 0); J(theta) = exp(-i theta/2 Z_i Z_j).  The qubit
- * mutation turns theta by +-(1 - f) mutationRange (Sec. IV-F).  QEQEA
- * encoding only; circuits given by the caller carry their angles as such
- * amplitude pairs (qe_eval_amp, qe_compose_amp). */
+ * mutation turns theta by +-(1 - f) mutationRange (Sec. IV-F).  Under
+ * QE_ENC_GA the genes are (gate, angle) pairs bred as the paper's comparator
+ * (Sec. V-B): see qe_step.  Circuits given by the caller carry their angles as
+ * such amplitude pairs (qe_eval_amp, qe_compose_amp). */
 #define QE_LIB_ISING 8u
 
 /* arithmetic of the composition */
@@ -266,7 +268,8 @@ qe_status qe_stage_times(qe_ctx *ctx, float *ms);
 /* The last generation of search prob as run by qe_step: its circuits
  * h_gate_idx[P*L], segment ids h_seg_id[P*L] (QEQEA), working-precision
  * fitness widened to double h_fitness[P], and top-k h_topk[max(topk,1)].
- * Any pointer may be NULL.  Synchronises. */
+ * Any pointer may be NULL.  Synchronises.  QE_ESTATE if no generation has run
+ * since qe_init or qe_load (a checkpoint does not hold the last generation). */
 qe_status qe_last_generation(qe_ctx *ctx, uint32_t prob, uint8_t *h_gate_idx, uint32_t *h_seg_id,
                              double *h_fitness, qe_ranked *h_topk);
 
@@ -284,6 +287,36 @@ qe_status qe_state_bytes(const qe_ctx *ctx, uint32_t prob, size_t *bytes);
  * Synchronises. */
 qe_status qe_get_state(qe_ctx *ctx, uint32_t prob, void *h_buf, size_t bytes);
 qe_status qe_set_state(qe_ctx *ctx, uint32_t prob, const void *h_buf, size_t bytes);
+
+/* Checkpoint / resume.  Every random draw is a Philox function of (seed,
+ * generation, ...) (Sec. IV-D sampling, Sec. IV-F mutation, Sec. V-B GA), so a
+ * run's whole state is each search's encoding state (the qe_get_state
+ * layout), its best-so-far record and the generation counter; a context that
+ * loads a checkpoint continues the saved run bit for bit.
+ *
+ * qe_save ranks a pending last generation, then writes the file at path (a
+ * temporary beside it, renamed over it once complete): a 48-byte header
+ * {"QECKPT1\0", version 1, n_probs, generation, sizeof(qe_problem),
+ * sizeof(qe_report), 0, payload bytes, FNV-1a 64-bit hash of the payload},
+ * then the payload {qe_problem[n_probs], qe_report[n_probs] (the records as
+ * qe_step reports them), and per search a uint64 byte count and its
+ * qe_get_state bytes}, little-endian.  Synchronises.  QE_EIO if the file
+ * cannot be written (the previous file, if any, is left in place).
+ *
+ * qe_load reads a checkpoint into a context created with the same problems
+ * (byte-equal qe_problem arrays): encoding state, records and generation
+ * counter; the launch plan is kept.  It checks the whole file first (magic,
+ * version, sizes, hash, problems, record generations, gene values) and
+ * returns QE_EINVAL with nothing changed if any check fails, QE_EIO if the
+ * file cannot be read.  Synchronises.
+ *
+ * qe_checkpoint_info reads and checks a checkpoint without a context or GPU:
+ * *n_probs and *gen (either may be NULL), and the problems into h_probs when
+ * capacity >= *n_probs (so qe_init can recreate the context). */
+qe_status qe_save(qe_ctx *ctx, const char *path);
+qe_status qe_load(qe_ctx *ctx, const char *path);
+qe_status qe_checkpoint_info(const char *path, qe_problem *h_probs, uint32_t capacity,
+                             uint32_t *n_probs, uint32_t *gen);
 
 /* Generations completed by qe_step. */
 qe_status qe_generation(const qe_ctx *ctx, uint32_t *gen);

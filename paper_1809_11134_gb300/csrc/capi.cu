@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <unistd.h>
+
 #include "../../include/qe.h"
 #include "qe_dev.cuh"
 #include "qe_host.h"
@@ -79,6 +81,7 @@ struct qe_ctx {
   cudaGraph_t dgraph = nullptr;      // ranking of the last generation alone (drain)
   cudaGraphExec_t dexec = nullptr;
   bool pending_rank = false;         // the last generation is not ranked yet
+  bool has_last = false;             // a generation ran since qe_init / qe_load
   // stage timing: events recorded inside the generation graph
   bool timing = false;
   cudaEvent_t tev[8] = {nullptr};
@@ -1010,7 +1013,7 @@ qe_status qe_step(qe_ctx *ctx, uint32_t n_gen, qe_report *h_reports) {
   }
   for (uint32_t k = 0; k < n_gen; ++k) QE_CUDA(ctx, cudaGraphLaunch(ctx->gexec, ctx->user));
   ctx->gen += n_gen;
-  if (n_gen) ctx->pending_rank = true;
+  if (n_gen) ctx->pending_rank = ctx->has_last = true;
   if (!h_reports) return QE_OK;  // enqueued only; the last generation ranks later
   {
     qe_status st = drain(ctx);
@@ -1100,7 +1103,7 @@ qe_status qe_autotune(qe_ctx *ctx, uint32_t gens_per_plan, float *h_ms, uint32_t
   }
   if (e == cudaSuccess && st == QE_OK) e = cudaStreamSynchronize(ctx->user);
   ctx->gen += launched;
-  if (launched) ctx->pending_rank = true;
+  if (launched) ctx->pending_rank = ctx->has_last = true;
   if (st != QE_OK || e != cudaSuccess) {
     cleanup(C);
     return st != QE_OK ? st : cuda_fail(ctx, e, "autotuning the generation graph");
@@ -1193,12 +1196,13 @@ qe_status qe_last_generation(qe_ctx *ctx, uint32_t prob, uint8_t *h_gate_idx, ui
                              double *h_fitness, qe_ranked *h_topk) {
   qe_status st = check_ctx(ctx, prob);
   if (st != QE_OK) return st;
+  if (!ctx->has_last) return fail(ctx, QE_ESTATE, "no generation has run since qe_init or qe_load");
   const DevProblem &d = ctx->hp[prob];
   cudaStream_t us = ctx->user;
   st = drain(ctx);
   if (st != QE_OK) return st;
   const size_t PL = (size_t)d.P * d.L;
-  const size_t b = ctx->gen ? ((ctx->gen - 1) & 1u) : 0;  // buffer of the last generation
+  const size_t b = (ctx->gen - 1) & 1u;  // buffer of the last generation
   std::vector<float> f32;
   std::vector<Ranked> tk;
   if (h_gate_idx)
@@ -1294,6 +1298,222 @@ qe_status qe_get_state(qe_ctx *ctx, uint32_t prob, void *h_buf, size_t bytes) {
 
 qe_status qe_set_state(qe_ctx *ctx, uint32_t prob, const void *h_buf, size_t bytes) {
   return state_copy(ctx, prob, const_cast<void *>(h_buf), bytes, false);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ checkpoints
+// File: CkptHeader, then the payload {qe_problem[n], qe_report[n], and per
+// search a uint64 byte count and its state in the qe_get_state layout}, all
+// little-endian as the host writes them; the header carries the payload's
+// FNV-1a 64-bit hash.  Philox draws are keyed by (seed, generation, ...), so
+// the encoding state, the best-so-far records and the generation counter are
+// the whole state of a run: a loaded context continues it bit for bit.
+namespace {
+
+struct CkptHeader {
+  char magic[8];  // "QECKPT1"
+  uint32_t version, n_probs, gen, problem_bytes, report_bytes, reserved;
+  uint64_t payload_bytes, hash;
+};
+static_assert(sizeof(CkptHeader) == 48, "checkpoint header layout");
+const char kCkptMagic[8] = {'Q', 'E', 'C', 'K', 'P', 'T', '1', 0};
+constexpr uint32_t kCkptVersion = 1;
+
+uint64_t fnv1a64(const char *b, size_t n) {
+  uint64_t h = 14695981039346656037ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= (uint8_t)b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// Reads and checks a whole checkpoint file: magic, version, struct sizes,
+// payload length and hash.  On success the payload starts with the problems.
+qe_status read_ckpt(qe_ctx *ctx, const char *path, CkptHeader &hd, std::vector<char> &pay) {
+  if (!path) return fail(ctx, QE_EINVAL, "null path");
+  FILE *f = fopen(path, "rb");
+  if (!f) return fail(ctx, QE_EIO, std::string("cannot open ") + path);
+  bool ok = fread(&hd, sizeof hd, 1, f) == 1;
+  if (ok && (memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != kCkptVersion ||
+             hd.problem_bytes != sizeof(qe_problem) || hd.report_bytes != sizeof(qe_report) ||
+             hd.n_probs == 0 || hd.payload_bytes > ((uint64_t)1 << 40))) {
+    fclose(f);
+    return fail(ctx, QE_EINVAL, "not a checkpoint of this format version");
+  }
+  if (ok) {
+    pay.resize(hd.payload_bytes);
+    ok = hd.payload_bytes == 0 || fread(pay.data(), 1, pay.size(), f) == pay.size();
+    char extra;
+    ok = ok && fread(&extra, 1, 1, f) == 0;  // nothing after the payload
+  }
+  fclose(f);
+  if (!ok || fnv1a64(pay.data(), pay.size()) != hd.hash)
+    return fail(ctx, QE_EINVAL, "checkpoint is truncated or corrupted");
+  if (pay.size() < (uint64_t)hd.n_probs * (sizeof(qe_problem) + sizeof(qe_report)))
+    return fail(ctx, QE_EINVAL, "checkpoint is truncated or corrupted");
+  return QE_OK;
+}
+
+void report_of(const Best &b, qe_report &r) {
+  memset(&r, 0, sizeof r);
+  r.generation = b.generation;
+  r.best_gen = b.best_gen;
+  r.best_fitness = b.best_fitness;
+  r.gen_best_fitness = b.gen_best_fitness;
+  r.mean_fitness = b.mean_fitness;
+  r.useful_flops = b.useful_flops;
+  r.best_cost = b.best_cost;
+  r.best_len = b.best_len;
+  r.error_word = b.error_word;
+  memcpy(r.best_gates, b.best_gates, 64);
+  memcpy(r.best_amps, b.best_amps, sizeof r.best_amps);
+}
+
+void best_of(const qe_report &r, Best &b) {
+  memset(&b, 0, sizeof b);
+  b.generation = r.generation;
+  b.best_gen = r.best_gen;
+  b.best_fitness = r.best_fitness;
+  b.gen_best_fitness = r.gen_best_fitness;
+  b.mean_fitness = r.mean_fitness;
+  b.useful_flops = r.useful_flops;
+  b.best_cost = r.best_cost;
+  b.best_len = r.best_len;
+  b.error_word = r.error_word;
+  memcpy(b.best_gates, r.best_gates, 64);
+  memcpy(b.best_amps, r.best_amps, sizeof b.best_amps);
+}
+
+}  // namespace
+
+extern "C" {
+
+qe_status qe_save(qe_ctx *ctx, const char *path) {
+  if (!ctx) return fail(nullptr, QE_EINVAL, "null context");
+  if (ctx->poisoned) return fail(ctx, QE_ESTATE, "context is poisoned by an earlier CUDA error");
+  if (!path) return fail(ctx, QE_EINVAL, "null path");
+  qe_status st = drain(ctx);  // the last generation's record
+  if (st != QE_OK) return st;
+  const uint32_t np = (uint32_t)ctx->probs.size();
+  QE_CUDA(ctx, cudaMemcpyAsync(ctx->h_recs, ctx->d_recs, np * sizeof(Best), cudaMemcpyDeviceToHost,
+                               ctx->user));
+  QE_CUDA(ctx, cudaStreamSynchronize(ctx->user));
+  std::vector<char> pay(np * (sizeof(qe_problem) + sizeof(qe_report)));
+  memcpy(pay.data(), ctx->probs.data(), np * sizeof(qe_problem));
+  for (uint32_t i = 0; i < np; ++i) {
+    qe_report r;
+    report_of(ctx->h_recs[i], r);
+    memcpy(pay.data() + np * sizeof(qe_problem) + i * sizeof(qe_report), &r, sizeof r);
+  }
+  for (uint32_t i = 0; i < np; ++i) {
+    size_t nb = 0;
+    qe_state_bytes(ctx, i, &nb);
+    const size_t at = pay.size();
+    pay.resize(at + 8 + nb);
+    const uint64_t nb64 = nb;
+    memcpy(pay.data() + at, &nb64, 8);
+    if ((st = state_copy(ctx, i, pay.data() + at + 8, nb, true)) != QE_OK) return st;
+  }
+  CkptHeader hd;
+  memset(&hd, 0, sizeof hd);
+  memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = kCkptVersion;
+  hd.n_probs = np;
+  hd.gen = ctx->gen;
+  hd.problem_bytes = sizeof(qe_problem);
+  hd.report_bytes = sizeof(qe_report);
+  hd.payload_bytes = pay.size();
+  hd.hash = fnv1a64(pay.data(), pay.size());
+  // write beside the target, then rename over it: a crash leaves the old file
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE *f = fopen(tmp.c_str(), "wb");
+  if (!f) return fail(ctx, QE_EIO, "cannot create " + tmp);
+  bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 && fwrite(pay.data(), 1, pay.size(), f) == pay.size();
+  ok = fflush(f) == 0 && ok;
+  ok = fsync(fileno(f)) == 0 && ok;
+  ok = fclose(f) == 0 && ok;
+  if (!ok || rename(tmp.c_str(), path) != 0) {
+    remove(tmp.c_str());
+    return fail(ctx, QE_EIO, std::string("cannot write ") + path);
+  }
+  return QE_OK;
+}
+
+qe_status qe_load(qe_ctx *ctx, const char *path) {
+  if (!ctx) return fail(nullptr, QE_EINVAL, "null context");
+  if (ctx->poisoned) return fail(ctx, QE_ESTATE, "context is poisoned by an earlier CUDA error");
+  CkptHeader hd;
+  std::vector<char> pay;
+  qe_status st = read_ckpt(ctx, path, hd, pay);
+  if (st != QE_OK) return st;
+  const uint32_t np = (uint32_t)ctx->probs.size();
+  if (hd.n_probs != np ||
+      memcmp(pay.data(), ctx->probs.data(), np * sizeof(qe_problem)) != 0)
+    return fail(ctx, QE_EINVAL, "checkpoint holds other searches than this context");
+  // check everything before changing anything
+  const char *reps = pay.data() + np * sizeof(qe_problem);
+  std::vector<size_t> off(np);
+  size_t at = np * (sizeof(qe_problem) + sizeof(qe_report));
+  for (uint32_t i = 0; i < np; ++i) {
+    qe_report r;
+    memcpy(&r, reps + i * sizeof(qe_report), sizeof r);
+    if (r.generation != hd.gen)
+      return fail(ctx, QE_EINVAL, "checkpoint record and generation counter disagree");
+    size_t nb = 0;
+    qe_state_bytes(ctx, i, &nb);
+    uint64_t nb64 = 0;
+    if (at + 8 > pay.size()) return fail(ctx, QE_EINVAL, "checkpoint is truncated or corrupted");
+    memcpy(&nb64, pay.data() + at, 8);
+    if (nb64 != nb || at + 8 + nb > pay.size())
+      return fail(ctx, QE_EINVAL, "checkpoint state has the wrong size");
+    off[i] = at + 8;
+    const DevProblem &d = ctx->hp[i];
+    if (d.enc == QE_ENC_GA) {
+      const uint8_t *g = (const uint8_t *)pay.data() + off[i];
+      for (size_t e = 0; e < (size_t)d.P * d.L; ++e)
+        if (g[e] >= d.G) return fail(ctx, QE_EINVAL, "checkpoint genome holds an invalid gene");
+    }
+    at += 8 + nb;
+  }
+  if (at != pay.size()) return fail(ctx, QE_EINVAL, "checkpoint is truncated or corrupted");
+  // the loaded generation is ranked already: the next generation graph skips
+  // the pipelined ranking of generation gen - 1
+  cudaStream_t us = ctx->user;
+  ctx->gen = hd.gen;
+  ctx->pending_rank = ctx->has_last = false;
+  for (uint32_t i = 0; i < np; ++i) {
+    qe_report r;
+    memcpy(&r, reps + i * sizeof(qe_report), sizeof r);
+    best_of(r, ctx->h_recs[i]);
+    size_t nb = 0;
+    qe_state_bytes(ctx, i, &nb);
+    if ((st = state_copy(ctx, i, pay.data() + off[i], nb, false)) != QE_OK) return st;
+    const DevProblem &d = ctx->hp[i];
+    if (d.mut_cnt) QE_CUDA(ctx, cudaMemsetAsync(d.mut_cnt, 0, 2 * 4, us));
+  }
+  QE_CUDA(ctx, cudaMemcpyAsync(ctx->d_recs, ctx->h_recs, np * sizeof(Best), cudaMemcpyHostToDevice,
+                               us));
+  QE_CUDA(ctx, cudaMemcpyAsync(ctx->g.gen, &hd.gen, 4, cudaMemcpyHostToDevice, us));
+  QE_CUDA(ctx, cudaMemcpyAsync(ctx->g.ranked, &hd.gen, 4, cudaMemcpyHostToDevice, us));
+  QE_CUDA(ctx, cudaMemsetAsync(ctx->g.rescore_n, 0, 4, us));
+  QE_CUDA(ctx, cudaMemsetAsync(ctx->g.rank_active, 0, 4, us));
+  QE_CUDA(ctx, cudaStreamSynchronize(us));
+  return QE_OK;
+}
+
+qe_status qe_checkpoint_info(const char *path, qe_problem *h_probs, uint32_t capacity,
+                             uint32_t *n_probs, uint32_t *gen) {
+  CkptHeader hd;
+  std::vector<char> pay;
+  qe_status st = read_ckpt(nullptr, path, hd, pay);
+  if (st != QE_OK) return st;
+  if (n_probs) *n_probs = hd.n_probs;
+  if (gen) *gen = hd.gen;
+  if (h_probs && capacity >= hd.n_probs)
+    memcpy(h_probs, pay.data(), hd.n_probs * sizeof(qe_problem));
+  return QE_OK;
 }
 
 }  // extern "C"

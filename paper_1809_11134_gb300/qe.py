@@ -16,9 +16,10 @@ from . import workloads as W
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libqe.so")
 
-QE_OK, QE_EINVAL, QE_ENOMEM, QE_ECUDA, QE_ETIMEOUT, QE_ENUMERIC, QE_ESTATE, QE_EUNSUPPORTED = range(8)
+(QE_OK, QE_EINVAL, QE_ENOMEM, QE_ECUDA, QE_ETIMEOUT, QE_ENUMERIC, QE_ESTATE, QE_EUNSUPPORTED,
+ QE_EIO) = range(9)
 STATUS_NAMES = ["QE_OK", "QE_EINVAL", "QE_ENOMEM", "QE_ECUDA", "QE_ETIMEOUT", "QE_ENUMERIC",
-                "QE_ESTATE", "QE_EUNSUPPORTED"]
+                "QE_ESTATE", "QE_EUNSUPPORTED", "QE_EIO"]
 QE_LIB_NCV, QE_LIB_HT, QE_LIB_IDENTITY, QE_LIB_ISING = 1, 2, 4, 8
 QE_PREC_FP64, QE_PREC_FP32, QE_PREC_SPLIT_TC = 0, 1, 2
 QE_FIT_TRACE, QE_FIT_PROB = 0, 1
@@ -30,7 +31,7 @@ EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_amp", 
            "qe_compose", "qe_compose_amp",
            "qe_update", "qe_step", "qe_last_generation", "qe_state_bytes", "qe_get_state",
            "qe_set_state", "qe_generation", "qe_autotune", "qe_launch_plan", "qe_stage_timing",
-           "qe_stage_times", "qe_measure_alu_peaks",
+           "qe_stage_times", "qe_measure_alu_peaks", "qe_save", "qe_load", "qe_checkpoint_info",
            "qe_eval_rank_static", "qe_last_error", "qe_destroy"]
 
 
@@ -59,7 +60,8 @@ class qe_report(C.Structure):
 class QeError(RuntimeError):
     def __init__(self, status, message):
         self.status = status
-        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, message))
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES)
+                                     else status, message))
 
 
 _lib = None
@@ -96,6 +98,10 @@ def lib():
         L.qe_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
         L.qe_eval_rank_static.argtypes = [C.POINTER(qe_problem), vp, u32, vp, vp, vp,
                                           C.c_char_p, sz]
+        L.qe_save.argtypes = [vp, C.c_char_p]
+        L.qe_load.argtypes = [vp, C.c_char_p]
+        L.qe_checkpoint_info.argtypes = [C.c_char_p, C.POINTER(qe_problem), u32, C.POINTER(u32),
+                                         C.POINTER(u32)]
         L.qe_last_error.argtypes = [vp]
         L.qe_last_error.restype = C.c_char_p
         L.qe_destroy.argtypes = [vp]
@@ -341,6 +347,26 @@ class Context:
                                   np.ascontiguousarray(best_f, np.float32).view(np.uint8).ravel()])
         _check(self.h, lib().qe_set_state(self.h, prob, buf.ctypes.data_as(C.c_void_p), buf.size))
 
+    def save(self, path):
+        """qe_save: checkpoint every search (state, records, generation) to path."""
+        _check(self.h, lib().qe_save(self.h, os.fsencode(path)))
+
+    def load(self, path):
+        """qe_load: resume the run saved at path (same problems as this context)."""
+        _check(self.h, lib().qe_load(self.h, os.fsencode(path)))
+
+    @classmethod
+    def from_checkpoint(cls, path, stream=None):
+        """A new context for the searches saved at path, resumed where they stopped."""
+        probs, _ = checkpoint_info(path)
+        ctx = cls(probs, stream)
+        try:
+            ctx.load(path)
+        except Exception:
+            ctx.close()
+            raise
+        return ctx
+
     def autotune(self, gens_per_plan=2):
         """qe_autotune: time every launch plan on real generations, keep the
         fastest; returns the mean generation time (ms) of each plan tried."""
@@ -416,6 +442,15 @@ def qe_compose(ctx: Context, prob, gate_idx, unitary, n_circuits=None):
 
 def qe_update(ctx: Context, prob, gen, seg_id, fitness):
     return ctx.update(prob, gen, seg_id, fitness)
+
+
+def checkpoint_info(path):
+    """qe_checkpoint_info: ([qe_problem], generation) of a checkpoint file; no GPU needed."""
+    n, gen = C.c_uint32(), C.c_uint32()
+    _check(None, lib().qe_checkpoint_info(os.fsencode(path), None, 0, C.byref(n), C.byref(gen)))
+    arr = (qe_problem * n.value)()
+    _check(None, lib().qe_checkpoint_info(os.fsencode(path), arr, n.value, C.byref(n), C.byref(gen)))
+    return list(arr), gen.value
 
 
 def qe_step(ctx: Context, n_gen=1):
