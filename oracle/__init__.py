@@ -26,7 +26,7 @@ class Problem(C.Structure):
     _fields_ = [("n", C.c_uint32), ("L", C.c_uint32), ("P", C.c_uint32), ("library", C.c_uint32),
                 ("fitness_kind", C.c_uint32), ("run", C.c_uint32), ("seed", C.c_uint64),
                 ("p_mutation", C.c_double), ("mutation_range", C.c_double),
-                ("cost_weight", C.c_double), ("perm", C.c_uint8 * 32)]
+                ("cost_weight", C.c_double), ("perm", C.c_uint8 * 32), ("shots", C.c_uint32)]
 
 
 class Report(C.Structure):
@@ -99,8 +99,9 @@ def lib():
 
 
 def make_problem(n, L, P, library, perm, seed=0, run=0, fitness_kind=FIT_TRACE, p_mutation=0.1,
-                 mutation_range=np.pi / 4, cost_weight=0.0):
+                 mutation_range=np.pi / 4, cost_weight=0.0, shots=1):
     p = Problem()
+    p.shots = shots
     p.n, p.L, p.P, p.library, p.fitness_kind, p.run = n, L, P, library, fitness_kind, run
     p.seed = seed
     p.p_mutation, p.mutation_range, p.cost_weight = p_mutation, mutation_range, cost_weight

@@ -66,7 +66,7 @@ static double unit(uint32_t u) { return ((double)u + 0.5) * 0x1p-32; }
 static float unit32(uint32_t u) { return ((float)(u >> 9) + 0.5f) * 0x1p-23f; }
 
 /* streams of the Philox counter's last word */
-enum { ST_SAMPLE = 0, ST_MUT_DECIDE = 1, ST_MUT_SEG = 2, ST_GA = 4, ST_GA_INIT = 5 };
+enum { ST_SAMPLE = 0, ST_MUT_DECIDE = 1, ST_MUT_SEG = 2, ST_SHOT = 3, ST_GA = 4, ST_GA_INIT = 5 };
 
 /* ======================================================================
  * Library and population geometry.
@@ -554,8 +554,25 @@ void oracle_sample_amp(const oracle_problem *p, const float *cur, uint32_t gen, 
       float p2 = q[4] * q[4] + q[5] * q[5];
       float p01 = p0 + p1;
       float s = p01 + p2;
-      float x = unit32(u[2]) * s;
-      uint32_t k = (x < p0) ? 0u : ((x < p01) ? 1u : 2u);
+      uint32_t k;
+      if (p->shots <= 1) {
+        float x = unit32(u[2]) * s;
+        k = (x < p0) ? 0u : ((x < p01) ? 1u : 2u);
+      } else {
+        /* Sec. IV-A1: the qutrit is measured K times and the most frequent
+           outcome taken (the lowest outcome on a tie); shot j uses word j mod 4
+           of the draw (c, t + 64 floor(j / 4), gen) of its own stream */
+        uint32_t count[3] = {0, 0, 0};
+        for (uint32_t j = 0; j < p->shots; ++j) {
+          uint32_t w[4];
+          draw(p, c, t + 64u * (j / 4u), gen, ST_SHOT, w);
+          float x = unit32(w[j % 4u]) * s;
+          count[(x < p0) ? 0 : ((x < p01) ? 1 : 2)] += 1;
+        }
+        k = 0;
+        if (count[1] > count[k]) k = 1;
+        if (count[2] > count[k]) k = 2;
+      }
       uint32_t g = oracle_region_gate(p->n, p->library, r, k);
       if (has_qubit) {
         /* qubit measurement: outcome 1 (gate present) with probability b1^2/(b0^2+b1^2) */

@@ -93,6 +93,7 @@ typedef struct {
   double mutation_range; /* mutationRange, radians */
   double cost_weight;    /* lambda: F = f - lambda * cost / L */
   uint8_t perm[32];      /* target: T|j> = |perm[j]> */
+  uint32_t shots;        /* qutrit measurements per slot, majority taken (Sec. IV-A1); 0 or 1 = one */
 } oracle_problem;
 
 /* ---- Philox4x32-10 (Salmon et al., SC'11) ---- */

@@ -79,6 +79,7 @@ class Search:
     mutation_range: float = float(np.pi / 4)
     ga_mutation_rate: float = 0.02
     cost_weight: float = 0.0
+    shots: int = 1  # qutrit measurements per slot, majority outcome taken
     name: str = field(default="")
     encoding: int = ENC_QEQEA
 

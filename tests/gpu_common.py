@@ -8,7 +8,8 @@ from paper_1809_11134_gb300 import workloads as W
 def oracle_problem(s: W.Search, run: int):
     return oracle.make_problem(s.n, s.L, s.P, s.library, s.perm, seed=s.seed, run=run,
                                fitness_kind=s.fitness_kind, p_mutation=s.p_mutation,
-                               mutation_range=s.mutation_range, cost_weight=s.cost_weight)
+                               mutation_range=s.mutation_range, cost_weight=s.cost_weight,
+                               shots=s.shots)
 
 
 def eps_d(L):
