@@ -100,6 +100,7 @@ typedef enum {
 #define QE_ENC_GA 1u    /* classical GA on integer gate strings (Sec. V-B comparison) */
 
 #define QE_MAX_QUBITS 5u
+#define QE_MAX_SHOTS 64u
 #define QE_MAX_LEN 64u
 #define QE_MAX_POP (1u << 20)
 #define QE_MAX_TOPK 1024u
@@ -126,6 +127,13 @@ typedef struct {
   double ga_mutation_rate;/* GA: per-gene replacement probability, [0,1] */
   double cost_weight;     /* lambda: F = f - lambda * cost / L; cost = non-identity gates */
   uint8_t target_perm[32];/* T|j> = |target_perm[j]>, a permutation of 0..2^n-1 */
+  uint32_t shots;         /* K: measurements of a slot's qutrit, 0..QE_MAX_SHOTS; K > 1 keeps
+                             the most frequent outcome, the lowest on a tie (Sec. IV-A1:
+                             the qutrit is measured repeatedly to approximate its state);
+                             0 and 1 measure once.  QEQEA only (the GA ignores it).  Shot j
+                             compares word j mod 4 of Philox (c, t + 64 floor(j/4), gen,
+                             run << 4 | 3) with the outcome CDF in binary32. */
+  uint32_t reserved;      /* 0 */
 } qe_problem;
 
 /* one ranked circuit: index in the population, gate cost, binary64 fitness */

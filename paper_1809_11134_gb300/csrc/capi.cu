@@ -64,6 +64,11 @@ struct qe_ctx {
   // all GA searches (breeding launches): ids and prefix sums of ceil(P/2) pairs
   uint32_t n_ga = 0, ga_pairs = 0;
   uint32_t *d_ga_ids = nullptr, *d_ga_prefix = nullptr;
+  // QEQEA searches measuring each qutrit K > 1 times (k_presample): ids and
+  // prefix sums of P*L slots
+  uint32_t n_shot = 0;
+  uint32_t *d_shot_ids = nullptr;
+  unsigned long long *d_shot_prefix = nullptr, shot_total = 0;
   // per-search single arrays for qe_update: {id}, {0, P*L}, {0, ceil(P/32)*R}
   uint32_t *d_single = nullptr;
   RankJob *d_jobs = nullptr;
@@ -176,6 +181,8 @@ qe_status validate(const qe_problem &p, uint32_t idx) {
     return bad("mutation_range must be finite and >= 0");
   if (!(p.ga_mutation_rate >= 0.0 && p.ga_mutation_rate <= 1.0))
     return bad("ga_mutation_rate must be in [0,1]");
+  if (p.shots > QE_MAX_SHOTS) return bad("shots must be in [0, 64]");
+  if (p.reserved != 0) return bad("reserved must be 0");
   if (!std::isfinite(p.cost_weight)) return bad("cost_weight must be finite");
   const uint64_t S = (uint64_t)R * p.circuit_len * p.population;
   if (S >= (1ull << 32)) return bad("regions * L * P must be < 2^32");
@@ -381,7 +388,10 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
   mark(0, cs);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-  // generation g: circuits, then the two update roles
+  // generation g: K-shot measurements, circuits, then the two update roles
+  if (e == cudaSuccess && ctx->n_shot)
+    e = launch_presample(lc, ctx->d_probs, ctx->d_shot_ids, ctx->d_shot_prefix, ctx->n_shot,
+                         ctx->shot_total, ctx->g, ctx->side);
   const bool conc = plan.concurrent && ctx->groups.size() > 1;
   if (conc && e == cudaSuccess) e = cudaEventRecord(ctx->gfork, ctx->side);
   for (size_t k = 0; k < ctx->groups.size(); ++k) {
@@ -591,6 +601,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     d.has_qubit = (q.library & (QE_LIB_IDENTITY | QE_LIB_ISING)) ? 1u : 0u;
     d.measure_qubit = (q.library & QE_LIB_IDENTITY) ? 1u : 0u;
     d.ising = q.library == QE_LIB_ISING ? 1u : 0u;
+    d.shots = (q.encoding == QE_ENC_QEQEA && q.shots > 1) ? q.shots : 1u;
     d.base = d.measure_qubit;
     d.key0 = (uint32_t)q.seed;
     d.key1 = (uint32_t)(q.seed >> 32);
@@ -650,7 +661,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   ar.take(&ctx->d_stage_gates, max_PL);
   ar.take(&ctx->d_stage_fit, max_P * 8);
   // groups: searches by (arithmetic, library kind, qubit count), widest first
-  std::vector<uint32_t> upd, ga;
+  std::vector<uint32_t> upd, ga, shot;
   for (int k = 0; k < 2; ++k)
     for (int is = 0; is < 2; ++is)
       for (uint32_t nq = QE_MAX_QUBITS; nq >= 1; --nq) {
@@ -669,6 +680,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   for (uint32_t i = 0; i < n_probs; ++i) {
     if (probs[i].encoding == QE_ENC_QEQEA) upd.push_back(i);
     else ga.push_back(i);
+    if (probs[i].encoding == QE_ENC_QEQEA && probs[i].shots > 1) shot.push_back(i);
     if (probs[i].precision != QE_PREC_FP64)
       ctx->rescore_nq[probs[i].n_qubits] |= probs[i].library == QE_LIB_ISING ? 2 : 1;
   }
@@ -683,6 +695,9 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   ctx->n_ga = (uint32_t)ga.size();
   ar.take(&ctx->d_ga_ids, (ga.size() + 1) * 4);
   ar.take(&ctx->d_ga_prefix, (ga.size() + 1) * 4);
+  ctx->n_shot = (uint32_t)shot.size();
+  ar.take(&ctx->d_shot_ids, (shot.size() + 1) * 4);
+  ar.take(&ctx->d_shot_prefix, (shot.size() + 1) * 8);
 
   size_t free_b = 0, total_b = 0;
   e = cudaMemGetInfo(&free_b, &total_b);
@@ -808,6 +823,16 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     ctx->ga_pairs = pg.back();
     if (e == cudaSuccess) e = put(ctx->d_ga_ids, ga);
     if (e == cudaSuccess) e = put(ctx->d_ga_prefix, pg);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
+  }
+  {
+    std::vector<unsigned long long> ps(shot.size() + 1, 0);
+    for (size_t k = 0; k < shot.size(); ++k)
+      ps[k + 1] = ps[k] + (unsigned long long)ctx->hp[shot[k]].P * ctx->hp[shot[k]].L;
+    ctx->shot_total = ps.back();
+    if (e == cudaSuccess) e = put(ctx->d_shot_ids, shot);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->d_shot_prefix, ps.data(), ps.size() * 8, cudaMemcpyHostToDevice, us);
     if (e == cudaSuccess) e = cudaStreamSynchronize(us);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->g.gen, 0, 4, us);

@@ -569,9 +569,41 @@ __device__ __forceinline__ void prefetch_mutated(const DevProblem &p, uint32_t i
 }
 
 // ------------------------------------------------------------------ sampling
+// Sec. IV-A1: the qutrit measured K > 1 times, the most frequent outcome kept
+// (the lowest on a tie).  Shot j compares word j mod 4 of the Philox draw
+// (c, t + 64 floor(j / 4), gen, stream 3) with the same binary32 CDF as one
+// measurement.  The circuit kernel never runs it (its register budget is
+// tight): searches with K > 1 are measured by k_presample ahead of it.
+__device__ __forceinline__ uint32_t measure_shots(const DevProblem &p, uint32_t c, uint32_t t,
+                                               uint32_t gen, float p0, float p01, float s) {
+  uint32_t n0 = 0, n1 = 0, n2 = 0;
+  const uint32_t K = p.shots;
+  for (uint32_t j = 0; j < K; j += 4) {
+    const uint4 w = draw(p, c, t + 64u * (j >> 2), gen, kStShot);
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      if (j + q < K) {
+        const float x = __fmul_rn(unit32(ws[q]), s);
+        if (x < p0) ++n0;
+        else if (x < p01) ++n1;
+        else ++n2;
+      }
+    }
+  }
+  uint32_t k = 0, best = n0;
+  if (n1 > best) {
+    k = 1;
+    best = n1;
+  }
+  if (n2 > best) k = 2;
+  return k;
+}
+
 // Sec. IV-D: draw whichIndividual and whichRotationOrInteraction, form the
-// segment index (Eq. (10)), measure the segment's qutrit (and qubit) in binary32.
-template <bool ISING>
+// segment index (Eq. (10)), measure the segment's qutrit (and qubit) in binary32
+// (SHOTS: K times when the search asks for it).
+template <bool ISING, bool SHOTS = false>
 __device__ __forceinline__ void sample_slot(const DevProblem &p, uint32_t c, uint32_t t,
                                             uint32_t gen, uint32_t &g_out, uint32_t &seg_out,
                                             float2 &amp_out) {
@@ -587,8 +619,13 @@ __device__ __forceinline__ void sample_slot(const DevProblem &p, uint32_t c, uin
   const float p2 = __fadd_rn(__fmul_rn(b.x, b.x), __fmul_rn(b.y, b.y));
   const float p01 = __fadd_rn(p0, p1);
   const float s = __fadd_rn(p01, p2);
-  const float x = __fmul_rn(unit32(u.z), s);
-  const uint32_t k = (x < p0) ? 0u : ((x < p01) ? 1u : 2u);
+  uint32_t k;
+  if (SHOTS && p.shots > 1) {
+    k = measure_shots(p, c, t, gen, p0, p01, s);
+  } else {
+    const float x = __fmul_rn(unit32(u.z), s);
+    k = (x < p0) ? 0u : ((x < p01) ? 1u : 2u);
+  }
   uint32_t g = p.base + 3u * r + k;
   if constexpr (ISING) {
     if (r >= p.n) g = 3u * p.n + (r - p.n);  // the interaction template of that pair
@@ -835,7 +872,23 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
     bool bad = false;
     const bool qeqea = p.enc == kEncQeqea;
     float2 a0 = make_float2(1.f, 0.f), a1 = a0;  // Ising: the slots' angles
-    if (qeqea) {
+    if (qeqea && p.shots > 1) {
+      // measured K times by k_presample ahead of this kernel
+      if ((uint32_t)lane < p.L) {
+        o0 = op_of(p, gate_idx[(size_t)c * p.L + lane], bad);
+        seg0 = p.seg_id[(size_t)c * p.L + lane];
+      }
+      if ((uint32_t)lane + 32 < p.L) {
+        o1 = op_of(p, gate_idx[(size_t)c * p.L + lane + 32], bad);
+        seg1 = p.seg_id[(size_t)c * p.L + lane + 32];
+      }
+      if constexpr (ISING) {
+        const float2 *amps = p.amps + (size_t)par * p.P * p.L + (size_t)c * p.L;
+        if ((uint32_t)lane < p.L) a0 = amps[lane];
+        if ((uint32_t)lane + 32 < p.L) a1 = amps[lane + 32];
+      }
+      prefetch_mutated(p, c, gen, lane);
+    } else if (qeqea) {
       float2 *amps = ISING ? p.amps + (size_t)par * p.P * p.L + (size_t)c * p.L : nullptr;
       if ((uint32_t)lane < p.L) {
         uint32_t gg;
@@ -886,6 +939,40 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
   }
 }
 
+// Measurement ahead of the circuit kernel for the searches that measure each
+// qutrit K > 1 times: one thread per slot over all of them (prefix sums of
+// P * L), writing this generation's gate_idx, seg_id and (Ising) angles.
+__global__ void __launch_bounds__(256) k_presample(const DevProblem *__restrict__ probs,
+                                                   const uint32_t *__restrict__ ids,
+                                                   const unsigned long long *__restrict__ prefix,
+                                                   uint32_t n_ids, unsigned long long total,
+                                                   DevGlobal g) {
+  const uint32_t gen = *g.gen;
+  const uint32_t par = gen & 1u;
+  for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+       e < total; e += (unsigned long long)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = n_ids;  // the search holding slot e
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (prefix[mid] <= e) lo = mid;
+      else hi = mid;
+    }
+    const DevProblem &p = probs[ids[lo]];
+    const size_t x = (size_t)(e - prefix[lo]);
+    const uint32_t c = (uint32_t)(x / p.L), t = (uint32_t)(x % p.L);
+    uint32_t gg, seg;
+    float2 amp;
+    if (p.ising) {
+      sample_slot<true, true>(p, c, t, gen, gg, seg, amp);
+      p.amps[(size_t)par * p.P * p.L + x] = amp;
+    } else {
+      sample_slot<false, true>(p, c, t, gen, gg, seg, amp);
+    }
+    p.gate_idx[(size_t)par * p.P * p.L + x] = (uint8_t)gg;
+    p.seg_id[x] = seg;
+  }
+}
+
 // Measurement only (qe_sample).
 __global__ void __launch_bounds__(256) k_sample(const DevProblem *__restrict__ probs,
                                                 uint32_t prob, uint32_t gen, uint8_t *gate_idx,
@@ -897,8 +984,8 @@ __global__ void __launch_bounds__(256) k_sample(const DevProblem *__restrict__ p
     const uint32_t c = (uint32_t)(e / p.L), t = (uint32_t)(e % p.L);
     uint32_t gg, seg;
     float2 amp;
-    if (p.ising) sample_slot<true>(p, c, t, gen, gg, seg, amp);
-    else sample_slot<false>(p, c, t, gen, gg, seg, amp);
+    if (p.ising) sample_slot<true, true>(p, c, t, gen, gg, seg, amp);
+    else sample_slot<false, true>(p, c, t, gen, gg, seg, amp);
     gate_idx[e] = (uint8_t)gg;
     seg_id[e] = seg;
   }
@@ -1019,6 +1106,17 @@ cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs
   QE_NQ_SWITCH(n, QE_L)
 #undef QE_L
 #undef QE_LK
+  return cudaGetLastError();
+}
+
+cudaError_t launch_presample(const LaunchCfg &lc, const DevProblem *probs, const uint32_t *ids,
+                             const unsigned long long *prefix, uint32_t n_ids,
+                             unsigned long long total, const DevGlobal &g, cudaStream_t st) {
+  if (!n_ids || !total) return cudaSuccess;
+  unsigned long long blocks = (total + 255) / 256;
+  const unsigned long long cap = (unsigned long long)lc.num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  k_presample<<<(uint32_t)blocks, 256, 0, st>>>(probs, ids, prefix, n_ids, total, g);
   return cudaGetLastError();
 }
 

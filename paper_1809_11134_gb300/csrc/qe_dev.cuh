@@ -35,7 +35,14 @@ constexpr double kH64 = 0x1.6a09e667f3bcdp-1;
 constexpr float kH32 = 0x1.6a09e6p-1f;
 
 // Philox4x32-10 counter words: (a, b, gen, run << 4 | stream)
-enum Stream : uint32_t { kStSample = 0, kStMutDecide = 1, kStMutSeg = 2, kStGa = 4, kStGaInit = 5 };
+enum Stream : uint32_t {
+  kStSample = 0,
+  kStMutDecide = 1,
+  kStMutSeg = 2,
+  kStShot = 3,  // repeated qutrit measurements
+  kStGa = 4,
+  kStGaInit = 5
+};
 
 // encodings (mirror QE_ENC_*)
 constexpr uint32_t kEncQeqea = 0u, kEncGa = 1u;
@@ -64,6 +71,7 @@ struct DevProblem {
   uint32_t run, has_qubit, base;                // base = 1 if I is library index 0
   uint32_t measure_qubit;  // the qubit decides "gate present" (identity in the library)
   uint32_t ising;          // the Ising library: every slot carries an angle
+  uint32_t shots;          // qutrit measurements per slot (1 = one; majority otherwise)
   uint32_t key0, key1;
   float eps_d;        // bound on |d32 - d64|, d = (N - |tr|)/N, for the binary32 path
   float pen_per_gate; // cost_weight / L in binary32 (ranking bounds only)

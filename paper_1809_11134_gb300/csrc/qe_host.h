@@ -53,6 +53,9 @@ cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs
                         const uint32_t *group, const uint32_t *prefix, uint32_t n_group,
                         uint32_t total, bool canon, bool ising, const DevGlobal &g,
                         cudaStream_t st);
+cudaError_t launch_presample(const LaunchCfg &lc, const DevProblem *probs, const uint32_t *ids,
+                             const unsigned long long *prefix, uint32_t n_ids,
+                             unsigned long long total, const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_sample(const LaunchCfg &lc, const DevProblem *probs, uint32_t prob, uint32_t P,
                           uint32_t L, uint32_t gen, uint8_t *gate_idx, uint32_t *seg_id,
                           cudaStream_t st);

@@ -41,7 +41,7 @@ class qe_problem(C.Structure):
                 ("precision", C.c_uint32), ("fitness_kind", C.c_uint32), ("topk", C.c_uint32),
                 ("seed", C.c_uint64), ("p_mutation", C.c_double), ("mutation_range", C.c_double),
                 ("ga_mutation_rate", C.c_double), ("cost_weight", C.c_double),
-                ("target_perm", C.c_uint8 * 32)]
+                ("target_perm", C.c_uint8 * 32), ("shots", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class qe_ranked(C.Structure):
@@ -131,6 +131,7 @@ def to_problem(s) -> qe_problem:
     p.seed = s.seed
     p.p_mutation, p.mutation_range = s.p_mutation, s.mutation_range
     p.ga_mutation_rate, p.cost_weight = s.ga_mutation_rate, s.cost_weight
+    p.shots = getattr(s, "shots", 1)
     for j in range(32):
         p.target_perm[j] = s.perm[j] if j < len(s.perm) else 0
     return p

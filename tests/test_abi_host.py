@@ -65,6 +65,7 @@ BAD = [
     dict(p_mutation=1.5), dict(p_mutation=float("nan")), dict(mutation_range=float("inf")),
     dict(perm=[0, 0, 1, 2, 3, 4, 5, 6]), dict(perm=[8, 1, 2, 3, 4, 5, 6, 7]),
     dict(precision=3), dict(fitness_kind=2), dict(encoding=2), dict(cost_weight=float("nan")),
+    dict(shots=65), dict(reserved=1),
 ]
 
 
@@ -76,6 +77,8 @@ def test_init_rejects_invalid_problems_without_a_gpu(qe, bad):
     p = qe.to_problem(s)
     if "encoding" in bad:
         p.encoding = bad["encoding"]
+    if "reserved" in bad:
+        p.reserved = bad["reserved"]
     probs = (qe.qe_problem * 1)(p)
     h = C.c_void_p()
     st = qe.lib().qe_init(C.byref(h), probs, 1, None)
@@ -108,7 +111,8 @@ def test_null_context_calls_are_rejected(qe):
 
 
 def test_struct_layouts(qe):
-    assert C.sizeof(qe.qe_problem) == 104
+    assert C.sizeof(qe.qe_problem) == 112
+    assert qe.qe_problem.shots.offset == 104
     assert C.sizeof(qe.qe_ranked) == 16
     assert C.sizeof(qe.qe_report) == 120 + 512
 
