@@ -26,7 +26,8 @@ class Problem(C.Structure):
     _fields_ = [("n", C.c_uint32), ("L", C.c_uint32), ("P", C.c_uint32), ("library", C.c_uint32),
                 ("fitness_kind", C.c_uint32), ("run", C.c_uint32), ("seed", C.c_uint64),
                 ("p_mutation", C.c_double), ("mutation_range", C.c_double),
-                ("cost_weight", C.c_double), ("perm", C.c_uint8 * 32), ("shots", C.c_uint32)]
+                ("cost_weight", C.c_double), ("perm", C.c_uint8 * 32), ("shots", C.c_uint32),
+                ("target", C.POINTER(C.c_double))]
 
 
 class Report(C.Structure):
@@ -71,6 +72,8 @@ def lib():
                                         _f32p]
         L.oracle_compose.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p, _f64p, _f64p]
         L.oracle_score.argtypes = [C.c_uint32, _f64p, _f64p, _u8p, C.c_uint32]
+        L.oracle_score_dense.argtypes = [C.c_uint32, _f64p, _f64p, _f64p]
+        L.oracle_score_dense.restype = C.c_double
         L.oracle_score.restype = C.c_double
         L.oracle_cost.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p]
         L.oracle_cost.restype = C.c_uint32
@@ -99,9 +102,14 @@ def lib():
 
 
 def make_problem(n, L, P, library, perm, seed=0, run=0, fitness_kind=FIT_TRACE, p_mutation=0.1,
-                 mutation_range=np.pi / 4, cost_weight=0.0, shots=1):
+                 mutation_range=np.pi / 4, cost_weight=0.0, shots=1, target=None):
+    """target: a dense N x N complex target unitary (Eq. (11)), else the permutation perm"""
     p = Problem()
     p.shots = shots
+    if target is not None:
+        t = np.ascontiguousarray(np.stack([np.real(target), np.imag(target)], -1), np.float64)
+        p._target = t  # kept alive with the problem
+        p.target = t.ctypes.data_as(C.POINTER(C.c_double))
     p.n, p.L, p.P, p.library, p.fitness_kind, p.run = n, L, P, library, fitness_kind, run
     p.seed = seed
     p.p_mutation, p.mutation_range, p.cost_weight = p_mutation, mutation_range, cost_weight
@@ -186,6 +194,14 @@ def score(n, S, perm, kind=FIT_TRACE):
     re = np.ascontiguousarray(S.real.ravel())
     im = np.ascontiguousarray(S.imag.ravel())
     return lib().oracle_score(n, re, im, np.ascontiguousarray(perm, np.uint8), kind)
+
+
+def score_dense(n, S, T):
+    """Eq. (11) against a dense target T (N x N complex)"""
+    S = np.asarray(S, np.complex128)
+    t = np.ascontiguousarray(np.stack([np.real(T), np.imag(T)], -1), np.float64).ravel()
+    return lib().oracle_score_dense(n, np.ascontiguousarray(S.real.ravel()),
+                                    np.ascontiguousarray(S.imag.ravel()), t)
 
 
 def cost(n, library, gates):

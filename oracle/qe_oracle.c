@@ -403,6 +403,29 @@ void oracle_compose_amp(uint32_t n, uint32_t library, uint32_t L, const uint8_t 
  * For a permutation target T|j> = |perm[j]>, tr(S^dag T) is the sum over j
  * of conj(S[perm[j]][j]); it is accumulated with j ascending.
  * ====================================================================== */
+/* Eq. (11) with a dense unitary T: tr(S^dag T) = sum_j (S^dag T)_jj, the
+   diagonal element (S^dag T)_jj = sum_i conj(S_ij) T_ij. */
+static double score_dense_c(uint32_t n, const cplx *S, const double *T) {
+  uint32_t N = 1u << n;
+  double size = (double)N;
+  double tr_re = 0.0, tr_im = 0.0;
+  for (uint32_t j = 0; j < N; ++j) {
+    double d_re = 0.0, d_im = 0.0; /* (S^dag T)_jj */
+    for (uint32_t i = 0; i < N; ++i) {
+      cplx s = S[i * N + j];
+      double t_re = T[2 * (i * N + j)], t_im = T[2 * (i * N + j) + 1];
+      d_re = d_re + (s.re * t_re + s.im * t_im);
+      d_im = d_im + (s.re * t_im - s.im * t_re);
+    }
+    tr_re = tr_re + d_re;
+    tr_im = tr_im + d_im;
+  }
+  double m = sqrt(tr_re * tr_re + tr_im * tr_im);
+  double d = (size - m) / size;
+  if (d < 0.0) d = 0.0;
+  return 1.0 - sqrt(d);
+}
+
 static double score_c(uint32_t n, const cplx *S, const uint8_t *perm, uint32_t kind) {
   uint32_t N = 1u << n;
   double size = (double)N;
@@ -426,6 +449,22 @@ static double score_c(uint32_t n, const cplx *S, const uint8_t *perm, uint32_t k
   double d = (size - m) / size;
   if (d < 0.0) d = 0.0;
   return 1.0 - sqrt(d);
+}
+
+/* the fitness of a search: Eq. (11) against its permutation or dense target
+   (the probability-overlap reading is defined for permutations only) */
+static double score_p(const oracle_problem *p, const cplx *S) {
+  if (p->target) return p->fitness_kind == ORC_FIT_PROB ? NAN : score_dense_c(p->n, S, p->target);
+  return score_c(p->n, S, p->perm, p->fitness_kind);
+}
+
+double oracle_score_dense(uint32_t n, const double *S_re, const double *S_im, const double *T) {
+  uint32_t N = 1u << n;
+  cplx *S = (cplx *)malloc(sizeof(cplx) * N * N);
+  for (uint32_t e = 0; e < N * N; ++e) S[e] = (cplx){S_re[e], S_im[e]};
+  double f = score_dense_c(n, S, T);
+  free(S);
+  return f;
 }
 
 double oracle_score(uint32_t n, const double *S_re, const double *S_im, const uint8_t *perm,
@@ -489,7 +528,7 @@ void oracle_eval_amp(const oracle_problem *p, const uint8_t *gates, const float 
   for (uint32_t c = 0; c < n_circuits; ++c) {
     const uint8_t *g = gates + (uint64_t)c * p->L;
     compose_c(p->n, p->library, p->L, g, amps ? amps + (uint64_t)c * 2 * p->L : NULL, S);
-    double f = score_c(p->n, S, p->perm, p->fitness_kind);
+    double f = score_p(p, S);
     uint32_t k = oracle_cost(p->n, p->library, p->L, g);
     double pen = p->cost_weight * ((double)k / (double)p->L);
     F[c] = f - pen;
@@ -877,6 +916,8 @@ void oracle_step(const oracle_problem *p, float *cur, float *best, float *best_f
   for (uint32_t c = 0; c < p->P; ++c) {
     mean = mean + F[c];
     flops += oracle_useful_flops(p->n, p->library, p->L, gate_idx + (uint64_t)c * p->L);
+    /* a dense score: four products and four sums per element instead of N complex adds */
+    if (p->target) flops += 8ull * (1ull << (2 * p->n)) - 2ull * (1ull << p->n);
   }
   rep->generation = gen;
   rep->best_circuit = b;

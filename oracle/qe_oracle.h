@@ -94,6 +94,8 @@ typedef struct {
   double cost_weight;    /* lambda: F = f - lambda * cost / L */
   uint8_t perm[32];      /* target: T|j> = |perm[j]> */
   uint32_t shots;        /* qutrit measurements per slot, majority taken (Sec. IV-A1); 0 or 1 = one */
+  const double *target;  /* dense target unitary, T[i][j] = (re, im) at 2 (i N + j), read by the
+                            trace fitness of Eq. (11); NULL = the permutation perm */
 } oracle_problem;
 
 /* ---- Philox4x32-10 (Salmon et al., SC'11) ---- */
@@ -127,6 +129,10 @@ void oracle_gate_matrix(uint32_t n, uint32_t library, uint32_t g, double *re, do
 void oracle_compose(uint32_t n, uint32_t library, uint32_t L, const uint8_t *gates, double *S_re,
                     double *S_im);
 /* fitness of an N x N matrix against the permutation target */
+/* Eq. (11) against a dense target T (interleaved as oracle_problem.target):
+   |tr(S^dag T)| with the diagonal elements of S^dag T each summed over i
+   ascending, then the trace over j ascending. */
+double oracle_score_dense(uint32_t n, const double *S_re, const double *S_im, const double *T);
 double oracle_score(uint32_t n, const double *S_re, const double *S_im, const uint8_t *perm,
                     uint32_t fitness_kind);
 uint32_t oracle_cost(uint32_t n, uint32_t library, uint32_t L, const uint8_t *gates);
