@@ -296,10 +296,23 @@ qe_status qe_state_bytes(const qe_ctx *ctx, uint32_t prob, size_t *bytes);
 qe_status qe_get_state(qe_ctx *ctx, uint32_t prob, void *h_buf, size_t bytes);
 qe_status qe_set_state(qe_ctx *ctx, uint32_t prob, const void *h_buf, size_t bytes);
 
+/* Dense target (Eq. (11) with a general unitary T instead of the permutation
+ * target_perm).  h_target: host T[i][j] as (re, im) doubles at 2 (i N + j),
+ * N = 2^n_qubits, copied; NULL restores the permutation.  The fitness is then
+ * f = 1 - sqrt((N - |tr(S^dag T)|) / N) with tr(S^dag T) = sum_j (S^dag T)_jj,
+ * (S^dag T)_jj = sum_i conj(S_ij) T_ij (binary64: i ascending within each j,
+ * then j ascending).  QE_EUNSUPPORTED for QE_FIT_PROB searches (the
+ * probability overlap is defined for permutations); QE_EINVAL unless every
+ * entry is finite and T^dag T = I to 1e-6.  A pending generation is ranked
+ * first against the old target; the best-so-far record is kept.  Applies to
+ * qe_step, qe_eval and qe_eval_host.  Synchronises. */
+qe_status qe_set_target(qe_ctx *ctx, uint32_t prob, const double *h_target);
+
 /* Checkpoint / resume.  Every random draw is a Philox function of (seed,
  * generation, ...) (Sec. IV-D sampling, Sec. IV-F mutation, Sec. V-B GA), so a
  * run's whole state is each search's encoding state (the qe_get_state
- * layout), its best-so-far record and the generation counter; a context that
+ * layout), its best-so-far record and target, and the generation counter; a
+ * context that
  * loads a checkpoint continues the saved run bit for bit.
  *
  * qe_save ranks a pending last generation, then writes the file at path (a
@@ -308,12 +321,13 @@ qe_status qe_set_state(qe_ctx *ctx, uint32_t prob, const void *h_buf, size_t byt
  * sizeof(qe_report), 0, payload bytes, FNV-1a 64-bit hash of the payload},
  * then the payload {qe_problem[n_probs], qe_report[n_probs] (the records as
  * qe_step reports them), and per search a uint64 byte count and its
- * qe_get_state bytes}, little-endian.  Synchronises.  QE_EIO if the file
+ * qe_get_state bytes, then a uint64 byte count (0, or 16 N^2) and its dense
+ * target as qe_set_target takes it}, little-endian.  Synchronises.  QE_EIO if the file
  * cannot be written (the previous file, if any, is left in place).
  *
  * qe_load reads a checkpoint into a context created with the same problems
- * (byte-equal qe_problem arrays): encoding state, records and generation
- * counter; the launch plan is kept.  It checks the whole file first (magic,
+ * (byte-equal qe_problem arrays): encoding state, records, dense targets and
+ * generation counter; the launch plan is kept.  It checks the whole file first (magic,
  * version, sizes, hash, problems, record generations, gene values) and
  * returns QE_EINVAL with nothing changed if any check fails, QE_EIO if the
  * file cannot be read.  Synchronises.

@@ -87,6 +87,7 @@ struct qe_ctx {
   cudaGraphExec_t dexec = nullptr;
   bool pending_rank = false;         // the last generation is not ranked yet
   bool has_last = false;             // a generation ran since qe_init / qe_load
+  std::vector<std::vector<double>> targets;  // dense targets (empty: the permutation)
   // stage timing: events recorded inside the generation graph
   bool timing = false;
   cudaEvent_t tev[8] = {nullptr};
@@ -222,6 +223,30 @@ struct Arena {
 // changes by at most N times the column error, d = (N - |tr|)/N by at most
 // the column error; the probability form doubles it.  Generous by a factor 2.
 float eps_d_for(uint32_t L) { return (float)((double)L * 8e-7 + 2e-6); }
+// with a dense target the binary32 score itself sums N products per column
+// (each column's terms bounded by 1 in sum): |tr| moves by at most ~N^2 ulps
+// more, d by ~N ulps; (N + 8) * 2^-23 is generous
+float eps_d_dense(uint32_t L, uint32_t N) {
+  return eps_d_for(L) + (float)((double)(N + 8) * 0x1p-23);
+}
+
+// a dense target: finite, and unitary to 1e-6 in every entry of T^dag T
+bool target_ok(const double *T, uint32_t N) {
+  for (uint32_t e = 0; e < 2 * N * N; ++e)
+    if (!std::isfinite(T[e])) return false;
+  for (uint32_t k = 0; k < N; ++k)
+    for (uint32_t l = 0; l < N; ++l) {
+      double re = 0.0, im = 0.0;  // (T^dag T)_kl
+      for (uint32_t i = 0; i < N; ++i) {
+        const double ar = T[2 * (i * N + k)], ai = T[2 * (i * N + k) + 1];
+        const double br = T[2 * (i * N + l)], bi = T[2 * (i * N + l) + 1];
+        re += ar * br + ai * bi;
+        im += ar * bi - ai * br;
+      }
+      if (std::fabs(re - (k == l ? 1.0 : 0.0)) > 1e-6 || std::fabs(im) > 1e-6) return false;
+    }
+  return true;
+}
 
 // Eq. (12) in binary32: index 0..2 of cv/sv = theta1..3 (c_k, s_k), 3..7 =
 // phi1..5 (cos, sin).  Phase factors e^{i(+-a +-b ...)} are products of the
@@ -577,6 +602,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   // ---- arena layout
   Arena ar;
   ctx->hp.resize(n_probs);
+  ctx->targets.assign(n_probs, std::vector<double>());
   size_t total_P = 0, max_PL = 0, max_P = 0;
   for (uint32_t i = 0; i < n_probs; ++i) {
     const qe_problem &q = probs[i];
@@ -641,6 +667,10 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     ar.take(&d.cand_f, P * 8);
     ar.take(&d.cand_n, 4);
     ar.take(&d.topk_out, d.k * sizeof(Ranked));
+    if (q.fitness_kind == QE_FIT_TRACE) {  // room for a dense target (qe_set_target)
+      ar.take(&d.tgt32, (size_t)d.N * d.N * sizeof(float2));
+      ar.take(&d.tgt64, (size_t)d.N * d.N * sizeof(double2));
+    }
     total_P += P;
     if (PL > max_PL) max_PL = PL;
     if (P > max_P) max_P = P;
@@ -1327,9 +1357,50 @@ qe_status qe_set_state(qe_ctx *ctx, uint32_t prob, const void *h_buf, size_t byt
 
 }  // extern "C"
 
+// Install (T != NULL, checked already) or clear search prob's dense target:
+// both binary32 and binary64 copies, the flag and the ranking bound in the
+// device descriptor.  Synchronises.
+static qe_status put_target(qe_ctx *ctx, uint32_t prob, const double *T) {
+  DevProblem &d = ctx->hp[prob];
+  cudaStream_t us = ctx->user;
+  const uint32_t NN = d.N * d.N;
+  std::vector<double> &keep = ctx->targets[prob];
+  if (T) {
+    keep.assign(T, T + 2 * NN);
+    std::vector<float2> t32(NN);
+    std::vector<double2> t64(NN);
+    for (uint32_t e = 0; e < NN; ++e) {
+      t32[e] = make_float2((float)T[2 * e], (float)T[2 * e + 1]);
+      t64[e] = make_double2(T[2 * e], T[2 * e + 1]);
+    }
+    QE_CUDA(ctx, cudaMemcpyAsync(d.tgt32, t32.data(), NN * sizeof(float2), cudaMemcpyHostToDevice, us));
+    QE_CUDA(ctx, cudaMemcpyAsync(d.tgt64, t64.data(), NN * sizeof(double2), cudaMemcpyHostToDevice, us));
+  } else {
+    keep.clear();
+  }
+  d.dense = T ? 1u : 0u;
+  d.eps_d = T ? eps_d_dense(d.L, d.N) : eps_d_for(d.L);
+  QE_CUDA(ctx, cudaMemcpyAsync(ctx->d_probs + prob, &d, sizeof(DevProblem), cudaMemcpyHostToDevice, us));
+  QE_CUDA(ctx, cudaStreamSynchronize(us));
+  return QE_OK;
+}
+
+extern "C" qe_status qe_set_target(qe_ctx *ctx, uint32_t prob, const double *h_target) {
+  qe_status st = check_ctx(ctx, prob);
+  if (st != QE_OK) return st;
+  const DevProblem &d = ctx->hp[prob];
+  if (h_target && d.fit_kind != QE_FIT_TRACE)
+    return fail(ctx, QE_EUNSUPPORTED, "a dense target takes the trace fitness of Eq. (11)");
+  if (h_target && !target_ok(h_target, d.N))
+    return fail(ctx, QE_EINVAL, "target is not a finite unitary (T^dag T = I to 1e-6)");
+  if ((st = drain(ctx)) != QE_OK) return st;  // rank a pending generation on its own target
+  return put_target(ctx, prob, h_target);
+}
+
 // ------------------------------------------------------------ checkpoints
 // File: CkptHeader, then the payload {qe_problem[n], qe_report[n], and per
-// search a uint64 byte count and its state in the qe_get_state layout}, all
+// search a uint64 byte count and its state in the qe_get_state layout, then a
+// uint64 byte count and its dense target (none: the permutation)}, all
 // little-endian as the host writes them; the header carries the payload's
 // FNV-1a 64-bit hash.  Philox draws are keyed by (seed, generation, ...), so
 // the encoding state, the best-so-far records and the generation counter are
@@ -1440,6 +1511,11 @@ qe_status qe_save(qe_ctx *ctx, const char *path) {
     const uint64_t nb64 = nb;
     memcpy(pay.data() + at, &nb64, 8);
     if ((st = state_copy(ctx, i, pay.data() + at + 8, nb, true)) != QE_OK) return st;
+    const std::vector<double> &T = ctx->targets[i];
+    const uint64_t tb = T.size() * sizeof(double);
+    pay.resize(pay.size() + 8 + tb);
+    memcpy(pay.data() + at + 8 + nb, &tb, 8);
+    if (tb) memcpy(pay.data() + at + 16 + nb, T.data(), tb);
   }
   CkptHeader hd;
   memset(&hd, 0, sizeof hd);
@@ -1479,7 +1555,7 @@ qe_status qe_load(qe_ctx *ctx, const char *path) {
     return fail(ctx, QE_EINVAL, "checkpoint holds other searches than this context");
   // check everything before changing anything
   const char *reps = pay.data() + np * sizeof(qe_problem);
-  std::vector<size_t> off(np);
+  std::vector<size_t> off(np), toff(np, 0);
   size_t at = np * (sizeof(qe_problem) + sizeof(qe_report));
   for (uint32_t i = 0; i < np; ++i) {
     qe_report r;
@@ -1501,6 +1577,20 @@ qe_status qe_load(qe_ctx *ctx, const char *path) {
         if (g[e] >= d.G) return fail(ctx, QE_EINVAL, "checkpoint genome holds an invalid gene");
     }
     at += 8 + nb;
+    uint64_t tb = 0;
+    if (at + 8 > pay.size()) return fail(ctx, QE_EINVAL, "checkpoint is truncated or corrupted");
+    memcpy(&tb, pay.data() + at, 8);
+    const uint64_t want = (uint64_t)d.N * d.N * 16;
+    if ((tb != 0 && tb != want) || at + 8 + tb > pay.size())
+      return fail(ctx, QE_EINVAL, "checkpoint target has the wrong size");
+    if (tb) {
+      std::vector<double> T(tb / 8);
+      memcpy(T.data(), pay.data() + at + 8, tb);
+      if (d.fit_kind != QE_FIT_TRACE || !target_ok(T.data(), d.N))
+        return fail(ctx, QE_EINVAL, "checkpoint target is not a unitary for the trace fitness");
+      toff[i] = at + 8;
+    }
+    at += 8 + tb;
   }
   if (at != pay.size()) return fail(ctx, QE_EINVAL, "checkpoint is truncated or corrupted");
   // the loaded generation is ranked already: the next generation graph skips
@@ -1515,6 +1605,12 @@ qe_status qe_load(qe_ctx *ctx, const char *path) {
     size_t nb = 0;
     qe_state_bytes(ctx, i, &nb);
     if ((st = state_copy(ctx, i, pay.data() + off[i], nb, false)) != QE_OK) return st;
+    std::vector<double> T;
+    if (toff[i]) {
+      T.resize((size_t)2 * ctx->hp[i].N * ctx->hp[i].N);
+      memcpy(T.data(), pay.data() + toff[i], T.size() * 8);
+    }
+    if ((st = put_target(ctx, i, toff[i] ? T.data() : nullptr)) != QE_OK) return st;
     const DevProblem &d = ctx->hp[i];
     if (d.mut_cnt) QE_CUDA(ctx, cudaMemsetAsync(d.mut_cnt, 0, 2 * 4, us));
   }

@@ -740,16 +740,36 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
   // this lane's S[perm[j]][j], if it holds that row.  Picked by an arithmetic
   // blend (exact: one term has weight 1, the rest weight 0) so that the state
   // array is never indexed dynamically and stays in registers.
-  int pj = p.perm[j];
-  if constexpr (kMapped) pj = phys_row5(pj, pos);
   R vr = R(0), vi = R(0);
-  {
+  const bool dense = p.dense != 0;
+  if (dense) out.work += 8u * N * N - 2u * N;  // the dense score
+  if (!dense) {
+    int pj = p.perm[j];
+    if constexpr (kMapped) pj = phys_row5(pj, pos);
     const uint32_t own = (!shadow && (pj >> Ly::RBR) == grp) ? (1u << (pj & (Ly::ROWS - 1))) : 0u;
 #pragma unroll
     for (int r = 0; r < Ly::ROWS; ++r) {
       const R m = (R)((own >> r) & 1u);
       vr = fma(m, re[r], vr);
       vi = fma(m, im[r], vi);
+    }
+  } else if constexpr (!CANON) {
+    // dense target, binary32: this lane's rows of the diagonal element
+    // (S^dag T)_jj = sum_i conj(S_ij) T_ij, any order
+    if (!shadow) {
+#pragma unroll
+      for (int r = 0; r < Ly::ROWS; ++r) {
+        int i = (grp << Ly::RBR) | r;
+        if constexpr (kMapped) {
+          int x = 0;
+#pragma unroll
+          for (int b = 0; b < 5; ++b) x |= ((r >> b) & 1) << (4 - (int)((inv >> (3 * b)) & 7));
+          i = x;
+        }
+        const float2 t = __ldg(p.tgt32 + i * N + j);
+        vr = fmaf(re[r], t.x, fmaf(im[r], t.y, vr));
+        vi = fmaf(re[r], t.y, fmaf(-im[r], t.x, vi));
+      }
     }
   }
   const double pen =
@@ -758,15 +778,48 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
     // sequential sum over j ascending, on lane 0 (the values arrive by shuffle;
     // the binary64 arithmetic runs on one lane only)
     double a = 0.0, b = 0.0;
-    for (int jj = 0; jj < N; ++jj) {
-      const int owner = ((p.perm[jj] >> Ly::RBR) << NQ) | jj;
-      const double xr = __shfl_sync(kFull, vr, owner), xi = __shfl_sync(kFull, vi, owner);
-      if (lane == 0) {
-        if (p.fit_kind == 1) {
-          a = __dadd_rn(a, __dadd_rn(__dmul_rn(xr, xr), __dmul_rn(xi, xi)));
-        } else {
+    if (dense) {
+      // the oracle's order: each diagonal element (S^dag T)_jj summed over rows
+      // i ascending (row group g continues group g - 1's sum), then the trace
+      // over j ascending
+      double dr = 0.0, di = 0.0;
+#pragma unroll
+      for (int g2 = 0; g2 < (1 << Ly::RBL); ++g2) {
+        if (g2 > 0) {
+          const double ur = __shfl_up_sync(kFull, dr, N), ui = __shfl_up_sync(kFull, di, N);
+          if (grp == g2) {
+            dr = ur;
+            di = ui;
+          }
+        }
+        if (grp == g2 && !shadow) {
+#pragma unroll
+          for (int r = 0; r < Ly::ROWS; ++r) {
+            const double2 t = __ldg(p.tgt64 + ((g2 << Ly::RBR) | r) * N + j);
+            dr = __dadd_rn(dr, __dadd_rn(__dmul_rn((double)re[r], t.x), __dmul_rn((double)im[r], t.y)));
+            di = __dadd_rn(di, __dsub_rn(__dmul_rn((double)re[r], t.y), __dmul_rn((double)im[r], t.x)));
+          }
+        }
+      }
+      const int last = ((1 << Ly::RBL) - 1) << NQ;
+      for (int jj = 0; jj < N; ++jj) {
+        const double xr = __shfl_sync(kFull, dr, last | jj), xi = __shfl_sync(kFull, di, last | jj);
+        if (lane == 0) {
           a = __dadd_rn(a, xr);
-          b = __dadd_rn(b, -xi);
+          b = __dadd_rn(b, xi);
+        }
+      }
+    } else {
+      for (int jj = 0; jj < N; ++jj) {
+        const int owner = ((p.perm[jj] >> Ly::RBR) << NQ) | jj;
+        const double xr = __shfl_sync(kFull, vr, owner), xi = __shfl_sync(kFull, vi, owner);
+        if (lane == 0) {
+          if (p.fit_kind == 1) {
+            a = __dadd_rn(a, __dadd_rn(__dmul_rn(xr, xr), __dmul_rn(xi, xi)));
+          } else {
+            a = __dadd_rn(a, xr);
+            b = __dadd_rn(b, -xi);
+          }
         }
       }
     }

@@ -72,6 +72,7 @@ struct DevProblem {
   uint32_t measure_qubit;  // the qubit decides "gate present" (identity in the library)
   uint32_t ising;          // the Ising library: every slot carries an angle
   uint32_t shots;          // qutrit measurements per slot (1 = one; majority otherwise)
+  uint32_t dense;          // the target is the dense unitary tgt32/tgt64, not perm
   uint32_t key0, key1;
   float eps_d;        // bound on |d32 - d64|, d = (N - |tr|)/N, for the binary32 path
   float pen_per_gate; // cost_weight / L in binary32 (ranking bounds only)
@@ -100,6 +101,9 @@ struct DevProblem {
   Best *rec;
   // mutation table: cos/sin of m * mutation_range / Q, m = 0..Q
   float2 *qubit_tab;
+  // dense target T[i][j] at i * N + j, in binary32 and binary64 (dense != 0)
+  float2 *tgt32;
+  double2 *tgt64;
   // Ising: each slot's qubit amplitudes (b0, b1) as sampled (its angle), 2 x P*L,
   // double-buffered by generation parity like gate_idx
   float2 *amps;

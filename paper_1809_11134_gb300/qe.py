@@ -32,6 +32,7 @@ EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_amp", 
            "qe_update", "qe_step", "qe_last_generation", "qe_state_bytes", "qe_get_state",
            "qe_set_state", "qe_generation", "qe_autotune", "qe_launch_plan", "qe_stage_timing",
            "qe_stage_times", "qe_measure_alu_peaks", "qe_save", "qe_load", "qe_checkpoint_info",
+           "qe_set_target",
            "qe_eval_rank_static", "qe_last_error", "qe_destroy"]
 
 
@@ -98,6 +99,7 @@ def lib():
         L.qe_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
         L.qe_eval_rank_static.argtypes = [C.POINTER(qe_problem), vp, u32, vp, vp, vp,
                                           C.c_char_p, sz]
+        L.qe_set_target.argtypes = [vp, u32, vp]
         L.qe_save.argtypes = [vp, C.c_char_p]
         L.qe_load.argtypes = [vp, C.c_char_p]
         L.qe_checkpoint_info.argtypes = [C.c_char_p, C.POINTER(qe_problem), u32, C.POINTER(u32),
@@ -175,6 +177,9 @@ class Context:
             raise QeError(st, (lib().qe_last_error(None) or b"").decode())
         self.h = h
         self.stream = stream
+        for i, s in enumerate(self.searches):
+            if getattr(s, "target", None) is not None:
+                self.set_target(i, s.target)
 
     def close(self):
         if getattr(self, "h", None):
@@ -347,6 +352,18 @@ class Context:
                                   np.ascontiguousarray(best, np.float32).view(np.uint8).ravel(),
                                   np.ascontiguousarray(best_f, np.float32).view(np.uint8).ravel()])
         _check(self.h, lib().qe_set_state(self.h, prob, buf.ctypes.data_as(C.c_void_p), buf.size))
+
+    def set_target(self, prob, T):
+        """qe_set_target: a dense N x N complex target unitary (None: the permutation)."""
+        if T is None:
+            _check(self.h, lib().qe_set_target(self.h, prob, None))
+            return
+        N = 1 << self._probs[prob].n_qubits
+        T = np.asarray(T, np.complex128)
+        if T.shape != (N, N):
+            raise ValueError("target must be %d x %d" % (N, N))
+        buf = np.ascontiguousarray(np.stack([T.real, T.imag], -1), np.float64)
+        _check(self.h, lib().qe_set_target(self.h, prob, buf.ctypes.data_as(C.c_void_p)))
 
     def save(self, path):
         """qe_save: checkpoint every search (state, records, generation) to path."""

@@ -9,7 +9,7 @@ library, so CPU-only tests can use it.
 Wire w is bit (n-1-w) of a basis index (wire 0 = most significant bit).
 """
 from dataclasses import dataclass, field
-from typing import List
+from typing import List, Optional
 
 import numpy as np
 
@@ -80,6 +80,7 @@ class Search:
     ga_mutation_rate: float = 0.02
     cost_weight: float = 0.0
     shots: int = 1  # qutrit measurements per slot, majority outcome taken
+    target: Optional[np.ndarray] = None  # dense N x N target unitary instead of perm
     name: str = field(default="")
     encoding: int = ENC_QEQEA
 

@@ -9,12 +9,13 @@ def oracle_problem(s: W.Search, run: int):
     return oracle.make_problem(s.n, s.L, s.P, s.library, s.perm, seed=s.seed, run=run,
                                fitness_kind=s.fitness_kind, p_mutation=s.p_mutation,
                                mutation_range=s.mutation_range, cost_weight=s.cost_weight,
-                               shots=s.shots)
+                               shots=s.shots, target=s.target)
 
 
-def eps_d(L):
-    """Bound on |d32 - d64|, d = (N - |tr|)/N, that the ranking guard band uses."""
-    return L * 8e-7 + 2e-6
+def eps_d(L, dense_N=0):
+    """Bound on |d32 - d64|, d = (N - |tr|)/N, that the ranking guard band uses
+    (a dense N x N target adds the binary32 score's own rounding)."""
+    return L * 8e-7 + 2e-6 + ((dense_N + 8) * 2.0**-23 if dense_N else 0.0)
 
 
 def d_of(F, s: W.Search, cost=None):
@@ -31,7 +32,8 @@ def assert_fp32_fitness(F32, F64, s: W.Search, cost=None):
     root of Eq. (11) no longer amplifies rounding."""
     d32, d64 = d_of(F32, s, cost), d_of(F64, s, cost)
     assert np.all(np.isfinite(F32))
-    assert np.abs(d32 - d64).max() <= eps_d(s.L), np.abs(d32 - d64).max()
+    bound = eps_d(s.L, (1 << s.n) if s.target is not None else 0)
+    assert np.abs(d32 - d64).max() <= bound, np.abs(d32 - d64).max()
     far = d64 >= 1e-4
     if far.any():
         err = np.abs(np.asarray(F32, np.float64)[far] - F64[far]).max()
