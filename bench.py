@@ -338,9 +338,8 @@ def run_ours(args):
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_step launch (a timed
 # step, right after the L2 flush) from an ncu capture of this workload
-# (profiles/k_step_3qubit_bench.md): the reads include the update's L2
-# prefetch, the writes mostly the flush buffer's dirty lines evicted meanwhile
-TRAFFIC = {(2, None): 80.661e6}
+# (profiles/k_step_3qubit_bench.md): the reads include the update's L2 prefetch
+TRAFFIC = {(2, None): 41.507e6}
 
 
 def roofline(dom, ms, flops, searches, pk, traffic=None):

@@ -423,9 +423,13 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
     const Group &gr = ctx->groups[k];
     cudaStream_t gs = (conc && k > 0) ? ctx->gstreams[k - 1] : ctx->side;
     if (conc && k > 0 && e == cudaSuccess) e = cudaStreamWaitEvent(gs, ctx->gfork, 0);
+    // the circuit kernel with the K-shot and dense-target paths only for a
+    // group that has a search using one of them
+    bool ext = false;
+    for (uint32_t id : gr.ids) ext = ext || ctx->hp[id].shots > 1 || ctx->hp[id].dense;
     if (e == cudaSuccess)
       e = launch_step(lc, gr.n, ctx->d_probs, gr.d_ids, gr.d_prefix,
-                      (uint32_t)gr.ids.size(), gr.total, gr.canon, gr.ising, ctx->g, gs);
+                      (uint32_t)gr.ids.size(), gr.total, gr.canon, gr.ising, ext, ctx->g, gs);
     if (conc && k > 0 && e == cudaSuccess) e = cudaEventRecord(ctx->gjoin[k - 1], gs);
   }
   for (size_t k = 1; conc && k < ctx->groups.size(); ++k)
@@ -1377,6 +1381,19 @@ static qe_status put_target(qe_ctx *ctx, uint32_t prob, const double *T) {
     QE_CUDA(ctx, cudaMemcpyAsync(d.tgt64, t64.data(), NN * sizeof(double2), cudaMemcpyHostToDevice, us));
   } else {
     keep.clear();
+  }
+  if ((d.dense != 0) != (T != nullptr)) {
+    // the search's group may need the other circuit kernel: recapture the
+    // generation graph at the next qe_step (the launch plan is kept)
+    QE_CUDA(ctx, cudaStreamSynchronize(us));
+    if (ctx->gexec) {
+      cudaGraphExecDestroy(ctx->gexec);
+      ctx->gexec = nullptr;
+    }
+    if (ctx->graph) {
+      cudaGraphDestroy(ctx->graph);
+      ctx->graph = nullptr;
+    }
   }
   d.dense = T ? 1u : 0u;
   d.eps_d = T ? eps_d_dense(d.L, d.N) : eps_d_for(d.L);

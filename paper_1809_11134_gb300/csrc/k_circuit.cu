@@ -669,7 +669,8 @@ struct CircuitOut {
 
 // ops0/ops1: this lane's op bytes for slots lane and lane + 32
 // ic0/is0, ic1/is1: cos/sin of theta/2 of this lane's slots (Ising)
-template <int NQ, typename R, bool CANON, bool ISING = false>
+// DENSE_OK = false compiles the dense-target score out (permutation targets only)
+template <int NQ, typename R, bool CANON, bool ISING = false, bool DENSE_OK = true>
 __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lane, uint32_t ops0,
                                                     uint32_t ops1, R *S_out, R ic0 = R(1),
                                                     R is0 = R(0), R ic1 = R(1), R is1 = R(0)) {
@@ -741,7 +742,7 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
   // blend (exact: one term has weight 1, the rest weight 0) so that the state
   // array is never indexed dynamically and stays in registers.
   R vr = R(0), vi = R(0);
-  const bool dense = p.dense != 0;
+  const bool dense = DENSE_OK && p.dense != 0;
   if (dense) out.work += 8u * N * N - 2u * N;  // the dense score
   if (!dense) {
     int pj = p.perm[j];
@@ -907,7 +908,9 @@ constexpr int min_blocks() {
   return (NQ == 5 && !CANON) ? 3 : ((NQ <= 3 && !CANON) ? 6 : 1);
 }
 
-template <int NQ, typename R, bool CANON, bool ISING>
+// EXT: the group holds a search measured K > 1 times (k_presample) or one with
+// a dense target; without it both paths are compiled out of the kernel
+template <int NQ, typename R, bool CANON, bool ISING, bool EXT>
 __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CANON>()) k_step(const DevProblem *__restrict__ probs,
                                               const uint32_t *__restrict__ group,
                                               const uint32_t *__restrict__ prefix,
@@ -925,7 +928,7 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
     bool bad = false;
     const bool qeqea = p.enc == kEncQeqea;
     float2 a0 = make_float2(1.f, 0.f), a1 = a0;  // Ising: the slots' angles
-    if (qeqea && p.shots > 1) {
+    if (EXT && qeqea && p.shots > 1) {
       // measured K times by k_presample ahead of this kernel
       if ((uint32_t)lane < p.L) {
         o0 = op_of(p, gate_idx[(size_t)c * p.L + lane], bad);
@@ -976,7 +979,7 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
       half_angle(a1.x, a1.y, ic1, is1);
     }
     CircuitOut out =
-        compose_score<NQ, R, CANON, ISING>(p, lane, o0, o1, (R *)nullptr, ic0, is0, ic1, is1);
+        compose_score<NQ, R, CANON, ISING, EXT>(p, lane, o0, o1, (R *)nullptr, ic0, is0, ic1, is1);
     const bool nonfinite = !isfinite(out.F);
     if (lane == 0) {
       if constexpr (CANON) p.fit64[(size_t)par * p.P + c] = out.F;
@@ -1138,7 +1141,7 @@ __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ 
 
 cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs,
                         const uint32_t *group, const uint32_t *prefix, uint32_t n_group,
-                        uint32_t total, bool canon, bool ising, const DevGlobal &g,
+                        uint32_t total, bool canon, bool ising, bool ext, const DevGlobal &g,
                         cudaStream_t st) {
   if (total == 0) return cudaSuccess;
   uint32_t per = canon ? lc.step64[n] : lc.step32[n];
@@ -1147,8 +1150,11 @@ cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs
 #define QE_LK(NQ, R, C, I)                                                                \
   {                                                                                       \
     constexpr int bt = block_threads<NQ, C>();                                            \
-    k_step<NQ, R, C, I><<<grid_for(lc, total, per, bt / 32), bt, 0, st>>>(               \
-        probs, group, prefix, n_group, total, g);                                         \
+    const dim3 grid = grid_for(lc, total, per, bt / 32);                                  \
+    if (ext)                                                                              \
+      k_step<NQ, R, C, I, true><<<grid, bt, 0, st>>>(probs, group, prefix, n_group, total, g); \
+    else                                                                                  \
+      k_step<NQ, R, C, I, false><<<grid, bt, 0, st>>>(probs, group, prefix, n_group, total, g); \
   }
 #define QE_L(NQ)                                                                          \
   if (canon) {                                                                            \
@@ -1226,10 +1232,14 @@ cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, bool ising, const D
 
 bool is_circuit_kernel(const void *f) {
 #define QE_K(NQ)                                                                          \
-  if (f == (const void *)k_step<NQ, float, false, false> ||                               \
-      f == (const void *)k_step<NQ, double, true, false> ||                               \
-      f == (const void *)k_step<NQ, float, false, true> ||                                \
-      f == (const void *)k_step<NQ, double, true, true>)                                  \
+  if (f == (const void *)k_step<NQ, float, false, false, false> ||                        \
+      f == (const void *)k_step<NQ, double, true, false, false> ||                        \
+      f == (const void *)k_step<NQ, float, false, true, false> ||                         \
+      f == (const void *)k_step<NQ, double, true, true, false> ||                         \
+      f == (const void *)k_step<NQ, float, false, false, true> ||                         \
+      f == (const void *)k_step<NQ, double, true, false, true> ||                         \
+      f == (const void *)k_step<NQ, float, false, true, true> ||                          \
+      f == (const void *)k_step<NQ, double, true, true, true>)                            \
     return true;
   QE_K(1) QE_K(2) QE_K(3) QE_K(4) QE_K(5)
 #undef QE_K
@@ -1241,11 +1251,11 @@ cudaError_t query_circuit_occupancy(LaunchCfg &lc) {
   int b = 0;
 #define QE_Q(NQ)                                                                            \
   if (e == cudaSuccess)                                                                     \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, float, false, false>,  \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, float, false, false, false>, \
                                                       block_threads<NQ, false>(), 0);       \
   lc.step32[NQ] = b > 0 ? b : 1;                                                            \
   if (e == cudaSuccess)                                                                     \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, double, true, false>,  \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, double, true, false, false>, \
                                                       block_threads<NQ, true>(), 0);        \
   lc.step64[NQ] = b > 0 ? b : 1;
   QE_Q(1) QE_Q(2) QE_Q(3) QE_Q(4) QE_Q(5)

@@ -51,7 +51,7 @@ bool is_circuit_kernel(const void *f);  // a generation circuit kernel (graph no
 // all searches of a launch have n qubits
 cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs,
                         const uint32_t *group, const uint32_t *prefix, uint32_t n_group,
-                        uint32_t total, bool canon, bool ising, const DevGlobal &g,
+                        uint32_t total, bool canon, bool ising, bool ext, const DevGlobal &g,
                         cudaStream_t st);
 cudaError_t launch_presample(const LaunchCfg &lc, const DevProblem *probs, const uint32_t *ids,
                              const unsigned long long *prefix, uint32_t n_ids,
