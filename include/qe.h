@@ -199,6 +199,31 @@ qe_status qe_eval(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_
 qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
                        uint32_t n_circuits, void *h_fitness, qe_ranked *h_topk);
 
+/* qe_eval_host for several searches in one call (Sec. IV-C composition,
+ * Eq. (11) score minus lambda*cost/L, as qe_eval).  Item m evaluates
+ * h_n_circuits[m] (<= P of that search) circuits of search h_probs[m]; the
+ * items' problems are distinct and either all binary64 or all binary32
+ * searches (QE_EINVAL otherwise), and none uses QE_LIB_ISING.  Host buffers,
+ * items back to back in item order:
+ *   h_gate_idx  uint8, item m's n_m * L_m gate indices (row-major c*L + t);
+ *   h_fitness   float (binary32 searches) or double (binary64), n_m per item;
+ *   h_topk      NULL, or k_m = min(max(topk_m, 1), n_m) entries per item: its
+ *               best circuits rescored in binary64 and sorted by (fitness
+ *               desc, cost asc, index asc), circuit indices local to the item.
+ * One host->device copy, one graph launch (the evaluations on three streams,
+ * then one ranking of every item) and the device->host copies, then one
+ * synchronisation.  The graph is captured on the first call with a given item
+ * layout (problems, counts, ranking or not) and replayed while the layout
+ * repeats; the first call, and any call needing more staging than before,
+ * allocates device staging (and pinned host staging for the top-k lists) that
+ * the context keeps until qe_destroy.  Pinned host buffers make the copies
+ * asynchronous with respect to other host work.  Invalid gate indices give
+ * NaN fitness and, when h_topk is given, QE_ENUMERIC (else the error bit, as
+ * qe_eval).  A pending generation's ranking is finished first. */
+qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
+                             const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
+                             void *h_fitness, qe_ranked *h_topk);
+
 /* The composed unitaries themselves: d_unitary receives n_circuits row-major
  * N x N complex matrices, (re, im) interleaved, float for QE_PREC_FP32 and
  * SPLIT_TC, double for QE_PREC_FP64 (same arithmetic as qe_eval). */
@@ -269,7 +294,14 @@ qe_status qe_launch_plan(const qe_ctx *ctx, char *h_buf, size_t len);
  * kernels (sample + compose + score + segment-fitness scatter), ms[1] ranking
  * selection, ms[2] binary64 rescoring, ms[3] ranking sort, ms[4] update
  * (elitism + mutation, concurrent with ms[1..3]), ms[5] the whole generation.
- * qe_stage_times synchronises.  Timing adds a few event records per generation. */
+ * Under mode 1 ms[0] and ms[1] run from the start of the generation, so they
+ * include waiting on the stages that run beside them.  qe_stage_timing(ctx, 2)
+ * serialises the generation instead: every kernel on one stream in the order
+ * circuits, update, ranking (no launch-completion edge), so each interval is
+ * that stage's own duration with nothing running beside it (ms[1] then runs
+ * from the end of the update); the results are the same as under mode 0.
+ * 0 turns timing off; other values are QE_EINVAL.  qe_stage_times
+ * synchronises.  Timing adds a few event records per generation. */
 qe_status qe_stage_timing(qe_ctx *ctx, int enable);
 qe_status qe_stage_times(qe_ctx *ctx, float *ms);
 

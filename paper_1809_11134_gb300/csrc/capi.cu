@@ -77,6 +77,17 @@ struct qe_ctx {
   Best *h_recs = nullptr;  // pinned
   uint8_t *d_stage_gates = nullptr;
   void *d_stage_fit = nullptr;
+  // qe_eval_host_batch: device staging (grown on demand), pinned host staging
+  // of the top-k lists, and the graph of the last batch layout (key: ranking
+  // flag, item count, the items' problems and circuit counts)
+  void *d_batch = nullptr;
+  size_t d_batch_bytes = 0;
+  void *h_batch = nullptr;
+  size_t h_batch_bytes = 0;
+  std::vector<uint32_t> batch_key;
+  std::vector<unsigned char> batch_meta;  // host copy of the jobs, offsets and gate table
+  cudaGraph_t bgraph = nullptr;
+  cudaGraphExec_t bexec = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   // launch plan of the generation graph (qe_autotune picks it by timing)
@@ -90,6 +101,7 @@ struct qe_ctx {
   std::vector<std::vector<double>> targets;  // dense targets (empty: the permutation)
   // stage timing: events recorded inside the generation graph
   bool timing = false;
+  bool timing_serial = false;  // every kernel of the generation on one stream
   cudaEvent_t tev[8] = {nullptr};
   uint32_t gen = 0;
   bool poisoned = false;
@@ -398,10 +410,14 @@ cudaError_t enqueue_rank_chain(qe_ctx *ctx, cudaStream_t cs) {
 // (its circuits and fitness sit in the other half of the double buffers).
 // Stage events (when timing): 0 start; 1 after the circuit kernels; 2 after
 // the selection, 3 after the rescoring, 4 after the sort (ranking of g - 1);
-// 5 before and 6 after the update; 7 end of the generation.
+// 5 before and 6 after the update; 7 end of the generation.  Serialised
+// stage timing puts every kernel on the capture stream in the order circuits,
+// update, ranking, so that each interval is its stage's own duration.
 qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
                           cudaGraphExec_t *out_exec) {
   cudaStream_t cs = ctx->cap;
+  const bool serial = ctx->timing && ctx->timing_serial;
+  cudaStream_t side = serial ? cs : ctx->side, side2 = serial ? cs : ctx->side2;
   LaunchCfg lc = ctx->lc;
   lc.grid_mode = plan.grid_mode;
   QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -412,16 +428,16 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
   };
   mark(0, cs);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, cs);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ctx->ev_fork, 0);
   // generation g: K-shot measurements, circuits, then the two update roles
   if (e == cudaSuccess && ctx->n_shot)
     e = launch_presample(lc, ctx->d_probs, ctx->d_shot_ids, ctx->d_shot_prefix, ctx->n_shot,
-                         ctx->shot_total, ctx->g, ctx->side);
-  const bool conc = plan.concurrent && ctx->groups.size() > 1;
-  if (conc && e == cudaSuccess) e = cudaEventRecord(ctx->gfork, ctx->side);
+                         ctx->shot_total, ctx->g, side);
+  const bool conc = plan.concurrent && ctx->groups.size() > 1 && !serial;
+  if (conc && e == cudaSuccess) e = cudaEventRecord(ctx->gfork, side);
   for (size_t k = 0; k < ctx->groups.size(); ++k) {
     const Group &gr = ctx->groups[k];
-    cudaStream_t gs = (conc && k > 0) ? ctx->gstreams[k - 1] : ctx->side;
+    cudaStream_t gs = (conc && k > 0) ? ctx->gstreams[k - 1] : side;
     if (conc && k > 0 && e == cudaSuccess) e = cudaStreamWaitEvent(gs, ctx->gfork, 0);
     // the circuit kernel with the K-shot and dense-target paths only for a
     // group that has a search using one of them
@@ -433,20 +449,20 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
     if (conc && k > 0 && e == cudaSuccess) e = cudaEventRecord(ctx->gjoin[k - 1], gs);
   }
   for (size_t k = 1; conc && k < ctx->groups.size(); ++k)
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->gjoin[k - 1], 0);
-  mark(1, ctx->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ctx->gjoin[k - 1], 0);
+  mark(1, side);
   if (e == cudaSuccess && ctx->n_ga)
-    e = launch_ga_prep(ctx->d_probs, ctx->d_ga_ids, ctx->n_ga, ctx->g, ctx->side);
-  mark(5, ctx->side);
-  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork2, ctx->side);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side2, ctx->ev_fork2, 0);
+    e = launch_ga_prep(ctx->d_probs, ctx->d_ga_ids, ctx->n_ga, ctx->g, side);
+  mark(5, side);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork2, side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(side2, ctx->ev_fork2, 0);
   if (e == cudaSuccess && ctx->n_upd)
     e = launch_update(ctx->lc, ctx->d_probs, ctx->d_upd_ids, ctx->d_upd_prefA, ctx->d_upd_prefB,
                       ctx->n_upd, ctx->upd_totalA, ctx->upd_totalB, ctx->g.gen, 0, nullptr, ctx->g,
-                      ctx->side, ctx->side2);
-  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_join2, 0);
-  mark(6, ctx->side);
+                      side, side2);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, side2);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ctx->ev_join2, 0);
+  mark(6, side);
   // generation g - 1: ranking
   if (e == cudaSuccess) e = launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, RankJob{}, ctx->g, cs);
   mark(2, cs);
@@ -457,7 +473,7 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
   mark(3, cs);
   if (e == cudaSuccess) e = launch_rank_sort(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, RankJob{}, ctx->g, cs);
   mark(4, cs);
-  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, side);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
   // GA breeding of generation g + 1 overwrites the buffer generation g - 1's
   // ranking has just read
@@ -474,7 +490,7 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
   }
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
   qe_status st = set_priorities(ctx, graph);
-  if (st == QE_OK && plan.select_first) st = add_select_first_edge(ctx, graph);
+  if (st == QE_OK && plan.select_first && !serial) st = add_select_first_edge(ctx, graph);
   if (st != QE_OK) {
     cudaGraphDestroy(graph);
     return st;
@@ -549,6 +565,10 @@ const char *qe_last_error(const qe_ctx *ctx) {
 
 void qe_destroy(qe_ctx *ctx) {
   if (!ctx) return;
+  if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
+  if (ctx->bgraph) cudaGraphDestroy(ctx->bgraph);
+  if (ctx->d_batch) cudaFree(ctx->d_batch);
+  if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   if (ctx->dexec) cudaGraphExecDestroy(ctx->dexec);
@@ -1023,6 +1043,217 @@ qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
   return st;
 }
 
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device staging of one batch (256-B aligned sections): the items' gates,
+// fitness and cost words back to back, the gathered top-k lists plus the
+// error word, the ranking jobs, their top-k offsets, and the per-problem gate
+// table the binary64 rescoring reads.
+struct BatchLayout {
+  size_t gates = 0, fit = 0, cost = 0, topk = 0, jobs = 0, koff = 0, gtab = 0, total = 0;
+};
+
+static BatchLayout batch_layout(size_t gate_bytes, size_t n_total, size_t fb, size_t k_total,
+                         size_t n_items, size_t n_probs) {
+  BatchLayout b;
+  size_t o = 0;
+  b.gates = o;
+  o += align256(gate_bytes ? gate_bytes : 1);
+  b.fit = o;
+  o += align256((n_total ? n_total : 1) * fb);
+  b.cost = o;
+  o += align256((n_total ? n_total : 1) * 4);
+  b.topk = o;
+  o += align256((k_total + 1) * sizeof(Ranked));
+  b.jobs = o;
+  o += align256(n_items * sizeof(RankJob));
+  b.koff = o;
+  o += align256((n_items + 1) * 4);
+  b.gtab = o;
+  o += align256(n_probs * sizeof(void *));
+  b.total = o;
+  return b;
+}
+
+qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
+                             const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
+                             void *h_fitness, qe_ranked *h_topk) {
+  if (!ctx) return fail(nullptr, QE_EINVAL, "null context");
+  if (ctx->poisoned) return fail(ctx, QE_ESTATE, "context is poisoned by an earlier CUDA error");
+  const uint32_t np = (uint32_t)ctx->probs.size();
+  if (!h_probs || !h_n_circuits) return fail(ctx, QE_EINVAL, "null item array");
+  if (n_items < 1 || n_items > np) return fail(ctx, QE_EINVAL, "n_items must be 1..n_probs");
+  std::vector<char> seen(np, 0);
+  uint32_t prec = 0;
+  size_t gate_bytes = 0, n_total = 0, k_total = 0;
+  for (uint32_t m = 0; m < n_items; ++m) {
+    const uint32_t q = h_probs[m];
+    if (q >= np) return fail(ctx, QE_EINVAL, "problem index out of range");
+    if (seen[q]) return fail(ctx, QE_EINVAL, "a problem appears twice in the batch");
+    seen[q] = 1;
+    const DevProblem &d = ctx->hp[q];
+    if (d.ising) return fail(ctx, QE_EINVAL, "Ising circuits need their angles (qe_eval_amp)");
+    if (h_n_circuits[m] > d.P) return fail(ctx, QE_EINVAL, "n_circuits must be <= population");
+    const uint32_t pr = d.prec == QE_PREC_FP64 ? 0u : 1u;
+    if (m == 0) prec = pr;
+    else if (pr != prec)
+      return fail(ctx, QE_EINVAL, "the batch mixes binary32 and binary64 searches");
+    gate_bytes += (size_t)h_n_circuits[m] * d.L;
+    n_total += h_n_circuits[m];
+    k_total += d.k < h_n_circuits[m] ? d.k : h_n_circuits[m];
+  }
+  if ((gate_bytes && !h_gate_idx) || (n_total && !h_fitness))
+    return fail(ctx, QE_EINVAL, "null buffer");
+  const size_t fb = prec == 0 ? 8 : 4;
+  const bool rank = h_topk != nullptr;
+  cudaStream_t us = ctx->user;
+  // the ranking scratch may still hold the last generation's pending ranking
+  qe_status st = drain(ctx);
+  if (st != QE_OK) return st;
+
+  const BatchLayout lay = batch_layout(gate_bytes, n_total, fb, k_total, n_items, np);
+  std::vector<uint32_t> key;
+  key.reserve(2 + 2 * (size_t)n_items);
+  key.push_back(rank ? 1u : 0u);
+  key.push_back(n_items);
+  for (uint32_t m = 0; m < n_items; ++m) {
+    key.push_back(h_probs[m]);
+    key.push_back(h_n_circuits[m]);
+  }
+  const bool regrow = lay.total > ctx->d_batch_bytes;
+  if (regrow || key != ctx->batch_key || !ctx->bexec) {
+    if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
+    if (ctx->bgraph) cudaGraphDestroy(ctx->bgraph);
+    ctx->bexec = nullptr;
+    ctx->bgraph = nullptr;
+    ctx->batch_key.clear();
+    if (regrow) {
+      QE_CUDA(ctx, cudaStreamSynchronize(us));
+      if (ctx->d_batch) cudaFree(ctx->d_batch);
+      ctx->d_batch = nullptr;
+      ctx->d_batch_bytes = 0;
+      QE_CUDA(ctx, cudaMalloc(&ctx->d_batch, lay.total));
+      ctx->d_batch_bytes = lay.total;
+    }
+    char *base = (char *)ctx->d_batch;
+    // jobs, top-k offsets and the gate table, uploaded once per layout
+    ctx->batch_meta.assign(lay.total - lay.jobs, 0);
+    RankJob *hj = (RankJob *)ctx->batch_meta.data();
+    uint32_t *hk = (uint32_t *)(ctx->batch_meta.data() + (lay.koff - lay.jobs));
+    const uint8_t **hg = (const uint8_t **)(ctx->batch_meta.data() + (lay.gtab - lay.jobs));
+    std::vector<uint32_t> items;  // items with circuits (ranked)
+    size_t go = 0, fo = 0, ko = 0;
+    std::vector<size_t> goff(n_items), foff(n_items);
+    for (uint32_t m = 0; m < n_items; ++m) {
+      const DevProblem &d = ctx->hp[h_probs[m]];
+      const uint32_t n = h_n_circuits[m];
+      goff[m] = go;
+      foff[m] = fo;
+      hg[h_probs[m]] = (const uint8_t *)(base + lay.gates + go);
+      if (n) {
+        RankJob &j = hj[items.size()];
+        j.prob = h_probs[m];
+        j.n = n;
+        j.fit = base + lay.fit + fo * fb;
+        j.meta = (const uint32_t *)(base + lay.cost) + fo;
+        j.gsrc = (const uint8_t *)(base + lay.gates + go);
+        j.asrc = nullptr;
+        j.update_record = 0;
+        j.pipelined = 0;
+        hk[items.size()] = (uint32_t)ko;
+        ko += d.k < n ? d.k : n;
+        items.push_back(m);
+      }
+      go += (size_t)n * d.L;
+      fo += n;
+    }
+    const uint32_t n_jobs = (uint32_t)items.size();
+    hk[n_jobs] = (uint32_t)ko;
+    QE_CUDA(ctx, cudaMemcpyAsync(base + lay.jobs, ctx->batch_meta.data(), ctx->batch_meta.size(),
+                                 cudaMemcpyHostToDevice, us));
+    // the device part of a call: the evaluations (spread over three captured
+    // streams), then the ranking of every item with circuits
+    cudaStream_t cs = ctx->cap;
+    cudaStream_t lanes[3] = {cs, ctx->side, ctx->side2};
+    QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(ctx->ev_fork, cs);
+    for (int l = 1; l < 3 && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(lanes[l], ctx->ev_fork, 0);
+    for (uint32_t x = 0; x < n_jobs && e == cudaSuccess; ++x) {
+      const uint32_t m = items[x];
+      const DevProblem &d = ctx->hp[h_probs[m]];
+      e = launch_eval(ctx->lc, d.n, ctx->d_probs, h_probs[m], prec == 0,
+                      (const uint8_t *)(base + lay.gates + goff[m]), nullptr, h_n_circuits[m],
+                      base + lay.fit + foff[m] * fb, (uint32_t *)(base + lay.cost) + foff[m],
+                      nullptr, ctx->g, lanes[x % 3]);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join2, 0);
+    if (rank && n_jobs) {
+      const RankJob *dj = (const RankJob *)(base + lay.jobs);
+      if (e == cudaSuccess) e = launch_reset_counter(ctx->g, cs);
+      if (e == cudaSuccess) e = launch_rank_select(ctx->d_probs, dj, n_jobs, RankJob{}, ctx->g, cs);
+      if (prec != 0) {
+        uint32_t widths = 0;
+        for (uint32_t x = 0; x < n_jobs; ++x) widths |= 1u << ctx->hp[h_probs[items[x]]].n;
+        for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
+          if (e == cudaSuccess && ((widths >> nq) & 1))
+            e = launch_rescore(ctx->lc, nq, false, ctx->d_probs, nullptr, nullptr, false, ctx->g,
+                               cs, (const uint8_t *const *)(base + lay.gtab));
+      }
+      if (e == cudaSuccess) e = launch_rank_sort(ctx->d_probs, dj, n_jobs, RankJob{}, ctx->g, cs);
+      if (e == cudaSuccess) e = launch_reset_counter(ctx->g, cs);
+    }
+    if (rank && e == cudaSuccess)
+      e = launch_gather_topk(ctx->d_probs, (const RankJob *)(base + lay.jobs),
+                             (const uint32_t *)(base + lay.koff), n_jobs,
+                             (Ranked *)(base + lay.topk), ctx->g, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(ctx, e, "capturing the batch evaluation graph");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+    ctx->bgraph = graph;
+    QE_CUDA(ctx, cudaGraphInstantiate(&ctx->bexec, graph, 0));
+    ctx->batch_key = key;
+  }
+  const size_t hb = (k_total + 1) * sizeof(Ranked);
+  if (rank && hb > ctx->h_batch_bytes) {
+    if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
+    ctx->h_batch = nullptr;
+    ctx->h_batch_bytes = 0;
+    QE_CUDA(ctx, cudaHostAlloc(&ctx->h_batch, hb, cudaHostAllocDefault));
+    ctx->h_batch_bytes = hb;
+  }
+  char *base = (char *)ctx->d_batch;
+  if (gate_bytes)
+    QE_CUDA(ctx, cudaMemcpyAsync(base + lay.gates, h_gate_idx, gate_bytes, cudaMemcpyHostToDevice, us));
+  QE_CUDA(ctx, cudaGraphLaunch(ctx->bexec, us));
+  if (n_total)
+    QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, base + lay.fit, n_total * fb, cudaMemcpyDeviceToHost, us));
+  if (rank)
+    QE_CUDA(ctx, cudaMemcpyAsync(ctx->h_batch, base + lay.topk, hb, cudaMemcpyDeviceToHost, us));
+  QE_CUDA(ctx, cudaStreamSynchronize(us));
+  if (!rank) return QE_OK;
+  const Ranked *r = (const Ranked *)ctx->h_batch;
+  for (size_t s = 0; s < k_total; ++s) {
+    h_topk[s].circuit = r[s].circuit;
+    h_topk[s].cost = r[s].cost;
+    h_topk[s].fitness = r[s].fitness;
+  }
+  const uint32_t errw = r[k_total].circuit;
+  if (errw) {
+    QE_CUDA(ctx, cudaMemsetAsync(ctx->g.err, 0, 4, us));
+    QE_CUDA(ctx, cudaStreamSynchronize(us));
+    return fail(ctx, QE_ENUMERIC, (errw & kErrBadGate) ? "invalid gate index in the circuits"
+                                                       : "non-finite fitness");
+  }
+  return QE_OK;
+}
+
 static qe_status compose_impl(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx,
                               const float2 *d_amps, uint32_t n_circuits, void *d_unitary) {
   qe_status st = check_ctx(ctx, prob);
@@ -1208,8 +1439,9 @@ qe_status qe_launch_plan(const qe_ctx *ctx, char *h_buf, size_t len) {
 qe_status qe_stage_timing(qe_ctx *ctx, int enable) {
   if (!ctx) return fail(nullptr, QE_EINVAL, "null context");
   if (ctx->poisoned) return fail(ctx, QE_ESTATE, "context is poisoned by an earlier CUDA error");
-  const bool want = enable != 0;
-  if (want == ctx->timing) return QE_OK;
+  if (enable < 0 || enable > 2) return fail(ctx, QE_EINVAL, "stage timing mode must be 0, 1 or 2");
+  const bool want = enable != 0, serial = enable == 2;
+  if (want == ctx->timing && (!want || serial == ctx->timing_serial)) return QE_OK;
   QE_CUDA(ctx, cudaStreamSynchronize(ctx->user));
   if (want && !ctx->tev[0])
     for (auto &ev : ctx->tev) QE_CUDA(ctx, cudaEventCreate(&ev));
@@ -1232,6 +1464,7 @@ qe_status qe_stage_timing(qe_ctx *ctx, int enable) {
     ctx->dgraph = nullptr;
   }
   ctx->timing = want;
+  ctx->timing_serial = want && serial;
   return QE_OK;
 }
 
@@ -1239,7 +1472,9 @@ qe_status qe_stage_times(qe_ctx *ctx, float *ms) {
   if (!ctx || !ms) return fail(ctx, QE_EINVAL, "null argument");
   if (!ctx->timing || !ctx->gexec) return fail(ctx, QE_ESTATE, "stage timing is not enabled");
   QE_CUDA(ctx, cudaStreamSynchronize(ctx->user));
-  const int pairs[6][2] = {{0, 1}, {0, 2}, {2, 3}, {3, 4}, {5, 6}, {0, 7}};
+  // serialised: the selection starts after the update, not with the generation
+  const int sel0 = ctx->timing_serial ? 6 : 0;
+  const int pairs[6][2] = {{0, 1}, {sel0, 2}, {2, 3}, {3, 4}, {5, 6}, {0, 7}};
   for (int k = 0; k < 6; ++k)
     QE_CUDA(ctx, cudaEventElapsedTime(&ms[k], ctx->tev[pairs[k][0]], ctx->tev[pairs[k][1]]));
   return QE_OK;

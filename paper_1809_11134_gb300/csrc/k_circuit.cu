@@ -1089,12 +1089,14 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
 
 // Binary64 rescoring of ranking candidates: list entries are problem << 20 | slot,
 // the circuit is cand[slot] of that problem, gates (and Ising angles) come from
-// gsrc/asrc (NULL = the problem's own generation buffers).  One launch per
+// gtab[problem] (a batch of several searches' caller circuits), else gsrc/asrc
+// (NULL = the problem's own generation buffers).  One launch per
 // (qubit count, library kind) present; other entries are skipped.
 template <int NQ, bool ISING>
 __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ probs,
                                                  const uint8_t *__restrict__ gsrc,
                                                  const float2 *__restrict__ asrc, int pipelined,
+                                                 const uint8_t *const *__restrict__ gtab,
                                                  DevGlobal g) {
   const int lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -1110,7 +1112,8 @@ __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ 
     const uint32_t slot = ent & 0xfffffu;
     const uint32_t c = p.cand[slot];
     const uint8_t *gates =
-        (gsrc ? gsrc : p.gate_idx + (size_t)par * p.P * p.L) + (size_t)c * p.L;
+        (gtab ? gtab[ent >> 20] : gsrc ? gsrc : p.gate_idx + (size_t)par * p.P * p.L) +
+        (size_t)c * p.L;
     bool bad = false;
     uint32_t o0 = kOpIdentity, o1 = kOpIdentity;
     if ((uint32_t)lane < p.L) o0 = op_of(p, gates[lane], bad);
@@ -1218,13 +1221,14 @@ cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *prob
 
 cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, bool ising, const DevProblem *probs,
                            const uint8_t *gsrc, const float2 *asrc, bool pipelined,
-                           const DevGlobal &g, cudaStream_t st) {
+                           const DevGlobal &g, cudaStream_t st, const uint8_t *const *gtab) {
   const uint32_t blocks = lc.num_sms * lc.step64[nq];
+  const int pl = pipelined ? 1 : 0;
 #define QE_L(NQ)                                                                           \
   if (ising)                                                                               \
-    k_rescore<NQ, true><<<blocks, 256, 0, st>>>(probs, gsrc, asrc, pipelined ? 1 : 0, g);  \
+    k_rescore<NQ, true><<<blocks, 256, 0, st>>>(probs, gsrc, asrc, pl, gtab, g);            \
   else                                                                                     \
-    k_rescore<NQ, false><<<blocks, 256, 0, st>>>(probs, gsrc, asrc, pipelined ? 1 : 0, g);
+    k_rescore<NQ, false><<<blocks, 256, 0, st>>>(probs, gsrc, asrc, pl, gtab, g);
   QE_NQ_SWITCH(nq, QE_L)
 #undef QE_L
   return cudaGetLastError();

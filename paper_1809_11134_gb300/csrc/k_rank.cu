@@ -440,6 +440,24 @@ __global__ void __launch_bounds__(kSortThreads) k_rank_sort(const DevProblem *__
   if (jb.update_record && tid < 32) record_best(p, jb, g, gen, kh[0], kl[0], kept, tid);
 }
 
+// top-k lists of a batch of ranked jobs, back to back, and the error word
+__global__ void __launch_bounds__(128) k_gather_topk(const DevProblem *__restrict__ probs,
+                                                     const RankJob *__restrict__ jobs,
+                                                     const uint32_t *__restrict__ koff,
+                                                     uint32_t n_jobs, Ranked *out, DevGlobal g) {
+  for (uint32_t m = blockIdx.x; m < n_jobs; m += gridDim.x) {
+    const RankJob jb = jobs[m];
+    const DevProblem &p = probs[jb.prob];
+    const uint32_t k = p.k < jb.n ? p.k : jb.n;
+    for (uint32_t s = threadIdx.x; s < k; s += blockDim.x) out[koff[m] + s] = p.topk_out[s];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Ranked e{};
+    e.circuit = *g.err;
+    out[koff[n_jobs]] = e;
+  }
+}
+
 __global__ void k_finish(DevGlobal g) {
   *g.gen += 1;
   *g.rescore_n = 0;
@@ -470,6 +488,13 @@ cudaError_t rank_init() {
 
 cudaError_t launch_finish(const DevGlobal &g, cudaStream_t st) {
   k_finish<<<1, 1, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_topk(const DevProblem *probs, const RankJob *jobs, const uint32_t *koff,
+                               uint32_t n_jobs, Ranked *out, const DevGlobal &g, cudaStream_t st) {
+  const uint32_t blocks = n_jobs ? (n_jobs < 1024 ? n_jobs : 1024) : 1;
+  k_gather_topk<<<blocks, 128, 0, st>>>(probs, jobs, koff, n_jobs, out, g);
   return cudaGetLastError();
 }
 

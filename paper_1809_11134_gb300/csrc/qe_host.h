@@ -66,10 +66,12 @@ cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *prob
                         cudaStream_t st);
 // gsrc == NULL: each candidate's search's own generation buffer; pipelined:
 // that buffer is the one of generation *gen - 1, and nothing runs unless the
-// chain is active
+// chain is active.  gtab != NULL (device array indexed by problem): each
+// candidate's gates come from gtab[its problem] instead.
 cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, bool ising, const DevProblem *probs,
                            const uint8_t *gsrc, const float2 *asrc, bool pipelined,
-                           const DevGlobal &g, cudaStream_t st);
+                           const DevGlobal &g, cudaStream_t st,
+                           const uint8_t *const *gtab = nullptr);
 
 // k_update.cu
 bool is_update_kernel(const void *f);  // an update kernel (graph node priorities)
@@ -96,6 +98,11 @@ cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uin
 cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
                              const RankJob &single, const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_finish(const DevGlobal &g, cudaStream_t st);
+// the top-k lists of n_jobs ranked jobs back to back (job m's from out[koff[m]],
+// koff has n_jobs + 1 entries), then the device error word in the entry
+// out[koff[n_jobs]]
+cudaError_t launch_gather_topk(const DevProblem *probs, const RankJob *jobs, const uint32_t *koff,
+                               uint32_t n_jobs, Ranked *out, const DevGlobal &g, cudaStream_t st);
 
 // GA (k_ga.cu): initial genome of one search into gate_idx buffer 0; per
 // generation the SUS prefix sums and elite of the searches in ids, then the

@@ -28,7 +28,7 @@ QE_ERRW_BAD_GATE, QE_ERRW_NONFINITE = 1, 2
 
 # every symbol include/qe.h declares
 EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_amp", "qe_eval_host",
-           "qe_compose", "qe_compose_amp",
+           "qe_eval_host_batch", "qe_compose", "qe_compose_amp",
            "qe_update", "qe_step", "qe_last_generation", "qe_state_bytes", "qe_get_state",
            "qe_set_state", "qe_generation", "qe_autotune", "qe_launch_plan", "qe_stage_timing",
            "qe_stage_times", "qe_measure_alu_peaks", "qe_save", "qe_load", "qe_checkpoint_info",
@@ -82,6 +82,8 @@ def lib():
         L.qe_sample.argtypes = [vp, u32, u32, vp, vp]
         L.qe_eval.argtypes = [vp, u32, vp, u32, vp, vp, C.POINTER(qe_ranked)]
         L.qe_eval_host.argtypes = [vp, u32, vp, u32, vp, C.POINTER(qe_ranked)]
+        L.qe_eval_host_batch.argtypes = [vp, u32, C.POINTER(u32), C.POINTER(u32), vp, vp,
+                                         C.POINTER(qe_ranked)]
         L.qe_compose.argtypes = [vp, u32, vp, u32, vp]
         L.qe_eval_amp.argtypes = [vp, u32, vp, vp, u32, vp, vp, C.POINTER(qe_ranked)]
         L.qe_compose_amp.argtypes = [vp, u32, vp, vp, u32, vp]
@@ -257,6 +259,43 @@ class Context:
         return _check(self.h, lib().qe_eval_host(self.h, prob, C.c_void_p(h_gates_ptr), n,
                                                  C.c_void_p(h_fit_ptr), topk_buf))
 
+    def eval_host_batch(self, items, topk=False):
+        """qe_eval_host_batch: items = [(prob, gate_idx ndarray [n, L]), ...]; returns
+        one fitness array per item and, with topk, one ranked list per item"""
+        probs = [int(q) for q, _ in items]
+        known = [p if 0 <= p < len(self._probs) else None for p in probs]
+        gs = [np.ascontiguousarray(g, np.uint8) for _, g in items]
+        gs = [g.reshape(-1, self._probs[q].circuit_len) if q is not None else g
+              for q, g in zip(known, gs)]
+        ns = [g.shape[0] for g in gs]
+        flat = np.concatenate([g.ravel() for g in gs]) if gs else np.zeros(0, np.uint8)
+        fp64 = known and known[0] is not None and \
+            self._probs[known[0]].precision == QE_PREC_FP64
+        fit = np.zeros(max(sum(ns), 1), np.float64 if fp64 else np.float32)
+        ks = [min(max(self._probs[q].topk, 1), n) if q is not None else 0
+              for q, n in zip(known, ns)]
+        out = (qe_ranked * max(sum(ks), 1))() if topk else None
+        u32a = C.c_uint32 * max(len(probs), 1)
+        _check(self.h, lib().qe_eval_host_batch(
+            self.h, len(probs), u32a(*probs), u32a(*ns),
+            flat.ctypes.data_as(C.c_void_p) if flat.size else None,
+            fit.ctypes.data_as(C.c_void_p), out))
+        fits, tops, fo, ko = [], [], 0, 0
+        for n, k in zip(ns, ks):
+            fits.append(fit[fo:fo + n].copy())
+            if topk:
+                tops.append([(r.circuit, r.cost, r.fitness) for r in out[ko:ko + k]])
+            fo += n
+            ko += k
+        return (fits, tops) if topk else fits
+
+    def eval_host_batch_ptr(self, probs_arr, n_arr, h_gates_ptr, h_fit_ptr, topk_buf=None):
+        """qe_eval_host_batch on raw host pointers (pinned buffers, for timing);
+        probs_arr / n_arr are ctypes uint32 arrays"""
+        return _check(self.h, lib().qe_eval_host_batch(self.h, len(probs_arr), probs_arr, n_arr,
+                                                       C.c_void_p(h_gates_ptr),
+                                                       C.c_void_p(h_fit_ptr), topk_buf))
+
     def compose(self, prob, gate_idx, unitary, n_circuits=None, amps=None):
         import torch
         p = self._probs[prob]
@@ -398,8 +437,11 @@ class Context:
         _check(self.h, lib().qe_launch_plan(self.h, b, 256))
         return b.value.decode()
 
-    def stage_timing(self, enable=True):
-        _check(self.h, lib().qe_stage_timing(self.h, 1 if enable else 0))
+    def stage_timing(self, enable=True, serial=False):
+        """events between the generation's kernels; serial=True runs them all on
+        one stream (each interval is that stage's own duration)"""
+        mode = 0 if not enable else (2 if serial else 1)
+        _check(self.h, lib().qe_stage_timing(self.h, mode))
 
     def stage_times(self):
         """ms of the last generation: circuits, select, rescore, sort, update, whole"""
@@ -452,6 +494,10 @@ def qe_eval(ctx: Context, prob, gate_idx, fitness, n_circuits=None, cost=None, t
 
 def qe_eval_host(ctx: Context, prob, gate_idx, topk=False):
     return ctx.eval_host(prob, gate_idx, topk)
+
+
+def qe_eval_host_batch(ctx: Context, items, topk=False):
+    return ctx.eval_host_batch(items, topk)
 
 
 def qe_compose(ctx: Context, prob, gate_idx, unitary, n_circuits=None):

@@ -73,3 +73,37 @@ def test_autotune_needs_stage_timing_off(qe, torch):
         assert len(ctx.autotune(1)) >= 4
         with pytest.raises(qe.QeError):
             ctx.autotune(0)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_stage_timing_leaves_the_trajectory_unchanged(qe, torch, mode):
+    """stage timing (events inside the graph, mode 1; every kernel serialised on
+    one stream, mode 2) changes only when the kernels run: the run follows the
+    untimed trajectory bit for bit, and every stage interval is positive"""
+    searches = (W.config(2, P=300)
+                + [W.Search(4, 9, 333, W.LIB_NCV | W.LIB_HT, W.cknot(4), seed=4, topk=5),
+                   W.Search(3, 30, 64, W.LIB_NCV | W.LIB_HT | W.LIB_IDENTITY, W.cknot(3),
+                            seed=5, encoding=W.ENC_GA)])
+    gens = 4
+    with qe.Context(searches) as a, qe.Context(searches) as b:
+        a.stage_timing(True, serial=(mode == 2))
+        for _ in range(gens):
+            a.step_raw(1, None)
+            ms = a.stage_times()
+            assert all(m > 0 for m in ms), ms
+            assert ms[0] <= ms[5] and ms[4] <= ms[5]
+        ra, rb = a.step(1), b.step(gens + 1)
+        a.stage_timing(False)
+        assert ra == rb
+        for r, s in enumerate(searches):
+            la, lb = a.last_generation(r), b.last_generation(r)
+            assert np.array_equal(la["gate_idx"], lb["gate_idx"])
+            assert np.array_equal(la["fitness"], lb["fitness"])
+            assert la["topk"] == lb["topk"]
+            sa, sb = a.get_state(r), b.get_state(r)
+            if s.encoding == W.ENC_GA:
+                assert np.array_equal(sa, sb)
+            else:
+                assert all(state_equal(x, y) for x, y in zip(sa, sb))
+        with pytest.raises(qe.QeError):
+            qe._check(a.h, qe.lib().qe_stage_timing(a.h, 3))

@@ -1,0 +1,169 @@
+"""qe_eval_host_batch (several searches' host circuits in one call) against the
+CPU oracle and against qe_eval_host, through the C ABI.
+
+Bit-exact: binary64 fitness, top-k (indices, costs, binary64 fitness) in both
+arithmetics, and the binary32 fitness against qe_eval_host's (same kernels).
+Within the stated bound: binary32 fitness against the oracle's binary64."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import assert_fp32_fitness, oracle_problem
+from paper_1809_11134_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+NCV, HT, ID = W.LIB_NCV, W.LIB_HT, W.LIB_IDENTITY
+
+
+@pytest.fixture(scope="module")
+def qe():
+    import __graft_entry__ as G
+    G.build()
+    from paper_1809_11134_gb300 import qe as Q
+    return Q
+
+
+def searches(prec):
+    # uneven widths, lengths, populations and top-k sizes in one context
+    return [W.Search(3, 16, 1000, NCV | HT | ID, W.cknot(3), seed=1, precision=prec, topk=32),
+            W.Search(4, 32, 300, NCV | HT, W.cknot(4), seed=7, precision=prec, topk=64,
+                     cost_weight=0.1),
+            W.Search(5, 64, 130, NCV | HT, W.cknot(5), seed=9, precision=prec, topk=128),
+            W.Search(2, 7, 33, NCV | ID, [0, 1, 3, 2], seed=4, precision=prec, topk=1),
+            W.Search(3, 5, 4096, NCV | ID, W.peres(), seed=0, precision=prec, topk=32,
+                     fitness_kind=W.FIT_PROB)]
+
+
+def gates_for(s, n, rng):
+    return W.random_gates(rng, n, s.L, oracle.num_gates(s.n, s.library))
+
+
+def check_item(s, g, fit, top):
+    F, C = oracle.eval_circuits(oracle_problem(s, 0), g)
+    if s.precision == W.PREC_FP64:
+        assert np.array_equal(fit, F)
+    else:
+        assert_fp32_fitness(fit, F, s, C)
+    if top is not None:
+        k = min(max(s.topk, 1), len(g))
+        order = oracle.topk(F, C, k) if len(g) else []
+        assert [t[0] for t in top] == list(order)
+        assert [t[1] for t in top] == list(C[order])
+        assert [t[2] for t in top] == list(F[order])
+
+
+@pytest.mark.parametrize("prec", [W.PREC_FP32, W.PREC_FP64])
+def test_batch_matches_oracle_and_single_calls(qe, prec):
+    ss = searches(prec)
+    rng = np.random.default_rng(11 + prec)
+    # items out of problem order, ragged counts (one at P, one of a single circuit)
+    plan = [(4, 4096), (1, 299), (0, 1000), (3, 1), (2, 77)]
+    items = [(q, gates_for(ss[q], n, rng)) for q, n in plan]
+    with qe.Context(ss) as ctx:
+        fits, tops = ctx.eval_host_batch(items, topk=True)
+        for (q, g), f, t in zip(items, fits, tops):
+            check_item(ss[q], g, f, t)
+            f1, t1 = ctx.eval_host(q, g, topk=True)
+            assert np.array_equal(f.view(np.uint8), f1.view(np.uint8))
+            assert t == t1
+        # without ranking: the same fitness
+        fits2 = ctx.eval_host_batch(items)
+        for f, f2 in zip(fits, fits2):
+            assert np.array_equal(f.view(np.uint8), f2.view(np.uint8))
+
+
+def test_batch_layouts_replay_and_change(qe):
+    """the captured graph is replayed while the layout repeats and rebuilt when
+    it changes (other problems, counts, a larger staging area); every call is
+    checked against the oracle"""
+    ss = searches(W.PREC_FP32)
+    rng = np.random.default_rng(5)
+    plans = [[(0, 1000), (1, 300)], [(0, 1000), (1, 300)], [(1, 17)],
+             [(4, 4096), (2, 130), (0, 999), (1, 300), (3, 33)], [(0, 1000), (1, 300)]]
+    with qe.Context(ss) as ctx:
+        for plan in plans:
+            items = [(q, gates_for(ss[q], n, rng)) for q, n in plan]
+            fits, tops = ctx.eval_host_batch(items, topk=True)
+            for (q, g), f, t in zip(items, fits, tops):
+                check_item(ss[q], g, f, t)
+
+
+def test_batch_empty_items(qe):
+    ss = searches(W.PREC_FP32)
+    rng = np.random.default_rng(9)
+    with qe.Context(ss) as ctx:
+        items = [(0, gates_for(ss[0], 0, rng)), (2, gates_for(ss[2], 64, rng)),
+                 (1, gates_for(ss[1], 0, rng))]
+        fits, tops = ctx.eval_host_batch(items, topk=True)
+        assert [len(f) for f in fits] == [0, 64, 0]
+        assert tops[0] == [] and tops[2] == []
+        check_item(ss[2], items[1][1], fits[1], tops[1])
+        # nothing to evaluate at all
+        fits, tops = ctx.eval_host_batch([(3, gates_for(ss[3], 0, rng))], topk=True)
+        assert len(fits[0]) == 0 and tops == [[]]
+
+
+def test_batch_rejects_bad_arguments(qe):
+    ss = searches(W.PREC_FP32)
+    rng = np.random.default_rng(3)
+    g0 = gates_for(ss[0], 10, rng)
+    with qe.Context(ss) as ctx:
+        bad = [[(0, g0), (0, g0)],                               # a problem twice
+               [(0, gates_for(ss[0], 1001, rng))],               # more than P circuits
+               [(7, g0)]]                                        # no such problem
+        for items in bad:
+            with pytest.raises(qe.QeError) as e:
+                ctx.eval_host_batch(items, topk=True)
+            assert e.value.status == qe.QE_EINVAL
+        with pytest.raises(qe.QeError) as e:
+            ctx.eval_host_batch([], topk=True)
+        assert e.value.status == qe.QE_EINVAL
+        # the context stays usable
+        fits, tops = ctx.eval_host_batch([(0, g0)], topk=True)
+        check_item(ss[0], g0, fits[0], tops[0])
+    mixed = [searches(W.PREC_FP32)[0], searches(W.PREC_FP64)[1]]
+    with qe.Context(mixed) as ctx:
+        with pytest.raises(qe.QeError) as e:
+            ctx.eval_host_batch([(0, gates_for(mixed[0], 4, rng)),
+                                 (1, gates_for(mixed[1], 4, rng))])
+        assert e.value.status == qe.QE_EINVAL
+    ising = W.Search(3, 8, 16, W.LIB_ISING, W.cknot(3), seed=1, topk=4)
+    with qe.Context([ising]) as ctx:
+        with pytest.raises(qe.QeError) as e:
+            ctx.eval_host_batch([(0, np.zeros((4, 8), np.uint8))])
+        assert e.value.status == qe.QE_EINVAL
+
+
+def test_batch_invalid_gate_index_is_reported(qe):
+    ss = searches(W.PREC_FP32)
+    rng = np.random.default_rng(4)
+    g0, g1 = gates_for(ss[0], 50, rng), gates_for(ss[1], 40, rng)
+    g1[7, 3] = 250
+    with qe.Context(ss) as ctx:
+        with pytest.raises(qe.QeError) as e:
+            ctx.eval_host_batch([(0, g0), (1, g1)], topk=True)
+        assert e.value.status == qe.QE_ENUMERIC
+        g1[7, 3] = 0
+        fits, tops = ctx.eval_host_batch([(0, g0), (1, g1)], topk=True)
+        for (q, g), f, t in zip([(0, g0), (1, g1)], fits, tops):
+            check_item(ss[q], g, f, t)
+
+
+def test_batch_between_generations_leaves_the_run_unchanged(qe):
+    """a batch evaluation between qe_step calls (it first ranks the pending
+    generation) changes nothing in the run: binary64 reports equal those of a
+    run without it"""
+    ss = [W.Search(3, 16, 512, NCV | HT | ID, W.cknot(3), seed=1, precision=W.PREC_FP64,
+                   topk=8),
+          W.Search(4, 12, 256, NCV | HT, W.cknot(4), seed=2, precision=W.PREC_FP64, topk=8)]
+    rng = np.random.default_rng(8)
+    with qe.Context(ss) as a, qe.Context(ss) as b:
+        for gen in range(4):
+            ra, rb = a.step(1), b.step(1)
+            assert ra == rb
+            items = [(1, gates_for(ss[1], 100, rng)), (0, gates_for(ss[0], 512, rng))]
+            fits, tops = a.eval_host_batch(items, topk=True)
+            for (q, g), f, t in zip(items, fits, tops):
+                check_item(ss[q], g, f, t)
+        assert a.step(1) == b.step(1)
