@@ -24,6 +24,12 @@ namespace qe {
 // contexts with at most this many QEQEA searches use the listed mutation role;
 // every block of that kernel walks the searches one after another
 constexpr uint32_t kListMaxSearches = 64;
+// role A runs four lanes per slot (k_update_elite4) from this many slots of
+// all searches together
+#ifndef QE_QUAD_MIN_SLOTS
+#define QE_QUAD_MIN_SLOTS (1u << 20)
+#endif
+constexpr uint64_t kQuadMinSlots = QE_QUAD_MIN_SLOTS;
 
 struct fc {
   float re, im;
@@ -54,16 +60,12 @@ __device__ __forceinline__ void elitism(const DevProblem &p, uint32_t seg, float
                                         float4 &c0, float4 &c1, const float4 b0,
                                         const float4 b1) {
   if (sf > bf) {
-    float4 *bp = best_of(p, seg);
-    bp[0] = c0;
-    bp[1] = c1;
+    st_rec(best_of(p, seg), c0, c1);
     *bestf_of(p, seg) = sf;
   } else {
     c0 = b0;
     c1 = b1;
-    float4 *cp = cur_of(p, seg);
-    cp[0] = b0;
-    cp[1] = b1;
+    st_rec(cur_of(p, seg), b0, b1);
   }
 }
 
@@ -109,8 +111,7 @@ __device__ __forceinline__ void mutate(const DevProblem &p, const DevGlobal &g, 
   a = make_float4(o[0].re, o[0].im, o[1].re, o[1].im);
   b.x = o[2].re;
   b.y = o[2].im;
-  cp[0] = a;
-  cp[1] = b;
+  st_rec(cp, a, b);
 }
 
 __device__ __forceinline__ uint32_t find_q(const uint32_t *prefix, uint32_t n, uint32_t x) {
@@ -141,8 +142,9 @@ __global__ void __launch_bounds__(256, 8) k_update_elite(const DevProblem *__res
     const uint32_t i = (seg % p.LP) / p.L;
     if (mutates(p, i, gen)) continue;
     const float4 *line = cur_of(p, seg);
-    float4 c0 = line[0], c1 = line[1];
-    const float4 b0 = line[2], b1 = line[3];
+    float4 c0, c1, b0, b1;
+    ld_rec(line, c0, c1);
+    ld_rec(line + 2, b0, b1);
     // best fitness and fitness key in one 64-bit atomic that clears the key
     // (low word: best_f bits, high word: key); one slot per segment sees it set
     const unsigned long long pr =
@@ -150,6 +152,66 @@ __global__ void __launch_bounds__(256, 8) k_update_elite(const DevProblem *__res
     const float bf = __uint_as_float((uint32_t)pr);
     const uint32_t key = (uint32_t)(pr >> 32);
     if (key) elitism(p, seg, fkey_inv(key), bf, c0, c1, b0, b1);
+  }
+}
+
+// Role A with four lanes per slot, for large populations, where role A is
+// bound by the number of scattered requests in flight rather than by their
+// latency: lane q of a quad moves the 16-B quarter q of the segment's 64-B line
+// (cur low, cur high, best low, best high), so every request covers whole
+// sectors of one line, and lane 0 of the quad takes the {best_f, key} word.
+// Elitism then copies a record through one shuffle: best <- cur on lanes 2, 3
+// (from lanes 0, 1), cur <- best on lanes 0, 1 (from lanes 2, 3).
+__global__ void __launch_bounds__(256, 8) k_update_elite4(const DevProblem *__restrict__ probs,
+                                                          const uint32_t *__restrict__ group,
+                                                          const uint32_t *__restrict__ prefA,
+                                                          uint32_t n_group, uint32_t totalA,
+                                                          const uint32_t *d_gen, uint32_t gen_arg,
+                                                          const uint32_t *seg_override) {
+  const uint32_t gen = d_gen ? *d_gen : gen_arg;
+  const int lane = threadIdx.x & 31, q4 = lane & 3, qbase = lane & ~3;
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  // the trip count is the same for every lane of a warp (shuffles below)
+  for (uint32_t base = w0 * 8u; base < totalA; base += nw * 8u) {
+    const uint32_t e = base + (uint32_t)(lane >> 2);
+    const DevProblem *pp = probs;
+    uint32_t seg = 0;
+    bool act = e < totalA;
+    if (act) {
+      const uint32_t q = find_q(prefA, n_group, e);
+      pp = probs + group[q];
+      const uint32_t local = e - prefA[q];
+      seg = seg_override ? seg_override[local] : pp->seg_id[local];
+      act = seg < pp->nseg;  // caller-provided ids are checked
+      if (act) act = !mutates(*pp, (seg % pp->LP) / pp->L, gen);
+    }
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned long long pr = 0;
+    if (act) {
+      v = cur_of(*pp, seg)[q4];
+      // best fitness and fitness key in one 64-bit atomic that clears the key
+      if (q4 == 0)
+        pr = atomicAnd(reinterpret_cast<unsigned long long *>(pp->fk + 2 * (size_t)seg),
+                       0xffffffffull);
+    }
+    pr = __shfl_sync(kFull, pr, qbase);
+    float4 o;
+    o.x = __shfl_xor_sync(kFull, v.x, 2);
+    o.y = __shfl_xor_sync(kFull, v.y, 2);
+    o.z = __shfl_xor_sync(kFull, v.z, 2);
+    o.w = __shfl_xor_sync(kFull, v.w, 2);
+    const uint32_t key = (uint32_t)(pr >> 32);
+    if (act && key) {
+      const float sf = fkey_inv(key), bf = __uint_as_float((uint32_t)pr);
+      float4 *line = cur_of(*pp, seg);
+      if (sf > bf) {
+        if (q4 >= 2) line[q4] = o;
+        if (q4 == 0) *bestf_of(*pp, seg) = sf;
+      } else if (q4 < 2) {
+        line[q4] = o;
+      }
+    }
   }
 }
 
@@ -161,9 +223,11 @@ __device__ __forceinline__ void mutate_segment(const DevProblem &p, const DevGlo
   const uint32_t key = fkv.y;
   float bf = __uint_as_float(fkv.x);
   const float4 *line = cur_of(p, seg);
-  float4 c0 = line[0], c1 = line[1];
+  float4 c0, c1;
+  ld_rec(line, c0, c1);
   if (key) {
-    const float4 b0 = line[2], b1 = line[3];
+    float4 b0, b1;
+    ld_rec(line + 2, b0, b1);
     *key_of(p, seg) = 0u;
     const float sf = fkey_inv(key);
     elitism(p, seg, sf, bf, c0, c1, b0, b1);
@@ -261,7 +325,8 @@ __global__ void __launch_bounds__(256) k_init_state(const DevProblem *__restrict
 }
 
 bool is_update_kernel(const void *f) {
-  return f == (const void *)k_update_elite || f == (const void *)k_update_mutate ||
+  return f == (const void *)k_update_elite || f == (const void *)k_update_elite4 ||
+         f == (const void *)k_update_mutate ||
          f == (const void *)k_update_mutate_list;
 }
 
@@ -291,7 +356,8 @@ cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const ui
                           uint32_t totalA, uint32_t totalB, const uint32_t *d_gen, uint32_t gen,
                           const uint32_t *seg_override, const DevGlobal &g, cudaStream_t stA,
                           cudaStream_t stB) {
-  uint64_t bA = ((uint64_t)totalA + 255) / 256;
+  const bool quad = (uint64_t)totalA >= kQuadMinSlots;
+  uint64_t bA = ((uint64_t)totalA * (quad ? 4 : 1) + 255) / 256;
   const uint64_t capA = (uint64_t)lc.num_sms * 8;
   if (bA > capA) bA = capA;
   if (!bA) bA = 1;
@@ -299,8 +365,12 @@ cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const ui
   const uint64_t capB = (uint64_t)lc.num_sms * 8;
   if (bB > capB) bB = capB;
   if (!bB) bB = 1;
-  k_update_elite<<<(uint32_t)bA, 256, 0, stA>>>(probs, group, prefA, n_group, totalA, d_gen, gen,
-                                                seg_override);
+  if (quad)
+    k_update_elite4<<<(uint32_t)bA, 256, 0, stA>>>(probs, group, prefA, n_group, totalA, d_gen,
+                                                   gen, seg_override);
+  else
+    k_update_elite<<<(uint32_t)bA, 256, 0, stA>>>(probs, group, prefA, n_group, totalA, d_gen,
+                                                  gen, seg_override);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (d_gen && n_group <= kListMaxSearches) {

@@ -192,6 +192,24 @@ __device__ __forceinline__ uint32_t *key_of(const DevProblem &p, uint32_t seg) {
   return p.fk + 2 * (size_t)seg + 1;
 }
 
+// ---------------------------------------------------------------- 32-B records
+// A segment's cur or best record is 32 B and 32-B aligned: each is moved as
+// one 256-bit access (sm_100 and later), half the load/store instructions of
+// two float4 moves, which matters where the update is bound by the number of
+// scattered memory requests in flight.
+__device__ __forceinline__ void ld_rec(const float4 *p, float4 &a, float4 &b) {
+  asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z),
+                 "=f"(b.w)
+               : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ void st_rec(float4 *p, const float4 a, const float4 b) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y),
+               "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+               : "memory");
+}
+
 // ---------------------------------------------------------------- lane layout
 // A warp holds one circuit's N x N unitary: lane = (row group g, column j),
 // j = lane & (N-1), g = the next RBL lane bits; each lane keeps ROWS rows of

@@ -246,6 +246,28 @@ def test_update_bit_exact(qe, torch, pm, si):
             assert state_equal(bf2, bf)
 
 
+@pytest.mark.parametrize("P", [16383, 16384])
+def test_update_bit_exact_many_slots(qe, torch, P):
+    """2^20 circuit slots (L = 64, P = 16384) and one circuit fewer: the two
+    sides of the size from which the elitism role runs four lanes per slot"""
+    s = W.Search(2, 64, P, NCV, [0, 1, 3, 2], seed=6, precision=W.PREC_FP64, p_mutation=0.1)
+    rng = np.random.default_rng(P)
+    with qe.Context([s]) as ctx:
+        p = oracle_problem(s, 0)
+        cur, best, bf = W.random_state(rng, oracle.num_segments(p), best_f_range=(-1.0, 0.9))
+        ctx.set_state(0, cur, best, bf)
+        for gen in (0, 1):
+            gi, sid = oracle.sample(p, cur, gen)
+            F = W.random_fitness(rng, s.P, discrete=gen == 0)
+            ctx.update(0, gen, torch.from_numpy(sid.view(np.int32).ravel()).cuda(),
+                       torch.from_numpy(F).cuda())
+            oracle.update(p, cur, best, bf, gen, sid, F)
+            c2, b2, bf2 = ctx.get_state(0)
+            assert state_equal(c2, cur)
+            assert state_equal(b2, best)
+            assert state_equal(bf2, bf)
+
+
 # ------------------------------------------------------------------ whole generations
 def _oracle_run(searches, gens):
     out = []
@@ -262,9 +284,13 @@ def _oracle_run(searches, gens):
     return out
 
 
-@pytest.mark.parametrize("cfg,P,gens", [(1, None, 20), (2, 256, 12)])
+@pytest.mark.parametrize("cfg,P,gens", [(1, None, 20), (2, 256, 12), (0, 16384, 3)])
 def test_step_trajectory_fp64_bit_exact(qe, torch, cfg, P, gens):
-    searches = W.config(cfg, precision=W.PREC_FP64, P=P)
+    if cfg == 0:  # 2^20 circuit slots per generation (L = 64): the four-lane elitism role
+        searches = [W.Search(2, 64, P, NCV | HT, [0, 1, 3, 2], seed=6, precision=W.PREC_FP64,
+                             topk=16)]
+    else:
+        searches = W.config(cfg, precision=W.PREC_FP64, P=P)
     ref = _oracle_run(searches, gens)
     with qe.Context(searches) as ctx:
         for gen in range(gens):
