@@ -392,6 +392,54 @@ qe_status add_select_first_edge(qe_ctx *ctx, cudaGraph_t graph) {
   return QE_OK;
 }
 
+// Programmatic dependent launch: every plain edge from a kernel node to a kernel
+// that begins by waiting for its predecessor (the update roles, the binary64
+// rescoring, the ranking sort) becomes a programmatic edge, so that the kernel
+// is launched while its predecessor's last blocks still run instead of after
+// the predecessor has completed; it then waits on the device for that
+// completion before reading what the predecessor wrote.
+qe_status add_pdl_edges(qe_ctx *ctx, cudaGraph_t graph) {
+  size_t nn = 0;
+  QE_CUDA(ctx, cudaGraphGetNodes(graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  QE_CUDA(ctx, cudaGraphGetNodes(graph, nodes.data(), &nn));
+  auto kernel_of = [&](cudaGraphNode_t nd, const void **f) -> qe_status {
+    cudaGraphNodeType ty;
+    QE_CUDA(ctx, cudaGraphNodeGetType(nd, &ty));
+    *f = nullptr;
+    if (ty != cudaGraphNodeTypeKernel) return QE_OK;
+    cudaKernelNodeParams kp;
+    QE_CUDA(ctx, cudaGraphKernelNodeGetParams(nd, &kp));
+    *f = kp.func;
+    return QE_OK;
+  };
+  cudaGraphEdgeData prog;
+  memset(&prog, 0, sizeof prog);
+  prog.from_port = cudaGraphKernelNodePortProgrammatic;
+  prog.type = cudaGraphDependencyTypeProgrammatic;
+  for (auto nd : nodes) {
+    const void *f = nullptr;
+    qe_status st = kernel_of(nd, &f);
+    if (st != QE_OK) return st;
+    if (!f || !(is_update_kernel(f) || is_rescore_kernel(f) || is_sort_kernel(f))) continue;
+    size_t nd_deps = 0;
+    QE_CUDA(ctx, cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &nd_deps));
+    if (!nd_deps) continue;
+    std::vector<cudaGraphNode_t> deps(nd_deps);
+    std::vector<cudaGraphEdgeData> eds(nd_deps);
+    QE_CUDA(ctx, cudaGraphNodeGetDependencies(nd, deps.data(), eds.data(), &nd_deps));
+    for (size_t k = 0; k < nd_deps; ++k) {
+      const void *pf = nullptr;
+      st = kernel_of(deps[k], &pf);
+      if (st != QE_OK) return st;
+      if (!pf || eds[k].type != cudaGraphDependencyTypeDefault || eds[k].from_port != 0) continue;
+      QE_CUDA(ctx, cudaGraphRemoveDependencies(graph, &deps[k], &nd, &eds[k], 1));
+      QE_CUDA(ctx, cudaGraphAddDependencies(graph, &deps[k], &nd, &prog, 1));
+    }
+  }
+  return QE_OK;
+}
+
 // the ranking chain of generation *gen - 1 (select -> binary64 rescoring -> sort)
 cudaError_t enqueue_rank_chain(qe_ctx *ctx, cudaStream_t cs) {
   RankJob none{};
@@ -490,6 +538,7 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
   }
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
   qe_status st = set_priorities(ctx, graph);
+  if (st == QE_OK) st = add_pdl_edges(ctx, graph);
   if (st == QE_OK && plan.select_first && !serial) st = add_select_first_edge(ctx, graph);
   if (st != QE_OK) {
     cudaGraphDestroy(graph);
@@ -532,6 +581,8 @@ qe_status build_graph(qe_ctx *ctx) {
   }
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
   ctx->dgraph = graph;
+  qe_status pst = add_pdl_edges(ctx, graph);
+  if (pst != QE_OK) return pst;
   QE_CUDA(ctx, cudaGraphInstantiate(&ctx->dexec, graph, 0));
   return QE_OK;
 }
@@ -1217,6 +1268,8 @@ qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_pr
     }
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
     ctx->bgraph = graph;
+    qe_status pst = add_pdl_edges(ctx, graph);
+    if (pst != QE_OK) return pst;
     QE_CUDA(ctx, cudaGraphInstantiate(&ctx->bexec, graph, 0));
     ctx->batch_key = key;
   }

@@ -1098,6 +1098,7 @@ __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ 
                                                  const float2 *__restrict__ asrc, int pipelined,
                                                  const uint8_t *const *__restrict__ gtab,
                                                  DevGlobal g) {
+  wait_predecessor();  // the selection's candidates and chain flag
   const int lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   if (pipelined && !*g.rank_active) return;
@@ -1244,6 +1245,15 @@ bool is_circuit_kernel(const void *f) {
       f == (const void *)k_step<NQ, double, true, false, true> ||                         \
       f == (const void *)k_step<NQ, float, false, true, true> ||                          \
       f == (const void *)k_step<NQ, double, true, true, true>)                            \
+    return true;
+  QE_K(1) QE_K(2) QE_K(3) QE_K(4) QE_K(5)
+#undef QE_K
+  return false;
+}
+
+bool is_rescore_kernel(const void *f) {
+#define QE_K(NQ)                                                                         \
+  if (f == (const void *)k_rescore<NQ, false> || f == (const void *)k_rescore<NQ, true>) \
     return true;
   QE_K(1) QE_K(2) QE_K(3) QE_K(4) QE_K(5)
 #undef QE_K

@@ -307,6 +307,7 @@ __device__ __forceinline__ void keep_side(unsigned long long &h, unsigned long l
 __global__ void __launch_bounds__(kSortThreads) k_rank_sort(const DevProblem *__restrict__ probs,
                                                             const RankJob *__restrict__ jobs,
                                                             RankJob single, DevGlobal g) {
+  wait_predecessor();  // the candidates and their binary64 fitness
   RankJob jb = jobs ? jobs[blockIdx.x] : single;
   const DevProblem &p = probs[jb.prob];
   uint32_t gen = 0;
@@ -480,6 +481,7 @@ cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint3
 }
 
 bool is_select_kernel(const void *f) { return f == (const void *)k_rank_select; }
+bool is_sort_kernel(const void *f) { return f == (const void *)k_rank_sort; }
 
 cudaError_t rank_init() {
   return cudaFuncSetAttribute(k_rank_select, cudaFuncAttributeMaxDynamicSharedMemorySize,

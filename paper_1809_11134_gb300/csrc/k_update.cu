@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(256, 8) k_update_elite(const DevProblem *__res
                                                          uint32_t n_group, uint32_t totalA,
                                                          const uint32_t *d_gen, uint32_t gen_arg,
                                                          const uint32_t *seg_override) {
+  wait_predecessor();  // the circuit kernel's ids, keys and lists
   const uint32_t gen = d_gen ? *d_gen : gen_arg;
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < totalA;
        e += gridDim.x * blockDim.x) {
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(256, 8) k_update_elite4(const DevProblem *__re
                                                           uint32_t n_group, uint32_t totalA,
                                                           const uint32_t *d_gen, uint32_t gen_arg,
                                                           const uint32_t *seg_override) {
+  wait_predecessor();  // the circuit kernel's ids, keys and lists
   const uint32_t gen = d_gen ? *d_gen : gen_arg;
   const int lane = threadIdx.x & 31, q4 = lane & 3, qbase = lane & ~3;
   const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -243,6 +245,7 @@ __global__ void __launch_bounds__(256) k_update_mutate_list(const DevProblem *__
                                                             const uint32_t *__restrict__ group,
                                                             uint32_t n_group,
                                                             const uint32_t *d_gen, DevGlobal g) {
+  wait_predecessor();  // the circuit kernel's ids, keys and lists
   const uint32_t gen = *d_gen, par = gen & 1u;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t q = 0; q < n_group; ++q) {
@@ -266,6 +269,7 @@ __global__ void __launch_bounds__(256) k_update_mutate(const DevProblem *__restr
                                                        uint32_t n_group, uint32_t totalB,
                                                        const uint32_t *d_gen, uint32_t gen_arg,
                                                        DevGlobal g) {
+  wait_predecessor();  // the circuit kernel's ids, keys and lists
   const uint32_t gen = d_gen ? *d_gen : gen_arg;
   const int lane = threadIdx.x & 31;
   const uint32_t nwB = (gridDim.x * blockDim.x) >> 5;

@@ -192,6 +192,16 @@ __device__ __forceinline__ uint32_t *key_of(const DevProblem &p, uint32_t seg) {
   return p.fk + 2 * (size_t)seg + 1;
 }
 
+// ---------------------------------------------------------------- dependent launch
+// A kernel behind a programmatic graph edge may be launched before the kernel
+// it depends on has finished (the launch overlaps that kernel's last blocks);
+// it waits here, before reading anything that kernel writes, until the
+// kernel has completed and its writes are visible.  Launched any other way it
+// returns at once.
+__device__ __forceinline__ void wait_predecessor() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- 32-B records
 // A segment's cur or best record is 32 B and 32-B aligned: each is moved as
 // one 256-bit access (sm_100 and later), half the load/store instructions of

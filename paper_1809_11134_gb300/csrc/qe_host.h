@@ -48,6 +48,7 @@ struct RankJob {
 // k_circuit.cu
 cudaError_t query_circuit_occupancy(LaunchCfg &lc);
 bool is_circuit_kernel(const void *f);  // a generation circuit kernel (graph node priorities)
+bool is_rescore_kernel(const void *f);  // binary64 rescoring (waits for its predecessor)
 // all searches of a launch have n qubits
 cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs,
                         const uint32_t *group, const uint32_t *prefix, uint32_t n_group,
@@ -93,6 +94,7 @@ cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const ui
 cudaError_t rank_init();  // once per device before the first ranking launch
 // jobs == NULL: one job given by value in `single`
 bool is_select_kernel(const void *f);  // the ranking's selection kernel (graph edges)
+bool is_sort_kernel(const void *f);    // the ranking's sort (waits for its predecessor)
 cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
                                const RankJob &single, const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
