@@ -197,6 +197,30 @@ def test_topk_bit_exact(qe, torch, prec, n, lib, L, P, k):
         assert [t[2] for t in top] == list(F[order])
 
 
+@pytest.mark.parametrize("prec", [W.PREC_FP32, W.PREC_FP64])
+def test_topk_exact_whatever_the_previous_ranking(qe, torch, prec):
+    """rankings in one context share their scratch (candidates, queue, top-k
+    buffer): each top-k must depend on its own circuits only; the same
+    population twice, a worse one after a better one, a better one after a
+    worse one, and populations of other sizes in between"""
+    s = S(3, 16, 4096, NCV | HT | ID, precision=prec, topk=32)
+    rng = np.random.default_rng(77 + prec)
+    g_good = W.random_gates(rng, 4096, 16, _G(s))
+    g_bad = g_good.copy()
+    g_bad[:, :] = 0  # all identities: every circuit scores f(I) (ties everywhere)
+    g_bad[::7] = W.random_gates(rng, len(g_bad[::7]), 16, _G(s))
+    dt = torch.float64 if prec == W.PREC_FP64 else torch.float32
+    with qe.Context([s]) as ctx:
+        for g in (g_good, g_good, g_bad, g_good, g_good[:100], g_good[:31], g_bad, g_bad):
+            n = len(g)
+            fit = torch.zeros(n, dtype=dt, device="cuda")
+            top = ctx.eval(0, torch.from_numpy(np.ascontiguousarray(g)).cuda(), fit, topk=True)
+            F, C = oracle.eval_circuits(oracle_problem(s, 0), g)
+            order = oracle.topk(F, C, min(32, n))
+            assert [t[0] for t in top] == list(order)
+            assert [t[2] for t in top] == list(F[order])
+
+
 def test_invalid_gate_index_is_reported(qe, torch):
     s = S(3, 4, 16, NCV | ID, precision=W.PREC_FP32, topk=4)
     g = np.zeros((16, 4), np.uint8)
