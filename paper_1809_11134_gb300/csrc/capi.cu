@@ -394,7 +394,8 @@ qe_status add_select_first_edge(qe_ctx *ctx, cudaGraph_t graph) {
 
 // Programmatic dependent launch: every plain edge from a kernel node to a kernel
 // that begins by waiting for its predecessor (the update roles, the binary64
-// rescoring, the ranking sort) becomes a programmatic edge, so that the kernel
+// rescoring, the ranking sort, the top-k gather, the generation counter's
+// finish) becomes a programmatic edge, so that the kernel
 // is launched while its predecessor's last blocks still run instead of after
 // the predecessor has completed; it then waits on the device for that
 // completion before reading what the predecessor wrote.
@@ -421,7 +422,7 @@ qe_status add_pdl_edges(qe_ctx *ctx, cudaGraph_t graph) {
     const void *f = nullptr;
     qe_status st = kernel_of(nd, &f);
     if (st != QE_OK) return st;
-    if (!f || !(is_update_kernel(f) || is_rescore_kernel(f) || is_sort_kernel(f))) continue;
+    if (!f || !(is_update_kernel(f) || is_rescore_kernel(f) || rank_kernel_waits(f))) continue;
     size_t nd_deps = 0;
     QE_CUDA(ctx, cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &nd_deps));
     if (!nd_deps) continue;

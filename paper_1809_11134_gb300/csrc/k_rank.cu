@@ -446,6 +446,7 @@ __global__ void __launch_bounds__(128) k_gather_topk(const DevProblem *__restric
                                                      const RankJob *__restrict__ jobs,
                                                      const uint32_t *__restrict__ koff,
                                                      uint32_t n_jobs, Ranked *out, DevGlobal g) {
+  wait_predecessor();  // the sorted lists
   for (uint32_t m = blockIdx.x; m < n_jobs; m += gridDim.x) {
     const RankJob jb = jobs[m];
     const DevProblem &p = probs[jb.prob];
@@ -460,6 +461,7 @@ __global__ void __launch_bounds__(128) k_gather_topk(const DevProblem *__restric
 }
 
 __global__ void k_finish(DevGlobal g) {
+  wait_predecessor();  // the ranking and the update read the counter
   *g.gen += 1;
   *g.rescore_n = 0;
 }
@@ -481,7 +483,10 @@ cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint3
 }
 
 bool is_select_kernel(const void *f) { return f == (const void *)k_rank_select; }
-bool is_sort_kernel(const void *f) { return f == (const void *)k_rank_sort; }
+bool rank_kernel_waits(const void *f) {
+  return f == (const void *)k_rank_sort || f == (const void *)k_finish ||
+         f == (const void *)k_gather_topk;
+}
 
 cudaError_t rank_init() {
   return cudaFuncSetAttribute(k_rank_select, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -94,7 +94,7 @@ cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const ui
 cudaError_t rank_init();  // once per device before the first ranking launch
 // jobs == NULL: one job given by value in `single`
 bool is_select_kernel(const void *f);  // the ranking's selection kernel (graph edges)
-bool is_sort_kernel(const void *f);    // the ranking's sort (waits for its predecessor)
+bool rank_kernel_waits(const void *f);  // sort, top-k gather, finish: wait for their predecessor
 cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
                                const RankJob &single, const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
