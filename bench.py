@@ -300,6 +300,7 @@ def run_ours(args):
         {"kernel": "k_step (sample + compose + score + scatter)", "bound": "alu",
          "achieved_tflops": roof["achieved"], "frac_of_derived_fp32": roof["frac"],
          "frac_of_measured_fp32": roof["achieved"] / alu32},
+        issue_roofline(roof, INSTR.get((args.config, args.population))),
         {"kernel": "k_update_elite + k_update_mutate_list", "bound": "hbm",
          "achieved_gbs": ub / (stage_serial["update"] / 1e3) / 1e9,
          "frac_of_measured_hbm": ub / (stage_serial["update"] / 1e3) / 1e9 / pk["hbm_gbs"]
@@ -351,6 +352,29 @@ def run_ours(args):
 # step, right after the L2 flush) from an ncu capture of this workload
 # (profiles/k_step_3qubit_bench.md): the reads include the update's L2 prefetch
 TRAFFIC = {(2, None): 41.507e6}
+# warp instructions of one k_step launch (smsp__inst_executed.sum) from the same
+# capture: the circuit kernel at n = 3 is bound by instruction issue, not by
+# the FP32 pipe, so its issue rate is reported beside the arithmetic roofline
+INSTR = {(2, None): 11330413}
+
+
+def issue_roofline(roof, instr):
+    """Issue rate of the circuit kernel: warp instructions per second against
+    152 SMs x 4 schedulers x one warp instruction per cycle at the maximum SM
+    clock (null without a capture of this workload)."""
+    pk = peaks()
+    peak = 152 * 4 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e9  # G warp instructions/s
+    if not instr:
+        return {"kernel": roof["kernel"], "bound": "issue", "achieved_ginst_per_s": None,
+                "peak": peak, "frac": None, "warp_instructions_per_launch": None}
+    ach = instr / (roof["ms"] / 1e3) / 1e9
+    return {"kernel": roof["kernel"], "bound": "issue", "achieved_ginst_per_s": ach,
+            "peak": peak, "unit": "G warp instructions/s", "frac": ach / peak,
+            "warp_instructions_per_launch": instr,
+            "peak_source": "derived: 152 SMs x 4 schedulers x 1 warp instruction/cycle x %.0f MHz"
+                           % pk.get("sm_max_mhz", 2070.0),
+            "instructions_source": "smsp__inst_executed.sum of one launch, ncu capture of this "
+                                   "workload (profiles/k_step_3qubit_bench.md)"}
 
 
 def roofline(dom, ms, flops, searches, pk, traffic=None):
