@@ -389,17 +389,22 @@ __device__ __forceinline__ void dispatch(int op, R (&re)[Lay<NQ>::ROWS], R (&im)
 // kernel keeps a map from wires to physical row bits: before each gate the
 // target wire's bit is exchanged with bit 0 (4 static cases of register moves),
 // then the gate acts on bit 0 with its control at any other bit (CNOT, CV:
-// 4 cases each; H, T: 1 each).  Rows are translated through the map only at
-// the end.  Binary32 arithmetic; the binary64 paths keep the direct switch.
-__device__ __forceinline__ void xchg(float &a, float &b) {
-  const float t = a;
+// 4 cases each; H, T: 1 each).  Binary32 translates rows through the map only
+// at the end.  Binary64 uses the same gate code: every row of a one- or
+// two-wire gate has two nonzero terms, whose sum does not depend on their
+// order, so each row gets the dense product's value wherever it sits; the map
+// is brought back to the identity before the score, which sums in the
+// oracle's row order.
+template <typename R>
+__device__ __forceinline__ void xchg(R &a, R &b) {
+  const R t = a;
   a = b;
   b = t;
 }
 
 // exchange physical row bits 0 and B of the column
-template <int B>
-__device__ __forceinline__ void swap_bit0(float (&re)[32], float (&im)[32]) {
+template <int B, typename R>
+__device__ __forceinline__ void swap_bit0(R (&re)[32], R (&im)[32]) {
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
     if ((r & 1) && !((r >> B) & 1)) {
@@ -410,13 +415,22 @@ __device__ __forceinline__ void swap_bit0(float (&re)[32], float (&im)[32]) {
   }
 }
 
+template <typename R>
+__device__ __forceinline__ void swap_bit0_dyn(int b, R (&re)[32], R (&im)[32]) {
+  switch (b) {
+    case 1: swap_bit0<1>(re, im); break;
+    case 2: swap_bit0<2>(re, im); break;
+    case 3: swap_bit0<3>(re, im); break;
+    default: swap_bit0<4>(re, im); break;
+  }
+}
+
 // gate of kind K on target bit 0, control at bit CB (-1: none); for the
 // interaction template CB is the bit of its other wire.  ic/is: cos/sin of
 // theta/2 (Ising kinds)
-template <int K, int CB>
-__device__ __forceinline__ void gate_bit0(float (&re)[32], float (&im)[32], float s, float ic,
-                                          float is) {
-  using A = Ar<float, false>;
+template <int K, int CB, typename R, bool CANON>
+__device__ __forceinline__ void gate_bit0(R (&re)[32], R (&im)[32], R s, R ic, R is) {
+  using A = Ar<R, CANON>;
   if constexpr (K == kRz || K == kJzz) {
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
@@ -431,7 +445,7 @@ __device__ __forceinline__ void gate_bit0(float (&re)[32], float (&im)[32], floa
     if (K != kRx && K != kRy && CB >= 0 && !((r0 >> CB) & 1)) continue;
     const int r1 = r0 | 1;
     if constexpr (K == kRx || K == kRy) {
-      const float xr = re[r0], xi = im[r0], yr = re[r1], yi = im[r1];
+      const R xr = re[r0], xi = im[r0], yr = re[r1], yi = im[r1];
       if constexpr (K == kRx) {
         A::rx_lane(re[r0], im[r0], yr, yi, ic, is);
         A::rx_lane(re[r1], im[r1], xr, xi, ic, is);
@@ -452,13 +466,22 @@ __device__ __forceinline__ void gate_bit0(float (&re)[32], float (&im)[32], floa
   }
 }
 
+// the wire at physical bit b moves to bit 0 and the wire at bit 0 to bit b
+__device__ __forceinline__ void remap5(int b, uint32_t &pos, uint32_t &inv) {
+  const int w0 = inv & 7, wb = (inv >> (3 * b)) & 7;
+  pos = (pos & ~(7u << (3 * w0))) | ((uint32_t)b << (3 * w0));
+  pos &= ~(7u << (3 * wb));
+  inv = (inv & ~(7u << (3 * b))) | ((uint32_t)w0 << (3 * b));
+  inv = (inv & ~7u) | (uint32_t)wb;
+}
+
 // apply one op: wire bits in pos (3 bits per wire), wire at each bit in inv
-template <bool ISING>
-__device__ __forceinline__ void apply5(int op, uint32_t &pos, uint32_t &inv, float (&re)[32],
-                                       float (&im)[32], float ic, float is) {
+template <bool ISING, typename R, bool CANON>
+__device__ __forceinline__ void apply5(int op, uint32_t &pos, uint32_t &inv, R (&re)[32],
+                                       R (&im)[32], R ic, R is) {
   constexpr int NP2 = 2 * 5 * 4;
   const int o = op & 0x7f;
-  const float s = (op & kOpNeg) ? -1.f : 1.f;
+  const R s = (op & kOpNeg) ? R(-1) : R(1);
   int kind, tw, cw = -1;
   if (ISING && o >= kOpIsingJ) {
     // template on wires (i, j): j goes to bit 0, i is the "control" bit
@@ -485,42 +508,52 @@ __device__ __forceinline__ void apply5(int op, uint32_t &pos, uint32_t &inv, flo
   }
   const int b = (pos >> (3 * tw)) & 7;
   if (b != 0) {
-    switch (b) {
-      case 1: swap_bit0<1>(re, im); break;
-      case 2: swap_bit0<2>(re, im); break;
-      case 3: swap_bit0<3>(re, im); break;
-      default: swap_bit0<4>(re, im); break;
-    }
-    const int w0 = inv & 7;  // wire now at bit 0
-    pos = (pos & ~(7u << (3 * w0))) | ((uint32_t)b << (3 * w0));
-    pos &= ~(7u << (3 * tw));
-    inv = (inv & ~(7u << (3 * b))) | ((uint32_t)w0 << (3 * b));
-    inv = (inv & ~7u) | (uint32_t)tw;
+    swap_bit0_dyn(b, re, im);
+    remap5(b, pos, inv);
   }
   const int cb = cw < 0 ? 0 : (int)((pos >> (3 * cw)) & 7);
   if constexpr (ISING) {
     switch (kind * 5 + cb) {
-      case kRx * 5: gate_bit0<kRx, -1>(re, im, s, ic, is); break;
-      case kRy * 5: gate_bit0<kRy, -1>(re, im, s, ic, is); break;
-      case kRz * 5: gate_bit0<kRz, -1>(re, im, s, ic, is); break;
-      case kJzz * 5 + 1: gate_bit0<kJzz, 1>(re, im, s, ic, is); break;
-      case kJzz * 5 + 2: gate_bit0<kJzz, 2>(re, im, s, ic, is); break;
-      case kJzz * 5 + 3: gate_bit0<kJzz, 3>(re, im, s, ic, is); break;
-      default: gate_bit0<kJzz, 4>(re, im, s, ic, is); break;
+      case kRx * 5: gate_bit0<kRx, -1, R, CANON>(re, im, s, ic, is); break;
+      case kRy * 5: gate_bit0<kRy, -1, R, CANON>(re, im, s, ic, is); break;
+      case kRz * 5: gate_bit0<kRz, -1, R, CANON>(re, im, s, ic, is); break;
+      case kJzz * 5 + 1: gate_bit0<kJzz, 1, R, CANON>(re, im, s, ic, is); break;
+      case kJzz * 5 + 2: gate_bit0<kJzz, 2, R, CANON>(re, im, s, ic, is); break;
+      case kJzz * 5 + 3: gate_bit0<kJzz, 3, R, CANON>(re, im, s, ic, is); break;
+      default: gate_bit0<kJzz, 4, R, CANON>(re, im, s, ic, is); break;
     }
     return;
   }
   switch (kind * 5 + cb) {
-    case kCnot * 5 + 1: gate_bit0<kCnot, 1>(re, im, s, ic, is); break;
-    case kCnot * 5 + 2: gate_bit0<kCnot, 2>(re, im, s, ic, is); break;
-    case kCnot * 5 + 3: gate_bit0<kCnot, 3>(re, im, s, ic, is); break;
-    case kCnot * 5 + 4: gate_bit0<kCnot, 4>(re, im, s, ic, is); break;
-    case kCvx * 5 + 1: gate_bit0<kCvx, 1>(re, im, s, ic, is); break;
-    case kCvx * 5 + 2: gate_bit0<kCvx, 2>(re, im, s, ic, is); break;
-    case kCvx * 5 + 3: gate_bit0<kCvx, 3>(re, im, s, ic, is); break;
-    case kCvx * 5 + 4: gate_bit0<kCvx, 4>(re, im, s, ic, is); break;
-    case kHad * 5: gate_bit0<kHad, -1>(re, im, s, ic, is); break;
-    default: gate_bit0<kTx, -1>(re, im, s, ic, is); break;
+    case kCnot * 5 + 1: gate_bit0<kCnot, 1, R, CANON>(re, im, s, ic, is); break;
+    case kCnot * 5 + 2: gate_bit0<kCnot, 2, R, CANON>(re, im, s, ic, is); break;
+    case kCnot * 5 + 3: gate_bit0<kCnot, 3, R, CANON>(re, im, s, ic, is); break;
+    case kCnot * 5 + 4: gate_bit0<kCnot, 4, R, CANON>(re, im, s, ic, is); break;
+    case kCvx * 5 + 1: gate_bit0<kCvx, 1, R, CANON>(re, im, s, ic, is); break;
+    case kCvx * 5 + 2: gate_bit0<kCvx, 2, R, CANON>(re, im, s, ic, is); break;
+    case kCvx * 5 + 3: gate_bit0<kCvx, 3, R, CANON>(re, im, s, ic, is); break;
+    case kCvx * 5 + 4: gate_bit0<kCvx, 4, R, CANON>(re, im, s, ic, is); break;
+    case kHad * 5: gate_bit0<kHad, -1, R, CANON>(re, im, s, ic, is); break;
+    default: gate_bit0<kTx, -1, R, CANON>(re, im, s, ic, is); break;
+  }
+}
+
+// bring the map back to the identity (wire w at physical bit 4 - w) by
+// exchanges of bit 0 with another bit: each exchange sends the wire at bit 0
+// home, or, when it is home, brings a misplaced wire to bit 0 (at most 8)
+template <typename R>
+__device__ __forceinline__ void restore5(uint32_t &pos, uint32_t &inv, R (&re)[32],
+                                         R (&im)[32]) {
+  for (int it = 0; it < 8; ++it) {
+    const int w0 = inv & 7;
+    int b = 4 - w0;  // the home bit of the wire at bit 0
+    if (b == 0) {
+      for (int c = 4; c >= 1; --c)
+        if ((int)((inv >> (3 * c)) & 7) != 4 - c) b = c;
+      if (b == 0) return;  // every wire is home
+    }
+    swap_bit0_dyn(b, re, im);
+    remap5(b, pos, inv);
   }
 }
 
@@ -690,11 +723,13 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
   const uint32_t cost = __reduce_add_sync(kFull, (ops0 != kOpIdentity) + (ops1 != kOpIdentity));
   const uint32_t work = __reduce_add_sync(kFull, op_work(p, (int)ops0) + op_work(p, (int)ops1));
   const uint32_t L = p.L;
-  // 5-qubit binary32: wire w starts at physical bit 4 - w (pos), bit b holds
-  // wire 4 - b (inv); both stay the identity map elsewhere
+  // 5 qubits: wire w starts at physical bit 4 - w (pos), bit b holds wire
+  // 4 - b (inv); binary32 translates rows through the map at the output,
+  // binary64 restores the identity map after the last gate
+  constexpr bool kMap5 = NQ == 5;
   constexpr bool kMapped = NQ == 5 && !CANON;
   uint32_t pos = 0, inv = 0;
-  if constexpr (kMapped) {
+  if constexpr (kMap5) {
 #pragma unroll
     for (int w = 0; w < 5; ++w) {
       pos |= (uint32_t)(4 - w) << (3 * w);
@@ -710,13 +745,14 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
       ic = __shfl_sync(kFull, t < 32 ? ic0 : ic1, (int)(t & 31));
       is = __shfl_sync(kFull, t < 32 ? is0 : is1, (int)(t & 31));
     }
-    if constexpr (kMapped) {
-      apply5<ISING>(op, pos, inv, re, im, ic, is);
+    if constexpr (kMap5) {
+      apply5<ISING, R, CANON>(op, pos, inv, re, im, ic, is);
     } else {
       const R s = (op & kOpNeg) ? R(-1) : R(1);
       dispatch<NQ, R, CANON, ISING>(op & 0x7f, re, im, lane, s, ic, is);
     }
   }
+  if constexpr (kMap5 && !kMapped) restore5(pos, inv, re, im);
   CircuitOut out;
   out.cost = cost;
   out.work = work + 2u * N;
