@@ -535,21 +535,29 @@ def _fp32_error(qe, torch, ctx32, searches, n_unitary=256):
     from paper_1809_11134_gb300 import workloads as W
     s64 = [W.Search(**{**s.__dict__, "precision": W.PREC_FP64}) for s in searches]
     ctx64 = qe.Context(s64)
-    f_err, u_err = 0.0, 0.0
+    f_err, u_err, bad = 0.0, 0.0, 0
     for r, s in enumerate(searches):
         last = ctx32.last_generation(r)
         g = torch.from_numpy(np.ascontiguousarray(last["gate_idx"])).cuda()
         f64 = torch.zeros(s.P, dtype=torch.float64, device="cuda")
-        ctx64.eval(r, g, f64)
-        f_err = max(f_err, float(np.abs(last["fitness"] - f64.cpu().numpy()).max()))
         m = min(n_unitary, s.P)
         N = 1 << s.n
         u32 = torch.zeros(m * N * N * 2, dtype=torch.float32, device="cuda")
         u64 = torch.zeros(m * N * N * 2, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()  # the buffers are filled before either context's stream runs
+        ctx64.eval(r, g, f64)
         ctx32.compose(r, g[:m], u32, n_circuits=m)
         ctx64.compose(r, g[:m], u64, n_circuits=m)
-        u_err = max(u_err, float((u32.double() - u64).abs().max().item()))
+        torch.cuda.synchronize()
+        df = np.abs(last["fitness"] - f64.cpu().numpy())
+        du = (u32.double() - u64).abs().cpu().numpy()
+        # a NaN would make max() skip it: count non-finite differences instead
+        bad += int((~np.isfinite(df)).sum() + (~np.isfinite(du)).sum())
+        f_err = max(f_err, float(np.nanmax(df)) if df.size else 0.0)
+        u_err = max(u_err, float(np.nanmax(du)) if du.size else 0.0)
     ctx64.close()
+    if bad:
+        raise RuntimeError("%d non-finite binary32/binary64 differences" % bad)
     return f_err, u_err
 
 
