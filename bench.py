@@ -566,8 +566,10 @@ def per_config(qe, torch, args):
     and generation rate, binary32 vs plain binary64, from the events inside the
     generation graph, with the binary32 path's largest error against binary64;
     the 1024 uneven searches (binary32); the GA run of the 5-qubit search on
-    the same evaluation; and the 3- and 5-qubit shapes on the paper's Ising gate
-    set (context next to the headline)."""
+    the same evaluation; the 3- and 5-qubit shapes on the paper's Ising gate
+    set; and the 3-qubit set with repeated measurement and with dense targets
+    (context next to the headline)."""
+    import numpy as np
     from paper_1809_11134_gb300 import workloads as W
     out = {}
     for cfg, gens32, gens64 in ((2, 20, 5), (3, 6, 2), (5, 4, 1)):
@@ -607,6 +609,25 @@ def per_config(qe, torch, args):
             res["fp32_over_fp64_generation"] = (res["fp32"]["generation_circuits_per_s"] /
                                                 res["fp64"]["generation_circuits_per_s"])
         out["config%d_ising" % cfg] = res
+    # the 3-qubit set with each slot's qutrit measured 8 times (majority outcome),
+    # and against dense targets (the permutations as full complex matrices, so
+    # the score is tr(S^dag T) over all N^2 entries)
+    searches = W.config(2)
+    for s in searches:
+        s.shots = 8
+    ctx, r = _stage_rates(qe, torch, searches, 10)
+    ctx.close()
+    out["config2_shots8"] = {"fp32": r}
+    searches = W.config(2)
+    for s in searches:
+        N = 1 << s.n
+        T = np.zeros((N, N), np.complex128)
+        for j in range(N):
+            T[s.perm[j], j] = 1.0
+        s.target = T
+    ctx, r = _stage_rates(qe, torch, searches, 10)
+    ctx.close()
+    out["config2_dense"] = {"fp32": r}
     return out
 
 
