@@ -8,8 +8,9 @@
 //   top-k; the candidates {F_hi >= tau} are rescored in binary64 (k_rescore in
 //   k_circuit.cu) and sorted by (F desc, cost asc, index asc).  Binary64
 //   searches use the degenerate band F_lo = F_hi = F.
-// One CTA per search does the selection (3-pass radix select over the top 24
-// bits of the F_lo keys) and, in a second launch, the sort (bitonic, in chunks
+// One CTA per search does the selection (radix select over the top 24 bits of
+// the F_lo keys, two 4096-bin histogram passes) and, in a second launch, the
+// sort (bitonic, in chunks
 // of up to 2048 so any number of candidates fits in shared memory).
 #include "qe_dev.cuh"
 #include "qe_host.h"
