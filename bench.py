@@ -281,7 +281,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel: the circuit kernel (sample +
     # compose + score + scatter), the largest kernel of a generation in the ncu
-    # launch list (profiles/launches_3qubit_bench.md); its time is the event
+    # launch list of this workload (summarised under profiles/); its time is the event
     # interval around it in the serialised generation graph
     pk = peaks()
     alu32, alu64 = qe.measure_alu_peaks()
@@ -350,7 +350,7 @@ def run_ours(args):
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_step launch (a timed
 # step, right after the L2 flush) from an ncu capture of this workload
-# (profiles/k_step_3qubit_bench.md): the reads include the update's L2 prefetch
+# (summarised under profiles/): the reads include the update's L2 prefetch
 TRAFFIC = {(2, None): 41.507e6}
 # warp instructions of one k_step launch (smsp__inst_executed.sum) from the same
 # capture: the circuit kernel at n = 3 is bound by instruction issue, not by
@@ -374,7 +374,7 @@ def issue_roofline(roof, instr):
             "peak_source": "derived: 152 SMs x 4 schedulers x 1 warp instruction/cycle x %.0f MHz"
                            % pk.get("sm_max_mhz", 2070.0),
             "instructions_source": "smsp__inst_executed.sum of one launch, ncu capture of this "
-                                   "workload (profiles/k_step_3qubit_bench.md)"}
+                                   "workload (k_step summary under profiles/)"}
 
 
 def roofline(dom, ms, flops, searches, pk, traffic=None):
