@@ -167,3 +167,43 @@ def test_batch_between_generations_leaves_the_run_unchanged(qe):
             for (q, g), f, t in zip(items, fits, tops):
                 check_item(ss[q], g, f, t)
         assert a.step(1) == b.step(1)
+
+
+def test_batch_pinned_buffers_match_pageable(qe):
+    """pinned (page-locked) gate and fitness buffers give the same results as
+    pageable ones, over repeated calls, new contents, other pinned buffers and
+    a switch back"""
+    import ctypes as C
+    import torch
+    ss = searches(W.PREC_FP32)
+    rng = np.random.default_rng(21)
+    plan = [(0, 1000), (1, 300), (3, 33)]
+    probs = (C.c_uint32 * len(plan))(*[q for q, _ in plan])
+    counts = (C.c_uint32 * len(plan))(*[n for _, n in plan])
+    ks = [min(max(ss[q].topk, 1), n) for q, n in plan]
+    n_tot = sum(n for _, n in plan)
+
+    def pinned_call(ctx, items, hg, hf):
+        flat = np.concatenate([g.ravel() for _, g in items])
+        hg[:flat.size].copy_(torch.from_numpy(flat))
+        tops = (qe.qe_ranked * sum(ks))()
+        ctx.eval_host_batch_ptr(probs, counts, hg.data_ptr(), hf.data_ptr(), tops)
+        fits, out, fo, ko = [], [], 0, 0
+        for (q, n), k in zip(plan, ks):
+            fits.append(hf[fo:fo + n].numpy().copy())
+            out.append([(t.circuit, t.cost, t.fitness) for t in tops[ko:ko + k]])
+            fo += n
+            ko += k
+        return fits, out
+
+    with qe.Context(ss) as ctx:
+        bufs = [(torch.zeros(sum(n * ss[q].L for q, n in plan), dtype=torch.uint8).pin_memory(),
+                 torch.zeros(n_tot, dtype=torch.float32).pin_memory()) for _ in range(2)]
+        for hg, hf in (bufs[0], bufs[0], bufs[1], bufs[0]):
+            items = [(q, gates_for(ss[q], n, rng)) for q, n in plan]
+            fits, tops = pinned_call(ctx, items, hg, hf)
+            fits2, tops2 = ctx.eval_host_batch(items, topk=True)  # pageable
+            for (q, g), f, t, f2, t2 in zip(items, fits, tops, fits2, tops2):
+                assert np.array_equal(f.view(np.uint8), f2.view(np.uint8))
+                assert t == t2
+                check_item(ss[q], g, f, t)
