@@ -1,0 +1,52 @@
+"""bench.py's host arithmetic without a GPU: the roofline records of the
+circuit kernel (useful flops against the derived FP32 peak, warp instructions
+against the derived issue peak), the update's algorithmic bytes, and the
+launches counted per generation."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1809_11134_gb300 import workloads as W  # noqa: E402
+
+
+def test_circuit_roofline_and_issue_rate():
+    searches = W.config(2)
+    pk = {"hbm_gbs": 6802.0, "sm_max_mhz": 2070.0}
+    roof = bench.roofline("circuits", 0.025, 13.5e6, searches, pk, traffic=41.5e6)
+    peak = 152 * 128 * 2 * 2070e6 / 1e12
+    assert roof["bound"] == "alu" and roof["unit"] == "TFLOP/s"
+    assert abs(roof["peak"] - peak) < 1e-9
+    assert abs(roof["achieved"] - 13.5e6 / 25e-6 / 1e12) < 1e-12
+    assert abs(roof["frac"] - roof["achieved"] / peak) < 1e-12
+    assert roof["traffic"] == 41.5e6
+    iss = bench.issue_roofline(roof, 11330413)
+    assert abs(iss["peak"] - 152 * 4 * 2.07) < 1e-9
+    assert abs(iss["achieved_ginst_per_s"] - 11330413 / 25e-6 / 1e9) < 1e-6
+    assert 0 < iss["frac"] < 1
+    assert bench.issue_roofline(roof, None)["frac"] is None
+
+
+def test_update_bytes_counts_slots_segments_and_mutations():
+    s = W.Search(3, 4, 8, W.LIB_NCV | W.LIB_HT, W.cknot(3), p_mutation=0.5)
+    sid = np.arange(32, dtype=np.uint32).reshape(8, 4)
+    sid[1, 0] = sid[0, 0]  # one segment used by two slots
+    R = 3 * 2 + 3
+    got = bench.update_bytes([s], [{"seg_id": sid}])
+    want = 32 * 8 + 31 * (32 + 32 + 4) + 0.5 * 8 * R * 4 * (32 + 32 + 4 + 4)
+    assert got == want
+
+
+def test_launches_per_generation():
+    # one circuit kernel group, two update roles, selection, one rescoring
+    # width, sort, finish
+    assert bench.launches_per_generation(W.config(2)) == 7
+    # three widths and one binary64 group: four circuit kernels, three rescoring widths
+    mixed = W.config(4)[:40] + [W.Search(3, 5, 64, W.LIB_NCV, W.cknot(3), precision=W.PREC_FP64)]
+    widths = len(set(s.n for s in mixed if s.precision != W.PREC_FP64))
+    groups = len(set((s.n, s.precision == W.PREC_FP64) for s in mixed))
+    assert bench.launches_per_generation(mixed) == groups + 2 + 1 + widths + 1 + 1
