@@ -5,7 +5,8 @@
 //  role A (k_update_elite), one thread per (circuit, slot): if the segment's
 //    individual is not mutated this generation, the first thread to take the
 //    segment's fitness key (a 64-bit atomicAnd that clears it) applies
-//    elitism to it;
+//    elitism to it; from 2^20 slots k_update_elite4 does the same with four
+//    lanes per slot, each moving a quarter of the segment's 64-B line;
 //  role B, for each segment of an individual that mutates: elitism where the
 //    segment was used, then mutation.  Inside the generation graph
 //    (k_update_mutate_list) one thread per segment of the individuals the
