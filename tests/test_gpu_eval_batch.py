@@ -207,3 +207,25 @@ def test_batch_pinned_buffers_match_pageable(qe):
                 assert np.array_equal(f.view(np.uint8), f2.view(np.uint8))
                 assert t == t2
                 check_item(ss[q], g, f, t)
+
+
+@pytest.mark.parametrize("prec", [W.PREC_FP32, W.PREC_FP64])
+def test_batch_with_dense_targets_and_shots(qe, prec):
+    """searches against dense target unitaries (Eq. (11) with a general T) and
+    a search measured K times share a batch with permutation searches; the
+    evaluation of given circuits does not depend on K"""
+    from test_gpu_dense import near_target
+    rng = np.random.default_rng(31 + prec)
+    lib = NCV | HT
+    ss = [W.Search(3, 16, 500, lib, W.cknot(3), seed=1, precision=prec, topk=8,
+                   target=near_target(rng, 3, lib, 6)),
+          W.Search(4, 20, 300, lib, W.cknot(4), seed=2, precision=prec, topk=16),
+          W.Search(5, 33, 120, lib, W.cknot(5), seed=3, precision=prec, topk=4,
+                   target=near_target(rng, 5, lib, 8)),
+          W.Search(3, 12, 256, lib | ID, W.peres(), seed=4, precision=prec, topk=8, shots=5)]
+    plan = [(2, 120), (0, 499), (3, 256), (1, 300)]
+    items = [(q, gates_for(ss[q], n, rng)) for q, n in plan]
+    with qe.Context(ss) as ctx:
+        fits, tops = ctx.eval_host_batch(items, topk=True)
+        for (q, g), f, t in zip(items, fits, tops):
+            check_item(ss[q], g, f, t)
