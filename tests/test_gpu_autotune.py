@@ -80,10 +80,15 @@ def test_stage_timing_leaves_the_trajectory_unchanged(qe, torch, mode):
     """stage timing (events inside the graph, mode 1; every kernel serialised on
     one stream, mode 2) changes only when the kernels run: the run follows the
     untimed trajectory bit for bit, and every stage interval is positive"""
+    T = np.eye(8, dtype=np.complex128)[[1, 0, 2, 3, 4, 5, 7, 6]]  # a dense target
     searches = (W.config(2, P=300)
                 + [W.Search(4, 9, 333, W.LIB_NCV | W.LIB_HT, W.cknot(4), seed=4, topk=5),
                    W.Search(3, 30, 64, W.LIB_NCV | W.LIB_HT | W.LIB_IDENTITY, W.cknot(3),
-                            seed=5, encoding=W.ENC_GA)])
+                            seed=5, encoding=W.ENC_GA),
+                   W.Search(3, 10, 128, W.LIB_NCV | W.LIB_HT, W.cknot(3), seed=6, topk=4,
+                            shots=6),
+                   W.Search(3, 11, 96, W.LIB_NCV | W.LIB_HT, W.cknot(3), seed=7, topk=3,
+                            target=T)])
     gens = 4
     with qe.Context(searches) as a, qe.Context(searches) as b:
         a.stage_timing(True, serial=(mode == 2))

@@ -229,3 +229,18 @@ def test_batch_with_dense_targets_and_shots(qe, prec):
         fits, tops = ctx.eval_host_batch(items, topk=True)
         for (q, g), f, t in zip(items, fits, tops):
             check_item(ss[q], g, f, t)
+
+
+def test_batch_benchmark_workload_full_size(qe):
+    """the end-to-end workload bench.py times: one call with all three 3-qubit
+    searches of the benchmark set at P = 4096, every circuit against the
+    oracle, twice in a row (the second call replays the captured graph)"""
+    ss = W.config(2)
+    rng = np.random.default_rng(2)
+    with qe.Context(ss) as ctx:
+        for _ in range(2):
+            items = [(q, gates_for(s, s.P, rng)) for q, s in enumerate(ss)]
+            fits, tops = ctx.eval_host_batch(items, topk=True)
+            for (q, g), f, t in zip(items, fits, tops):
+                assert len(f) == 4096 and len(t) == 32
+                check_item(ss[q], g, f, t)
