@@ -140,16 +140,27 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *
   // histogram of the top 12 bits of the low keys, the mean and the work.
   // Histogram updates are aggregated per warp (__match_any_sync): fitness
   // values are often discrete, and many lanes hit the same bin.
-  double sum = 0.0;  // mean fitness: binary64 sum of the working-precision values
+  // Mean fitness: binary64 searches sum in binary64; binary32 searches sum in
+  // binary32 within each warp and in binary64 across warps, so that their
+  // selection issues almost no binary64 instruction (GB300's binary64 pipe is
+  // thin, and this kernel runs on one SM per search).
+  double sum = 0.0;
+  float sum32 = 0.f;
   unsigned long long work = 0;
   for (uint32_t c0 = 0; c0 < n; c0 += kRankThreads) {
     const uint32_t c = c0 + tid;
     uint32_t bin = 4096u;
     if (c < n) {
-      const double Fw = p.prec == 0 ? ((const double *)jb.fit)[c] : (double)((const float *)jb.fit)[c];
-      const float F = (float)Fw;
+      float F;
+      if (p.prec == 0) {
+        const double Fw = ((const double *)jb.fit)[c];
+        F = (float)Fw;
+        sum += Fw;
+      } else {
+        F = ((const float *)jb.fit)[c];
+        sum32 += F;
+      }
       const uint32_t meta = jb.meta[c];
-      sum += Fw;
       work += meta >> 8;
       uint32_t lo, hi;
       bounds(p, jb, c, F, lo, hi);
@@ -163,11 +174,16 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *
     if (bin < 4096u && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
   }
   if (jb.update_record) {
+    if (p.prec == 0) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sum += __shfl_xor_sync(kFull, sum, o);
-      work += __shfl_xor_sync(kFull, work, o);
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+    } else {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum32 += __shfl_xor_sync(kFull, sum32, o);
+      sum = (double)sum32;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) work += __shfl_xor_sync(kFull, work, o);
     if (lane == 0) {
       s_sum[wid] = sum;
       s_work[wid] = work;
