@@ -40,6 +40,9 @@ def gates_for(s, n, rng):
 
 
 def check_item(s, g, fit, top):
+    if len(g) == 0:
+        assert len(fit) == 0 and (top is None or top == [])
+        return
     F, C = oracle.eval_circuits(oracle_problem(s, 0), g)
     if s.precision == W.PREC_FP64:
         assert np.array_equal(fit, F)
@@ -244,3 +247,28 @@ def test_batch_benchmark_workload_full_size(qe):
             for (q, g), f, t in zip(items, fits, tops):
                 assert len(f) == 4096 and len(t) == 32
                 check_item(ss[q], g, f, t)
+
+
+@pytest.mark.parametrize("prec", [W.PREC_FP32, W.PREC_FP64])
+def test_batch_many_searches_of_every_width(qe, prec):
+    """64 small searches of 1 to 5 qubits (shadow lanes at 1 and 2 qubits,
+    every rescoring width, ragged populations and top-k sizes) in one batch,
+    items in a shuffled order, every circuit against the oracle"""
+    rng = np.random.default_rng(64 + prec)
+    ss, plan = [], []
+    for q in range(64):
+        n = 1 + q % 5
+        lib = HT if n == 1 else ((NCV | HT) if q % 3 else (NCV | ID))
+        L = int(rng.integers(1, 40))
+        P = int(rng.integers(1, 200))
+        perm = [int(v) for v in rng.permutation(1 << n)]
+        ss.append(W.Search(n, L, P, lib, perm, seed=q, precision=prec,
+                           topk=int(rng.integers(0, min(12, P) + 1))))
+        plan.append((q, int(rng.integers(0, P + 1))))
+    order = rng.permutation(64)
+    items = [(plan[i][0], gates_for(ss[plan[i][0]], plan[i][1], rng)) for i in order]
+    with qe.Context(ss) as ctx:
+        fits, tops = ctx.eval_host_batch(items, topk=True)
+        for (q, g), f, t in zip(items, fits, tops):
+            assert len(f) == len(g)
+            check_item(ss[q], g, f, t)
