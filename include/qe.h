@@ -393,10 +393,17 @@ qe_status qe_generation(const qe_ctx *ctx, uint32_t *gen);
  * and calls that overlap on the GPU -- on different streams, or from
  * different threads -- race on that scratch.  The first call on a device
  * looks up the array's device address and launch shapes, so make that first
- * call before any stream capture.  It calls no cudaMalloc, cudaFree or other
+ * call before any stream capture; under lazy module loading (the CUDA default
+ * since 12.2) it also loads the library's code for that device, and the
+ * driver allocates the array then, so make the first call while allocation
+ * is still allowed.  Calls after it call no cudaMalloc, cudaFree or other
  * allocating routine.  Errors are returned as a status with a message written
- * to h_msg (msg_len bytes, may be NULL); invalid gate indices give NaN
- * fitness.  QE_PREC_SPLIT_TC is QE_EUNSUPPORTED. */
+ * to h_msg (msg_len bytes, may be NULL); the first N entries of
+ * prob->target_perm (held in the struct) must be a permutation of 0..N-1
+ * (QE_EINVAL otherwise).  An invalid gate index gives that
+ * circuit a NaN fitness and leaves d_topk unspecified (the call does not
+ * synchronise, so it cannot report it): pass valid indices, or check
+ * d_fitness.  QE_PREC_SPLIT_TC is QE_EUNSUPPORTED. */
 qe_status qe_eval_rank_static(const qe_problem *prob, const uint8_t *d_gate_idx,
                               uint32_t n_circuits, void *d_fitness, qe_ranked *d_topk,
                               void *cuda_stream, char *h_msg, size_t msg_len);

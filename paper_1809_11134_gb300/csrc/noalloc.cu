@@ -13,7 +13,10 @@
 //
 // Host code never passes the array's name to a kernel (on the host that name
 // is only a stand-in, not a device address); the first call on each device
-// looks up the device address with cudaGetSymbolAddress and caches it.
+// looks up the device address with cudaGetSymbolAddress and caches it.  Under
+// lazy module loading (CUDA_MODULE_LOADING=LAZY, the default since CUDA 12.2)
+// that first call is also what loads this file's module, and the driver then
+// allocates the array and the code; calls after it allocate nothing.
 #include <cuda_runtime.h>
 
 #include <cmath>

@@ -470,8 +470,15 @@ def qe_eval_rank_static(search, gate_idx, fitness, topk=None, n_circuits=None, s
     For callers that may not allocate while it runs, every buffer must exist
     beforehand; see include/qe.h for the limits and the race between
     overlapping calls."""
+    import torch
     p = to_problem(search)
     n = gate_idx.shape[0] if n_circuits is None else n_circuits
+    if n > 0:
+        _need(gate_idx, torch.uint8, n * p.circuit_len, "gate_idx")
+        _need(fitness, torch.float64 if p.precision == QE_PREC_FP64 else torch.float32, n,
+              "fitness")
+        if topk is not None:
+            _need(topk, torch.uint8, 16 * min(max(p.topk, 1), n), "topk")
     msg = C.create_string_buffer(256)
     st = lib().qe_eval_rank_static(C.byref(p), _ptr(gate_idx), n, _ptr(fitness), _ptr(topk),
                                    _stream_handle(stream), msg, 256)

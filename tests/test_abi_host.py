@@ -135,3 +135,22 @@ def test_ising_library_geometry_and_acceptance(qe, monkeypatch):
     s = W.Search(3, 8, 64, W.LIB_ISING | W.LIB_NCV, W.cknot(3), encoding=W.ENC_GA)
     probs = (qe.qe_problem * 1)(qe.to_problem(s))
     assert qe.lib().qe_init(C.byref(C.c_void_p()), probs, 1, None) == qe.QE_EINVAL
+
+
+def test_static_entry_rejects_bad_arguments_without_a_gpu(qe):
+    """qe_eval_rank_static checks its problem on the host before any CUDA call:
+    a NULL problem, a target that is not a permutation and an oversized batch
+    are QE_EINVAL with a message."""
+    s = W.Search(3, 8, 64, W.LIB_NCV | W.LIB_HT, W.cknot(3), precision=W.PREC_FP32)
+    L = qe.lib()
+    msg = C.create_string_buffer(256)
+    assert L.qe_eval_rank_static(None, None, 16, None, None, None, msg, 256) == qe.QE_EINVAL
+    assert msg.value
+    s.perm = [0, 0, 1, 2, 3, 4, 5, 6]
+    p = qe.to_problem(s)
+    assert L.qe_eval_rank_static(C.byref(p), None, 16, None, None, None, msg, 256) == qe.QE_EINVAL
+    assert b"permutation" in msg.value
+    s.perm = W.cknot(3)
+    p = qe.to_problem(s)
+    assert L.qe_eval_rank_static(C.byref(p), None, 65537, None, None, None, msg, 256) == qe.QE_EINVAL
+    assert b"65536" in msg.value
