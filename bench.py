@@ -234,6 +234,10 @@ def run_ours(args):
     # launch plan picked by timing real generations (results do not depend on it)
     tune_ms = ctx.autotune(3)
     plan = ctx.launch_plan()
+    # the clock sampler starts before the warm-up, so that its own start-up
+    # (nvidia-smi initialising NVML) does not fall into the timed region
+    clk = ClockSampler(local).__enter__()
+    time.sleep(0.5)
     for _ in range(args.warmup):
         ctx.step(1)
     # ---- timed region: K generations, L2 flushed before each
@@ -242,17 +246,25 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            do_flush()
-            starts[k].record(stream)
-            ctx.step_raw(1, None)
-            ends[k].record(stream)
-        stream.synchronize()
-        wall = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        do_flush()
+        starts[k].record(stream)
+        ctx.step_raw(1, None)
+        ends[k].record(stream)
+    stream.synchronize()
+    wall = time.perf_counter() - t0
     torch.cuda.synchronize()
+    clk.__exit__(None, None, None)
     step_ms = [starts[k].elapsed_time(ends[k]) for k in range(args.steps)]
+    # host-driven rate: the same generations back to back, as a caller drives
+    # them (no flush, no events), timed by the host clock
+    stream.synchronize()
+    h0 = time.perf_counter()
+    for k in range(args.steps):
+        ctx.step_raw(1, None)
+    stream.synchronize()
+    host_wall = time.perf_counter() - h0
     total_ms = max_over_ranks(sum(step_ms), ws, "cuda")
     if ws > 1:
         dist.barrier()
@@ -337,6 +349,10 @@ def run_ours(args):
             "gpu_launches": launches_per_generation(searches) * args.steps,
             "clocks": clocks,
             "wall_s": wall,
+            "host_driven": {"generations": args.steps, "wall_s": host_wall,
+                            "circuits_per_s": n_circ * args.steps / host_wall,
+                            "how": "generations launched back to back by the host (no L2 "
+                                   "flush, no events), host clock around them"},
         }
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

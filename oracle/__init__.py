@@ -4,6 +4,7 @@ Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
 reference legs import this package.  It never imports the CUDA library and
 the CUDA library never imports it.  Arrays are numpy, on the host.
 """
+import contextlib
 import ctypes as C
 import os
 
@@ -44,61 +45,81 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        L.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
-        L.oracle_num_gates.argtypes = [C.c_uint32, C.c_uint32]
-        L.oracle_num_gates.restype = C.c_uint32
-        L.oracle_num_regions.argtypes = [C.c_uint32, C.c_uint32]
-        L.oracle_num_regions.restype = C.c_uint32
-        L.oracle_gate_desc.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_int),
-                                       C.POINTER(C.c_int), C.POINTER(C.c_int)]
-        L.oracle_gate_desc.restype = C.c_int
-        L.oracle_region_gate.argtypes = [C.c_uint32] * 4
-        L.oracle_region_gate.restype = C.c_uint32
-        L.oracle_segment_index.argtypes = [C.c_uint64] * 5
-        L.oracle_segment_index.restype = C.c_uint64
-        L.oracle_num_segments.argtypes = [C.POINTER(Problem)]
-        L.oracle_num_segments.restype = C.c_uint64
-        L.oracle_gate_matrix.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _f64p, _f64p]
-        L.oracle_half_angle.argtypes = [C.c_float, C.c_float, C.POINTER(C.c_double),
-                                        C.POINTER(C.c_double)]
-        L.oracle_gate_matrix_amp.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_float,
-                                             C.c_float, _f64p, _f64p]
-        L.oracle_compose_amp.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p, _f32p, _f64p,
-                                         _f64p]
-        L.oracle_eval_amp.argtypes = [C.POINTER(Problem), _u8p, _f32p, C.c_uint32, _f64p, _u32p]
-        L.oracle_sample_amp.argtypes = [C.POINTER(Problem), _f32p, C.c_uint32, _u8p, _u32p,
-                                        _f32p]
-        L.oracle_compose.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p, _f64p, _f64p]
-        L.oracle_score.argtypes = [C.c_uint32, _f64p, _f64p, _u8p, C.c_uint32]
-        L.oracle_score_dense.argtypes = [C.c_uint32, _f64p, _f64p, _f64p]
-        L.oracle_score_dense.restype = C.c_double
-        L.oracle_score.restype = C.c_double
-        L.oracle_cost.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p]
-        L.oracle_cost.restype = C.c_uint32
-        L.oracle_eval.argtypes = [C.POINTER(Problem), _u8p, C.c_uint32, _f64p, _u32p]
-        L.oracle_useful_flops.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p]
-        L.oracle_useful_flops.restype = C.c_uint64
-        L.oracle_init_state.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f32p]
-        L.oracle_sample.argtypes = [C.POINTER(Problem), _f32p, C.c_uint32, _u8p, _u32p]
-        L.oracle_update.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f32p, C.c_uint32, _u32p,
-                                    _f64p]
-        L.oracle_su3.argtypes = [_f64p, _f64p, _f64p, _f64p]
-        L.oracle_su3_f32.argtypes = [_f32p, _f32p, _f32p, _f32p]
-        L.oracle_su3_angles.argtypes = [_f64p, _f64p, _f64p]
-        L.oracle_topk.argtypes = [_f64p, _u32p, C.c_uint32, C.c_uint32, _u32p]
-        L.oracle_step.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f32p, C.c_uint32,
-                                  C.c_uint32, _u8p, _u32p, _f64p, _u32p, _u32p,
-                                  C.POINTER(Report)]
-        L.oracle_ga_init.argtypes = [C.POINTER(Problem), C.c_uint32, _u8p]
-        L.oracle_ga_init_amp.argtypes = [C.POINTER(Problem), C.c_uint32, _u8p, _f32p]
-        L.oracle_ga_next_amp.argtypes = [C.POINTER(Problem), C.c_uint32, C.c_uint32, C.c_double,
-                                         _u8p, _f32p, _f64p, _u32p, _u8p, _f32p]
-        L.oracle_ga_next.argtypes = [C.POINTER(Problem), C.c_uint32, C.c_uint32, C.c_double,
-                                     _u8p, _f64p, _u32p, _u8p]
-        _lib = L
+        _lib = _configure(C.CDLL(_build.build()))
     return _lib
+
+
+def load(path):
+    """A handle of an oracle library built from another copy of the source
+    (tests plant a mistake in a copy to check that the pins catch it)."""
+    return _configure(C.CDLL(path))
+
+
+@contextlib.contextmanager
+def using(handle):
+    """Route every function of this module through `handle` inside the block."""
+    global _lib
+    saved = lib()
+    _lib = handle
+    try:
+        yield handle
+    finally:
+        _lib = saved
+
+
+def _configure(L):
+    L.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+    L.oracle_num_gates.argtypes = [C.c_uint32, C.c_uint32]
+    L.oracle_num_gates.restype = C.c_uint32
+    L.oracle_num_regions.argtypes = [C.c_uint32, C.c_uint32]
+    L.oracle_num_regions.restype = C.c_uint32
+    L.oracle_gate_desc.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.oracle_gate_desc.restype = C.c_int
+    L.oracle_region_gate.argtypes = [C.c_uint32] * 4
+    L.oracle_region_gate.restype = C.c_uint32
+    L.oracle_segment_index.argtypes = [C.c_uint64] * 5
+    L.oracle_segment_index.restype = C.c_uint64
+    L.oracle_num_segments.argtypes = [C.POINTER(Problem)]
+    L.oracle_num_segments.restype = C.c_uint64
+    L.oracle_gate_matrix.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _f64p, _f64p]
+    L.oracle_half_angle.argtypes = [C.c_float, C.c_float, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]
+    L.oracle_gate_matrix_amp.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_float,
+                                         C.c_float, _f64p, _f64p]
+    L.oracle_compose_amp.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p, _f32p, _f64p,
+                                     _f64p]
+    L.oracle_eval_amp.argtypes = [C.POINTER(Problem), _u8p, _f32p, C.c_uint32, _f64p, _u32p]
+    L.oracle_sample_amp.argtypes = [C.POINTER(Problem), _f32p, C.c_uint32, _u8p, _u32p,
+                                    _f32p]
+    L.oracle_compose.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p, _f64p, _f64p]
+    L.oracle_score.argtypes = [C.c_uint32, _f64p, _f64p, _u8p, C.c_uint32]
+    L.oracle_score_dense.argtypes = [C.c_uint32, _f64p, _f64p, _f64p]
+    L.oracle_score_dense.restype = C.c_double
+    L.oracle_score.restype = C.c_double
+    L.oracle_cost.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p]
+    L.oracle_cost.restype = C.c_uint32
+    L.oracle_eval.argtypes = [C.POINTER(Problem), _u8p, C.c_uint32, _f64p, _u32p]
+    L.oracle_useful_flops.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, _u8p]
+    L.oracle_useful_flops.restype = C.c_uint64
+    L.oracle_init_state.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f32p]
+    L.oracle_sample.argtypes = [C.POINTER(Problem), _f32p, C.c_uint32, _u8p, _u32p]
+    L.oracle_update.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f32p, C.c_uint32, _u32p,
+                                _f64p]
+    L.oracle_su3.argtypes = [_f64p, _f64p, _f64p, _f64p]
+    L.oracle_su3_f32.argtypes = [_f32p, _f32p, _f32p, _f32p]
+    L.oracle_su3_angles.argtypes = [_f64p, _f64p, _f64p]
+    L.oracle_topk.argtypes = [_f64p, _u32p, C.c_uint32, C.c_uint32, _u32p]
+    L.oracle_step.argtypes = [C.POINTER(Problem), _f32p, _f32p, _f32p, C.c_uint32,
+                              C.c_uint32, _u8p, _u32p, _f64p, _u32p, _u32p,
+                              C.POINTER(Report)]
+    L.oracle_ga_init.argtypes = [C.POINTER(Problem), C.c_uint32, _u8p]
+    L.oracle_ga_init_amp.argtypes = [C.POINTER(Problem), C.c_uint32, _u8p, _f32p]
+    L.oracle_ga_next_amp.argtypes = [C.POINTER(Problem), C.c_uint32, C.c_uint32, C.c_double,
+                                     _u8p, _f32p, _f64p, _u32p, _u8p, _f32p]
+    L.oracle_ga_next.argtypes = [C.POINTER(Problem), C.c_uint32, C.c_uint32, C.c_double,
+                                 _u8p, _f64p, _u32p, _u8p]
+    return L
 
 
 def make_problem(n, L, P, library, perm, seed=0, run=0, fitness_kind=FIT_TRACE, p_mutation=0.1,

@@ -25,5 +25,17 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+def build_variant(source: str, out_path: str) -> str:
+    """Compile `source` (a modified copy of qe_oracle.c) with the oracle's own
+    flags into out_path; its #include of qe_oracle.h resolves to this folder."""
+    src = os.path.splitext(out_path)[0] + ".c"
+    with open(src, "w") as f:
+        f.write(source)
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-I" + HERE, "-o", out_path, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out_path
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))
