@@ -109,6 +109,11 @@ typedef enum {
 /* device error word bits (qe_report.error_word) */
 #define QE_ERRW_BAD_GATE 1u    /* a gate index >= the library size was evaluated */
 #define QE_ERRW_NONFINITE 2u   /* a fitness value was NaN or infinite */
+/* a binary32 search's rescored binary64 fitness lay outside the interval that
+ * its binary32 fitness and the bound eps_d = 8e-7 L + 2e-6 on the error of
+ * d = (N - |tr|)/N imply, so the top-k may be inexact; every rescored
+ * candidate is checked */
+#define QE_ERRW_GUARD_BAND 4u
 
 /* One search.  sizeOfIndividual = circuit_len, sizeOfPopulation = population,
  * numberOfWires = n_qubits (Sec. IV-B). */
@@ -191,6 +196,26 @@ qe_status qe_sample(qe_ctx *ctx, uint32_t prob, uint32_t gen, uint8_t *d_gate_id
  * give NaN fitness and QE_ENUMERIC (when h_topk is given) or the error bit. */
 qe_status qe_eval(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_t n_circuits,
                   void *d_fitness, uint32_t *d_cost, qe_ranked *h_topk);
+
+/* Ranking of given fitness values (the selection and binary64 rescoring of
+ * the top-k; Sec. IV-E ranks circuits by Eq. (11)): n_circuits circuits
+ * d_gate_idx[c*L + t] of search prob with their working-precision fitness
+ * d_fitness (float[n] for binary32 searches, double[n] for binary64) and gate
+ * costs d_cost (uint32[n], as qe_eval writes them), e.g. evaluated on several
+ * devices and gathered; d_amps: the Ising library's slot angles (float2 per
+ * slot, as qe_eval_amp), NULL otherwise.  The best min(topk, n) circuits
+ * (topk at least 1) are rescored in binary64 from their gates and written to
+ * h_topk sorted by (fitness desc, cost asc, index asc).  A binary32 search
+ * keeps every circuit whose binary64 fitness can reach the k-th best given
+ * the bound on its binary32 error, and checks every rescored candidate
+ * against that bound: a candidate outside it (a fitness that is not the
+ * binary32 value of its circuit, or a composition error above the bound)
+ * returns QE_ENUMERIC with QE_ERRW_GUARD_BAND in the message's sense, as do
+ * invalid gates and non-finite fitness.  n_circuits <= P; synchronises; a
+ * pending generation's ranking is finished first. */
+qe_status qe_rank(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, const float *d_amps,
+                  const void *d_fitness, const uint32_t *d_cost, uint32_t n_circuits,
+                  qe_ranked *h_topk);
 
 /* qe_eval on HOST buffers: copies h_gate_idx to the device, evaluates, copies
  * the fitness (float or double by precision) back to h_fitness and fills

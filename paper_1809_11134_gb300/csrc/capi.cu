@@ -991,6 +991,14 @@ qe_status qe_sample(qe_ctx *ctx, uint32_t prob, uint32_t gen, uint8_t *d_gate_id
   return QE_OK;
 }
 
+// the message of a nonzero device error word (the first bit set, in QE_ERRW_* order)
+static const char *errw_text(uint32_t errw) {
+  if (errw & kErrBadGate) return "invalid gate index in the circuits";
+  if (errw & kErrNonFinite) return "non-finite fitness";
+  return "a binary64 fitness lay outside the guard band of its binary32 value (the top-k may "
+         "be inexact)";
+}
+
 static qe_status rank_single(qe_ctx *ctx, uint32_t prob, uint32_t n, const void *fit,
                              const uint32_t *meta, const uint8_t *gsrc, const float2 *asrc,
                              qe_ranked *h_topk) {
@@ -1026,8 +1034,7 @@ static qe_status rank_single(qe_ctx *ctx, uint32_t prob, uint32_t n, const void 
   if (errw) {
     QE_CUDA(ctx, cudaMemsetAsync(ctx->g.err, 0, 4, us));
     QE_CUDA(ctx, cudaStreamSynchronize(us));
-    return fail(ctx, QE_ENUMERIC, (errw & kErrBadGate) ? "invalid gate index in the circuits"
-                                                       : "non-finite fitness");
+    return fail(ctx, QE_ENUMERIC, errw_text(errw));
   }
   return QE_OK;
 }
@@ -1065,6 +1072,23 @@ qe_status qe_eval_amp(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, con
                       uint32_t n_circuits, void *d_fitness, uint32_t *d_cost, qe_ranked *h_topk) {
   return eval_impl(ctx, prob, d_gate_idx, (const float2 *)d_amps, n_circuits, d_fitness, d_cost,
                    h_topk);
+}
+
+qe_status qe_rank(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, const float *d_amps,
+                  const void *d_fitness, const uint32_t *d_cost, uint32_t n_circuits,
+                  qe_ranked *h_topk) {
+  qe_status st = check_ctx(ctx, prob);
+  if (st != QE_OK) return st;
+  const DevProblem &d = ctx->hp[prob];
+  if (!h_topk) return fail(ctx, QE_EINVAL, "null h_topk");
+  if (n_circuits == 0) return QE_OK;
+  if (!d_gate_idx || !d_fitness || !d_cost) return fail(ctx, QE_EINVAL, "null buffer");
+  if (d.ising && !d_amps) return fail(ctx, QE_EINVAL, "Ising circuits need their angles");
+  if (n_circuits > d.P) return fail(ctx, QE_EINVAL, "ranking needs n_circuits <= population");
+  st = drain(ctx);  // the ranking scratch may still hold a pending ranking
+  if (st != QE_OK) return st;
+  return rank_single(ctx, prob, n_circuits, d_fitness, d_cost, d_gate_idx,
+                     d.ising ? (const float2 *)d_amps : nullptr, h_topk);
 }
 
 qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
@@ -1302,8 +1326,7 @@ qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_pr
   if (errw) {
     QE_CUDA(ctx, cudaMemsetAsync(ctx->g.err, 0, 4, us));
     QE_CUDA(ctx, cudaStreamSynchronize(us));
-    return fail(ctx, QE_ENUMERIC, (errw & kErrBadGate) ? "invalid gate index in the circuits"
-                                                       : "non-finite fitness");
+    return fail(ctx, QE_ENUMERIC, errw_text(errw));
   }
   return QE_OK;
 }
@@ -1385,7 +1408,7 @@ qe_status qe_step(qe_ctx *ctx, uint32_t n_gen, qe_report *h_reports) {
     memcpy(r.best_gates, b.best_gates, 64);
     memcpy(r.best_amps, b.best_amps, sizeof r.best_amps);
   }
-  if (errw) return fail(ctx, QE_ENUMERIC, "a search reported an invalid gate or non-finite fitness");
+  if (errw) return fail(ctx, QE_ENUMERIC, errw_text(errw));
   return QE_OK;
 }
 

@@ -1163,9 +1163,18 @@ __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ 
       if ((uint32_t)lane < p.L) half_angle(am[lane].x, am[lane].y, ic0, is0);
       if ((uint32_t)lane + 32 < p.L) half_angle(am[lane + 32].x, am[lane + 32].y, ic1, is1);
     }
+    const double F32 = p.cand_f[slot];  // the binary32 fitness the selection ranked by
     CircuitOut out = compose_score<NQ, double, true, ISING>(p, lane, o0, o1, (double *)nullptr,
                                                             ic0, is0, ic1, is1);
-    if (lane == 0) p.cand_f[slot] = anybad ? __longlong_as_double(0x7ff8000000000000ll) : out.F;
+    if (lane == 0) {
+      p.cand_f[slot] = anybad ? __longlong_as_double(0x7ff8000000000000ll) : out.F;
+      // the exactness of the top-k rests on every binary64 fitness lying in the
+      // interval its binary32 fitness implies: check it on every candidate
+      float lo, hi;
+      guard_band(p, (float)F32, out.cost, lo, hi);
+      if (!anybad && F32 == F32 && !(out.F >= (double)lo && out.F <= (double)hi))
+        atomicOr(g.err, kErrGuardBand);
+    }
   }
 }
 

@@ -42,15 +42,10 @@ __device__ __forceinline__ void bounds(const DevProblem &p, const RankJob &jb, u
     khi = fkey(__double2float_ru(D));
     return;
   }
-  const float pen = p.pen_per_gate * (float)(jb.meta[c] & 0xffu);
-  const float f = F + pen;
-  const float t = 1.f - f;
-  const float d = t * t;
-  const float dl = fmaxf(0.f, d - p.eps_d), dh = d + p.eps_d;
-  const float fhi = 1.f - sqrtf(dl), flo = 1.f - sqrtf(dh);
-  const float slop = 2e-6f;
-  klo = fkey(flo - pen - slop);
-  khi = fkey(fhi - pen + slop);
+  float lo, hi;
+  guard_band(p, F, jb.meta[c], lo, hi);
+  klo = fkey(lo);
+  khi = fkey(hi);
 }
 
 // suffix scan of the 4096-bin histogram: finds the bin where the count taken
@@ -252,7 +247,10 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *
     if (take) {
       const uint32_t slot = wbase + __popc(bal & ((1u << lane) - 1));
       p.cand[slot] = c;
-      if (p.prec == 0) p.cand_f[slot] = ((const double *)jb.fit)[c];
+      // binary64 searches: the final value; binary32 searches: the binary32
+      // value, which the rescoring checks against the guard band and replaces
+      p.cand_f[slot] = p.prec == 0 ? ((const double *)jb.fit)[c]
+                                   : (double)((const float *)jb.fit)[c];
     }
   }
   __syncthreads();

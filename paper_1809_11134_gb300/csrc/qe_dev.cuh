@@ -48,7 +48,7 @@ enum Stream : uint32_t {
 constexpr uint32_t kEncQeqea = 0u, kEncGa = 1u;
 
 // device error word bits (mirrors QE_ERRW_*)
-constexpr uint32_t kErrBadGate = 1u, kErrNonFinite = 2u;
+constexpr uint32_t kErrBadGate = 1u, kErrNonFinite = 2u, kErrGuardBand = 4u;
 
 struct Ranked {
   uint32_t circuit, cost;
@@ -176,6 +176,26 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
 __device__ __forceinline__ unsigned long long dkey(double f) {
   unsigned long long b = (unsigned long long)__double_as_longlong(f);
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// The ranking's guard band: the interval [lo, hi] that must hold the binary64
+// fitness of a circuit whose binary32 fitness is F and whose gate cost is
+// cost, given |d32 - d64| <= eps_d with d = (1 - f)^2 = ((N - |tr|)/N) and
+// f = F + cost_weight * cost / L (binary32 arithmetic; the slop covers the
+// rounding of these few operations).  The selection keeps every circuit whose
+// hi reaches the k-th largest lo; the rescoring checks each candidate's
+// binary64 fitness against the same interval.
+__device__ __forceinline__ void guard_band(const DevProblem &p, float F, uint32_t cost, float &lo,
+                                           float &hi) {
+  const float pen = p.pen_per_gate * (float)(cost & 0xffu);
+  const float f = F + pen;
+  const float t = 1.f - f;
+  const float d = t * t;
+  const float dl = fmaxf(0.f, d - p.eps_d), dh = d + p.eps_d;
+  const float fhi = 1.f - sqrtf(dl), flo = 1.f - sqrtf(dh);
+  const float slop = 2e-6f;
+  lo = flo - pen - slop;
+  hi = fhi - pen + slop;
 }
 
 // ---------------------------------------------------------------- state access

@@ -24,10 +24,11 @@ QE_LIB_NCV, QE_LIB_HT, QE_LIB_IDENTITY, QE_LIB_ISING = 1, 2, 4, 8
 QE_PREC_FP64, QE_PREC_FP32, QE_PREC_SPLIT_TC = 0, 1, 2
 QE_FIT_TRACE, QE_FIT_PROB = 0, 1
 QE_ENC_QEQEA, QE_ENC_GA = 0, 1
-QE_ERRW_BAD_GATE, QE_ERRW_NONFINITE = 1, 2
+QE_ERRW_BAD_GATE, QE_ERRW_NONFINITE, QE_ERRW_GUARD_BAND = 1, 2, 4
 
 # every symbol include/qe.h declares
-EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_amp", "qe_eval_host",
+EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_amp", "qe_rank",
+           "qe_eval_host",
            "qe_eval_host_batch", "qe_compose", "qe_compose_amp",
            "qe_update", "qe_step", "qe_last_generation", "qe_state_bytes", "qe_get_state",
            "qe_set_state", "qe_generation", "qe_autotune", "qe_launch_plan", "qe_stage_timing",
@@ -238,6 +239,24 @@ class Context:
         if topk:
             return [(r.circuit, r.cost, r.fitness) for r in out[:k]]
         return None
+
+    def rank(self, prob, gate_idx, fitness, cost, n_circuits=None, amps=None):
+        """qe_rank: the top-k of given fitness values (device tensors), rescored in
+        binary64 from the gates; returns [(circuit, cost, fitness)]"""
+        import torch
+        p = self._probs[prob]
+        n = gate_idx.shape[0] if n_circuits is None else n_circuits
+        _need(gate_idx, torch.uint8, n * p.circuit_len, "gate_idx")
+        if amps is not None:
+            _need(amps, torch.float32, n * p.circuit_len * 2, "amps")
+        _need(fitness, torch.float64 if p.precision == QE_PREC_FP64 else torch.float32, n,
+              "fitness")
+        _need(cost, torch.int32, n, "cost")
+        k = min(max(p.topk, 1), n)
+        out = (qe_ranked * max(k, 1))()
+        _check(self.h, lib().qe_rank(self.h, prob, _ptr(gate_idx), _ptr(amps), _ptr(fitness),
+                                     _ptr(cost), n, out))
+        return [(r.circuit, r.cost, r.fitness) for r in out[:k]]
 
     def eval_host(self, prob, gate_idx: np.ndarray, topk=False):
         p = self._probs[prob]
@@ -497,6 +516,10 @@ def qe_sample(ctx: Context, prob, gen, gate_idx, seg_id):
 
 def qe_eval(ctx: Context, prob, gate_idx, fitness, n_circuits=None, cost=None, topk=False):
     return ctx.eval(prob, gate_idx, fitness, n_circuits, cost, topk)
+
+
+def qe_rank(ctx: Context, prob, gate_idx, fitness, cost, n_circuits=None, amps=None):
+    return ctx.rank(prob, gate_idx, fitness, cost, n_circuits, amps)
 
 
 def qe_eval_host(ctx: Context, prob, gate_idx, topk=False):
