@@ -105,6 +105,29 @@ def peaks():
         return {}
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_generation(oracle, p, state, gen, pool, k=32, chunk=64):
+    """One whole generation of the oracle as it stands (sample, dense binary64
+    compose/score, full sort, update) with its evaluation, nearly all of the
+    time, split over `pool`'s threads in chunks of circuits (the oracle's calls
+    release the interpreter lock); sampling and update run on one thread."""
+    import numpy as np
+    cur, best, bf = state
+    gi, sid = oracle.sample(p, cur, gen)
+    spans = [(lo, min(p.P, lo + chunk)) for lo in range(0, p.P, chunk)]
+    parts = list(pool.map(lambda c: oracle.eval_circuits(p, gi[c[0]:c[1]]), spans))
+    F = np.concatenate([f for f, _ in parts])
+    cost = np.concatenate([c for _, c in parts])
+    oracle.topk(F, cost, k)
+    oracle.update(p, cur, best, bf, gen, sid, F)
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args):
     """The oracle as it stands, on a bounded sample of the same workload."""
@@ -120,12 +143,13 @@ def run_reference(args):
     probs = [oracle.make_problem(s.n, s.L, P, s.library, s.perm, seed=s.seed, run=r)
              for r, s in enumerate(searches)]
     states = [oracle.init_state(p) for p in probs]
-    reps = [oracle.new_report() for _ in probs]
+    cores = host_cores()
+    from concurrent.futures import ThreadPoolExecutor
+    pool = ThreadPoolExecutor(cores)
 
     def one(step):
         j = step % len(probs)
-        cur, best, bf = states[j]
-        oracle.step(probs[j], cur, best, bf, step // len(probs), 32, reps[j])
+        oracle_generation(oracle, probs[j], states[j], step // len(probs), pool)
 
     for w in range(args.warmup):
         one(w)
@@ -133,6 +157,7 @@ def run_reference(args):
     for k in range(args.steps):
         one(args.warmup + k)
     dt = time.perf_counter() - t0
+    pool.shutdown()
     value = P * args.steps / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -140,11 +165,12 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": workload_name(args), "circuits_per_step": P,
-                   "parallelism": "one host thread", "l2": "host memory"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "parallelism": "%d host threads (evaluation)" % cores, "l2": "host memory"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "each step: one generation of one of the searches with its "
                                    "population capped at P=%d (sample, dense Kronecker compose, "
-                                   "score, sort, update)" % P},
+                                   "score, sort, update), the evaluation on %d threads"
+                                   % (P, cores)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -152,26 +178,40 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm
 def cpu_baseline(seconds=10.0):
-    """Oracle (single thread, binary64, dense Kronecker + matmul) on circuits of
-    the benchmark workload: whole generations of the Toffoli search at P=4096
-    repeated until `seconds` elapsed."""
+    """The oracle as it stands on the benchmark workload's Toffoli search
+    (P=4096, L=16): whole generations repeated for `seconds`/2 on every host
+    core (evaluation threaded, as oracle_generation) and for `seconds`/2 on
+    one core (the oracle's own generation step)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle
     from paper_1809_11134_gb300 import workloads as W
     s = W.config(2)[0]
-    p = oracle.make_problem(s.n, s.L, s.P, s.library, s.perm, seed=s.seed)
-    cur, best, bf = oracle.init_state(p)
-    rep = oracle.new_report()
-    n = 0
-    t0 = time.perf_counter()
-    gen = 0
-    while time.perf_counter() - t0 < seconds:
-        oracle.step(p, cur, best, bf, gen, 32, rep)
-        gen += 1
-        n += s.P
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d whole generations of the Toffoli search (P=4096, L=16): sample, "
-                      "dense binary64 compose/score, full sort, update; %.1f s" % (gen, dt)}
+    cores = host_cores()
+
+    def rate(secs, pool):
+        p = oracle.make_problem(s.n, s.L, s.P, s.library, s.perm, seed=s.seed)
+        state = oracle.init_state(p)
+        rep = oracle.new_report()
+        gen = 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < secs:
+            if pool is None:
+                oracle.step(p, *state, gen, 32, rep)
+            else:
+                oracle_generation(oracle, p, state, gen, pool)
+            gen += 1
+        return s.P * gen / (time.perf_counter() - t0), gen
+
+    v1, g1 = rate(seconds / 2, None)
+    with ThreadPoolExecutor(cores) as pool:
+        vn, gn = rate(seconds / 2, pool)
+    return {"value": vn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "one_core": {"value": v1, "unit": UNIT, "cores": 1},
+            "sample": "whole generations of the Toffoli search (P=4096, L=16): sample, dense "
+                      "binary64 compose/score, full sort, update; %d generations with the "
+                      "evaluation on %d threads (chunks of 64 circuits), %d on one core; %.1f s "
+                      "each" % (gn, cores, g1, seconds / 2)}
 
 
 def workload_name(args):
@@ -647,6 +687,19 @@ def per_config(qe, torch, args):
     return out
 
 
+def launch_ranks(n):
+    """Run this command as n ranks on this node (torch.distributed.run, one
+    process per GPU, rendezvous on 127.0.0.1) and return their exit status."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node",
+           str(n), "--master-addr", "127.0.0.1", "--master-port", str(port),
+           os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -663,6 +716,12 @@ def main():
                     help="cap P (for profiling smaller cases of a configuration)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # not started by a launcher: start one process per GPU of this node
+        sys.exit(launch_ranks(args.gpus))
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws != args.gpus:
+        sys.exit("bench.py: --gpus %d, but the launcher started %d ranks" % (args.gpus, ws))
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -50,3 +50,33 @@ def test_launches_per_generation():
     widths = len(set(s.n for s in mixed if s.precision != W.PREC_FP64))
     groups = len(set((s.n, s.precision == W.PREC_FP64) for s in mixed))
     assert bench.launches_per_generation(mixed) == groups + 2 + 1 + widths + 1 + 1
+
+
+def test_rank_count_must_match_gpus():
+    """Under a launcher, --gpus must equal the launched world size (a silent
+    single-process run of --gpus 8 would report n_gpus 1)."""
+    import subprocess
+    env = dict(os.environ, WORLD_SIZE="2", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "1",
+                        "--impl", "reference", "--steps", "1"], env=env, capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode != 0 and "launcher started 2 ranks" in r.stderr
+
+
+def test_oracle_generation_threads_match_the_oracle_step():
+    """The threaded generation of the CPU baseline computes what the oracle's
+    own generation step computes (same state afterwards)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    s = W.config(2)[0]
+    p = oracle.make_problem(s.n, s.L, 300, s.library, s.perm, seed=s.seed)
+    a = oracle.init_state(p)
+    b = tuple(x.copy() for x in a)
+    rep = oracle.new_report()
+    with ThreadPoolExecutor(4) as pool:
+        for g in range(3):
+            bench.oracle_generation(oracle, p, a, g, pool)
+            oracle.step(p, *b, g, 32, rep)
+    for x, y in zip(a, b):
+        assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
