@@ -592,6 +592,7 @@ def _fp32_error(qe, torch, ctx32, searches, n_unitary=256):
     s64 = [W.Search(**{**s.__dict__, "precision": W.PREC_FP64}) for s in searches]
     ctx64 = qe.Context(s64)
     f_err, u_err, bad = 0.0, 0.0, 0
+    hi_err, hi_n = 0.0, 0
     for r, s in enumerate(searches):
         last = ctx32.last_generation(r)
         g = torch.from_numpy(np.ascontiguousarray(last["gate_idx"])).cuda()
@@ -611,10 +612,15 @@ def _fp32_error(qe, torch, ctx32, searches, n_unitary=256):
         bad += int((~np.isfinite(df)).sum() + (~np.isfinite(du)).sum())
         f_err = max(f_err, float(np.nanmax(df)) if df.size else 0.0)
         u_err = max(u_err, float(np.nanmax(du)) if du.size else 0.0)
+        # near f = 1 the square root of Eq. (11) amplifies the rounding of d
+        hi = f64.cpu().numpy() > 0.99
+        hi_n += int(hi.sum())
+        if hi.any():
+            hi_err = max(hi_err, float(np.nanmax(df[hi])))
     ctx64.close()
     if bad:
         raise RuntimeError("%d non-finite binary32/binary64 differences" % bad)
-    return f_err, u_err
+    return f_err, u_err, hi_err, hi_n
 
 
 def per_config(qe, torch, args):
@@ -634,8 +640,17 @@ def per_config(qe, torch, args):
             searches = W.config(cfg, precision=prec)
             ctx, r = _stage_rates(qe, torch, searches, gens)
             if prec == W.PREC_FP32:
-                r["max_abs_fitness_err_vs_fp64"], r["max_abs_unitary_err_vs_fp64"] = \
-                    _fp32_error(qe, torch, ctx, searches)
+                fe, ue, he, hn = _fp32_error(qe, torch, ctx, searches)
+                r["max_abs_fitness_err_vs_fp64"], r["max_abs_unitary_err_vs_fp64"] = fe, ue
+                r["above_0.99"] = {"circuits": hn, "max_abs_fitness_err_vs_fp64": he}
+                if cfg == 2:
+                    # converged searches: most of the population sits near f = 1
+                    ctx.step(300, reports=False)
+                    fe, ue, he, hn = _fp32_error(qe, torch, ctx, searches)
+                    r["after_320_generations"] = {
+                        "max_abs_fitness_err_vs_fp64": fe, "above_0.99": {
+                            "circuits": hn, "max_abs_fitness_err_vs_fp64": he,
+                            "d_space_bound": 8e-7 * searches[0].L + 2e-6}}
             ctx.close()
             res["fp32" if prec else "fp64"] = r
         res["fp32_over_fp64_circuit_kernel"] = (res["fp32"]["circuit_kernel_circuits_per_s"] /

@@ -700,6 +700,216 @@ struct CircuitOut {
   bool bad;       // an op byte was invalid
 };
 
+// Eq. (11) in binary32 from every lane's share (vr, vi) of the trace (or, for
+// the probability overlap, of its row's amplitude), minus the cost penalty pen
+__device__ __forceinline__ double fitness32(const DevProblem &p, float vr, float vi, double pen,
+                                            int N) {
+  float a, b;
+  if (p.fit_kind == 1) {
+    a = vr * vr + vi * vi;
+    b = 0.f;
+  } else {
+    a = vr;
+    b = vi;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(kFull, a, o);
+    b += __shfl_xor_sync(kFull, b, o);
+  }
+  const float size = (float)N, inv = 1.f / (float)N;
+  float d;
+  if (p.fit_kind == 1) {
+    d = (size - a) * inv;
+  } else {
+    d = (size - sqrtf(a * a + b * b)) * inv;
+  }
+  d = fmaxf(d, 0.f);
+  const float f = 1.f - sqrtf(d);
+  return pen == 0.0 ? (double)f : (double)(float)((double)f - pen);
+}
+
+// ------------------------------------------------------------------ 5 qubits in shared memory
+// Binary32 composition of a 5-qubit circuit with the unitary in shared memory:
+// lane j owns column j (32 rows of 8 B, 256 B apart, so a warp's access to one
+// row is 256 contiguous bytes), and rows are addressed through a map from
+// logical to physical rows that is linear over GF(2): physical row A x, with
+// the columns a_k = A e_k of A packed 5 bits each.  A gate on logical target
+// bit t (control c) pairs logical rows x and x ^ e_t, i.e. physical rows p and
+// p ^ a_t; the rows of a gate are enumerated in Gray-code order over the
+// columns of the free bits, one XOR per row.  A CNOT moves no data: it maps
+// logical row x to x ^ x_c e_t, which is the column update a_c ^= a_t.  Every
+// pair gets the same binary32 operations as in the register kernels.
+struct Op5Table {
+  uint32_t v[40 + 10];
+};
+// op byte -> kind | target bit << 2 | control bit << 5 (7 = none) | free
+// bits (ascending, 3 bits each) << 8: pair ops 0..39 (2 * pair + {CNOT, CV})
+// and wire ops 40..49 (H, T), wire w at bit 4 - w
+constexpr uint32_t op5_fields(int o) {
+  int kind = 0, tw = 0, cw = -1;
+  if (o < 40) {
+    const int pr = o >> 1, tt = pr & 3;
+    cw = pr >> 2;
+    tw = tt >= cw ? tt + 1 : tt;
+    kind = (o & 1) ? kCvx : kCnot;
+  } else {
+    tw = (o - 40) >> 1;
+    kind = (o & 1) ? kTx : kHad;
+  }
+  const int tb = 4 - tw, cb = cw < 0 ? 7 : 4 - cw;
+  uint32_t v = (uint32_t)kind | ((uint32_t)tb << 2) | ((uint32_t)cb << 5);
+  int k = 0;
+  for (int b = 0; b < 5; ++b)
+    if (b != tb && b != cb) v |= (uint32_t)b << (8 + 3 * k++);
+  return v;
+}
+constexpr Op5Table make_op5() {
+  Op5Table t{};
+  for (int o = 0; o < 50; ++o) t.v[o] = op5_fields(o);
+  return t;
+}
+__constant__ Op5Table c_op5 = make_op5();
+
+constexpr uint32_t kMap5Identity = 1u | (2u << 5) | (4u << 10) | (8u << 15) | (16u << 20);
+
+__device__ __forceinline__ uint32_t col5(uint32_t A, uint32_t k) { return (A >> (5 * k)) & 31u; }
+
+// physical row of logical row x
+__device__ __forceinline__ uint32_t phys5(uint32_t A, uint32_t x) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) r ^= ((x >> k) & 1u) ? col5(A, k) : 0u;
+  return r;
+}
+
+constexpr int ctz_c(int v) {
+  int n = 0;
+  while (!(v & 1)) {
+    v >>= 1;
+    ++n;
+  }
+  return n;
+}
+
+// the free-bit columns g[0..M) and the Gray-code order of 2^M rows from q:
+// row i of the gate is q ^ (XOR of g[b] over the bits b of gray(i))
+template <int M>
+__device__ __forceinline__ void gray_rows(uint32_t q, const uint32_t (&g)[4], uint32_t (&rows)[1 << M]) {
+#pragma unroll
+  for (int i = 0; i < (1 << M); ++i) {
+    rows[i] = q;
+    if (i + 1 < (1 << M)) q ^= g[ctz_c(i + 1)];
+  }
+}
+
+template <int KIND, int M>
+__device__ __forceinline__ void gate5_smem(float2 *col, uint32_t q, uint32_t at,
+                                           const uint32_t (&g)[4], float s) {
+  using A = Ar<float, false>;
+  uint32_t rows[1 << M];
+  gray_rows<M>(q, g, rows);
+  // four pairs (or rows) per batch: every load of a batch before its stores
+#pragma unroll
+  for (int b = 0; b < (1 << M); b += 4) {
+    if constexpr (KIND == kTx) {
+      float2 y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) y[u] = col[rows[b + u] << 5];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) A::tx(y[u].x, y[u].y, s);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) col[rows[b + u] << 5] = y[u];
+    } else {
+      float2 x[4], y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        x[u] = col[rows[b + u] << 5];
+        y[u] = col[(rows[b + u] ^ at) << 5];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if constexpr (KIND == kCvx) A::cvx_pair(x[u].x, x[u].y, y[u].x, y[u].y, s);
+        else A::had_pair(x[u].x, x[u].y, y[u].x, y[u].y);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        col[rows[b + u] << 5] = x[u];
+        col[(rows[b + u] ^ at) << 5] = y[u];
+      }
+    }
+  }
+}
+
+// the whole circuit: gates from the op bytes (slots t < L, ops0 for t < 32 and
+// ops1 above, by lane t & 31), then this lane's share of the score and, if
+// S_out is given, the unitary; blocks of 128 threads (four circuits)
+template <bool DENSE_OK>
+__device__ __forceinline__ CircuitOut compose5_smem(const DevProblem &p, int lane, uint32_t ops0,
+                                                    uint32_t ops1, float *S_out) {
+  __shared__ float2 s_state[4][32 * 32];
+  float2 *col = &s_state[(threadIdx.x >> 5) & 3][lane];
+  const uint32_t cost = __reduce_add_sync(kFull, (ops0 != kOpIdentity) + (ops1 != kOpIdentity));
+  const uint32_t work = __reduce_add_sync(kFull, op_work(p, (int)ops0) + op_work(p, (int)ops1));
+#pragma unroll
+  for (int r = 0; r < 32; ++r) col[r << 5] = make_float2(r == lane ? 1.f : 0.f, 0.f);
+  uint32_t Amap = kMap5Identity;
+  const uint32_t L = p.L;
+  for (uint32_t t = 0; t < L; ++t) {
+    const uint32_t src = t < 32 ? ops0 : ops1;
+    const int op = __shfl_sync(kFull, (int)src, (int)(t & 31));
+    if (op == kOpIdentity) continue;
+    const uint32_t d = c_op5.v[op & 0x7f];
+    const float s = (op & kOpNeg) ? -1.f : 1.f;
+    const uint32_t kind = d & 3u, tb = (d >> 2) & 7u, cb = (d >> 5) & 7u;
+    const uint32_t at = col5(Amap, tb);
+    if (kind == kCnot) {
+      Amap ^= at << (5 * cb);
+      continue;
+    }
+    const uint32_t g[4] = {col5(Amap, (d >> 8) & 7u), col5(Amap, (d >> 11) & 7u),
+                           col5(Amap, (d >> 14) & 7u), col5(Amap, (d >> 17) & 7u)};
+    if (kind == kCvx) gate5_smem<kCvx, 3>(col, col5(Amap, cb), at, g, s);
+    else if (kind == kHad) gate5_smem<kHad, 4>(col, 0u, at, g, s);
+    else gate5_smem<kTx, 4>(col, at, at, g, s);
+  }
+  CircuitOut out;
+  out.cost = cost;
+  out.work = work + 2u * 32u;
+  out.bad = false;
+  const int j = lane;
+  if (S_out) {
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+      const float2 v = col[phys5(Amap, (uint32_t)i) << 5];
+      S_out[2 * (i * 32 + j)] = v.x;
+      S_out[2 * (i * 32 + j) + 1] = v.y;
+    }
+  }
+  float vr = 0.f, vi = 0.f;
+  const bool dense = DENSE_OK && p.dense != 0;
+  if (!dense) {
+    const float2 v = col[phys5(Amap, p.perm[j]) << 5];
+    vr = v.x;
+    vi = v.y;
+  } else {
+    // (S^dag T)_jj = sum_i conj(S_ij) T_ij, rows in Gray-code order
+    out.work += 8u * 32u * 32u - 2u * 32u;
+    uint32_t x = 0;
+    for (int i = 0; i < 32; ++i) {
+      const float2 v = col[phys5(Amap, x) << 5];
+      const float2 tt = __ldg(p.tgt32 + x * 32 + j);
+      vr = fmaf(v.x, tt.x, fmaf(v.y, tt.y, vr));
+      vi = fmaf(v.x, tt.y, fmaf(-v.y, tt.x, vi));
+      x ^= 1u << __ffs(i + 1) - 1;
+    }
+  }
+  const double pen =
+      p.cost_weight == 0.0 ? 0.0 : __dmul_rn(p.cost_weight, __ddiv_rn((double)cost, (double)p.L));
+  out.F = fitness32(p, vr, vi, pen, 32);
+  return out;
+}
+
 // ops0/ops1: this lane's op bytes for slots lane and lane + 32
 // ic0/is0, ic1/is1: cos/sin of theta/2 of this lane's slots (Ising)
 // DENSE_OK = false compiles the dense-target score out (permutation targets only)
@@ -707,6 +917,9 @@ template <int NQ, typename R, bool CANON, bool ISING = false, bool DENSE_OK = tr
 __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lane, uint32_t ops0,
                                                     uint32_t ops1, R *S_out, R ic0 = R(1),
                                                     R is0 = R(0), R ic1 = R(1), R is1 = R(0)) {
+  if constexpr (NQ == 5 && !CANON && !ISING) {
+    return compose5_smem<DENSE_OK>(p, lane, ops0, ops1, (float *)S_out);
+  } else {
   using Ly = Lay<NQ>;
   constexpr int N = Ly::N;
   const int j = lane & (N - 1);
@@ -878,31 +1091,10 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
     }
     out.F = __shfl_sync(kFull, F, 0);
   } else {
-    float a, b;
-    if (p.fit_kind == 1) {
-      a = vr * vr + vi * vi;
-      b = 0.f;
-    } else {
-      a = vr;
-      b = vi;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(kFull, a, o);
-      b += __shfl_xor_sync(kFull, b, o);
-    }
-    const float size = (float)N, inv = 1.f / (float)N;
-    float d;
-    if (p.fit_kind == 1) {
-      d = (size - a) * inv;
-    } else {
-      d = (size - sqrtf(a * a + b * b)) * inv;
-    }
-    d = fmaxf(d, 0.f);
-    const float f = 1.f - sqrtf(d);
-    out.F = pen == 0.0 ? (double)f : (double)(float)((double)f - pen);
+    out.F = fitness32(p, (float)vr, (float)vi, pen, N);
   }
   return out;
+  }
 }
 
 // op byte of library gate g (kOpIdentity also for out-of-range g; bad flags it)
@@ -931,23 +1123,24 @@ __device__ __forceinline__ uint32_t find_problem(const uint32_t *prefix, uint32_
 // capped at 128 registers (its 64 state registers plus temporaries); the
 // scheduler otherwise interleaves every row pair of a gate and asks for ~190.
 //
-// The 5-qubit binary32 kernel runs 128-thread blocks, at least three per SM,
-// so each thread may use 168 registers: its 64 state registers and the gate
-// temporaries then fit without spilling (with 256-thread blocks the same
-// occupancy allows 128 registers and spills ~220 B per thread).
+// The 5-qubit binary32 kernel runs 128-thread blocks (four circuits, 32 KB of
+// shared memory for their unitaries, see compose5_smem): six fit an SM's
+// shared memory, so each thread may use 85 registers.  Its Ising variant
+// keeps the unitary in registers (64 state registers plus the gate
+// temporaries): three blocks per SM, 168 registers, no spills.
 template <int NQ, bool CANON>
 constexpr int block_threads() {
   return (NQ == 5 && !CANON) ? 128 : 256;
 }
-template <int NQ, bool CANON>
+template <int NQ, bool CANON, bool ISING>
 constexpr int min_blocks() {
-  return (NQ == 5 && !CANON) ? 3 : ((NQ <= 3 && !CANON) ? 6 : 1);
+  return (NQ == 5 && !CANON) ? (ISING ? 3 : 6) : ((NQ <= 3 && !CANON) ? 6 : 1);
 }
 
 // EXT: the group holds a search measured K > 1 times (k_presample) or one with
 // a dense target; without it both paths are compiled out of the kernel
 template <int NQ, typename R, bool CANON, bool ISING, bool EXT>
-__global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CANON>()) k_step(const DevProblem *__restrict__ probs,
+__global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CANON, ISING>()) k_step(const DevProblem *__restrict__ probs,
                                               const uint32_t *__restrict__ group,
                                               const uint32_t *__restrict__ prefix,
                                               uint32_t n_group, uint32_t total, DevGlobal g) {
@@ -1086,7 +1279,7 @@ __global__ void __launch_bounds__(256) k_sample(const DevProblem *__restrict__ p
 // Fitness (and optionally the unitaries) of caller-provided gate strings
 // (Ising: with every slot's angle as qubit amplitudes in amps).
 template <int NQ, typename R, bool CANON, bool ISING>
-__global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CANON>()) k_eval(const DevProblem *__restrict__ probs, uint32_t prob,
+__global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CANON, ISING>()) k_eval(const DevProblem *__restrict__ probs, uint32_t prob,
                                               const uint8_t *__restrict__ gates,
                                               const float2 *__restrict__ amps, uint32_t n,
                                               R *fit, uint32_t *cost, R *S, DevGlobal g) {
@@ -1308,6 +1501,15 @@ bool is_rescore_kernel(const void *f) {
 cudaError_t query_circuit_occupancy(LaunchCfg &lc) {
   cudaError_t e = cudaSuccess;
   int b = 0;
+  // the 5-qubit binary32 kernels keep their unitaries in shared memory: ask
+  // for the largest shared-memory carveout so that six blocks fit an SM
+  const void *smem5[] = {(const void *)k_step<5, float, false, false, false>,
+                         (const void *)k_step<5, float, false, false, true>,
+                         (const void *)k_eval<5, float, false, false>};
+  for (const void *f : smem5)
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
 #define QE_Q(NQ)                                                                            \
   if (e == cudaSuccess)                                                                     \
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<NQ, float, false, false, false>, \
