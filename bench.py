@@ -572,14 +572,44 @@ def _stage_rates(qe, torch, searches, gens):
            "launch_plan": ctx.launch_plan()}
     if searches[0].precision != W.PREC_FP64:
         res["circuit_kernel_alu_frac"] = res["circuit_kernel_useful_tflops"] / fp32_peak
+        last = [ctx.last_generation(r) for r in range(len(searches))]
+        if all(s.n == 5 and not (s.library & W.LIB_ISING) for s in searches):
+            sb = sum(smem_bytes5(s, l["gate_idx"]) for s, l in zip(searches, last))
+            peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            res["circuit_kernel_smem"] = {
+                "bound": "shared memory", "achieved_tbs": sb / (t[0] / 1e3) / 1e12,
+                "peak_tbs": peak, "frac": sb / (t[0] / 1e3) / 1e12 / peak,
+                "bytes_per_launch": sb,
+                "model": "the kernel's own shared-memory traffic: 8 KB per CV (8 row pairs "
+                         "read and written), 16 KB per H, 8 KB per T, none per CNOT, 8 KB "
+                         "per circuit to set the identity; peak 152 SMs x 128 B/cycle x "
+                         "the maximum SM clock (derived)"}
         if searches[0].encoding == W.ENC_QEQEA:
-            last = [ctx.last_generation(r) for r in range(len(searches))]
             ub = update_bytes(searches, last)
             res["update_ms"] = round(float(t[4]), 4)
             res["update_algorithmic_gbs"] = ub / (t[4] / 1e3) / 1e9
             res["update_hbm_frac"] = res["update_algorithmic_gbs"] / pk["hbm_gbs"] \
                 if pk.get("hbm_gbs") else None
     return ctx, res
+
+
+def smem_bytes5(s, gate_idx):
+    """Shared-memory bytes the 5-qubit binary32 circuit kernel moves for these
+    circuits (library indices: [I], then CNOT, CV, CV^dag per ordered wire
+    pair, then H, T, T^dag per wire)."""
+    import numpy as np
+    from paper_1809_11134_gb300 import workloads as W
+    g = np.asarray(gate_idx, np.int64).ravel()
+    base = 1 if s.library & W.LIB_IDENTITY else 0
+    npair = 3 * s.n * (s.n - 1) if s.library & W.LIB_NCV else 0
+    x = g - base
+    pair = (x >= 0) & (x < npair)
+    wire = x >= npair
+    cv = int((pair & (x % 3 != 0)).sum())
+    h = int((wire & ((x - npair) % 3 == 0)).sum())
+    t = int((wire & ((x - npair) % 3 != 0)).sum())
+    n_circ = np.asarray(gate_idx).shape[0]
+    return 8192 * cv + 16384 * h + 8192 * t + (8192 + 256) * n_circ
 
 
 def _fp32_error(qe, torch, ctx32, searches, n_unitary=256):

@@ -260,40 +260,6 @@ bool target_ok(const double *T, uint32_t N) {
   return true;
 }
 
-// Eq. (12) in binary32: index 0..2 of cv/sv = theta1..3 (c_k, s_k), 3..7 =
-// phi1..5 (cos, sin).  Phase factors e^{i(+-a +-b ...)} are products of the
-// single-parameter phases taken left to right, real factors are applied left
-// to right, every operation rounded (this file is built without FMA
-// contraction), so the table equals a per-segment evaluation in that order.
-struct F2 {
-  float re, im;
-};
-static F2 f2mul(F2 a, F2 b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-static F2 f2sub(F2 a, F2 b) { return {a.re - b.re, a.im - b.im}; }
-static F2 f2scale(F2 a, float s) { return {a.re * s, a.im * s}; }
-static F2 f2neg(F2 a) { return {-a.re, -a.im}; }
-
-void su3_binary32(const float *cv, const float *sv, float2 *out) {
-  const float c1 = cv[0], c2 = cv[1], c3 = cv[2], s1 = sv[0], s2 = sv[1], s3 = sv[2];
-  auto ep = [&](int k) { return F2{cv[2 + k], sv[2 + k]}; };
-  auto em = [&](int k) { return F2{cv[2 + k], -sv[2 + k]}; };
-  F2 U[9];
-  U[0] = f2scale(f2scale(ep(1), c1), c2);
-  U[1] = f2scale(ep(3), s1);
-  U[2] = f2scale(f2scale(ep(4), c1), s2);
-  U[3] = f2sub(f2scale(f2scale(f2mul(em(4), em(5)), s2), s3),
-               f2scale(f2scale(f2scale(f2mul(f2mul(ep(1), ep(2)), em(3)), s1), c2), c3));
-  U[4] = f2scale(f2scale(ep(2), c1), c3);
-  U[5] = f2sub(f2neg(f2scale(f2scale(f2mul(em(1), em(5)), c2), s3)),
-               f2scale(f2scale(f2scale(f2mul(f2mul(ep(2), em(3)), ep(4)), s1), s2), c3));
-  U[6] = f2sub(f2neg(f2scale(f2scale(f2mul(em(2), em(4)), s2), c3)),
-               f2scale(f2scale(f2scale(f2mul(f2mul(ep(1), em(3)), ep(5)), s1), c2), s3));
-  U[7] = f2scale(f2scale(ep(5), c1), s3);
-  U[8] = f2sub(f2scale(f2scale(f2mul(em(1), em(2)), c2), c3),
-               f2scale(f2scale(f2scale(f2mul(f2mul(em(3), ep(4)), ep(5)), s1), s2), s3));
-  for (int k = 0; k < 9; ++k) out[k] = make_float2(U[k].re, U[k].im);
-}
-
 unsigned long long threshold(double p) {
   // number of u in [0, 2^32) with (u + 1/2) 2^-32 < p
   const double X = p * 4294967296.0;
@@ -755,7 +721,6 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   ar.take(&ctx->d_probs, n_probs * sizeof(DevProblem));
   ar.take(&ctx->g.th_tab, (kQ + 1) * sizeof(float2));
   ar.take(&ctx->g.ph_tab, (kQ + 1) * sizeof(float2));
-  ar.take(&ctx->g.su3_tab, (size_t)8 * kQ * 9 * sizeof(float2));
   ar.take(&ctx->g.gen, 4);
   ar.take(&ctx->g.err, 4);
   ar.take(&ctx->g.rescore_n, 4);
@@ -840,27 +805,6 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     return bail(cuda_fail(ctx, e, "uploading tables"));
   if ((e = trig((2.0 * pi) / (double)kQ, ctx->g.ph_tab, us)) != cudaSuccess)
     return bail(cuda_fail(ctx, e, "uploading tables"));
-  {
-    std::vector<float2> U((size_t)8 * kQ * 9);
-    for (int j = 0; j < 8; ++j) {
-      const double step = (j < 3 ? pi / 2.0 : 2.0 * pi) / (double)kQ;
-      for (int m = 0; m < kQ; ++m) {
-        float cv[8], sv[8];
-        for (int k = 0; k < 8; ++k) {
-          cv[k] = 1.0f;
-          sv[k] = 0.0f;
-        }
-        const double ang = (double)m * step;
-        cv[j] = (float)std::cos(ang);
-        sv[j] = (float)std::sin(ang);
-        su3_binary32(cv, sv, &U[((size_t)j * kQ + m) * 9]);
-      }
-    }
-    e = cudaMemcpyAsync(ctx->g.su3_tab, U.data(), U.size() * sizeof(float2),
-                        cudaMemcpyHostToDevice, us);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
-    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "uploading the SU(3) table"));
-  }
   std::vector<Best> recs(n_probs);
   std::vector<RankJob> jobs(n_probs);
   std::vector<uint32_t> single(n_probs * 5);

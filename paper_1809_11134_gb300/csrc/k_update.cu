@@ -15,8 +15,7 @@
 // A segment belongs to exactly one role, so no segment is touched twice.
 // All mutation arithmetic is binary32 with _rn intrinsics in the order the
 // oracle fixes (no contraction), so the state stays bit-identical to it; the
-// SU(3) operator of Eq. (12) for each (parameter, level) pair is precomputed on
-// the host in the same order (capi.cu).
+// SU(3) operator of Eq. (12) is evaluated per segment in that order (su3).
 #include "qe_dev.cuh"
 #include "qe_host.h"
 
@@ -47,6 +46,38 @@ __device__ __forceinline__ fc fsubc(fc a, fc b) {
 }
 __device__ __forceinline__ fc fscale(fc a, float s) { return {__fmul_rn(a.re, s), __fmul_rn(a.im, s)}; }
 __device__ __forceinline__ fc fneg(fc a) { return {-a.re, -a.im}; }
+
+// Eq. (12) in binary32 with parameter j (0..2: theta_1..3, 3..7: phi_1..5) at
+// cos/sin (c, s) and every other parameter zero (cos 1, sin 0): phase factors
+// e^{i(+-a +-b ...)} are products of the single-parameter phases taken left
+// to right, real factors applied left to right, every operation rounded on
+// its own -- the evaluation order of the oracle, so each entry is the
+// oracle's bit for bit.  (Evaluated per segment: a table of every (j, level)
+// pair would cost 72 scattered bytes per mutated segment.)
+__device__ __forceinline__ void su3(uint32_t j, float c, float s, fc (&U)[9]) {
+  float cv[8], sv[8];
+#pragma unroll
+  for (uint32_t k = 0; k < 8; ++k) {
+    cv[k] = k == j ? c : 1.f;
+    sv[k] = k == j ? s : 0.f;
+  }
+  const float c1 = cv[0], c2 = cv[1], c3 = cv[2], s1 = sv[0], s2 = sv[1], s3 = sv[2];
+  auto ep = [&](int k) { return fc{cv[2 + k], sv[2 + k]}; };
+  auto em = [&](int k) { return fc{cv[2 + k], -sv[2 + k]}; };
+  U[0] = fscale(fscale(ep(1), c1), c2);
+  U[1] = fscale(ep(3), s1);
+  U[2] = fscale(fscale(ep(4), c1), s2);
+  U[3] = fsubc(fscale(fscale(fmulc(em(4), em(5)), s2), s3),
+               fscale(fscale(fscale(fmulc(fmulc(ep(1), ep(2)), em(3)), s1), c2), c3));
+  U[4] = fscale(fscale(ep(2), c1), c3);
+  U[5] = fsubc(fneg(fscale(fscale(fmulc(em(1), em(5)), c2), s3)),
+               fscale(fscale(fscale(fmulc(fmulc(ep(2), em(3)), ep(4)), s1), s2), c3));
+  U[6] = fsubc(fneg(fscale(fscale(fmulc(em(2), em(4)), s2), c3)),
+               fscale(fscale(fscale(fmulc(fmulc(ep(1), em(3)), ep(5)), s1), c2), s3));
+  U[7] = fscale(fscale(ep(5), c1), s3);
+  U[8] = fsubc(fscale(fscale(fmulc(em(1), em(2)), c2), c3),
+               fscale(fscale(fscale(fmulc(fmulc(em(3), ep(4)), ep(5)), s1), s2), s3));
+}
 
 __device__ __forceinline__ bool mutates(const DevProblem &p, uint32_t i, uint32_t gen) {
   const uint4 v = draw(p, i, 0, gen, kStMutDecide);
@@ -89,17 +120,12 @@ __device__ __forceinline__ void mutate(const DevProblem &p, const DevGlobal &g, 
     cp[1] = b;
     return;
   }
-  // qutrit: one Eq. (12) parameter set to a draw from its domain times (1 - f);
-  // U comes from the host-built table of every (parameter, level) pair
+  // qutrit: one Eq. (12) parameter set to a draw from its domain times (1 - f)
   const uint32_t j = below(w.y, 8);
   const uint32_t m = (uint32_t)floorf(__fmul_rn(__fmul_rn(unit32(w.z), e), (float)kQ));
-  const float2 *Ut = g.su3_tab + ((size_t)j * kQ + m) * 9;
+  const float2 cs = __ldg((j < 3 ? g.th_tab : g.ph_tab) + m);
   fc U[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const float2 u = __ldg(Ut + k);
-    U[k] = {u.x, u.y};
-  }
+  su3(j, cs.x, cs.y, U);
   const fc q[3] = {{a.x, a.y}, {a.z, a.w}, {b.x, b.y}};
   fc o[3];
 #pragma unroll
@@ -143,27 +169,37 @@ __global__ void __launch_bounds__(256, 8) k_update_elite(const DevProblem *__res
     if (seg >= p.nseg) continue;  // caller-provided ids are checked
     const uint32_t i = (seg % p.LP) / p.L;
     if (mutates(p, i, gen)) continue;
-    const float4 *line = cur_of(p, seg);
-    float4 c0, c1, b0, b1;
-    ld_rec(line, c0, c1);
-    ld_rec(line + 2, b0, b1);
     // best fitness and fitness key in one 64-bit atomic that clears the key
     // (low word: best_f bits, high word: key); one slot per segment sees it set
     const unsigned long long pr =
         atomicAnd(reinterpret_cast<unsigned long long *>(p.fk + 2 * (size_t)seg), 0xffffffffull);
     const float bf = __uint_as_float((uint32_t)pr);
     const uint32_t key = (uint32_t)(pr >> 32);
-    if (key) elitism(p, seg, fkey_inv(key), bf, c0, c1, b0, b1);
+    if (!key) continue;
+    // only the record that is copied is read: cur when it becomes the best,
+    // else best, which replaces cur
+    const float sf = fkey_inv(key);
+    float4 *line = cur_of(p, seg);
+    float4 r0, r1;
+    if (sf > bf) {
+      ld_rec(line, r0, r1);
+      st_rec(best_of(p, seg), r0, r1);
+      *bestf_of(p, seg) = sf;
+    } else {
+      ld_rec(line + 2, r0, r1);
+      st_rec(line, r0, r1);
+    }
   }
 }
 
 // Role A with four lanes per slot, for large populations, where role A is
 // bound by the number of scattered requests in flight rather than by their
-// latency: lane q of a quad moves the 16-B quarter q of the segment's 64-B line
-// (cur low, cur high, best low, best high), so every request covers whole
-// sectors of one line, and lane 0 of the quad takes the {best_f, key} word.
-// Elitism then copies a record through one shuffle: best <- cur on lanes 2, 3
-// (from lanes 0, 1), cur <- best on lanes 0, 1 (from lanes 2, 3).
+// latency: lane 0 of a quad takes the {best_f, key} word first; then the two
+// lanes holding the record that is copied read its 16-B halves (lanes 0, 1:
+// cur; lanes 2, 3: best, the quarters of the segment's 64-B line) and elitism
+// copies it through one shuffle: best <- cur on lanes 2, 3 (from lanes 0, 1),
+// cur <- best on lanes 0, 1 (from lanes 2, 3).  Each request covers whole
+// sectors, and the record that is not copied is never read.
 __global__ void __launch_bounds__(256, 8) k_update_elite4(const DevProblem *__restrict__ probs,
                                                           const uint32_t *__restrict__ group,
                                                           const uint32_t *__restrict__ prefA,
@@ -189,26 +225,27 @@ __global__ void __launch_bounds__(256, 8) k_update_elite4(const DevProblem *__re
       act = seg < pp->nseg;  // caller-provided ids are checked
       if (act) act = !mutates(*pp, (seg % pp->LP) / pp->L, gen);
     }
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     unsigned long long pr = 0;
-    if (act) {
-      v = cur_of(*pp, seg)[q4];
-      // best fitness and fitness key in one 64-bit atomic that clears the key
-      if (q4 == 0)
-        pr = atomicAnd(reinterpret_cast<unsigned long long *>(pp->fk + 2 * (size_t)seg),
-                       0xffffffffull);
-    }
+    // best fitness and fitness key in one 64-bit atomic that clears the key
+    if (act && q4 == 0)
+      pr = atomicAnd(reinterpret_cast<unsigned long long *>(pp->fk + 2 * (size_t)seg),
+                     0xffffffffull);
     pr = __shfl_sync(kFull, pr, qbase);
+    const uint32_t key = (uint32_t)(pr >> 32);
+    const float sf = fkey_inv(key), bf = __uint_as_float((uint32_t)pr);
+    const bool up = sf > bf;  // cur becomes the best: lanes 0, 1 read, 2, 3 write
+    // only the record that is copied is read (lanes 0, 1 hold cur's quarters,
+    // lanes 2, 3 best's)
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 *line = act && key ? cur_of(*pp, seg) : nullptr;
+    if (line && (up ? q4 < 2 : q4 >= 2)) v = line[q4];
     float4 o;
     o.x = __shfl_xor_sync(kFull, v.x, 2);
     o.y = __shfl_xor_sync(kFull, v.y, 2);
     o.z = __shfl_xor_sync(kFull, v.z, 2);
     o.w = __shfl_xor_sync(kFull, v.w, 2);
-    const uint32_t key = (uint32_t)(pr >> 32);
-    if (act && key) {
-      const float sf = fkey_inv(key), bf = __uint_as_float((uint32_t)pr);
-      float4 *line = cur_of(*pp, seg);
-      if (sf > bf) {
+    if (line) {
+      if (up) {
         if (q4 >= 2) line[q4] = o;
         if (q4 == 0) *bestf_of(*pp, seg) = sf;
       } else if (q4 < 2) {

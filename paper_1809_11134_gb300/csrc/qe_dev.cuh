@@ -121,7 +121,6 @@ struct DevProblem {
 struct DevGlobal {
   float2 *th_tab;     // cos/sin of m * (pi/2) / Q
   float2 *ph_tab;     // cos/sin of m * (2 pi) / Q
-  float2 *su3_tab;    // Eq. (12) for parameter j at level m: [8][Q][9] complex
   uint32_t *gen;      // generation counter (graph replays read it)
   uint32_t *err;      // error word
   uint32_t *rescore_list;  // (problem << 20 | slot) pairs to rescore in binary64
