@@ -593,6 +593,33 @@ def _stage_rates(qe, torch, searches, gens):
     return ctx, res
 
 
+def _best_error(qe, torch, ctx32, searches, gens):
+    """Run `gens` more generations, then evaluate every search's best-so-far
+    circuit in binary32 (this context) and binary64: the error where the
+    square root of Eq. (11) amplifies the rounding of d (f near 1)."""
+    import numpy as np
+    from paper_1809_11134_gb300 import workloads as W
+    ctx32.step(gens, reports=False)
+    reps = ctx32.step(1)
+    s64 = [W.Search(**{**s.__dict__, "precision": W.PREC_FP64}) for s in searches]
+    ctx64 = qe.Context(s64)
+    out = []
+    for r, (s, rep) in enumerate(zip(searches, reps)):
+        g = torch.tensor([rep["best_gates"]], dtype=torch.uint8, device="cuda")
+        f32 = torch.zeros(1, dtype=torch.float32, device="cuda")
+        f64 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        ctx32.eval(r, g, f32)
+        ctx64.eval(r, g, f64)
+        torch.cuda.synchronize()
+        a, b = float(f32.item()), float(f64.item())
+        out.append({"fitness_fp64": b, "abs_err": abs(a - b),
+                    "d_err": abs((1 - a) ** 2 - (1 - b) ** 2)})
+    ctx64.close()
+    return {"circuits": out, "max_abs_fitness_err_vs_fp64": max(o["abs_err"] for o in out),
+            "d_space_bound": 8e-7 * searches[0].L + 2e-6}
+
+
 def smem_bytes5(s, gate_idx):
     """Shared-memory bytes the 5-qubit binary32 circuit kernel moves for these
     circuits (library indices: [I], then CNOT, CV, CV^dag per ordered wire
@@ -674,13 +701,10 @@ def per_config(qe, torch, args):
                 r["max_abs_fitness_err_vs_fp64"], r["max_abs_unitary_err_vs_fp64"] = fe, ue
                 r["above_0.99"] = {"circuits": hn, "max_abs_fitness_err_vs_fp64": he}
                 if cfg == 2:
-                    # converged searches: most of the population sits near f = 1
-                    ctx.step(300, reports=False)
-                    fe, ue, he, hn = _fp32_error(qe, torch, ctx, searches)
-                    r["after_320_generations"] = {
-                        "max_abs_fitness_err_vs_fp64": fe, "above_0.99": {
-                            "circuits": hn, "max_abs_fitness_err_vs_fp64": he,
-                            "d_space_bound": 8e-7 * searches[0].L + 2e-6}}
+                    # near f = 1: the searches' best circuits after 320 generations
+                    # (the Toffoli and Peres searches reach exact circuits)
+                    r["best_circuits_after_320_generations"] = _best_error(
+                        qe, torch, ctx, searches, 300)
             ctx.close()
             res["fp32" if prec else "fp64"] = r
         res["fp32_over_fp64_circuit_kernel"] = (res["fp32"]["circuit_kernel_circuits_per_s"] /

@@ -21,6 +21,10 @@ namespace {
 
 thread_local std::string g_init_error;
 
+// the update's lines per generation that the circuit kernel may prefetch into
+// L2 (half of GB300's 129 MB L2)
+constexpr double kPrefetchBudget = 64.0 * 1024 * 1024;
+
 struct Group {
   bool canon = false;
   bool ising = false;  // the Ising library (slots carry angles)
@@ -716,6 +720,21 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     total_P += P;
     if (PL > max_PL) max_PL = PL;
     if (P > max_P) max_P = P;
+  }
+  // the update's lines of one generation, all searches together: the used
+  // segments' 64-B records and the mutating individuals' records and fitness
+  // words; the circuit kernel prefetches them into L2 only when they fit in
+  // half of it (otherwise they are evicted before the update reads them)
+  {
+    double upd_bytes = 0.0;
+    for (uint32_t i = 0; i < n_probs; ++i) {
+      const DevProblem &d = ctx->hp[i];
+      if (d.enc != QE_ENC_QEQEA) continue;
+      const double PL = (double)d.P * d.L;
+      upd_bytes += PL * 64.0 + d.p_mut * PL * d.R * 72.0;
+    }
+    const uint32_t pf = upd_bytes <= kPrefetchBudget ? 1u : 0u;
+    for (uint32_t i = 0; i < n_probs; ++i) ctx->hp[i].prefetch = pf;
   }
   ar.take(&ctx->d_recs, n_probs * sizeof(Best));
   ar.take(&ctx->d_probs, n_probs * sizeof(DevProblem));

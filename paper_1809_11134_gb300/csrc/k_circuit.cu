@@ -580,10 +580,11 @@ __device__ __forceinline__ void prefetch_l2(const void *ptr) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
 }
 
-// If individual i mutates in this generation, the update will walk all of its
-// R*L segments (their 64-B records and fitness pairs): prefetch them into L2
-// from the circuit kernel, which is instruction-bound, so that the update,
-// which is latency-bound, finds them there.
+// If individual i mutates in this generation, list it for the update, which
+// will walk all of its R*L segments (their 64-B records and fitness pairs);
+// when the update's lines fit in L2 (p.prefetch), prefetch them into L2 from
+// the circuit kernel so that the update, which is latency-bound, finds them
+// there (with more lines than L2 holds they would be evicted before use).
 __device__ __forceinline__ void prefetch_mutated(const DevProblem &p, uint32_t i, uint32_t gen,
                                                  int lane) {
   const uint4 v = draw(p, i, 0, gen, kStMutDecide);
@@ -592,6 +593,7 @@ __device__ __forceinline__ void prefetch_mutated(const DevProblem &p, uint32_t i
   // list the individual for the update's mutation role (any order: the
   // individuals' segments are disjoint)
   if (lane == 0) p.mut_list[(size_t)(gen & 1u) * p.P + atomicAdd(p.mut_cnt + (gen & 1u), 1u)] = i;
+  if (!p.prefetch) return;
   const uint32_t RL = p.R * p.L;
   for (uint32_t x = lane; x < RL; x += 32) {
     const uint32_t r = x / p.L, t = x - r * p.L;
@@ -646,7 +648,7 @@ __device__ __forceinline__ void sample_slot(const DevProblem &p, uint32_t c, uin
   const float4 a = __ldg(cur_of(p, seg));
   const float4 b = __ldg(cur_of(p, seg) + 1);
   // the update reads this segment's best record next: bring it into L2 now
-  prefetch_l2(best_of(p, seg));
+  if (p.prefetch) prefetch_l2(best_of(p, seg));
   const float p0 = __fadd_rn(__fmul_rn(a.x, a.x), __fmul_rn(a.y, a.y));
   const float p1 = __fadd_rn(__fmul_rn(a.z, a.z), __fmul_rn(a.w, a.w));
   const float p2 = __fadd_rn(__fmul_rn(b.x, b.x), __fmul_rn(b.y, b.y));

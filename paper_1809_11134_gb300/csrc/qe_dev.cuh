@@ -73,6 +73,7 @@ struct DevProblem {
   uint32_t ising;          // the Ising library: every slot carries an angle
   uint32_t shots;          // qutrit measurements per slot (1 = one; majority otherwise)
   uint32_t dense;          // the target is the dense unitary tgt32/tgt64, not perm
+  uint32_t prefetch;       // the circuit kernel prefetches the update's lines into L2
   uint32_t key0, key1;
   float eps_d;        // bound on |d32 - d64|, d = (N - |tr|)/N, for the binary32 path
   float pen_per_gate; // cost_weight / L in binary32 (ranking bounds only)
