@@ -912,6 +912,148 @@ __device__ __forceinline__ CircuitOut compose5_smem(const DevProblem &p, int lan
   return out;
 }
 
+// 5-qubit binary32 composition on the Ising library (Sec. III: R_x, R_y, R_z
+// per wire, the interaction templates J_ij per pair) in shared memory, one
+// column per lane as above; the library has no CNOT, so rows are not mapped.
+// Of the 25 ops, the diagonal ones (R_z and every J) are deferred: a diagonal
+// factor D[p] per row, shared by the warp's 32 columns, accumulates their
+// phases (lane p updates D[p]: no row of S is touched), and the next R_x or
+// R_y, which reads every row anyway, multiplies each row by its D[p] as it
+// loads it and then resets D to 1.  A diagonal op thus moves 512 B of shared
+// memory instead of the whole 8 KB column set twice.  Binary32 only: the
+// phases of consecutive diagonal ops are multiplied together before they
+// reach S, which changes the rounding (the binary64 kernels, which match the
+// oracle bit for bit, apply every gate in order).
+template <bool DENSE_OK>
+__device__ __forceinline__ CircuitOut compose5_smem_ising(const DevProblem &p, int lane,
+                                                          uint32_t ops0, uint32_t ops1,
+                                                          float *S_out, float ic0, float is0,
+                                                          float ic1, float is1) {
+  using A = Ar<float, false>;
+  __shared__ float2 s_state[4][32 * 32];
+  __shared__ float2 s_diag[4][32];
+  const int w = (threadIdx.x >> 5) & 3;
+  float2 *col = &s_state[w][lane];
+  float2 *D = s_diag[w];
+  const uint32_t cost = __reduce_add_sync(kFull, (ops0 != kOpIdentity) + (ops1 != kOpIdentity));
+  const uint32_t work = __reduce_add_sync(kFull, op_work(p, (int)ops0) + op_work(p, (int)ops1));
+  __syncwarp();  // the previous circuit's reads of D
+#pragma unroll
+  for (int r = 0; r < 32; ++r) col[r << 5] = make_float2(r == lane ? 1.f : 0.f, 0.f);
+  bool pending = false;  // D holds phases not yet applied to S
+  const uint32_t L = p.L;
+  for (uint32_t t = 0; t < L; ++t) {
+    const uint32_t src = t < 32 ? ops0 : ops1;
+    const int op = __shfl_sync(kFull, (int)src, (int)(t & 31));
+    if (op == kOpIdentity) continue;
+    const float c = __shfl_sync(kFull, t < 32 ? ic0 : ic1, (int)(t & 31));
+    const float sn = __shfl_sync(kFull, t < 32 ? is0 : is1, (int)(t & 31));
+    const int o = op & 0x7f;
+    if (o >= kOpIsingJ || (o - kOpIsingRot) % 3 == 2) {
+      // R_z on wire w (row bit tb): rows with bit 0 take c - i s, bit 1 c + i s;
+      // J on wires (i, j): c - i s where the two bits agree, c + i s elsewhere
+      int tb, ib = -1;
+      if (o >= kOpIsingJ) {
+        int q = o - kOpIsingJ, i = 0;
+        while (q >= 4 - i) {
+          q -= 4 - i;
+          ++i;
+        }
+        tb = 4 - (i + 1 + q);
+        ib = 4 - i;
+      } else {
+        tb = 4 - (o - kOpIsingRot) / 3;
+      }
+      int odd = (lane >> tb) & 1;
+      if (ib >= 0) odd ^= (lane >> ib) & 1;
+      const float ds = odd ? -sn : sn;
+      float2 v = pending ? D[lane] : make_float2(1.f, 0.f);
+      A::phase(v.x, v.y, c, ds);
+      D[lane] = v;
+      pending = true;
+      continue;
+    }
+    // R_x or R_y on wire w: row pairs (r, r | 1 << tb), each row first taking
+    // its pending phase
+    const int k = (o - kOpIsingRot) % 3;
+    const int tb = 4 - (o - kOpIsingRot) / 3;
+    if (pending) __syncwarp();  // the lanes' writes of D
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+      const int r0 = ((i >> tb) << (tb + 1)) | (i & ((1 << tb) - 1));
+      const int r1 = r0 | (1 << tb);
+      float2 x = col[r0 << 5], y = col[r1 << 5];
+      if (pending) {
+        const float2 d0 = D[r0], d1 = D[r1];
+        const float xr = x.x, yr = y.x;
+        x.x = d0.x * xr - d0.y * x.y;
+        x.y = d0.x * x.y + d0.y * xr;
+        y.x = d1.x * yr - d1.y * y.y;
+        y.y = d1.x * y.y + d1.y * yr;
+      }
+      const float2 x0 = x, y0 = y;
+      if (k == 0) {
+        A::rx_lane(x.x, x.y, y0.x, y0.y, c, sn);
+        A::rx_lane(y.x, y.y, x0.x, x0.y, c, sn);
+      } else {
+        A::ry_lane(x.x, x.y, y0.x, y0.y, false, c, sn);
+        A::ry_lane(y.x, y.y, x0.x, x0.y, true, c, sn);
+      }
+      col[r0 << 5] = x;
+      col[r1 << 5] = y;
+    }
+    if (pending) {
+      __syncwarp();  // every lane has read D
+      D[lane] = make_float2(1.f, 0.f);
+      pending = false;
+    }
+  }
+  if (pending) __syncwarp();
+  // the logical rows of S with their pending phases
+  auto row = [&](int i) {
+    float2 v = col[i << 5];
+    if (pending) {
+      const float2 d = D[i];
+      const float vr = v.x;
+      v.x = d.x * vr - d.y * v.y;
+      v.y = d.x * v.y + d.y * vr;
+    }
+    return v;
+  };
+  CircuitOut out;
+  out.cost = cost;
+  out.work = work + 2u * 32u;
+  out.bad = false;
+  const int j = lane;
+  if (S_out) {
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+      const float2 v = row(i);
+      S_out[2 * (i * 32 + j)] = v.x;
+      S_out[2 * (i * 32 + j) + 1] = v.y;
+    }
+  }
+  float vr = 0.f, vi = 0.f;
+  const bool dense = DENSE_OK && p.dense != 0;
+  if (!dense) {
+    const float2 v = row(p.perm[j]);
+    vr = v.x;
+    vi = v.y;
+  } else {
+    out.work += 8u * 32u * 32u - 2u * 32u;
+    for (int i = 0; i < 32; ++i) {
+      const float2 v = row(i);
+      const float2 tt = __ldg(p.tgt32 + i * 32 + j);
+      vr = fmaf(v.x, tt.x, fmaf(v.y, tt.y, vr));
+      vi = fmaf(v.x, tt.y, fmaf(-v.y, tt.x, vi));
+    }
+  }
+  const double pen =
+      p.cost_weight == 0.0 ? 0.0 : __dmul_rn(p.cost_weight, __ddiv_rn((double)cost, (double)p.L));
+  out.F = fitness32(p, vr, vi, pen, 32);
+  return out;
+}
+
 // ops0/ops1: this lane's op bytes for slots lane and lane + 32
 // ic0/is0, ic1/is1: cos/sin of theta/2 of this lane's slots (Ising)
 // DENSE_OK = false compiles the dense-target score out (permutation targets only)
@@ -921,6 +1063,9 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
                                                     R is0 = R(0), R ic1 = R(1), R is1 = R(0)) {
   if constexpr (NQ == 5 && !CANON && !ISING) {
     return compose5_smem<DENSE_OK>(p, lane, ops0, ops1, (float *)S_out);
+  } else if constexpr (NQ == 5 && !CANON && ISING) {
+    return compose5_smem_ising<DENSE_OK>(p, lane, ops0, ops1, (float *)S_out, (float)ic0,
+                                         (float)is0, (float)ic1, (float)is1);
   } else {
   using Ly = Lay<NQ>;
   constexpr int N = Ly::N;
@@ -1127,16 +1272,15 @@ __device__ __forceinline__ uint32_t find_problem(const uint32_t *prefix, uint32_
 //
 // The 5-qubit binary32 kernel runs 128-thread blocks (four circuits, 32 KB of
 // shared memory for their unitaries, see compose5_smem): six fit an SM's
-// shared memory, so each thread may use 85 registers.  Its Ising variant
-// keeps the unitary in registers (64 state registers plus the gate
-// temporaries): three blocks per SM, 168 registers, no spills.
+// shared memory, so each thread may use 85 registers (its Ising variant too,
+// with 1 KB more for the deferred diagonal factors).
 template <int NQ, bool CANON>
 constexpr int block_threads() {
   return (NQ == 5 && !CANON) ? 128 : 256;
 }
 template <int NQ, bool CANON, bool ISING>
 constexpr int min_blocks() {
-  return (NQ == 5 && !CANON) ? (ISING ? 3 : 6) : ((NQ <= 3 && !CANON) ? 6 : 1);
+  return (NQ == 5 && !CANON) ? 6 : ((NQ <= 3 && !CANON) ? 6 : 1);
 }
 
 // EXT: the group holds a search measured K > 1 times (k_presample) or one with
@@ -1507,7 +1651,10 @@ cudaError_t query_circuit_occupancy(LaunchCfg &lc) {
   // for the largest shared-memory carveout so that six blocks fit an SM
   const void *smem5[] = {(const void *)k_step<5, float, false, false, false>,
                          (const void *)k_step<5, float, false, false, true>,
-                         (const void *)k_eval<5, float, false, false>};
+                         (const void *)k_eval<5, float, false, false>,
+                         (const void *)k_step<5, float, false, true, false>,
+                         (const void *)k_step<5, float, false, true, true>,
+                         (const void *)k_eval<5, float, false, true>};
   for (const void *f : smem5)
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,

@@ -181,3 +181,37 @@ def test_target_validation_and_checkpoint(qe, torch, tmp_path):
         ctx.eval(0, g, f)
         F, _ = oracle.eval_circuits(oracle_problem(s, 0), g.cpu().numpy())
         assert np.array_equal(f.cpu().numpy(), F)
+
+
+@pytest.mark.parametrize("n,L", [(3, 16), (5, 24), (5, 64)])
+def test_ising_dense_fp64_bit_exact_and_fp32_within_bound(qe, torch, n, L):
+    """The paper's Ising library against a dense target: the 5-qubit binary32
+    kernel defers its diagonal gates (R_z, J) and applies their phases when a
+    rotation next reads the rows, or before the score; binary64 applies every
+    gate in order and matches the oracle bit for bit."""
+    rng = np.random.default_rng(700 + n * 10 + L)
+    G = oracle.num_gates(n, W.LIB_ISING)
+    g0 = rng.integers(0, G, L).astype(np.uint8)
+    th0 = rng.uniform(0, 2 * np.pi, L)
+    a0 = np.stack([np.cos(th0), np.sin(th0)], -1).astype(np.float32)
+    re, im = oracle.compose(n, W.LIB_ISING, g0, a0)
+    T = re + 1j * im
+    nc = 300
+    s64 = W.Search(n, L, nc, W.LIB_ISING, W.cknot(n), precision=W.PREC_FP64, target=T)
+    s32 = W.Search(n, L, nc, W.LIB_ISING, W.cknot(n), precision=W.PREC_FP32, target=T)
+    gates = rng.integers(0, G, (nc, L)).astype(np.uint8)
+    gates[0] = g0  # one circuit that reaches the target exactly
+    th = rng.uniform(0, 2 * np.pi, (nc, L))
+    amps = np.stack([np.cos(th), np.sin(th)], -1).astype(np.float32)
+    amps[0] = a0
+    F, _ = oracle.eval_circuits(oracle_problem(s64, 0), gates, amps)
+    assert F[0] > 1 - 1e-6
+    g = torch.from_numpy(gates).cuda()
+    a = torch.from_numpy(amps).cuda()
+    with qe.Context([s64, s32]) as ctx:
+        f64 = torch.zeros(nc, dtype=torch.float64, device="cuda")
+        ctx.eval(0, g, f64, amps=a)
+        assert np.array_equal(f64.cpu().numpy(), F)
+        f32 = torch.zeros(nc, dtype=torch.float32, device="cuda")
+        ctx.eval(1, g, f32, amps=a)
+        assert_fp32_fitness(f32.cpu().numpy().astype(np.float64), F, s32)
