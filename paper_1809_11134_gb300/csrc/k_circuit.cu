@@ -1096,20 +1096,26 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
       inv |= (uint32_t)w << (3 * (4 - w));
     }
   }
-  for (uint32_t t = 0; t < L; ++t) {
-    const uint32_t src = t < 32 ? ops0 : ops1;
-    const int op = __shfl_sync(kFull, (int)src, (int)(t & 31));
-    if (op == kOpIdentity) continue;
-    R ic = R(1), is = R(0);
-    if constexpr (ISING) {
-      ic = __shfl_sync(kFull, t < 32 ? ic0 : ic1, (int)(t & 31));
-      is = __shfl_sync(kFull, t < 32 ? is0 : is1, (int)(t & 31));
-    }
-    if constexpr (kMap5) {
-      apply5<ISING, R, CANON>(op, pos, inv, re, im, ic, is);
-    } else {
-      const R s = (op & kOpNeg) ? R(-1) : R(1);
-      dispatch<NQ, R, CANON, ISING>(op & 0x7f, re, im, lane, s, ic, is);
+  // the non-identity slots in ascending order: slots 0..31 from the lanes'
+  // ops0, then 32..63 from ops1 (slots at or beyond L carry kOpIdentity)
+  for (int half = 0; half < (L > 32u ? 2 : 1); ++half) {
+    const uint32_t src = half ? ops1 : ops0;
+    uint32_t m = __ballot_sync(kFull, src != kOpIdentity);
+    while (m) {
+      const int t = __ffs(m) - 1;
+      m &= m - 1;
+      const int op = __shfl_sync(kFull, (int)src, t);
+      R ic = R(1), is = R(0);
+      if constexpr (ISING) {
+        ic = __shfl_sync(kFull, half ? ic1 : ic0, t);
+        is = __shfl_sync(kFull, half ? is1 : is0, t);
+      }
+      if constexpr (kMap5) {
+        apply5<ISING, R, CANON>(op, pos, inv, re, im, ic, is);
+      } else {
+        const R s = (op & kOpNeg) ? R(-1) : R(1);
+        dispatch<NQ, R, CANON, ISING>(op & 0x7f, re, im, lane, s, ic, is);
+      }
     }
   }
   if constexpr (kMap5 && !kMapped) restore5(pos, inv, re, im);
