@@ -59,7 +59,10 @@ class TorchComm:
 
 
 class QeShardDevice:
-    """One search of a qe.Context on this rank's GPU (discrete libraries)."""
+    """One search of a qe.Context on this rank's GPU (discrete libraries).
+
+    The library runs on the context's stream, torch (allocations, the
+    collectives) on its current stream: each call orders the two both ways."""
 
     def __init__(self, ctx, prob=0):
         import torch
@@ -68,29 +71,46 @@ class QeShardDevice:
         self.P, self.L = s.P, s.L
         self.fp64 = s.precision == 0
         self.device = torch.device("cuda", torch.cuda.current_device())
-        self.gates = torch.zeros(self.P * self.L, dtype=torch.uint8, device=self.device)
-        self.seg = torch.zeros(self.P * self.L, dtype=torch.int32, device=self.device)
+        self.stream = ctx.stream if ctx.stream is not None else torch.cuda.current_stream()
+        self.gates = torch.empty(self.P * self.L, dtype=torch.uint8, device=self.device)
+        self.seg = torch.empty(self.P * self.L, dtype=torch.int32, device=self.device)
+
+    def _enter(self):
+        import torch
+        self.stream.wait_stream(torch.cuda.current_stream())
+
+    def _leave(self):
+        import torch
+        torch.cuda.current_stream().wait_stream(self.stream)
 
     def sample(self, gen):
+        self._enter()
         self.ctx.sample(self.prob, gen, self.gates, self.seg)
+        self._leave()
         return self.gates, self.seg
 
     def evaluate(self, gates, lo, hi):
         import torch
         n = hi - lo
-        f = torch.zeros(n, dtype=torch.float64 if self.fp64 else torch.float32, device=self.device)
-        c = torch.zeros(n, dtype=torch.int32, device=self.device)
+        f = torch.empty(n, dtype=torch.float64 if self.fp64 else torch.float32, device=self.device)
+        c = torch.empty(n, dtype=torch.int32, device=self.device)
         if n:
             g = gates[lo * self.L:hi * self.L]
+            self._enter()
             self.ctx.eval(self.prob, g, f, n_circuits=n, cost=c)
+            self._leave()
         return f, c
 
     def rank(self, gates, fitness, cost):
+        self._enter()
         return self.ctx.rank(self.prob, gates, fitness, cost, n_circuits=self.P)
 
     def update(self, gen, seg, fitness):
         import torch
-        self.ctx.update(self.prob, gen, seg, fitness.to(torch.float64))
+        f64 = fitness.to(torch.float64)
+        self._enter()
+        self.ctx.update(self.prob, gen, seg, f64)
+        self._leave()
 
     def state(self):
         return self.ctx.get_state(self.prob)

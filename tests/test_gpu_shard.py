@@ -25,9 +25,11 @@ def env():
     return qe, shard, torch
 
 
-def _run_sharded(qe, shard, torch, s, ws, gens):
-    stream = torch.cuda.current_stream()
-    ctxs = [qe.Context([s], stream=stream) for _ in range(ws)]
+def _run_sharded(qe, shard, torch, s, ws, gens, own_streams=False):
+    # own_streams: every context on a stream of its own, not torch's current
+    # one (the device wrapper orders the two)
+    ctxs = [qe.Context([s], stream=torch.cuda.Stream() if own_streams
+                       else torch.cuda.current_stream()) for _ in range(ws)]
     runs = [shard.ShardedSearch(shard.QeShardDevice(c), rank=r, world=ws)
             for r, c in enumerate(ctxs)]
     traj = []
@@ -45,13 +47,13 @@ def _run_sharded(qe, shard, torch, s, ws, gens):
     return traj, states
 
 
-@pytest.mark.parametrize("ws", [2, 3])
-def test_sharded_binary64_search_is_the_oracles_trajectory(env, ws):
+@pytest.mark.parametrize("ws,own", [(2, False), (3, False), (2, True)])
+def test_sharded_binary64_search_is_the_oracles_trajectory(env, ws, own):
     qe, shard, torch = env
     s = W.Search(3, 16, 1000, W.LIB_NCV | W.LIB_HT | W.LIB_IDENTITY, W.cknot(3), seed=5,
                  precision=W.PREC_FP64, topk=16)
     gens = 5
-    traj, states = _run_sharded(qe, shard, torch, s, ws, gens)
+    traj, states = _run_sharded(qe, shard, torch, s, ws, gens, own_streams=own)
     p = oracle_problem(s, 0)
     cur, best, bf = oracle.init_state(p)
     rep = oracle.new_report()
