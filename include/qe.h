@@ -210,9 +210,10 @@ qe_status qe_eval(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, uint32_
  * the bound on its binary32 error, and checks every rescored candidate
  * against that bound: a candidate outside it (a fitness that is not the
  * binary32 value of its circuit, or a composition error above the bound)
- * returns QE_ENUMERIC with QE_ERRW_GUARD_BAND in the message's sense, as do
- * invalid gates and non-finite fitness.  n_circuits <= P; synchronises; a
- * pending generation's ranking is finished first. */
+ * makes the call return QE_ENUMERIC (error word bit QE_ERRW_GUARD_BAND; the
+ * message says so), as do invalid gates and non-finite fitness.
+ * n_circuits <= P; synchronises; a pending generation's ranking is finished
+ * first. */
 qe_status qe_rank(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx, const float *d_amps,
                   const void *d_fitness, const uint32_t *d_cost, uint32_t n_circuits,
                   qe_ranked *h_topk);
