@@ -1264,7 +1264,7 @@ __device__ __forceinline__ uint32_t find_problem(const uint32_t *prefix, uint32_
   uint32_t lo = 0, hi = n;
   while (hi - lo > 1) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (prefix[mid] <= x) lo = mid;
+    if (__ldg(prefix + mid) <= x) lo = mid;
     else hi = mid;
   }
   return lo;
@@ -1297,17 +1297,12 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
                                               const uint32_t *__restrict__ prefix,
                                               uint32_t n_group, uint32_t total, DevGlobal g) {
   const int lane = threadIdx.x & 31;
-  // the group's prefix sums in shared memory (launched with n_group * 4 bytes
-  // of dynamic shared memory): each circuit's binary search stays on chip
-  extern __shared__ uint32_t s_prefix[];
-  for (uint32_t i = threadIdx.x; i < n_group; i += blockDim.x) s_prefix[i] = prefix[i];
-  __syncthreads();
   const uint32_t gen = *g.gen;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
-    const uint32_t q = find_problem(s_prefix, n_group, w);
+    const uint32_t q = find_problem(prefix, n_group, w);
     const DevProblem &p = probs[group[q]];
-    const uint32_t c = w - s_prefix[q];
+    const uint32_t c = w - prefix[q];
     const uint32_t par = gen & 1u;  // generation buffer
     uint8_t *gate_idx = p.gate_idx + (size_t)par * p.P * p.L;
     uint32_t o0 = kOpIdentity, o1 = kOpIdentity, seg0 = 0, seg1 = 0;
@@ -1550,11 +1545,10 @@ cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs
   {                                                                                       \
     constexpr int bt = block_threads<NQ, C>();                                            \
     const dim3 grid = grid_for(lc, total, per, bt / 32);                                  \
-    const size_t sm = (size_t)n_group * sizeof(uint32_t);                                 \
     if (ext)                                                                              \
-      k_step<NQ, R, C, I, true><<<grid, bt, sm, st>>>(probs, group, prefix, n_group, total, g); \
+      k_step<NQ, R, C, I, true><<<grid, bt, 0, st>>>(probs, group, prefix, n_group, total, g); \
     else                                                                                  \
-      k_step<NQ, R, C, I, false><<<grid, bt, sm, st>>>(probs, group, prefix, n_group, total, g); \
+      k_step<NQ, R, C, I, false><<<grid, bt, 0, st>>>(probs, group, prefix, n_group, total, g); \
   }
 #define QE_L(NQ)                                                                          \
   if (canon) {                                                                            \

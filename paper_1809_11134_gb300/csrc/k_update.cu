@@ -141,22 +141,11 @@ __device__ __forceinline__ void mutate(const DevProblem &p, const DevGlobal &g, 
   st_rec(cp, a, b);
 }
 
-// the group's prefix sums in shared memory (a binary search per slot over
-// global memory would be a chain of dependent loads for each of them, with
-// 1024 searches ten); the kernels are launched with n * 4 bytes of dynamic
-// shared memory
-__device__ __forceinline__ const uint32_t *stage_prefix(const uint32_t *prefix, uint32_t n) {
-  extern __shared__ uint32_t s_prefix[];
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_prefix[i] = prefix[i];
-  __syncthreads();
-  return s_prefix;
-}
-
 __device__ __forceinline__ uint32_t find_q(const uint32_t *prefix, uint32_t n, uint32_t x) {
   uint32_t lo = 0, hi = n;
   while (hi - lo > 1) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (prefix[mid] <= x) lo = mid;
+    if (__ldg(prefix + mid) <= x) lo = mid;
     else hi = mid;
   }
   return lo;
@@ -169,14 +158,13 @@ __global__ void __launch_bounds__(256, 8) k_update_elite(const DevProblem *__res
                                                          uint32_t n_group, uint32_t totalA,
                                                          const uint32_t *d_gen, uint32_t gen_arg,
                                                          const uint32_t *seg_override) {
-  const uint32_t *s_pref = stage_prefix(prefA, n_group);
   wait_predecessor();  // the circuit kernel's ids, keys and lists
   const uint32_t gen = d_gen ? *d_gen : gen_arg;
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < totalA;
        e += gridDim.x * blockDim.x) {
-    const uint32_t q = find_q(s_pref, n_group, e);
+    const uint32_t q = find_q(prefA, n_group, e);
     const DevProblem &p = probs[group[q]];
-    const uint32_t local = e - s_pref[q];
+    const uint32_t local = e - prefA[q];
     const uint32_t seg = seg_override ? seg_override[local] : p.seg_id[local];
     if (seg >= p.nseg) continue;  // caller-provided ids are checked
     const uint32_t i = (seg % p.LP) / p.L;
@@ -218,7 +206,6 @@ __global__ void __launch_bounds__(256, 8) k_update_elite4(const DevProblem *__re
                                                           uint32_t n_group, uint32_t totalA,
                                                           const uint32_t *d_gen, uint32_t gen_arg,
                                                           const uint32_t *seg_override) {
-  const uint32_t *s_pref = stage_prefix(prefA, n_group);
   wait_predecessor();  // the circuit kernel's ids, keys and lists
   const uint32_t gen = d_gen ? *d_gen : gen_arg;
   const int lane = threadIdx.x & 31, q4 = lane & 3, qbase = lane & ~3;
@@ -231,9 +218,9 @@ __global__ void __launch_bounds__(256, 8) k_update_elite4(const DevProblem *__re
     uint32_t seg = 0;
     bool act = e < totalA;
     if (act) {
-      const uint32_t q = find_q(s_pref, n_group, e);
+      const uint32_t q = find_q(prefA, n_group, e);
       pp = probs + group[q];
-      const uint32_t local = e - s_pref[q];
+      const uint32_t local = e - prefA[q];
       seg = seg_override ? seg_override[local] : pp->seg_id[local];
       act = seg < pp->nseg;  // caller-provided ids are checked
       if (act) act = !mutates(*pp, (seg % pp->LP) / pp->L, gen);
@@ -320,15 +307,14 @@ __global__ void __launch_bounds__(256) k_update_mutate(const DevProblem *__restr
                                                        uint32_t n_group, uint32_t totalB,
                                                        const uint32_t *d_gen, uint32_t gen_arg,
                                                        DevGlobal g) {
-  const uint32_t *s_pref = stage_prefix(prefB, n_group);
   wait_predecessor();  // the circuit kernel's ids, keys and lists
   const uint32_t gen = d_gen ? *d_gen : gen_arg;
   const int lane = threadIdx.x & 31;
   const uint32_t nwB = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < totalB; w += nwB) {
-    const uint32_t q = find_q(s_pref, n_group, w);
+    const uint32_t q = find_q(prefB, n_group, w);
     const DevProblem &p = probs[group[q]];
-    const uint32_t local = w - s_pref[q];
+    const uint32_t local = w - prefB[q];
     const uint32_t groups = (p.P + 31) / 32;
     const uint32_t r = local / groups;
     const uint32_t i0 = (local - r * groups) * 32;
@@ -413,7 +399,6 @@ cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const ui
                           const uint32_t *seg_override, const DevGlobal &g, cudaStream_t stA,
                           cudaStream_t stB) {
   const bool quad = (uint64_t)totalA >= kQuadMinSlots;
-  const size_t smem = (size_t)n_group * sizeof(uint32_t);  // the staged prefix sums
   uint64_t bA = ((uint64_t)totalA * (quad ? 4 : 1) + 255) / 256;
   const uint64_t capA = (uint64_t)lc.num_sms * 8;
   if (bA > capA) bA = capA;
@@ -423,19 +408,19 @@ cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const ui
   if (bB > capB) bB = capB;
   if (!bB) bB = 1;
   if (quad)
-    k_update_elite4<<<(uint32_t)bA, 256, smem, stA>>>(probs, group, prefA, n_group, totalA,
-                                                      d_gen, gen, seg_override);
+    k_update_elite4<<<(uint32_t)bA, 256, 0, stA>>>(probs, group, prefA, n_group, totalA, d_gen,
+                                                   gen, seg_override);
   else
-    k_update_elite<<<(uint32_t)bA, 256, smem, stA>>>(probs, group, prefA, n_group, totalA,
-                                                     d_gen, gen, seg_override);
+    k_update_elite<<<(uint32_t)bA, 256, 0, stA>>>(probs, group, prefA, n_group, totalA, d_gen,
+                                                  gen, seg_override);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (d_gen && n_group <= kListMaxSearches) {
     // generation graph: the circuit kernel listed the mutating individuals
     k_update_mutate_list<<<lc.num_sms * 8, 256, 0, stB>>>(probs, group, n_group, d_gen, g);
   } else {
-    k_update_mutate<<<(uint32_t)bB, 256, smem, stB>>>(probs, group, prefB, n_group, totalB,
-                                                      d_gen, gen, g);
+    k_update_mutate<<<(uint32_t)bB, 256, 0, stB>>>(probs, group, prefB, n_group, totalB, d_gen,
+                                                   gen, g);
   }
   return cudaGetLastError();
 }
