@@ -216,15 +216,17 @@ def cpu_baseline(seconds=10.0):
 
 def workload_name(args):
     return (WORKLOADS.get(args.config, "benchmark search set %d" % args.config)
+            + (" on the paper's Ising gate set" if getattr(args, "library", "discrete") == "ising"
+               else "")
             + ("" if args.population is None else " (P capped at %d)" % args.population)
             + "; one step = one generation")
 
 
-def replica_searches(W, config, population, rank):
+def replica_searches(W, config, population, rank, library=None):
     """The searches one rank runs: the benchmark set, seeds offset by rank so
     that every GPU runs an independent replica (weak scaling, no data-path
-    collective)."""
-    searches = W.config(config, P=population)
+    collective); library=LIB_ISING: the same shapes on the paper's Ising set."""
+    searches = W.config(config, P=population, library=library)
     for s in searches:
         s.seed = s.seed + 1000 * rank
     return searches
@@ -261,7 +263,8 @@ def run_ours(args):
     from paper_1809_11134_gb300 import qe
     from paper_1809_11134_gb300 import workloads as W
 
-    searches = replica_searches(W, args.config, args.population, rank)
+    searches = replica_searches(W, args.config, args.population, rank,
+                                W.LIB_ISING if args.library == "ising" else None)
     n_circ = sum(s.P for s in searches)
     stream = torch.cuda.Stream()
     ctx = qe.Context(searches, stream=stream)
@@ -781,6 +784,9 @@ def main():
     ap.add_argument("--ref-population", type=int, default=512)
     ap.add_argument("--config", type=int, default=2,
                     help="benchmark search set 1-5 (2 = the 3-qubit headline workload)")
+    ap.add_argument("--library", default="discrete", choices=["discrete", "ising"],
+                    help="the benchmark's gate library, or the paper's Ising set on the same "
+                         "shapes (for profiling)")
     ap.add_argument("--population", type=int, default=None,
                     help="cap P (for profiling smaller cases of a configuration)")
     args = ap.parse_args()
