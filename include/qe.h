@@ -244,11 +244,37 @@ qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
  * allocates device staging (and pinned host staging for the top-k lists) that
  * the context keeps until qe_destroy.  Pinned host buffers make the copies
  * asynchronous with respect to other host work.  Invalid gate indices give
- * NaN fitness and, when h_topk is given, QE_ENUMERIC (else the error bit, as
- * qe_eval).  A pending generation's ranking is finished first. */
+ * NaN fitness and QE_ENUMERIC (the fitness is still written).  A pending
+ * generation's ranking is finished first.  The evaluations run on a stream of
+ * the context's own (not ordered after other work on the context's stream,
+ * which they do not touch); the ranking runs on the context's stream.
+ * Equivalent to qe_eval_host_batch_async followed by qe_eval_host_batch_wait;
+ * QE_ESTATE if two asynchronous calls are in flight. */
 qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
                              const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
                              void *h_fitness, qe_ranked *h_topk);
+
+/* qe_eval_host_batch without the synchronisation: enqueues the call and
+ * returns a ticket (*ticket, nonzero) for qe_eval_host_batch_wait.  The
+ * context has two staging slots, each with its own stream and graphs, so two
+ * calls can be in flight: the second call's gate copy and evaluations run
+ * while the first call's ranking does (every ranking runs on the context's
+ * stream, in call order).  Until its wait returns, a call still reads
+ * h_gate_idx and writes h_fitness and h_topk: the caller keeps them alive and
+ * untouched, and gives two calls in flight distinct buffers.  h_probs and
+ * h_n_circuits are read before return.  Arguments are checked as by
+ * qe_eval_host_batch; QE_ESTATE when both slots are in flight, QE_EINVAL for a
+ * NULL ticket.  Each slot's graphs follow the layout of its last call, so
+ * alternating two fixed layouts replays captured graphs. */
+qe_status qe_eval_host_batch_async(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
+                                   const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
+                                   void *h_fitness, qe_ranked *h_topk, uint64_t *ticket);
+
+/* Waits for the call with this ticket, fills its h_topk and frees its slot;
+ * QE_ENUMERIC as qe_eval_host_batch; QE_EINVAL for a ticket that is not in
+ * flight (never issued, or already waited for).  Calls may be waited for in
+ * any order. */
+qe_status qe_eval_host_batch_wait(qe_ctx *ctx, uint64_t ticket);
 
 /* The composed unitaries themselves: d_unitary receives n_circuits row-major
  * N x N complex matrices, (re, im) interleaved, float for QE_PREC_FP32 and

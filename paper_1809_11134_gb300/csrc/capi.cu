@@ -44,6 +44,30 @@ struct Plan {
   bool concurrent = false;   // circuit kernels of different widths on parallel streams
 };
 
+// One slot of the batched host evaluation: device staging (grown on
+// demand), pinned host staging of the top-k lists, the graphs of the last
+// layout (key: ranking flag, item count, the items' problems and circuit
+// counts) -- the evaluations, run on the slot's stream, and the ranking, run
+// on the context's stream after them -- and the call in flight.
+struct BatchSlot {
+  void *d = nullptr;
+  size_t d_bytes = 0;
+  void *h = nullptr;
+  size_t h_bytes = 0;
+  std::vector<uint32_t> key;
+  std::vector<unsigned char> meta;  // host copy of the jobs, offsets and gate table
+  cudaGraph_t eg = nullptr, rg = nullptr;
+  cudaGraphExec_t ex = nullptr, rx = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev_eval = nullptr, ev_fit = nullptr, ev_done = nullptr;
+  size_t err_off = 0;  // the slot's error word in its staging
+  // the call in flight
+  bool busy = false;
+  uint64_t ticket = 0;
+  qe_ranked *h_topk = nullptr;
+  size_t k_total = 0;
+};
+
 struct qe_ctx {
   int device = 0;
   cudaStream_t user = nullptr;
@@ -81,17 +105,10 @@ struct qe_ctx {
   Best *h_recs = nullptr;  // pinned
   uint8_t *d_stage_gates = nullptr;
   void *d_stage_fit = nullptr;
-  // qe_eval_host_batch: device staging (grown on demand), pinned host staging
-  // of the top-k lists, and the graph of the last batch layout (key: ranking
-  // flag, item count, the items' problems and circuit counts)
-  void *d_batch = nullptr;
-  size_t d_batch_bytes = 0;
-  void *h_batch = nullptr;
-  size_t h_batch_bytes = 0;
-  std::vector<uint32_t> batch_key;
-  std::vector<unsigned char> batch_meta;  // host copy of the jobs, offsets and gate table
-  cudaGraph_t bgraph = nullptr;
-  cudaGraphExec_t bexec = nullptr;
+  // qe_eval_host_batch(_async): two slots, so that one call's copies and
+  // evaluations overlap the previous call's ranking
+  BatchSlot bslot[2];
+  uint64_t next_ticket = 1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   // launch plan of the generation graph (qe_autotune picks it by timing)
@@ -587,10 +604,19 @@ const char *qe_last_error(const qe_ctx *ctx) {
 
 void qe_destroy(qe_ctx *ctx) {
   if (!ctx) return;
-  if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
-  if (ctx->bgraph) cudaGraphDestroy(ctx->bgraph);
-  if (ctx->d_batch) cudaFree(ctx->d_batch);
-  if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
+  for (BatchSlot &b : ctx->bslot) {
+    if (b.st) cudaStreamSynchronize(b.st);
+    if (b.ex) cudaGraphExecDestroy(b.ex);
+    if (b.rx) cudaGraphExecDestroy(b.rx);
+    if (b.eg) cudaGraphDestroy(b.eg);
+    if (b.rg) cudaGraphDestroy(b.rg);
+    if (b.d) cudaFree(b.d);
+    if (b.h) cudaFreeHost(b.h);
+    if (b.ev_eval) cudaEventDestroy(b.ev_eval);
+    if (b.ev_fit) cudaEventDestroy(b.ev_fit);
+    if (b.ev_done) cudaEventDestroy(b.ev_done);
+    if (b.st) cudaStreamDestroy(b.st);
+  }
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   if (ctx->dexec) cudaGraphExecDestroy(ctx->dexec);
@@ -1089,13 +1115,15 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // error word, the ranking jobs, their top-k offsets, and the per-problem gate
 // table the binary64 rescoring reads.
 struct BatchLayout {
-  size_t gates = 0, fit = 0, cost = 0, topk = 0, jobs = 0, koff = 0, gtab = 0, total = 0;
+  size_t err = 0, gates = 0, fit = 0, cost = 0, topk = 0, jobs = 0, koff = 0, gtab = 0, total = 0;
 };
 
 static BatchLayout batch_layout(size_t gate_bytes, size_t n_total, size_t fb, size_t k_total,
                          size_t n_items, size_t n_probs) {
   BatchLayout b;
   size_t o = 0;
+  b.err = o;  // the slot's device error word
+  o += 256;
   b.gates = o;
   o += align256(gate_bytes ? gate_bytes : 1);
   b.fit = o;
@@ -1114,9 +1142,13 @@ static BatchLayout batch_layout(size_t gate_bytes, size_t n_total, size_t fb, si
   return b;
 }
 
-qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
-                             const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
-                             void *h_fitness, qe_ranked *h_topk) {
+// Enqueue one batched host evaluation in a free slot: the copy of the gates
+// and the evaluations on the slot's stream, the fitness copy back as soon as
+// they finish, the ranking and the top-k copy on the context's stream (where
+// every other use of the ranking scratch is ordered).
+static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
+                              const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
+                              void *h_fitness, qe_ranked *h_topk, uint64_t *ticket) {
   if (!ctx) return fail(nullptr, QE_EINVAL, "null context");
   if (ctx->poisoned) return fail(ctx, QE_ESTATE, "context is poisoned by an earlier CUDA error");
   const uint32_t np = (uint32_t)ctx->probs.size();
@@ -1143,9 +1175,23 @@ qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_pr
   }
   if ((gate_bytes && !h_gate_idx) || (n_total && !h_fitness))
     return fail(ctx, QE_EINVAL, "null buffer");
+  BatchSlot *slot = nullptr;
+  for (BatchSlot &b : ctx->bslot)
+    if (!b.busy) {
+      slot = &b;
+      break;
+    }
+  if (!slot) return fail(ctx, QE_ESTATE, "two batched calls are in flight: wait for one first");
+  BatchSlot &b = *slot;
   const size_t fb = prec == 0 ? 8 : 4;
   const bool rank = h_topk != nullptr;
   cudaStream_t us = ctx->user;
+  if (!b.st) {
+    QE_CUDA(ctx, cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking));
+    QE_CUDA(ctx, cudaEventCreateWithFlags(&b.ev_eval, cudaEventDisableTiming));
+    QE_CUDA(ctx, cudaEventCreateWithFlags(&b.ev_fit, cudaEventDisableTiming));
+    QE_CUDA(ctx, cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming));
+  }
   // the ranking scratch may still hold the last generation's pending ranking
   qe_status st = drain(ctx);
   if (st != QE_OK) return st;
@@ -1159,27 +1205,34 @@ qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_pr
     key.push_back(h_probs[m]);
     key.push_back(h_n_circuits[m]);
   }
-  const bool regrow = lay.total > ctx->d_batch_bytes;
-  if (regrow || key != ctx->batch_key || !ctx->bexec) {
-    if (ctx->bexec) cudaGraphExecDestroy(ctx->bexec);
-    if (ctx->bgraph) cudaGraphDestroy(ctx->bgraph);
-    ctx->bexec = nullptr;
-    ctx->bgraph = nullptr;
-    ctx->batch_key.clear();
+  const bool regrow = lay.total > b.d_bytes;
+  if (regrow || key != b.key || !b.ex) {
+    if (b.ex) cudaGraphExecDestroy(b.ex);
+    if (b.rx) cudaGraphExecDestroy(b.rx);
+    if (b.eg) cudaGraphDestroy(b.eg);
+    if (b.rg) cudaGraphDestroy(b.rg);
+    b.ex = b.rx = nullptr;
+    b.eg = b.rg = nullptr;
+    b.key.clear();
     if (regrow) {
-      QE_CUDA(ctx, cudaStreamSynchronize(us));
-      if (ctx->d_batch) cudaFree(ctx->d_batch);
-      ctx->d_batch = nullptr;
-      ctx->d_batch_bytes = 0;
-      QE_CUDA(ctx, cudaMalloc(&ctx->d_batch, lay.total));
-      ctx->d_batch_bytes = lay.total;
+      QE_CUDA(ctx, cudaStreamSynchronize(b.st));
+      if (b.d) cudaFree(b.d);
+      b.d = nullptr;
+      b.d_bytes = 0;
+      QE_CUDA(ctx, cudaMalloc(&b.d, lay.total));
+      b.d_bytes = lay.total;
+      QE_CUDA(ctx, cudaMemsetAsync((char *)b.d + lay.err, 0, 4, b.st));
     }
-    char *base = (char *)ctx->d_batch;
+    b.err_off = lay.err;
+    char *base = (char *)b.d;
+    // this slot's copy of the context's device pointers, with its own error word
+    DevGlobal gs = ctx->g;
+    gs.err = (uint32_t *)(base + lay.err);
     // jobs, top-k offsets and the gate table, uploaded once per layout
-    ctx->batch_meta.assign(lay.total - lay.jobs, 0);
-    RankJob *hj = (RankJob *)ctx->batch_meta.data();
-    uint32_t *hk = (uint32_t *)(ctx->batch_meta.data() + (lay.koff - lay.jobs));
-    const uint8_t **hg = (const uint8_t **)(ctx->batch_meta.data() + (lay.gtab - lay.jobs));
+    b.meta.assign(lay.total - lay.jobs, 0);
+    RankJob *hj = (RankJob *)b.meta.data();
+    uint32_t *hk = (uint32_t *)(b.meta.data() + (lay.koff - lay.jobs));
+    const uint8_t **hg = (const uint8_t **)(b.meta.data() + (lay.gtab - lay.jobs));
     std::vector<uint32_t> items;  // items with circuits (ranked)
     size_t go = 0, fo = 0, ko = 0;
     std::vector<size_t> goff(n_items), foff(n_items);
@@ -1208,10 +1261,9 @@ qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_pr
     }
     const uint32_t n_jobs = (uint32_t)items.size();
     hk[n_jobs] = (uint32_t)ko;
-    QE_CUDA(ctx, cudaMemcpyAsync(base + lay.jobs, ctx->batch_meta.data(), ctx->batch_meta.size(),
-                                 cudaMemcpyHostToDevice, us));
-    // the device part of a call: the evaluations (spread over three captured
-    // streams), then the ranking of every item with circuits
+    QE_CUDA(ctx, cudaMemcpyAsync(base + lay.jobs, b.meta.data(), b.meta.size(),
+                                 cudaMemcpyHostToDevice, b.st));
+    // the evaluations, spread over three captured streams
     cudaStream_t cs = ctx->cap;
     cudaStream_t lanes[3] = {cs, ctx->side, ctx->side2};
     QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -1223,31 +1275,12 @@ qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_pr
       e = launch_eval(ctx->lc, d.n, ctx->d_probs, h_probs[m], prec == 0,
                       (const uint8_t *)(base + lay.gates + goff[m]), nullptr, h_n_circuits[m],
                       base + lay.fit + foff[m] * fb, (uint32_t *)(base + lay.cost) + foff[m],
-                      nullptr, ctx->g, lanes[x % 3]);
+                      nullptr, gs, lanes[x % 3]);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join2, 0);
-    if (rank && n_jobs) {
-      const RankJob *dj = (const RankJob *)(base + lay.jobs);
-      if (e == cudaSuccess) e = launch_reset_counter(ctx->g, cs);
-      if (e == cudaSuccess) e = launch_rank_select(ctx->d_probs, dj, n_jobs, RankJob{}, ctx->g, cs);
-      if (prec != 0) {
-        uint32_t widths = 0;
-        for (uint32_t x = 0; x < n_jobs; ++x) widths |= 1u << ctx->hp[h_probs[items[x]]].n;
-        for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
-          if (e == cudaSuccess && ((widths >> nq) & 1))
-            e = launch_rescore(ctx->lc, nq, false, ctx->d_probs, nullptr, nullptr, false, ctx->g,
-                               cs, (const uint8_t *const *)(base + lay.gtab));
-      }
-      if (e == cudaSuccess) e = launch_rank_sort(ctx->d_probs, dj, n_jobs, RankJob{}, ctx->g, cs);
-      if (e == cudaSuccess) e = launch_reset_counter(ctx->g, cs);
-    }
-    if (rank && e == cudaSuccess)
-      e = launch_gather_topk(ctx->d_probs, (const RankJob *)(base + lay.jobs),
-                             (const uint32_t *)(base + lay.koff), n_jobs,
-                             (Ranked *)(base + lay.topk), ctx->g, cs);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e != cudaSuccess) {
@@ -1255,43 +1288,125 @@ qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_pr
       return cuda_fail(ctx, e, "capturing the batch evaluation graph");
     }
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
-    ctx->bgraph = graph;
-    qe_status pst = add_pdl_edges(ctx, graph);
-    if (pst != QE_OK) return pst;
-    QE_CUDA(ctx, cudaGraphInstantiate(&ctx->bexec, graph, 0));
-    ctx->batch_key = key;
+    b.eg = graph;
+    QE_CUDA(ctx, cudaGraphInstantiate(&b.ex, graph, 0));
+    // the ranking of every item with circuits and the gathered top-k lists
+    if (rank) {
+      QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      const RankJob *dj = (const RankJob *)(base + lay.jobs);
+      e = cudaSuccess;
+      if (n_jobs) {
+        e = launch_reset_counter(gs, cs);
+        if (e == cudaSuccess) e = launch_rank_select(ctx->d_probs, dj, n_jobs, RankJob{}, gs, cs);
+        if (prec != 0) {
+          uint32_t widths = 0;
+          for (uint32_t x = 0; x < n_jobs; ++x) widths |= 1u << ctx->hp[h_probs[items[x]]].n;
+          for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
+            if (e == cudaSuccess && ((widths >> nq) & 1))
+              e = launch_rescore(ctx->lc, nq, false, ctx->d_probs, nullptr, nullptr, false, gs,
+                                 cs, (const uint8_t *const *)(base + lay.gtab));
+        }
+        if (e == cudaSuccess) e = launch_rank_sort(ctx->d_probs, dj, n_jobs, RankJob{}, gs, cs);
+        if (e == cudaSuccess) e = launch_reset_counter(gs, cs);
+      }
+      if (e == cudaSuccess)
+        e = launch_gather_topk(ctx->d_probs, dj, (const uint32_t *)(base + lay.koff), n_jobs,
+                               (Ranked *)(base + lay.topk), gs, cs);
+      graph = nullptr;
+      e2 = cudaStreamEndCapture(cs, &graph);
+      if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ctx, e, "capturing the batch ranking graph");
+      }
+      if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+      b.rg = graph;
+      qe_status pst = add_pdl_edges(ctx, graph);
+      if (pst != QE_OK) return pst;
+      QE_CUDA(ctx, cudaGraphInstantiate(&b.rx, graph, 0));
+    }
+    b.key = key;
   }
-  const size_t hb = (k_total + 1) * sizeof(Ranked);
-  if (rank && hb > ctx->h_batch_bytes) {
-    if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
-    ctx->h_batch = nullptr;
-    ctx->h_batch_bytes = 0;
-    QE_CUDA(ctx, cudaHostAlloc(&ctx->h_batch, hb, cudaHostAllocDefault));
-    ctx->h_batch_bytes = hb;
+  // pinned host staging: the top-k lists and, after them, the error word
+  // (the gathered lists end with it; without a ranking it is copied alone)
+  const size_t kt = rank ? k_total : 0;
+  const size_t hb = (kt + 1) * sizeof(Ranked);
+  if (hb > b.h_bytes) {
+    if (b.h) cudaFreeHost(b.h);
+    b.h = nullptr;
+    b.h_bytes = 0;
+    QE_CUDA(ctx, cudaHostAlloc(&b.h, hb, cudaHostAllocDefault));
+    b.h_bytes = hb;
   }
-  char *base = (char *)ctx->d_batch;
+  char *base = (char *)b.d;
   if (gate_bytes)
-    QE_CUDA(ctx, cudaMemcpyAsync(base + lay.gates, h_gate_idx, gate_bytes, cudaMemcpyHostToDevice, us));
-  QE_CUDA(ctx, cudaGraphLaunch(ctx->bexec, us));
+    QE_CUDA(ctx, cudaMemcpyAsync(base + lay.gates, h_gate_idx, gate_bytes, cudaMemcpyHostToDevice,
+                                 b.st));
+  QE_CUDA(ctx, cudaGraphLaunch(b.ex, b.st));
+  QE_CUDA(ctx, cudaEventRecord(b.ev_eval, b.st));
   if (n_total)
-    QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, base + lay.fit, n_total * fb, cudaMemcpyDeviceToHost, us));
-  if (rank)
-    QE_CUDA(ctx, cudaMemcpyAsync(ctx->h_batch, base + lay.topk, hb, cudaMemcpyDeviceToHost, us));
-  QE_CUDA(ctx, cudaStreamSynchronize(us));
-  if (!rank) return QE_OK;
-  const Ranked *r = (const Ranked *)ctx->h_batch;
-  for (size_t s = 0; s < k_total; ++s) {
-    h_topk[s].circuit = r[s].circuit;
-    h_topk[s].cost = r[s].cost;
-    h_topk[s].fitness = r[s].fitness;
+    QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, base + lay.fit, n_total * fb, cudaMemcpyDeviceToHost,
+                                 b.st));
+  if (!rank)
+    QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.err, 4, cudaMemcpyDeviceToHost, b.st));
+  QE_CUDA(ctx, cudaEventRecord(b.ev_fit, b.st));
+  QE_CUDA(ctx, cudaStreamWaitEvent(us, b.ev_eval, 0));
+  if (rank) {
+    QE_CUDA(ctx, cudaGraphLaunch(b.rx, us));
+    QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.topk, hb, cudaMemcpyDeviceToHost, us));
   }
-  const uint32_t errw = r[k_total].circuit;
+  QE_CUDA(ctx, cudaEventRecord(b.ev_done, us));
+  b.busy = true;
+  b.ticket = ctx->next_ticket++;
+  b.h_topk = h_topk;
+  b.k_total = kt;
+  if (ticket) *ticket = b.ticket;
+  return QE_OK;
+}
+
+// Wait for a slot's call and hand out its top-k lists and error status.
+static qe_status batch_complete(qe_ctx *ctx, BatchSlot &b) {
+  b.busy = false;
+  QE_CUDA(ctx, cudaEventSynchronize(b.ev_fit));
+  QE_CUDA(ctx, cudaEventSynchronize(b.ev_done));
+  const Ranked *r = (const Ranked *)b.h;
+  for (size_t s = 0; s < b.k_total; ++s) {
+    b.h_topk[s].circuit = r[s].circuit;
+    b.h_topk[s].cost = r[s].cost;
+    b.h_topk[s].fitness = r[s].fitness;
+  }
+  const uint32_t errw = r[b.k_total].circuit;
   if (errw) {
-    QE_CUDA(ctx, cudaMemsetAsync(ctx->g.err, 0, 4, us));
-    QE_CUDA(ctx, cudaStreamSynchronize(us));
+    QE_CUDA(ctx, cudaMemsetAsync((char *)b.d + b.err_off, 0, 4, b.st));
+    QE_CUDA(ctx, cudaStreamSynchronize(b.st));
     return fail(ctx, QE_ENUMERIC, errw_text(errw));
   }
   return QE_OK;
+}
+
+qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
+                             const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
+                             void *h_fitness, qe_ranked *h_topk) {
+  uint64_t t = 0;
+  qe_status st = batch_submit(ctx, n_items, h_probs, h_n_circuits, h_gate_idx, h_fitness, h_topk,
+                              &t);
+  if (st != QE_OK) return st;
+  return qe_eval_host_batch_wait(ctx, t);
+}
+
+qe_status qe_eval_host_batch_async(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
+                                   const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
+                                   void *h_fitness, qe_ranked *h_topk, uint64_t *ticket) {
+  if (!ticket) return fail(ctx, QE_EINVAL, "null ticket");
+  return batch_submit(ctx, n_items, h_probs, h_n_circuits, h_gate_idx, h_fitness, h_topk,
+                      ticket);
+}
+
+qe_status qe_eval_host_batch_wait(qe_ctx *ctx, uint64_t ticket) {
+  if (!ctx) return fail(nullptr, QE_EINVAL, "null context");
+  if (ctx->poisoned) return fail(ctx, QE_ESTATE, "context is poisoned by an earlier CUDA error");
+  for (BatchSlot &b : ctx->bslot)
+    if (b.busy && b.ticket == ticket) return batch_complete(ctx, b);
+  return fail(ctx, QE_EINVAL, "no batched call in flight with this ticket");
 }
 
 static qe_status compose_impl(qe_ctx *ctx, uint32_t prob, const uint8_t *d_gate_idx,

@@ -29,7 +29,8 @@ QE_ERRW_BAD_GATE, QE_ERRW_NONFINITE, QE_ERRW_GUARD_BAND = 1, 2, 4
 # every symbol include/qe.h declares
 EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_amp", "qe_rank",
            "qe_eval_host",
-           "qe_eval_host_batch", "qe_compose", "qe_compose_amp",
+           "qe_eval_host_batch", "qe_eval_host_batch_async", "qe_eval_host_batch_wait",
+           "qe_compose", "qe_compose_amp",
            "qe_update", "qe_step", "qe_last_generation", "qe_state_bytes", "qe_get_state",
            "qe_set_state", "qe_generation", "qe_autotune", "qe_launch_plan", "qe_stage_timing",
            "qe_stage_times", "qe_measure_alu_peaks", "qe_save", "qe_load", "qe_checkpoint_info",
@@ -85,6 +86,9 @@ def lib():
         L.qe_eval_host.argtypes = [vp, u32, vp, u32, vp, C.POINTER(qe_ranked)]
         L.qe_eval_host_batch.argtypes = [vp, u32, C.POINTER(u32), C.POINTER(u32), vp, vp,
                                          C.POINTER(qe_ranked)]
+        L.qe_eval_host_batch_async.argtypes = [vp, u32, C.POINTER(u32), C.POINTER(u32), vp, vp,
+                                               C.POINTER(qe_ranked), C.POINTER(u64)]
+        L.qe_eval_host_batch_wait.argtypes = [vp, u64]
         L.qe_compose.argtypes = [vp, u32, vp, u32, vp]
         L.qe_eval_amp.argtypes = [vp, u32, vp, vp, u32, vp, vp, C.POINTER(qe_ranked)]
         L.qe_compose_amp.argtypes = [vp, u32, vp, vp, u32, vp]
@@ -314,6 +318,21 @@ class Context:
         return _check(self.h, lib().qe_eval_host_batch(self.h, len(probs_arr), probs_arr, n_arr,
                                                        C.c_void_p(h_gates_ptr),
                                                        C.c_void_p(h_fit_ptr), topk_buf))
+
+    def eval_host_batch_async_ptr(self, probs_arr, n_arr, h_gates_ptr, h_fit_ptr,
+                                  topk_buf=None):
+        """qe_eval_host_batch_async on raw host pointers; returns the ticket.  The
+        buffers must stay alive and untouched until eval_host_batch_wait(ticket)."""
+        t = C.c_uint64()
+        _check(self.h, lib().qe_eval_host_batch_async(self.h, len(probs_arr), probs_arr, n_arr,
+                                                      C.c_void_p(h_gates_ptr),
+                                                      C.c_void_p(h_fit_ptr), topk_buf,
+                                                      C.byref(t)))
+        return t.value
+
+    def eval_host_batch_wait(self, ticket):
+        """qe_eval_host_batch_wait: the call's fitness and top-k buffers are filled."""
+        return _check(self.h, lib().qe_eval_host_batch_wait(self.h, C.c_uint64(ticket)))
 
     def compose(self, prob, gate_idx, unitary, n_circuits=None, amps=None):
         import torch

@@ -272,3 +272,148 @@ def test_batch_many_searches_of_every_width(qe, prec):
         for (q, g), f, t in zip(items, fits, tops):
             assert len(f) == len(g)
             check_item(ss[q], g, f, t)
+
+
+class _Call:
+    """Pinned buffers of one asynchronous batched call (items = [(prob, gates)])."""
+
+    def __init__(self, qe, ss, items):
+        import ctypes as C
+        import torch
+        self.items = items
+        self.ns = [len(g) for _, g in items]
+        self.ks = [min(max(ss[q].topk, 1), n) for (q, _), n in zip(items, self.ns)]
+        flat = np.concatenate([g.ravel() for _, g in items])
+        self.hg = torch.from_numpy(flat).pin_memory()
+        fp64 = ss[items[0][0]].precision == W.PREC_FP64
+        self.hf = torch.full((max(sum(self.ns), 1),), -7.0,
+                             dtype=torch.float64 if fp64 else torch.float32).pin_memory()
+        self.tops = (qe.qe_ranked * max(sum(self.ks), 1))()
+        self.probs = (C.c_uint32 * len(items))(*[q for q, _ in items])
+        self.counts = (C.c_uint32 * len(items))(*self.ns)
+
+    def submit(self, ctx):
+        return ctx.eval_host_batch_async_ptr(self.probs, self.counts, self.hg.data_ptr(),
+                                             self.hf.data_ptr(), self.tops)
+
+    def results(self):
+        fits, tops, fo, ko = [], [], 0, 0
+        for n, k in zip(self.ns, self.ks):
+            fits.append(self.hf[fo:fo + n].numpy().copy())
+            tops.append([(t.circuit, t.cost, t.fitness) for t in self.tops[ko:ko + k]])
+            fo += n
+            ko += k
+        return fits, tops
+
+
+@pytest.mark.parametrize("prec", [W.PREC_FP32, W.PREC_FP64])
+def test_async_calls_in_flight_match_the_oracle(qe, prec):
+    """two asynchronous calls in flight (different layouts, waited for in both
+    orders, a slot reused with a new layout and with its old one), every result
+    against the oracle and against the synchronous call"""
+    ss = searches(prec)
+    rng = np.random.default_rng(41 + prec)
+    plans = [[(0, 1000), (1, 300)], [(4, 4096), (2, 130), (3, 33)], [(1, 17), (0, 999)],
+             [(0, 1000), (1, 300)], [(2, 77)], [(4, 4095), (0, 5)]]
+    calls = [_Call(qe, ss, [(q, gates_for(ss[q], n, rng)) for q, n in plan]) for plan in plans]
+    with qe.Context(ss) as ctx:
+        for a, b, first in ((0, 1, 0), (2, 3, 1), (4, 5, 0)):
+            ta, tb = calls[a].submit(ctx), calls[b].submit(ctx)
+            assert ta != tb
+            order = (ta, tb) if first == 0 else (tb, ta)
+            for t in order:
+                ctx.eval_host_batch_wait(t)
+        for c in calls:
+            fits, tops = c.results()
+            for (q, g), f, t in zip(c.items, fits, tops):
+                check_item(ss[q], g, f, t)
+            fits2, tops2 = ctx.eval_host_batch(c.items, topk=True)
+            for f, t, f2, t2 in zip(fits, tops, fits2, tops2):
+                assert np.array_equal(f.view(np.uint8), f2.view(np.uint8))
+                assert t == t2
+
+
+def test_async_slot_and_ticket_errors(qe):
+    """a third call while two are in flight is QE_ESTATE, the ticket of a call
+    already waited for or never issued is QE_EINVAL; the calls in flight are
+    not disturbed and the context stays usable"""
+    ss = searches(W.PREC_FP32)
+    rng = np.random.default_rng(43)
+    calls = [_Call(qe, ss, [(0, gates_for(ss[0], 500, rng))]),
+             _Call(qe, ss, [(1, gates_for(ss[1], 300, rng))]),
+             _Call(qe, ss, [(2, gates_for(ss[2], 64, rng))])]
+    with qe.Context(ss) as ctx:
+        t0, t1 = calls[0].submit(ctx), calls[1].submit(ctx)
+        with pytest.raises(qe.QeError) as e:
+            calls[2].submit(ctx)
+        assert e.value.status == qe.QE_ESTATE
+        with pytest.raises(qe.QeError) as e:
+            ctx.eval_host_batch(calls[2].items, topk=True)
+        assert e.value.status == qe.QE_ESTATE
+        with pytest.raises(qe.QeError) as e:
+            ctx.eval_host_batch_wait(max(t0, t1) + 100)
+        assert e.value.status == qe.QE_EINVAL
+        ctx.eval_host_batch_wait(t1)
+        with pytest.raises(qe.QeError) as e:
+            ctx.eval_host_batch_wait(t1)
+        assert e.value.status == qe.QE_EINVAL
+        t2 = calls[2].submit(ctx)
+        ctx.eval_host_batch_wait(t0)
+        ctx.eval_host_batch_wait(t2)
+        for c in calls:
+            fits, tops = c.results()
+            for (q, g), f, t in zip(c.items, fits, tops):
+                check_item(ss[q], g, f, t)
+
+
+def test_async_invalid_gate_reported_with_or_without_ranking(qe):
+    """an invalid gate index gives NaN fitness for its circuit and QE_ENUMERIC
+    from the wait, with and without top-k lists; the other call in flight and
+    the slot's next call are exact"""
+    import torch
+    ss = searches(W.PREC_FP32)
+    rng = np.random.default_rng(47)
+    g0 = gates_for(ss[0], 200, rng)
+    g0[13, 2] = 200
+    bad = _Call(qe, ss, [(0, g0)])
+    good = _Call(qe, ss, [(1, gates_for(ss[1], 300, rng))])
+    with qe.Context(ss) as ctx:
+        for ranked in (True, False):
+            tops = bad.tops if ranked else None
+            tb = ctx.eval_host_batch_async_ptr(bad.probs, bad.counts, bad.hg.data_ptr(),
+                                               bad.hf.data_ptr(), tops)
+            tg = good.submit(ctx)
+            with pytest.raises(qe.QeError) as e:
+                ctx.eval_host_batch_wait(tb)
+            assert e.value.status == qe.QE_ENUMERIC
+            ctx.eval_host_batch_wait(tg)
+            f = bad.hf.numpy()
+            assert np.isnan(f[13]) and np.isfinite(np.delete(f[:200], 13)).all()
+            fits, tops2 = good.results()
+            check_item(ss[1], good.items[0][1], fits[0], tops2[0])
+        # the error word was cleared: the slot's next call is clean
+        g0[13, 2] = 0
+        bad.hg.copy_(torch.from_numpy(g0.ravel()))
+        ctx.eval_host_batch_wait(bad.submit(ctx))
+        fits, tops = bad.results()
+        check_item(ss[0], g0, fits[0], tops[0])
+
+
+def test_async_call_across_generations_leaves_the_run_unchanged(qe):
+    """a call in flight while qe_step runs generations (binary64): its results
+    are exact and the run's reports equal those of a run without it"""
+    ss = [W.Search(3, 16, 512, NCV | HT | ID, W.cknot(3), seed=1, precision=W.PREC_FP64,
+                   topk=8),
+          W.Search(4, 12, 256, NCV | HT, W.cknot(4), seed=2, precision=W.PREC_FP64, topk=8)]
+    rng = np.random.default_rng(53)
+    with qe.Context(ss) as a, qe.Context(ss) as b:
+        for gen in range(3):
+            c = _Call(qe, ss, [(1, gates_for(ss[1], 100, rng)), (0, gates_for(ss[0], 512, rng))])
+            t = c.submit(a)
+            ra, rb = a.step(1), b.step(1)
+            assert ra == rb
+            a.eval_host_batch_wait(t)
+            fits, tops = c.results()
+            for (q, g), f, tk in zip(c.items, fits, tops):
+                check_item(ss[q], g, f, tk)
+        assert a.step(1) == b.step(1)
