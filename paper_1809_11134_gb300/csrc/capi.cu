@@ -86,6 +86,7 @@ struct qe_ctx {
   std::vector<Group> groups;  // circuit launches, one per (arithmetic, qubit count)
   // widths with binary32 searches: bit 0 discrete libraries, bit 1 Ising
   uint8_t rescore_nq[QE_MAX_QUBITS + 1] = {0};
+  uint32_t max_P = 0;    // the largest population
   // all QEQEA searches (update launch)
   uint32_t n_upd = 0, upd_totalA = 0, upd_totalB = 0;
   uint32_t *d_upd_ids = nullptr, *d_upd_prefA = nullptr, *d_upd_prefB = nullptr;
@@ -331,7 +332,8 @@ qe_status set_priorities(qe_ctx *ctx, cudaGraph_t graph) {
 // once (many searches), where waiting for all of them to start would delay the
 // circuits instead.
 qe_status add_select_first_edge(qe_ctx *ctx, cudaGraph_t graph) {
-  if (ctx->n_jobs > 2 * ctx->lc.num_sms) return QE_OK;  // see above
+  // see above (two 1024-thread selection CTAs fit an SM)
+  if (select_quarters(ctx->n_jobs, ctx->max_P) > 4u * ctx->lc.num_sms) return QE_OK;
   size_t nn = 0;
   QE_CUDA(ctx, cudaGraphGetNodes(graph, nullptr, &nn));
   std::vector<cudaGraphNode_t> nodes(nn);
@@ -431,7 +433,8 @@ qe_status add_pdl_edges(qe_ctx *ctx, cudaGraph_t graph) {
 // the ranking chain of generation *gen - 1 (select -> binary64 rescoring -> sort)
 cudaError_t enqueue_rank_chain(qe_ctx *ctx, cudaStream_t cs) {
   RankJob none{};
-  cudaError_t e = launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, none, ctx->g, cs);
+  cudaError_t e =
+      launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, none, ctx->g, cs, ctx->max_P);
   for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
     for (int is = 0; is < 2; ++is)
       if (e == cudaSuccess && ((ctx->rescore_nq[nq] >> is) & 1))
@@ -500,7 +503,9 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
   if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ctx->ev_join2, 0);
   mark(6, side);
   // generation g - 1: ranking
-  if (e == cudaSuccess) e = launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, RankJob{}, ctx->g, cs);
+  if (e == cudaSuccess)
+    e = launch_rank_select(ctx->d_probs, ctx->d_jobs, ctx->n_jobs, RankJob{}, ctx->g, cs,
+                           ctx->max_P);
   mark(2, cs);
   for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
     for (int is = 0; is < 2; ++is)
@@ -746,6 +751,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     total_P += P;
     if (PL > max_PL) max_PL = PL;
     if (P > max_P) max_P = P;
+    if (P > ctx->max_P) ctx->max_P = (uint32_t)P;
   }
   // the update's lines of one generation, all searches together: the used
   // segments' 64-B records and the mutating individuals' records and fitness
@@ -1002,7 +1008,7 @@ static qe_status rank_single(qe_ctx *ctx, uint32_t prob, uint32_t n, const void 
   j.update_record = 0;
   cudaStream_t us = ctx->user;
   QE_CUDA(ctx, launch_reset_counter(ctx->g, us));
-  QE_CUDA(ctx, launch_rank_select(ctx->d_probs, nullptr, 1, j, ctx->g, us));
+  QE_CUDA(ctx, launch_rank_select(ctx->d_probs, nullptr, 1, j, ctx->g, us, n));
   if (d.prec != QE_PREC_FP64)
     QE_CUDA(ctx, launch_rescore(ctx->lc, d.n, d.ising != 0, ctx->d_probs, gsrc, asrc, false,
                                 ctx->g, us));
@@ -1297,7 +1303,11 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
       e = cudaSuccess;
       if (n_jobs) {
         e = launch_reset_counter(gs, cs);
-        if (e == cudaSuccess) e = launch_rank_select(ctx->d_probs, dj, n_jobs, RankJob{}, gs, cs);
+        uint32_t max_n = 0;
+        for (uint32_t x = 0; x < n_jobs; ++x)
+          max_n = h_n_circuits[items[x]] > max_n ? h_n_circuits[items[x]] : max_n;
+        if (e == cudaSuccess)
+          e = launch_rank_select(ctx->d_probs, dj, n_jobs, RankJob{}, gs, cs, max_n);
         if (prec != 0) {
           uint32_t widths = 0;
           for (uint32_t x = 0; x < n_jobs; ++x) widths |= 1u << ctx->hp[h_probs[items[x]]].n;

@@ -163,10 +163,10 @@ struct Ar<double, true> {
 };
 
 // ------------------------------------------------------------------ one gate
-template <int NQ, typename R, bool CANON, int KIND, int CW, int TW>
-__device__ __forceinline__ void apply_gate(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>::ROWS],
+template <int NQ, typename R, bool CANON, int KIND, int CW, int TW, int WB = 0>
+__device__ __forceinline__ void apply_gate(R (&re)[Lay<NQ, WB>::ROWS], R (&im)[Lay<NQ, WB>::ROWS],
                                            int lane, R s) {
-  using Ly = Lay<NQ>;
+  using Ly = Lay<NQ, WB>;
   using A = Ar<R, CANON>;
   constexpr int tb = NQ - 1 - TW;                 // target row bit
   constexpr int cb = CW < 0 ? -1 : NQ - 1 - CW;   // control row bit
@@ -174,7 +174,7 @@ __device__ __forceinline__ void apply_gate(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<N
   constexpr bool C_REG = cb >= 0 && cb < Ly::RBR;
   constexpr bool C_LANE = cb >= Ly::RBR;
   bool cl = true;
-  if constexpr (C_LANE) cl = (lane >> (NQ + cb - Ly::RBR)) & 1;
+  if constexpr (C_LANE) cl = (lane >> (Ly::CB + cb - Ly::RBR)) & 1;
 
   if constexpr (KIND == kTx) {
     // diagonal: rows whose target bit is 1 take the phase
@@ -183,7 +183,7 @@ __device__ __forceinline__ void apply_gate(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<N
       for (int r = 0; r < Ly::ROWS; ++r)
         if ((r >> tb) & 1) A::tx(re[r], im[r], s);
     } else {
-      const bool up = (lane >> (NQ + tb - Ly::RBR)) & 1;
+      const bool up = (lane >> (Ly::CB + tb - Ly::RBR)) & 1;
 #pragma unroll
       for (int r = 0; r < Ly::ROWS; ++r) {
         R a = re[r], b = im[r];
@@ -223,7 +223,7 @@ __device__ __forceinline__ void apply_gate(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<N
       }
     }
   } else {
-    constexpr int tl = NQ + tb - Ly::RBR;  // lane bit of the target
+    constexpr int tl = Ly::CB + tb - Ly::RBR;  // lane bit of the target
     const bool up = (lane >> tl) & 1;
 #pragma unroll
     for (int r = 0; r < Ly::ROWS; ++r) {
@@ -247,10 +247,10 @@ __device__ __forceinline__ void apply_gate(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<N
 
 // Ising gate of kind R_x / R_y / R_z on wire TW, or the interaction template on
 // wires (WI, TW); c = cos(theta/2), s = sin(theta/2) of the slot
-template <int NQ, typename R, bool CANON, int KIND, int WI, int TW>
-__device__ __forceinline__ void apply_ising(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>::ROWS],
+template <int NQ, typename R, bool CANON, int KIND, int WI, int TW, int WB = 0>
+__device__ __forceinline__ void apply_ising(R (&re)[Lay<NQ, WB>::ROWS], R (&im)[Lay<NQ, WB>::ROWS],
                                             int lane, R c, R s) {
-  using Ly = Lay<NQ>;
+  using Ly = Lay<NQ, WB>;
   using A = Ar<R, CANON>;
   constexpr int tb = NQ - 1 - TW;  // row bit of wire TW
   constexpr bool T_REG = tb < Ly::RBR;
@@ -260,8 +260,8 @@ __device__ __forceinline__ void apply_ising(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<
     constexpr int ib = KIND == kJzz ? NQ - 1 - WI : 0;
     constexpr bool I_REG = ib < Ly::RBR;
     int lt = 0, li = 0;
-    if constexpr (!T_REG) lt = (lane >> (NQ + tb - Ly::RBR)) & 1;
-    if constexpr (KIND == kJzz && !I_REG) li = (lane >> (NQ + ib - Ly::RBR)) & 1;
+    if constexpr (!T_REG) lt = (lane >> (Ly::CB + tb - Ly::RBR)) & 1;
+    if constexpr (KIND == kJzz && !I_REG) li = (lane >> (Ly::CB + ib - Ly::RBR)) & 1;
 #pragma unroll
     for (int r = 0; r < Ly::ROWS; ++r) {
       const int bt = T_REG ? ((r >> tb) & 1) : lt;
@@ -284,7 +284,7 @@ __device__ __forceinline__ void apply_ising(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<
       }
     }
   } else {
-    constexpr int tl = NQ + tb - Ly::RBR;  // lane bit of the target
+    constexpr int tl = Ly::CB + tb - Ly::RBR;  // lane bit of the target
     const bool up = (lane >> tl) & 1;
 #pragma unroll
     for (int r = 0; r < Ly::ROWS; ++r) {
@@ -320,23 +320,24 @@ constexpr int pair_tgt(int nq, int pr) {
                 : 0;
 }
 
-template <int NQ, typename R, bool CANON, int OP>
-__device__ __forceinline__ void apply_op(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>::ROWS], int lane,
-                                         R s, R ic, R is) {
+template <int NQ, typename R, bool CANON, int OP, int WB = 0>
+__device__ __forceinline__ void apply_op(R (&re)[Lay<NQ, WB>::ROWS], R (&im)[Lay<NQ, WB>::ROWS],
+                                         int lane, R s, R ic, R is) {
   constexpr int NP = NQ * (NQ - 1);
   if constexpr (OP >= kOpIsingJ) {
     constexpr int q = OP - kOpIsingJ;
-    apply_ising<NQ, R, CANON, kJzz, jpair_i(NQ, q), jpair_j(NQ, q)>(re, im, lane, ic, is);
+    apply_ising<NQ, R, CANON, kJzz, jpair_i(NQ, q), jpair_j(NQ, q), WB>(re, im, lane, ic, is);
   } else if constexpr (OP >= kOpIsingRot) {
     constexpr int w = (OP - kOpIsingRot) / 3, k = (OP - kOpIsingRot) % 3;
-    apply_ising<NQ, R, CANON, k == 0 ? kRx : (k == 1 ? kRy : kRz), 0, w>(re, im, lane, ic, is);
+    apply_ising<NQ, R, CANON, k == 0 ? kRx : (k == 1 ? kRy : kRz), 0, w, WB>(re, im, lane, ic,
+                                                                             is);
   } else if constexpr (OP < 2 * NP) {
     constexpr int pr = OP >> 1;
-    apply_gate<NQ, R, CANON, (OP & 1) ? kCvx : kCnot, pair_ctrl(NQ, pr), pair_tgt(NQ, pr)>(
+    apply_gate<NQ, R, CANON, (OP & 1) ? kCvx : kCnot, pair_ctrl(NQ, pr), pair_tgt(NQ, pr), WB>(
         re, im, lane, s);
   } else {
     constexpr int w = (OP - 2 * NP) >> 1;
-    apply_gate<NQ, R, CANON, (OP & 1) ? kTx : kHad, -1, w>(re, im, lane, s);
+    apply_gate<NQ, R, CANON, (OP & 1) ? kTx : kHad, -1, w, WB>(re, im, lane, s);
   }
 }
 
@@ -344,23 +345,23 @@ __device__ __forceinline__ void apply_op(R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>
 #define QE_CASE(k)                                                      \
   case k:                                                               \
     if constexpr (!ISING && (k) < 2 * NQ * NQ)                          \
-      apply_op<NQ, R, CANON, (k)>(re, im, lane, s, ic, is);             \
+      apply_op<NQ, R, CANON, (k), WB>(re, im, lane, s, ic, is);         \
     break;
 // Ising rotations exist for wires < NQ, templates for pairs < NQ (NQ - 1) / 2
 #define QE_ICASE(k)                                                     \
   case kOpIsingRot + (k):                                               \
     if constexpr (ISING && (k) < 3 * NQ)                                \
-      apply_op<NQ, R, CANON, kOpIsingRot + (k)>(re, im, lane, s, ic, is); \
+      apply_op<NQ, R, CANON, kOpIsingRot + (k), WB>(re, im, lane, s, ic, is); \
     break;
 #define QE_JCASE(k)                                                     \
   case kOpIsingJ + (k):                                                 \
     if constexpr (ISING && (k) < NQ * (NQ - 1) / 2)                     \
-      apply_op<NQ, R, CANON, kOpIsingJ + (k)>(re, im, lane, s, ic, is); \
+      apply_op<NQ, R, CANON, kOpIsingJ + (k), WB>(re, im, lane, s, ic, is); \
     break;
 
-template <int NQ, typename R, bool CANON, bool ISING>
-__device__ __forceinline__ void dispatch(int op, R (&re)[Lay<NQ>::ROWS], R (&im)[Lay<NQ>::ROWS],
-                                         int lane, R s, R ic, R is) {
+template <int NQ, typename R, bool CANON, bool ISING, int WB = 0>
+__device__ __forceinline__ void dispatch(int op, R (&re)[Lay<NQ, WB>::ROWS],
+                                         R (&im)[Lay<NQ, WB>::ROWS], int lane, R s, R ic, R is) {
   switch (op) {
     QE_CASE(0) QE_CASE(1) QE_CASE(2) QE_CASE(3) QE_CASE(4) QE_CASE(5) QE_CASE(6) QE_CASE(7)
     QE_CASE(8) QE_CASE(9) QE_CASE(10) QE_CASE(11) QE_CASE(12) QE_CASE(13) QE_CASE(14)
@@ -1054,24 +1055,42 @@ __device__ __forceinline__ CircuitOut compose5_smem_ising(const DevProblem &p, i
   return out;
 }
 
+// the group of 2^WB warps that shares one circuit (binary64, WB > 0): this
+// warp's index in it, the group's named barrier and its shared-memory row of
+// per-column score terms
+struct Split {
+  int sub = 0;
+  int bar = 0;
+  double2 *sv = nullptr;
+};
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // ops0/ops1: this lane's op bytes for slots lane and lane + 32
 // ic0/is0, ic1/is1: cos/sin of theta/2 of this lane's slots (Ising)
 // DENSE_OK = false compiles the dense-target score out (permutation targets only)
-template <int NQ, typename R, bool CANON, bool ISING = false, bool DENSE_OK = true>
+// WB > 0 (binary64 only): this warp composes its 2^-WB share of the columns;
+// the score's terms meet in sp.sv and lane 0 of warp sp.sub == 0 folds them
+// (out.F is valid there only)
+template <int NQ, typename R, bool CANON, bool ISING = false, bool DENSE_OK = true, int WB = 0>
 __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lane, uint32_t ops0,
                                                     uint32_t ops1, R *S_out, R ic0 = R(1),
-                                                    R is0 = R(0), R ic1 = R(1), R is1 = R(0)) {
+                                                    R is0 = R(0), R ic1 = R(1), R is1 = R(0),
+                                                    const Split &sp = Split{}) {
+  static_assert(WB == 0 || CANON, "the column split is a binary64 form");
   if constexpr (NQ == 5 && !CANON && !ISING) {
     return compose5_smem<DENSE_OK>(p, lane, ops0, ops1, (float *)S_out);
   } else if constexpr (NQ == 5 && !CANON && ISING) {
     return compose5_smem_ising<DENSE_OK>(p, lane, ops0, ops1, (float *)S_out, (float)ic0,
                                          (float)is0, (float)ic1, (float)is1);
   } else {
-  using Ly = Lay<NQ>;
+  using Ly = Lay<NQ, WB>;
   constexpr int N = Ly::N;
-  const int j = lane & (N - 1);
-  const int grp = (lane >> NQ) & ((1 << Ly::RBL) - 1);
-  const bool shadow = (lane >> (NQ + Ly::RBL)) != 0;
+  const int j = (sp.sub << Ly::CB) | (lane & ((1 << Ly::CB) - 1));
+  const int grp = (lane >> Ly::CB) & ((1 << Ly::RBL) - 1);
+  const bool shadow = (lane >> (Ly::CB + Ly::RBL)) != 0;
   R re[Ly::ROWS], im[Ly::ROWS];
 #pragma unroll
   for (int r = 0; r < Ly::ROWS; ++r) {
@@ -1086,7 +1105,7 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
   // 5 qubits: wire w starts at physical bit 4 - w (pos), bit b holds wire
   // 4 - b (inv); binary32 translates rows through the map at the output,
   // binary64 restores the identity map after the last gate
-  constexpr bool kMap5 = NQ == 5;
+  constexpr bool kMap5 = NQ == 5 && WB == 0;
   constexpr bool kMapped = NQ == 5 && !CANON;
   uint32_t pos = 0, inv = 0;
   if constexpr (kMap5) {
@@ -1114,7 +1133,7 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
         apply5<ISING, R, CANON>(op, pos, inv, re, im, ic, is);
       } else {
         const R s = (op & kOpNeg) ? R(-1) : R(1);
-        dispatch<NQ, R, CANON, ISING>(op & 0x7f, re, im, lane, s, ic, is);
+        dispatch<NQ, R, CANON, ISING, WB>(op & 0x7f, re, im, lane, s, ic, is);
       }
     }
   }
@@ -1189,7 +1208,8 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
 #pragma unroll
       for (int g2 = 0; g2 < (1 << Ly::RBL); ++g2) {
         if (g2 > 0) {
-          const double ur = __shfl_up_sync(kFull, dr, N), ui = __shfl_up_sync(kFull, di, N);
+          const double ur = __shfl_up_sync(kFull, dr, 1 << Ly::CB);
+          const double ui = __shfl_up_sync(kFull, di, 1 << Ly::CB);
           if (grp == g2) {
             dr = ur;
             di = ui;
@@ -1204,14 +1224,20 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
           }
         }
       }
-      const int last = ((1 << Ly::RBL) - 1) << NQ;
-      for (int jj = 0; jj < N; ++jj) {
-        const double xr = __shfl_sync(kFull, dr, last | jj), xi = __shfl_sync(kFull, di, last | jj);
-        if (lane == 0) {
-          a = __dadd_rn(a, xr);
-          b = __dadd_rn(b, xi);
+      if constexpr (WB > 0) {
+        if (grp == (1 << Ly::RBL) - 1 && !shadow) sp.sv[j] = make_double2(dr, di);
+      } else {
+        const int last = ((1 << Ly::RBL) - 1) << NQ;
+        for (int jj = 0; jj < N; ++jj) {
+          const double xr = __shfl_sync(kFull, dr, last | jj), xi = __shfl_sync(kFull, di, last | jj);
+          if (lane == 0) {
+            a = __dadd_rn(a, xr);
+            b = __dadd_rn(b, xi);
+          }
         }
       }
+    } else if constexpr (WB > 0) {
+      if (!shadow && (p.perm[j] >> Ly::RBR) == grp) sp.sv[j] = make_double2(vr, vi);
     } else {
       for (int jj = 0; jj < N; ++jj) {
         const int owner = ((p.perm[jj] >> Ly::RBR) << NQ) | jj;
@@ -1225,6 +1251,25 @@ __device__ __forceinline__ CircuitOut compose_score(const DevProblem &p, int lan
           }
         }
       }
+    }
+    if constexpr (WB > 0) {
+      // the same sums in the same order (columns ascending), from shared memory
+      named_sync(sp.bar, 32 << WB);
+      if (sp.sub == 0 && lane == 0) {
+        for (int jj = 0; jj < N; ++jj) {
+          const double xr = sp.sv[jj].x, xi = sp.sv[jj].y;
+          if (dense) {
+            a = __dadd_rn(a, xr);
+            b = __dadd_rn(b, xi);
+          } else if (p.fit_kind == 1) {
+            a = __dadd_rn(a, __dadd_rn(__dmul_rn(xr, xr), __dmul_rn(xi, xi)));
+          } else {
+            a = __dadd_rn(a, xr);
+            b = __dadd_rn(b, -xi);
+          }
+        }
+      }
+      named_sync(sp.bar, 32 << WB);  // sp.sv is free for the group's next circuit
     }
     double F = 0.0;
     if (lane == 0) {
@@ -1473,6 +1518,13 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
 // gtab[problem] (a batch of several searches' caller circuits), else gsrc/asrc
 // (NULL = the problem's own generation buffers).  One launch per
 // (qubit count, library kind) present; other entries are skipped.
+// warps per binary64 rescoring candidate, log2: 2 at 3 qubits (one row per
+// lane), 4 at 4 and 5 qubits
+template <int NQ>
+constexpr int rescore_split() {
+  return NQ == 3 ? 1 : (NQ >= 4 ? 2 : 0);
+}
+
 template <int NQ, bool ISING>
 __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ probs,
                                                  const uint8_t *__restrict__ gsrc,
@@ -1480,14 +1532,26 @@ __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ 
                                                  const uint8_t *const *__restrict__ gtab,
                                                  DevGlobal g) {
   wait_predecessor();  // the selection's candidates and chain flag
-  const int lane = threadIdx.x & 31;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  // 2^WB warps per candidate, each composing a share of its columns: a
+  // binary64 instruction of one warp issues once per ~68 cycles on GB300's
+  // thin binary64 pipe, so a candidate's latency shrinks with the warps that
+  // share it (up to the SM's rate, ~3.4 warps' worth)
+  constexpr int WB = rescore_split<NQ>();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = warp >> WB, sub = warp & ((1 << WB) - 1);
+  const uint32_t groups = (blockDim.x >> 5) >> WB;
+  const uint32_t ng = gridDim.x * groups;
+  __shared__ double2 s_terms[256 / 32][32];
+  Split sp;
+  sp.sub = sub;
+  sp.bar = 1 + grp;
+  sp.sv = s_terms[grp];
   if (pipelined && !*g.rank_active) return;
   const uint32_t par = pipelined ? ((*g.gen - 1u) & 1u) : 0u;
   const uint32_t total = *g.rescore_n;
   // entries are dealt block-first (entry w -> block w % gridDim) so that a
   // short queue spreads one binary64 circuit per SM before doubling up
-  for (uint32_t w = blockIdx.x + gridDim.x * (threadIdx.x >> 5); w < total; w += nw) {
+  for (uint32_t w = blockIdx.x + gridDim.x * grp; w < total; w += ng) {
     const uint32_t ent = g.rescore_list[w];
     const DevProblem &p = probs[ent >> 20];
     if (p.n != (uint32_t)NQ || (p.ising != 0) != ISING) continue;
@@ -1509,9 +1573,9 @@ __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ 
       if ((uint32_t)lane + 32 < p.L) half_angle(am[lane + 32].x, am[lane + 32].y, ic1, is1);
     }
     const double F32 = p.cand_f[slot];  // the binary32 fitness the selection ranked by
-    CircuitOut out = compose_score<NQ, double, true, ISING>(p, lane, o0, o1, (double *)nullptr,
-                                                            ic0, is0, ic1, is1);
-    if (lane == 0) {
+    CircuitOut out = compose_score<NQ, double, true, ISING, true, WB>(
+        p, lane, o0, o1, (double *)nullptr, ic0, is0, ic1, is1, sp);
+    if (lane == 0 && sub == 0) {
       p.cand_f[slot] = anybad ? __longlong_as_double(0x7ff8000000000000ll) : out.F;
       // the exactness of the top-k rests on every binary64 fitness lying in the
       // interval its binary32 fitness implies: check it on every candidate

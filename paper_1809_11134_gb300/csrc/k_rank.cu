@@ -8,20 +8,37 @@
 //   top-k; the candidates {F_hi >= tau} are rescored in binary64 (k_rescore in
 //   k_circuit.cu) and sorted by (F desc, cost asc, index asc).  Binary64
 //   searches use the degenerate band F_lo = F_hi = F.
-// One CTA per search does the selection (radix select over the top 24 bits of
-// the F_lo keys, two 4096-bin histogram passes) and, in a second launch, the
-// sort (bitonic, in chunks
-// of up to 2048 so any number of candidates fits in shared memory).
+// The selection is a radix select over the top 24 bits of the F_lo keys (two
+// 4096-bin histogram passes).  Up to kSelClusterFrom circuits per search it
+// runs on one 1024-thread CTA per search; above, on a thread-block cluster of
+// kSelCta CTAs per search: each CTA histograms a contiguous slice of the
+// population, the cluster combines the histograms through distributed shared
+// memory (CTA r sums bins [512 r, 512 r + 512) over all CTAs) and every CTA
+// finds the threshold from the combined counts (the cluster's barriers cost
+// more than they save on small populations).  A later launch sorts the
+// candidates (bitonic, in chunks of up to 2048 so any number fits in shared
+// memory).
+#include <cooperative_groups.h>
+
 #include "qe_dev.cuh"
 #include "qe_host.h"
 
+namespace cg = cooperative_groups;
+
 namespace qe {
 
+// one CTA per search (populations up to kSelClusterFrom circuits)
 constexpr int kRankThreads = 1024;
-constexpr int kSortThreads = 256;
-constexpr int kSortN = 2048;
 constexpr size_t kSelectSmem = (4096 + 2 * 4096) * sizeof(uint32_t);
 constexpr int kKeyCache = 4096;  // circuits whose keys the selection keeps in shared memory
+// a cluster per search (larger populations)
+constexpr uint32_t kSelClusterFrom = 16384;
+constexpr int kSelCta = 8;                    // CTAs per search (one cluster)
+constexpr int kSelThreads = 256;
+constexpr int kSelSlice = 4096 / kSelCta;     // histogram bins each CTA combines
+constexpr int kSelCache = 2048;  // circuits per CTA whose keys stay in shared memory
+constexpr int kSortThreads = 256;
+constexpr int kSortN = 2048;
 
 __device__ __forceinline__ double dkey_inv(unsigned long long k) {
   const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
@@ -84,6 +101,79 @@ __device__ __forceinline__ void find_bin(const uint32_t *hist, uint32_t rem, uin
     if (run < rem && run + h[q] >= rem) {
       *s_bin = 4095 - 4 * tid - q;
       *s_rem = rem - run;
+    }
+    run += h[q];
+  }
+  __syncthreads();
+}
+
+// Combine the cluster's histograms and find the bin where the count taken from
+// the top first reaches rem: this CTA sums its slice of bins over every CTA
+// into tot (block_rank r: bins [kSelSlice r, kSelSlice (r + 1))), then, after
+// a cluster barrier (no histogram is read after it), every CTA locates the
+// slice from the slice totals and the bin inside it from that slice's counts.
+// Returns the bin (0..4095) in *s_bin and the count still wanted inside it in
+// *s_rem.  The caller keeps tot unchanged until the next cluster barrier.
+__device__ __forceinline__ void cluster_find_bin(cg::cluster_group &cl, const uint32_t *hist,
+                                                 uint32_t *tot, uint32_t *s_stot,
+                                                 uint32_t *s_wsum, uint32_t rem,
+                                                 uint32_t *s_bin, uint32_t *s_rem) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t r = cl.block_rank();
+  uint32_t part = 0;
+  for (int i = tid; i < kSelSlice; i += kSelThreads) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int q = 0; q < kSelCta; ++q) v += cl.map_shared_rank(hist, q)[r * kSelSlice + i];
+    tot[i] = v;
+    part += v;
+  }
+  part = __reduce_add_sync(kFull, part);
+  if (lane == 0) s_wsum[wid] = part;
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) t += s_wsum[w];
+    s_stot[kSelCta] = t;  // this CTA's slice total, read by the others
+  }
+  cl.sync();
+  if (tid < kSelCta) s_stot[tid] = cl.map_shared_rank(s_stot, tid)[kSelCta];
+  __syncthreads();
+  // the slice: from the highest (CTA kSelCta - 1) down
+  int sl = 0;
+  uint32_t above = 0;
+  for (int q = kSelCta - 1; q >= 0; --q) {
+    if (above + s_stot[q] >= rem || q == 0) {
+      sl = q;
+      break;
+    }
+    above += s_stot[q];
+  }
+  const uint32_t want = rem - above;
+  // the bin inside it: thread t owns bins kSelSlice-1-2t and kSelSlice-2-2t
+  const uint32_t *ts = cl.map_shared_rank(tot, sl);
+  uint32_t h[2], loc = 0;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    h[q] = ts[kSelSlice - 1 - 2 * tid - q];
+    loc += h[q];
+  }
+  uint32_t v = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += u;
+  }
+  __syncthreads();  // s_wsum is free again
+  if (lane == 31) s_wsum[wid] = v;
+  __syncthreads();
+  uint32_t run = v - loc;
+  for (int w = 0; w < wid; ++w) run += s_wsum[w];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (run < want && run + h[q] >= want) {
+      *s_bin = (uint32_t)(sl * kSelSlice + kSelSlice - 1 - 2 * tid - q);
+      *s_rem = want - run;
     }
     run += h[q];
   }
@@ -262,6 +352,189 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *
   __syncthreads();
   if (p.prec != 0)
     for (uint32_t s = tid; s < M; s += kRankThreads) g.rescore_list[s_base + s] = (jb.prob << 20) | s;
+}
+
+__global__ void __cluster_dims__(kSelCta, 1, 1) __launch_bounds__(kSelThreads)
+    k_rank_select_cl(const DevProblem *__restrict__ probs, const RankJob *__restrict__ jobs,
+                  RankJob single, DevGlobal g) {
+  cg::cluster_group cl = cg::this_cluster();
+  const uint32_t rank = cl.block_rank();
+  RankJob jb = jobs ? jobs[blockIdx.x / kSelCta] : single;
+  const DevProblem &p = probs[jb.prob];
+  if (jb.pipelined) {
+    // the chain of generation gen - 1 runs once: skip when there is none or
+    // when it was already ranked (drained); every CTA takes the same decision,
+    // before any cluster barrier
+    const uint32_t gen = *g.gen;
+    const bool active = gen > 0 && *g.ranked < gen;
+    if (threadIdx.x == 0 && blockIdx.x == 0) *g.rank_active = active ? 1u : 0u;
+    if (!active) return;
+    jb = resolve(jb, p, gen);
+  }
+  const uint32_t n = jb.n;
+  const uint32_t k = p.k < n ? p.k : n;
+  // this CTA's circuits [c_lo, c_hi)
+  const uint32_t chunk = (n + kSelCta - 1) / kSelCta;
+  const uint32_t c_lo = rank * chunk < n ? rank * chunk : n;
+  const uint32_t c_hi = c_lo + chunk < n ? c_lo + chunk : n;
+  const bool cached = chunk <= (uint32_t)kSelCache;
+  __shared__ uint32_t hist[4096];
+  __shared__ uint32_t s_lo[kSelCache], s_hi[kSelCache];
+  __shared__ uint32_t tot[kSelSlice];
+  __shared__ uint32_t s_stot[kSelCta + 1];
+  __shared__ uint32_t s_wsum[32];
+  __shared__ uint32_t s_bin, s_rem, s_cnt, s_base;
+  __shared__ double s_sum[kSelThreads / 32], s_part[kSelCta];
+  __shared__ unsigned long long s_work[kSelThreads / 32], s_pwork[kSelCta];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int b = tid; b < 4096; b += kSelThreads) hist[b] = 0;
+  if (tid == 0) s_cnt = 0;
+  __syncthreads();
+
+  // pass 1: one read of every fitness: keys (cached in shared memory), the
+  // histogram of the top 12 bits of the low keys, the mean and the work.
+  // Histogram updates are aggregated per warp (__match_any_sync): fitness
+  // values are often discrete, and many lanes hit the same bin.
+  // Mean fitness: binary64 searches sum in binary64; binary32 searches sum in
+  // binary32 within each warp and in binary64 across warps, so that their
+  // selection issues almost no binary64 instruction (GB300's binary64 pipe is
+  // thin).
+  double sum = 0.0;
+  float sum32 = 0.f;
+  unsigned long long work = 0;
+  for (uint32_t c0 = c_lo; c0 < c_hi; c0 += kSelThreads) {
+    const uint32_t c = c0 + tid;
+    uint32_t bin = 4096u;
+    if (c < c_hi) {
+      float F;
+      if (p.prec == 0) {
+        const double Fw = ((const double *)jb.fit)[c];
+        F = (float)Fw;
+        sum += Fw;
+      } else {
+        F = ((const float *)jb.fit)[c];
+        sum32 += F;
+      }
+      const uint32_t meta = jb.meta[c];
+      work += meta >> 8;
+      uint32_t lo, hi;
+      bounds(p, jb, c, F, lo, hi);
+      if (cached) {
+        s_lo[c - c_lo] = lo;
+        s_hi[c - c_lo] = hi;
+      }
+      bin = lo >> 20;
+    }
+    const uint32_t peers = __match_any_sync(kFull, bin);
+    if (bin < 4096u && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+  }
+  if (jb.update_record) {
+    if (p.prec == 0) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+    } else {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum32 += __shfl_xor_sync(kFull, sum32, o);
+      sum = (double)sum32;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) work += __shfl_xor_sync(kFull, work, o);
+    if (lane == 0) {
+      s_sum[wid] = sum;
+      s_work[wid] = work;
+    }
+  }
+  cl.sync();  // every CTA's histogram is final; the leader's counter is zero
+
+  // tau = the k-th largest low key with its last 8 bits cleared (top 12 bits,
+  // then the next 12), so tau <= the exact k-th largest and at least k circuits
+  // have F_lo >= tau (a lower tau only adds candidates)
+  cluster_find_bin(cl, hist, tot, s_stot, s_wsum, k, &s_bin, &s_rem);
+  const uint32_t b1 = s_bin, rem = s_rem;
+  for (int b = tid; b < 4096; b += kSelThreads) hist[b] = 0;
+  __syncthreads();
+  for (uint32_t c0 = c_lo; c0 < c_hi; c0 += kSelThreads) {
+    const uint32_t c = c0 + tid;
+    uint32_t bin = 4096u;
+    if (c < c_hi) {
+      uint32_t lo, hi;
+      if (cached) lo = s_lo[c - c_lo];
+      else {
+        const float F = p.prec == 0 ? (float)((const double *)jb.fit)[c] : ((const float *)jb.fit)[c];
+        bounds(p, jb, c, F, lo, hi);
+      }
+      if ((lo >> 20) == b1) bin = (lo >> 8) & 4095u;
+    }
+    const uint32_t peers = __match_any_sync(kFull, bin);
+    if (bin < 4096u && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+  }
+  // every CTA has read the slice counts of the first search (their owner may
+  // now overwrite them) and every fine histogram is final
+  cl.sync();
+  cluster_find_bin(cl, hist, tot, s_stot, s_wsum, rem, &s_bin, &s_rem);
+  const uint32_t tau = (b1 << 20) | (s_bin << 8);
+
+  // candidates: F_hi >= tau, slots from the leader's counter
+  uint32_t *cnt0 = cl.map_shared_rank(&s_cnt, 0);
+  for (uint32_t c0 = c_lo; c0 < c_hi; c0 += kSelThreads) {
+    const uint32_t c = c0 + tid;
+    bool take = false;
+    if (c < c_hi) {
+      uint32_t lo, hi;
+      if (cached) hi = s_hi[c - c_lo];
+      else {
+        const float F = p.prec == 0 ? (float)((const double *)jb.fit)[c] : ((const float *)jb.fit)[c];
+        bounds(p, jb, c, F, lo, hi);
+      }
+      take = hi >= tau;
+    }
+    const uint32_t bal = __ballot_sync(kFull, take);
+    uint32_t wbase = 0;
+    if (lane == 0 && bal) wbase = atomicAdd(cnt0, __popc(bal));
+    wbase = __shfl_sync(kFull, wbase, 0);
+    if (take) {
+      const uint32_t slot = wbase + __popc(bal & ((1u << lane) - 1));
+      p.cand[slot] = c;
+      // binary64 searches: the final value; binary32 searches: the binary32
+      // value, which the rescoring checks against the guard band and replaces
+      p.cand_f[slot] = p.prec == 0 ? ((const double *)jb.fit)[c]
+                                   : (double)((const float *)jb.fit)[c];
+    }
+  }
+  // this CTA's share of the mean and the work, to the leader
+  if (jb.update_record && wid == 0) {
+    double t = lane < kSelThreads / 32 ? s_sum[lane] : 0.0;
+    unsigned long long wt = lane < kSelThreads / 32 ? s_work[lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      t += __shfl_xor_sync(kFull, t, o);
+      wt += __shfl_xor_sync(kFull, wt, o);
+    }
+    if (lane == 0) {
+      cl.map_shared_rank(s_part, 0)[rank] = t;
+      cl.map_shared_rank(s_pwork, 0)[rank] = wt;
+    }
+  }
+  cl.sync();  // every candidate is counted and written; the shares delivered
+  if (rank != 0) return;
+  const uint32_t M = s_cnt;
+  if (tid == 0) {
+    *p.cand_n = M;
+    s_base = (p.prec == 0) ? 0u : atomicAdd(g.rescore_n, M);
+    if (jb.update_record) {
+      double t = 0.0;
+      unsigned long long wt = 0;
+      for (int q = 0; q < kSelCta; ++q) {
+        t += s_part[q];
+        wt += s_pwork[q];
+      }
+      p.rec->mean_fitness = n ? t / (double)n : 0.0;
+      p.rec->useful_flops = wt;
+    }
+  }
+  __syncthreads();
+  if (p.prec != 0)
+    for (uint32_t s = tid; s < M; s += kSelThreads) g.rescore_list[s_base + s] = (jb.prob << 20) | s;
 }
 
 __device__ __forceinline__ bool key_less(unsigned long long ah, unsigned long long al,
@@ -484,9 +757,13 @@ __global__ void k_finish(DevGlobal g) {
 __global__ void k_reset_counter(DevGlobal g) { *g.rescore_n = 0; }
 
 cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
-                               const RankJob &single, const DevGlobal &g, cudaStream_t st) {
+                               const RankJob &single, const DevGlobal &g, cudaStream_t st,
+                               uint32_t max_n) {
   if (!n_jobs) return cudaSuccess;
-  k_rank_select<<<n_jobs, kRankThreads, kSelectSmem, st>>>(probs, jobs, single, g);
+  if (max_n < kSelClusterFrom)
+    k_rank_select<<<n_jobs, kRankThreads, kSelectSmem, st>>>(probs, jobs, single, g);
+  else
+    k_rank_select_cl<<<n_jobs * kSelCta, kSelThreads, 0, st>>>(probs, jobs, single, g);
   return cudaGetLastError();
 }
 
@@ -497,7 +774,9 @@ cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint3
   return cudaGetLastError();
 }
 
-bool is_select_kernel(const void *f) { return f == (const void *)k_rank_select; }
+bool is_select_kernel(const void *f) {
+  return f == (const void *)k_rank_select || f == (const void *)k_rank_select_cl;
+}
 bool rank_kernel_waits(const void *f) {
   return f == (const void *)k_rank_sort || f == (const void *)k_finish ||
          f == (const void *)k_gather_topk;
@@ -506,6 +785,11 @@ bool rank_kernel_waits(const void *f) {
 cudaError_t rank_init() {
   return cudaFuncSetAttribute(k_rank_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kSelectSmem);
+}
+
+// 1024-thread CTAs of a selection launch, in quarters of an SM's threads
+uint32_t select_quarters(uint32_t n_jobs, uint32_t max_n) {
+  return max_n < kSelClusterFrom ? 2 * n_jobs : n_jobs * kSelCta / 2;
 }
 
 cudaError_t launch_finish(const DevGlobal &g, cudaStream_t st) {

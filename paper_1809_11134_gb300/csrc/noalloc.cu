@@ -209,7 +209,7 @@ extern "C" qe_status qe_eval_rank_static(const qe_problem *prob, const uint8_t *
     j.meta = d.meta;
     j.gsrc = d_gate_idx;
     j.update_record = 0;
-    if (e == cudaSuccess) e = qe::launch_rank_select(probs, nullptr, 1, j, g, st);
+    if (e == cudaSuccess) e = qe::launch_rank_select(probs, nullptr, 1, j, g, st, n_circuits);
     if (e == cudaSuccess && !canon)
       e = qe::launch_rescore(slot.lc, d.n, false, probs, d_gate_idx, nullptr, false, g, st);
     if (e == cudaSuccess) e = qe::launch_rank_sort(probs, nullptr, 1, j, g, st);

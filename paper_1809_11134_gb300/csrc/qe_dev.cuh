@@ -241,18 +241,22 @@ __device__ __forceinline__ void st_rec(float4 *p, const float4 a, const float4 b
 }
 
 // ---------------------------------------------------------------- lane layout
-// A warp holds one circuit's N x N unitary: lane = (row group g, column j),
-// j = lane & (N-1), g = the next RBL lane bits; each lane keeps ROWS rows of
-// its column in registers: row i = (g << RBR) | r.  The top RBL row bits live
-// in lane bits, the low RBR row bits in register indices.  For n <= 2 the
-// upper lanes are shadows that compute but never write.
-template <int NQ>
+// A warp holds one circuit's N x N unitary (WB = 0) or its 2^-WB share of the
+// columns (2^WB warps per circuit, warp w holding columns w 2^CB .. (w + 1)
+// 2^CB - 1; columns evolve independently, so the split changes no value):
+// lane = (row group g, column j), the column's low CB bits in the low lane
+// bits, g in the next RBL lane bits; each lane keeps ROWS rows of its column in
+// registers: row i = (g << RBR) | r.  The top RBL row bits live in lane bits,
+// the low RBR row bits in register indices.  Lanes beyond USED are shadows
+// that compute but never write.
+template <int NQ, int WB = 0>
 struct Lay {
   static constexpr int N = 1 << NQ;
-  static constexpr int RBL = (NQ < 5 - NQ) ? NQ : 5 - NQ;
+  static constexpr int CB = NQ - WB;  // column bits in the lane index
+  static constexpr int RBL = (NQ < 5 - CB) ? NQ : 5 - CB;
   static constexpr int RBR = NQ - RBL;
   static constexpr int ROWS = 1 << RBR;
-  static constexpr int USED = N << RBL;  // lanes that hold data
+  static constexpr int USED = 1 << (CB + RBL);  // lanes that hold data
 };
 
 }  // namespace qe

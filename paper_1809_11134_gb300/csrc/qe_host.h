@@ -94,9 +94,14 @@ cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const ui
 cudaError_t rank_init();  // once per device before the first ranking launch
 // jobs == NULL: one job given by value in `single`
 bool is_select_kernel(const void *f);  // the ranking's selection kernel (graph edges)
+// threads of a selection launch over n_jobs searches of at most max_n
+// circuits, in units of 512 (a quarter of an SM's 2048)
+uint32_t select_quarters(uint32_t n_jobs, uint32_t max_n);
 bool rank_kernel_waits(const void *f);  // sort, top-k gather, finish: wait for their predecessor
+// max_n: the most circuits of any job (picks one CTA or a cluster per search)
 cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
-                               const RankJob &single, const DevGlobal &g, cudaStream_t st);
+                               const RankJob &single, const DevGlobal &g, cudaStream_t st,
+                               uint32_t max_n);
 cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
                              const RankJob &single, const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_finish(const DevGlobal &g, cudaStream_t st);
