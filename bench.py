@@ -496,10 +496,11 @@ def end_to_end(qe, ctx_unused, searches, last, steps):
     of every search, host gate strings) go host -> device from pinned memory in
     one copy, binary32 evaluation and binary64 top-k ranking of every search run
     on the GPU, and the fitness and top-k lists come back to pinned host memory.
-    Timed twice: through the asynchronous pair (two calls in flight on two sets
-    of pinned buffers, so one step's copies and evaluations overlap the previous
-    step's ranking; the headline) and through the synchronous call (one
-    synchronisation per step)."""
+    Timed twice: through the asynchronous pair (as many calls in flight as the
+    context has batch slots, each on its own set of pinned buffers, so that the
+    copies, evaluations and rankings of consecutive steps overlap; the
+    headline) and through the synchronous call (one synchronisation per
+    step)."""
     import ctypes as C
     import numpy as np
     import torch
@@ -512,24 +513,25 @@ def end_to_end(qe, ctx_unused, searches, last, steps):
     gates = np.concatenate([np.ascontiguousarray(l["gate_idx"]).ravel() for l in last])
     n = sum(s.P for s in searches)
     k_total = sum(min(max(s.topk, 1), s.P) for s in searches)
+    depth = qe.QE_BATCH_SLOTS
     bufs = [(torch.from_numpy(gates.copy()).pin_memory(),
              torch.zeros(n, dtype=torch.float32).pin_memory(), (qe.qe_ranked * k_total)())
-            for _ in range(2)]
+            for _ in range(depth)]
     probs = (C.c_uint32 * len(searches))(*range(len(searches)))
     counts = (C.c_uint32 * len(searches))(*[s.P for s in searches])
 
     def submit(i):
-        hg, hf, tops = bufs[i % 2]
+        hg, hf, tops = bufs[i % depth]
         return ctx.eval_host_batch_async_ptr(probs, counts, hg.data_ptr(), hf.data_ptr(), tops)
 
     def pipelined(k):
-        prev = None
+        flight = []
         for i in range(k):
-            t = submit(i)
-            if prev is not None:
-                ctx.eval_host_batch_wait(prev)
-            prev = t
-        ctx.eval_host_batch_wait(prev)
+            if len(flight) == depth:
+                ctx.eval_host_batch_wait(flight.pop(0))
+            flight.append(submit(i))
+        for t in flight:
+            ctx.eval_host_batch_wait(t)
 
     def synchronous(k):
         hg, hf, tops = bufs[0]
@@ -543,16 +545,17 @@ def end_to_end(qe, ctx_unused, searches, last, steps):
         t0 = time.perf_counter()
         fn(steps)
         out[name] = n * steps / (time.perf_counter() - t0)
-    # both buffer sets hold the same circuits: the same results
-    assert torch.equal(bufs[0][1], bufs[1][1])
+    # every buffer set holds the same circuits: the same results
+    assert all(torch.equal(bufs[0][1], b[1]) for b in bufs[1:])
     ctx.close()
     return {"value": out["pipelined"], "unit": UNIT,
             "h2d_bytes_per_step": int(gates.size),
             "d2h_bytes_per_step": n * 4 + (k_total + 1) * 16,
             "sync_value": out["sync"],
             "call": "qe_eval_host_batch_async / _wait: every search's circuits in one call "
-                    "(binary32 eval + binary64 top-k), pinned host buffers, two calls in "
-                    "flight; sync_value: qe_eval_host_batch, one synchronisation per step"}
+                    "(binary32 eval + binary64 top-k), pinned host buffers, %d calls in "
+                    "flight; sync_value: qe_eval_host_batch, one synchronisation per step"
+                    % depth}
 
 
 def _stage_rates(qe, torch, searches, gens):

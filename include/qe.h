@@ -115,6 +115,9 @@ typedef enum {
  * candidate is checked */
 #define QE_ERRW_GUARD_BAND 4u
 
+/* calls of qe_eval_host_batch_async that can be in flight at once */
+#define QE_BATCH_SLOTS 3u
+
 /* One search.  sizeOfIndividual = circuit_len, sizeOfPopulation = population,
  * numberOfWires = n_qubits (Sec. IV-B). */
 typedef struct {
@@ -244,28 +247,27 @@ qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
  * allocates device staging (and pinned host staging for the top-k lists) that
  * the context keeps until qe_destroy.  Pinned host buffers make the copies
  * asynchronous with respect to other host work.  Invalid gate indices give
- * NaN fitness and QE_ENUMERIC (the fitness is still written).  A pending
- * generation's ranking is finished first.  The evaluations run on a stream of
- * the context's own (not ordered after other work on the context's stream,
- * which they do not touch); the ranking runs on the context's stream.
- * Equivalent to qe_eval_host_batch_async followed by qe_eval_host_batch_wait;
- * QE_ESTATE if two asynchronous calls are in flight. */
+ * NaN fitness and QE_ENUMERIC (the fitness is still written).  The call runs
+ * on a stream and scratch memory of its own (not ordered after other work on
+ * the context's stream, and touching no state of the context's searches: it
+ * can run beside qe_step).  Equivalent to qe_eval_host_batch_async followed by
+ * qe_eval_host_batch_wait; QE_ESTATE if every slot has a call in flight. */
 qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
                              const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
                              void *h_fitness, qe_ranked *h_topk);
 
 /* qe_eval_host_batch without the synchronisation: enqueues the call and
  * returns a ticket (*ticket, nonzero) for qe_eval_host_batch_wait.  The
- * context has two staging slots, each with its own stream and graphs, so two
- * calls can be in flight: the second call's gate copy and evaluations run
- * while the first call's ranking does (every ranking runs on the context's
- * stream, in call order).  Until its wait returns, a call still reads
- * h_gate_idx and writes h_fitness and h_topk: the caller keeps them alive and
- * untouched, and gives two calls in flight distinct buffers.  h_probs and
- * h_n_circuits are read before return.  Arguments are checked as by
- * qe_eval_host_batch; QE_ESTATE when both slots are in flight, QE_EINVAL for a
- * NULL ticket.  Each slot's graphs follow the layout of its last call, so
- * alternating two fixed layouts replays captured graphs. */
+ * context has QE_BATCH_SLOTS staging slots, each with its own stream, device
+ * scratch (candidates, rescoring queue, error word) and graphs, so that many
+ * calls can be in flight and run concurrently: copies, evaluations and
+ * rankings of different calls overlap.  Until its wait returns, a call still
+ * reads h_gate_idx and writes h_fitness and h_topk: the caller keeps them
+ * alive and untouched, and gives calls in flight distinct buffers.  h_probs
+ * and h_n_circuits are read before return.  Arguments are checked as by
+ * qe_eval_host_batch; QE_ESTATE when every slot has a call in flight,
+ * QE_EINVAL for a NULL ticket.  Each slot's graphs follow the layout of its
+ * last call, so repeating fixed layouts replays captured graphs. */
 qe_status qe_eval_host_batch_async(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
                                    const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
                                    void *h_fitness, qe_ranked *h_topk, uint64_t *ticket);

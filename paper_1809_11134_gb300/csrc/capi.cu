@@ -44,11 +44,15 @@ struct Plan {
   bool concurrent = false;   // circuit kernels of different widths on parallel streams
 };
 
-// One slot of the batched host evaluation: device staging (grown on
-// demand), pinned host staging of the top-k lists, the graphs of the last
-// layout (key: ranking flag, item count, the items' problems and circuit
-// counts) -- the evaluations, run on the slot's stream, and the ranking, run
-// on the context's stream after them -- and the call in flight.
+constexpr int kBatchSlots = (int)QE_BATCH_SLOTS;  // qe_eval_host_batch_async calls in flight
+
+// One slot of the batched host evaluation: device staging (grown on demand:
+// the items' gates, fitness and costs, and the slot's own ranking scratch),
+// pinned host staging of the top-k lists, the graphs of the last layout (key:
+// ranking flag, item count, the items' problems and circuit counts) -- the
+// evaluations and the ranking, both run on the slot's stream -- and the call
+// in flight.
+
 struct BatchSlot {
   void *d = nullptr;
   size_t d_bytes = 0;
@@ -59,7 +63,7 @@ struct BatchSlot {
   cudaGraph_t eg = nullptr, rg = nullptr;
   cudaGraphExec_t ex = nullptr, rx = nullptr;
   cudaStream_t st = nullptr;
-  cudaEvent_t ev_eval = nullptr, ev_fit = nullptr, ev_done = nullptr;
+  cudaEvent_t ev_fit = nullptr, ev_done = nullptr;
   size_t err_off = 0;  // the slot's error word in its staging
   // the call in flight
   bool busy = false;
@@ -106,9 +110,10 @@ struct qe_ctx {
   Best *h_recs = nullptr;  // pinned
   uint8_t *d_stage_gates = nullptr;
   void *d_stage_fit = nullptr;
-  // qe_eval_host_batch(_async): two slots, so that one call's copies and
-  // evaluations overlap the previous call's ranking
-  BatchSlot bslot[2];
+  // qe_eval_host_batch(_async): kBatchSlots slots, each call's copies,
+  // evaluations and ranking on its slot's stream and scratch, so that calls
+  // in flight overlap
+  BatchSlot bslot[kBatchSlots];
   uint64_t next_ticket = 1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -617,7 +622,6 @@ void qe_destroy(qe_ctx *ctx) {
     if (b.rg) cudaGraphDestroy(b.rg);
     if (b.d) cudaFree(b.d);
     if (b.h) cudaFreeHost(b.h);
-    if (b.ev_eval) cudaEventDestroy(b.ev_eval);
     if (b.ev_fit) cudaEventDestroy(b.ev_fit);
     if (b.ev_done) cudaEventDestroy(b.ev_done);
     if (b.st) cudaStreamDestroy(b.st);
@@ -1121,7 +1125,14 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // error word, the ranking jobs, their top-k offsets, and the per-problem gate
 // table the binary64 rescoring reads.
 struct BatchLayout {
-  size_t err = 0, gates = 0, fit = 0, cost = 0, topk = 0, jobs = 0, koff = 0, gtab = 0, total = 0;
+  size_t err = 0, gates = 0, fit = 0, cost = 0, topk = 0;
+  // the slot's own ranking scratch: candidates, their fitness and counts, the
+  // binary64 rescoring queue and its length, the generation words the
+  // ranking kernels may read
+  size_t cand = 0, cand_f = 0, cand_n = 0, rq = 0, words = 0;
+  // uploaded once per layout: jobs, top-k offsets, gate table, the jobs'
+  // search descriptors pointing at the slot's scratch
+  size_t jobs = 0, koff = 0, gtab = 0, probs = 0, total = 0;
 };
 
 static BatchLayout batch_layout(size_t gate_bytes, size_t n_total, size_t fb, size_t k_total,
@@ -1138,20 +1149,36 @@ static BatchLayout batch_layout(size_t gate_bytes, size_t n_total, size_t fb, si
   o += align256((n_total ? n_total : 1) * 4);
   b.topk = o;
   o += align256((k_total + 1) * sizeof(Ranked));
+  b.cand = o;
+  o += align256((n_total ? n_total : 1) * 4);
+  b.cand_f = o;
+  o += align256((n_total ? n_total : 1) * 8);
+  b.cand_n = o;
+  o += align256(n_items * 4);
+  b.rq = o;
+  o += align256((n_total ? n_total : 1) * 4);
+  b.words = o;  // rescore_n, gen, ranked, rank_active
+  o += 256;
   b.jobs = o;
   o += align256(n_items * sizeof(RankJob));
   b.koff = o;
   o += align256((n_items + 1) * 4);
   b.gtab = o;
-  o += align256(n_probs * sizeof(void *));
+  o += align256(n_items * sizeof(void *));
+  b.probs = o;
+  o += align256(n_items * sizeof(DevProblem));
   b.total = o;
+  (void)n_probs;
   return b;
 }
 
-// Enqueue one batched host evaluation in a free slot: the copy of the gates
-// and the evaluations on the slot's stream, the fitness copy back as soon as
-// they finish, the ranking and the top-k copy on the context's stream (where
-// every other use of the ranking scratch is ordered).
+// Enqueue one batched host evaluation in a free slot, all on the slot's
+// stream: the copy of the gates, the evaluations, the fitness copy back, the
+// ranking (on the slot's own scratch: the jobs' search descriptors are slot
+// copies whose candidate lists, counts and top-k lists live in the slot's
+// staging, with the slot's own rescoring queue and error word) and the top-k
+// copy back.  Calls in different slots share no device memory, so their
+// rankings, latency chains on a few SMs each, run concurrently.
 static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
                               const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
                               void *h_fitness, qe_ranked *h_topk, uint64_t *ticket) {
@@ -1187,20 +1214,15 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
       slot = &b;
       break;
     }
-  if (!slot) return fail(ctx, QE_ESTATE, "two batched calls are in flight: wait for one first");
+  if (!slot) return fail(ctx, QE_ESTATE, "every batch slot has a call in flight: wait for one first");
   BatchSlot &b = *slot;
   const size_t fb = prec == 0 ? 8 : 4;
   const bool rank = h_topk != nullptr;
-  cudaStream_t us = ctx->user;
   if (!b.st) {
     QE_CUDA(ctx, cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking));
-    QE_CUDA(ctx, cudaEventCreateWithFlags(&b.ev_eval, cudaEventDisableTiming));
     QE_CUDA(ctx, cudaEventCreateWithFlags(&b.ev_fit, cudaEventDisableTiming));
     QE_CUDA(ctx, cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming));
   }
-  // the ranking scratch may still hold the last generation's pending ranking
-  qe_status st = drain(ctx);
-  if (st != QE_OK) return st;
 
   const BatchLayout lay = batch_layout(gate_bytes, n_total, fb, k_total, n_items, np);
   std::vector<uint32_t> key;
@@ -1228,17 +1250,25 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
       QE_CUDA(ctx, cudaMalloc(&b.d, lay.total));
       b.d_bytes = lay.total;
       QE_CUDA(ctx, cudaMemsetAsync((char *)b.d + lay.err, 0, 4, b.st));
+      QE_CUDA(ctx, cudaMemsetAsync((char *)b.d + lay.words, 0, 256, b.st));
     }
     b.err_off = lay.err;
     char *base = (char *)b.d;
-    // this slot's copy of the context's device pointers, with its own error word
+    // this slot's copy of the context's device pointers, with its own error
+    // word, rescoring queue and generation words
     DevGlobal gs = ctx->g;
     gs.err = (uint32_t *)(base + lay.err);
+    gs.rescore_list = (uint32_t *)(base + lay.rq);
+    gs.rescore_n = (uint32_t *)(base + lay.words);
+    gs.gen = gs.rescore_n + 1;
+    gs.ranked = gs.rescore_n + 2;
+    gs.rank_active = gs.rescore_n + 3;
     // jobs, top-k offsets and the gate table, uploaded once per layout
     b.meta.assign(lay.total - lay.jobs, 0);
     RankJob *hj = (RankJob *)b.meta.data();
     uint32_t *hk = (uint32_t *)(b.meta.data() + (lay.koff - lay.jobs));
     const uint8_t **hg = (const uint8_t **)(b.meta.data() + (lay.gtab - lay.jobs));
+    DevProblem *hd = (DevProblem *)(b.meta.data() + (lay.probs - lay.jobs));
     std::vector<uint32_t> items;  // items with circuits (ranked)
     size_t go = 0, fo = 0, ko = 0;
     std::vector<size_t> goff(n_items), foff(n_items);
@@ -1247,10 +1277,20 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
       const uint32_t n = h_n_circuits[m];
       goff[m] = go;
       foff[m] = fo;
-      hg[h_probs[m]] = (const uint8_t *)(base + lay.gates + go);
       if (n) {
-        RankJob &j = hj[items.size()];
-        j.prob = h_probs[m];
+        // job x ranks its search through the slot's descriptor x
+        const uint32_t x = (uint32_t)items.size();
+        DevProblem &dp = hd[x];
+        dp = d;
+        dp.cand = (uint32_t *)(base + lay.cand) + fo;
+        dp.cand_f = (double *)(base + lay.cand_f) + fo;
+        dp.cand_n = (uint32_t *)(base + lay.cand_n) + x;
+        // the sort writes the job's list where the gather expects it
+        dp.topk_out = (Ranked *)(base + lay.topk) + ko;
+        dp.rec = nullptr;  // no job of a batch updates a record
+        hg[x] = (const uint8_t *)(base + lay.gates + go);
+        RankJob &j = hj[x];
+        j.prob = x;
         j.n = n;
         j.fit = base + lay.fit + fo * fb;
         j.meta = (const uint32_t *)(base + lay.cost) + fo;
@@ -1300,27 +1340,27 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     if (rank) {
       QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       const RankJob *dj = (const RankJob *)(base + lay.jobs);
+      const DevProblem *sprobs = (const DevProblem *)(base + lay.probs);
       e = cudaSuccess;
       if (n_jobs) {
         e = launch_reset_counter(gs, cs);
         uint32_t max_n = 0;
         for (uint32_t x = 0; x < n_jobs; ++x)
           max_n = h_n_circuits[items[x]] > max_n ? h_n_circuits[items[x]] : max_n;
-        if (e == cudaSuccess)
-          e = launch_rank_select(ctx->d_probs, dj, n_jobs, RankJob{}, gs, cs, max_n);
+        if (e == cudaSuccess) e = launch_rank_select(sprobs, dj, n_jobs, RankJob{}, gs, cs, max_n);
         if (prec != 0) {
           uint32_t widths = 0;
           for (uint32_t x = 0; x < n_jobs; ++x) widths |= 1u << ctx->hp[h_probs[items[x]]].n;
           for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
             if (e == cudaSuccess && ((widths >> nq) & 1))
-              e = launch_rescore(ctx->lc, nq, false, ctx->d_probs, nullptr, nullptr, false, gs,
-                                 cs, (const uint8_t *const *)(base + lay.gtab));
+              e = launch_rescore(ctx->lc, nq, false, sprobs, nullptr, nullptr, false, gs, cs,
+                                 (const uint8_t *const *)(base + lay.gtab));
         }
-        if (e == cudaSuccess) e = launch_rank_sort(ctx->d_probs, dj, n_jobs, RankJob{}, gs, cs);
+        if (e == cudaSuccess) e = launch_rank_sort(sprobs, dj, n_jobs, RankJob{}, gs, cs);
         if (e == cudaSuccess) e = launch_reset_counter(gs, cs);
       }
       if (e == cudaSuccess)
-        e = launch_gather_topk(ctx->d_probs, dj, (const uint32_t *)(base + lay.koff), n_jobs,
+        e = launch_gather_topk(sprobs, dj, (const uint32_t *)(base + lay.koff), n_jobs,
                                (Ranked *)(base + lay.topk), gs, cs);
       graph = nullptr;
       e2 = cudaStreamEndCapture(cs, &graph);
@@ -1352,19 +1392,17 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     QE_CUDA(ctx, cudaMemcpyAsync(base + lay.gates, h_gate_idx, gate_bytes, cudaMemcpyHostToDevice,
                                  b.st));
   QE_CUDA(ctx, cudaGraphLaunch(b.ex, b.st));
-  QE_CUDA(ctx, cudaEventRecord(b.ev_eval, b.st));
   if (n_total)
     QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, base + lay.fit, n_total * fb, cudaMemcpyDeviceToHost,
                                  b.st));
   if (!rank)
     QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.err, 4, cudaMemcpyDeviceToHost, b.st));
   QE_CUDA(ctx, cudaEventRecord(b.ev_fit, b.st));
-  QE_CUDA(ctx, cudaStreamWaitEvent(us, b.ev_eval, 0));
   if (rank) {
-    QE_CUDA(ctx, cudaGraphLaunch(b.rx, us));
-    QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.topk, hb, cudaMemcpyDeviceToHost, us));
+    QE_CUDA(ctx, cudaGraphLaunch(b.rx, b.st));
+    QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.topk, hb, cudaMemcpyDeviceToHost, b.st));
   }
-  QE_CUDA(ctx, cudaEventRecord(b.ev_done, us));
+  QE_CUDA(ctx, cudaEventRecord(b.ev_done, b.st));
   b.busy = true;
   b.ticket = ctx->next_ticket++;
   b.h_topk = h_topk;

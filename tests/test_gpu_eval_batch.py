@@ -308,19 +308,23 @@ class _Call:
 
 @pytest.mark.parametrize("prec", [W.PREC_FP32, W.PREC_FP64])
 def test_async_calls_in_flight_match_the_oracle(qe, prec):
-    """two asynchronous calls in flight (different layouts, waited for in both
-    orders, a slot reused with a new layout and with its old one), every result
-    against the oracle and against the synchronous call"""
+    """asynchronous calls in flight together (every slot busy, different
+    layouts sharing searches, waited for in several orders, slots reused with
+    new layouts and with old ones), every result against the oracle and
+    against the synchronous call"""
     ss = searches(prec)
     rng = np.random.default_rng(41 + prec)
     plans = [[(0, 1000), (1, 300)], [(4, 4096), (2, 130), (3, 33)], [(1, 17), (0, 999)],
-             [(0, 1000), (1, 300)], [(2, 77)], [(4, 4095), (0, 5)]]
+             [(0, 1000), (1, 300)], [(2, 77)], [(4, 4095), (0, 5)], [(0, 1000), (2, 130)],
+             [(3, 33), (1, 300), (4, 4096)], [(0, 998)]]
     calls = [_Call(qe, ss, [(q, gates_for(ss[q], n, rng)) for q, n in plan]) for plan in plans]
+    S = qe.QE_BATCH_SLOTS
+    assert S >= 2
     with qe.Context(ss) as ctx:
-        for a, b, first in ((0, 1, 0), (2, 3, 1), (4, 5, 0)):
-            ta, tb = calls[a].submit(ctx), calls[b].submit(ctx)
-            assert ta != tb
-            order = (ta, tb) if first == 0 else (tb, ta)
+        for r, start in enumerate(range(0, len(calls) - S + 1, S)):
+            ts = [calls[start + i].submit(ctx) for i in range(S)]
+            assert len(set(ts)) == S
+            order = ts if r % 3 == 0 else (ts[::-1] if r % 3 == 1 else ts[1:] + ts[:1])
             for t in order:
                 ctx.eval_host_batch_wait(t)
         for c in calls:
@@ -334,32 +338,32 @@ def test_async_calls_in_flight_match_the_oracle(qe, prec):
 
 
 def test_async_slot_and_ticket_errors(qe):
-    """a third call while two are in flight is QE_ESTATE, the ticket of a call
+    """one call more than there are slots is QE_ESTATE, the ticket of a call
     already waited for or never issued is QE_EINVAL; the calls in flight are
     not disturbed and the context stays usable"""
     ss = searches(W.PREC_FP32)
     rng = np.random.default_rng(43)
-    calls = [_Call(qe, ss, [(0, gates_for(ss[0], 500, rng))]),
-             _Call(qe, ss, [(1, gates_for(ss[1], 300, rng))]),
-             _Call(qe, ss, [(2, gates_for(ss[2], 64, rng))])]
+    S = qe.QE_BATCH_SLOTS
+    sizes = [(0, 500), (1, 300), (2, 64), (3, 33), (4, 700)]
+    calls = [_Call(qe, ss, [(q, gates_for(ss[q], n, rng))]) for q, n in sizes[:S + 1]]
     with qe.Context(ss) as ctx:
-        t0, t1 = calls[0].submit(ctx), calls[1].submit(ctx)
+        ts = [calls[i].submit(ctx) for i in range(S)]
         with pytest.raises(qe.QeError) as e:
-            calls[2].submit(ctx)
+            calls[S].submit(ctx)
         assert e.value.status == qe.QE_ESTATE
         with pytest.raises(qe.QeError) as e:
-            ctx.eval_host_batch(calls[2].items, topk=True)
+            ctx.eval_host_batch(calls[S].items, topk=True)
         assert e.value.status == qe.QE_ESTATE
         with pytest.raises(qe.QeError) as e:
-            ctx.eval_host_batch_wait(max(t0, t1) + 100)
+            ctx.eval_host_batch_wait(max(ts) + 100)
         assert e.value.status == qe.QE_EINVAL
-        ctx.eval_host_batch_wait(t1)
+        ctx.eval_host_batch_wait(ts[1])
         with pytest.raises(qe.QeError) as e:
-            ctx.eval_host_batch_wait(t1)
+            ctx.eval_host_batch_wait(ts[1])
         assert e.value.status == qe.QE_EINVAL
-        t2 = calls[2].submit(ctx)
-        ctx.eval_host_batch_wait(t0)
-        ctx.eval_host_batch_wait(t2)
+        tl = calls[S].submit(ctx)
+        for t in [ts[0]] + ts[2:] + [tl]:
+            ctx.eval_host_batch_wait(t)
         for c in calls:
             fits, tops = c.results()
             for (q, g), f, t in zip(c.items, fits, tops):
