@@ -524,10 +524,10 @@ def end_to_end(qe, ctx_unused, searches, last, steps):
         hg, hf, tops = bufs[i % depth]
         return ctx.eval_host_batch_async_ptr(probs, counts, hg.data_ptr(), hf.data_ptr(), tops)
 
-    def pipelined(k):
+    def pipelined(k, d=depth):
         flight = []
         for i in range(k):
-            if len(flight) == depth:
+            if len(flight) == d:
                 ctx.eval_host_batch_wait(flight.pop(0))
             flight.append(submit(i))
         for t in flight:
@@ -545,6 +545,14 @@ def end_to_end(qe, ctx_unused, searches, last, steps):
         t0 = time.perf_counter()
         fn(steps)
         out[name] = n * steps / (time.perf_counter() - t0)
+    by_depth = {}
+    for d in sorted({1, 2, depth - 1} - {depth, 0}):
+        pipelined(4, d)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pipelined(steps, d)
+        by_depth[d] = n * steps / (time.perf_counter() - t0)
+    by_depth[depth] = out["pipelined"]
     # every buffer set holds the same circuits: the same results
     assert all(torch.equal(bufs[0][1], b[1]) for b in bufs[1:])
     ctx.close()
@@ -552,6 +560,7 @@ def end_to_end(qe, ctx_unused, searches, last, steps):
             "h2d_bytes_per_step": int(gates.size),
             "d2h_bytes_per_step": n * 4 + (k_total + 1) * 16,
             "sync_value": out["sync"],
+            "by_calls_in_flight": {str(d): round(v) for d, v in by_depth.items()},
             "call": "qe_eval_host_batch_async / _wait: every search's circuits in one call "
                     "(binary32 eval + binary64 top-k), pinned host buffers, %d calls in "
                     "flight; sync_value: qe_eval_host_batch, one synchronisation per step"

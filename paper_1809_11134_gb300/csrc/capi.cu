@@ -49,9 +49,9 @@ constexpr int kBatchSlots = (int)QE_BATCH_SLOTS;  // qe_eval_host_batch_async ca
 // One slot of the batched host evaluation: device staging (grown on demand:
 // the items' gates, fitness and costs, and the slot's own ranking scratch),
 // pinned host staging of the top-k lists, the graphs of the last layout (key:
-// ranking flag, item count, the items' problems and circuit counts) -- the
-// evaluations and the ranking, both run on the slot's stream -- and the call
-// in flight.
+// ranking flag, item count, the items' problems and circuit counts): one
+// graph of the evaluations and the ranking, run on the slot's stream -- and
+// the call in flight.
 
 struct BatchSlot {
   void *d = nullptr;
@@ -60,10 +60,10 @@ struct BatchSlot {
   size_t h_bytes = 0;
   std::vector<uint32_t> key;
   std::vector<unsigned char> meta;  // host copy of the jobs, offsets and gate table
-  cudaGraph_t eg = nullptr, rg = nullptr;
-  cudaGraphExec_t ex = nullptr, rx = nullptr;
+  cudaGraph_t eg = nullptr;
+  cudaGraphExec_t ex = nullptr;
   cudaStream_t st = nullptr;
-  cudaEvent_t ev_fit = nullptr, ev_done = nullptr;
+  cudaEvent_t ev_done = nullptr;
   size_t err_off = 0;  // the slot's error word in its staging
   // the call in flight
   bool busy = false;
@@ -617,12 +617,9 @@ void qe_destroy(qe_ctx *ctx) {
   for (BatchSlot &b : ctx->bslot) {
     if (b.st) cudaStreamSynchronize(b.st);
     if (b.ex) cudaGraphExecDestroy(b.ex);
-    if (b.rx) cudaGraphExecDestroy(b.rx);
     if (b.eg) cudaGraphDestroy(b.eg);
-    if (b.rg) cudaGraphDestroy(b.rg);
     if (b.d) cudaFree(b.d);
     if (b.h) cudaFreeHost(b.h);
-    if (b.ev_fit) cudaEventDestroy(b.ev_fit);
     if (b.ev_done) cudaEventDestroy(b.ev_done);
     if (b.st) cudaStreamDestroy(b.st);
   }
@@ -1220,7 +1217,6 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
   const bool rank = h_topk != nullptr;
   if (!b.st) {
     QE_CUDA(ctx, cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking));
-    QE_CUDA(ctx, cudaEventCreateWithFlags(&b.ev_fit, cudaEventDisableTiming));
     QE_CUDA(ctx, cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming));
   }
 
@@ -1236,11 +1232,9 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
   const bool regrow = lay.total > b.d_bytes;
   if (regrow || key != b.key || !b.ex) {
     if (b.ex) cudaGraphExecDestroy(b.ex);
-    if (b.rx) cudaGraphExecDestroy(b.rx);
     if (b.eg) cudaGraphDestroy(b.eg);
-    if (b.rg) cudaGraphDestroy(b.rg);
-    b.ex = b.rx = nullptr;
-    b.eg = b.rg = nullptr;
+    b.ex = nullptr;
+    b.eg = nullptr;
     b.key.clear();
     if (regrow) {
       QE_CUDA(ctx, cudaStreamSynchronize(b.st));
@@ -1327,21 +1321,11 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join2, 0);
-    cudaGraph_t graph = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-    if (e != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      return cuda_fail(ctx, e, "capturing the batch evaluation graph");
-    }
-    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
-    b.eg = graph;
-    QE_CUDA(ctx, cudaGraphInstantiate(&b.ex, graph, 0));
-    // the ranking of every item with circuits and the gathered top-k lists
-    if (rank) {
-      QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    // then, in the same graph, the ranking of every item with circuits and the
+    // gathered top-k lists
+    if (rank && e == cudaSuccess) {
       const RankJob *dj = (const RankJob *)(base + lay.jobs);
       const DevProblem *sprobs = (const DevProblem *)(base + lay.probs);
-      e = cudaSuccess;
       if (n_jobs) {
         e = launch_reset_counter(gs, cs);
         uint32_t max_n = 0;
@@ -1362,18 +1346,18 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
       if (e == cudaSuccess)
         e = launch_gather_topk(sprobs, dj, (const uint32_t *)(base + lay.koff), n_jobs,
                                (Ranked *)(base + lay.topk), gs, cs);
-      graph = nullptr;
-      e2 = cudaStreamEndCapture(cs, &graph);
-      if (e != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        return cuda_fail(ctx, e, "capturing the batch ranking graph");
-      }
-      if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
-      b.rg = graph;
-      qe_status pst = add_pdl_edges(ctx, graph);
-      if (pst != QE_OK) return pst;
-      QE_CUDA(ctx, cudaGraphInstantiate(&b.rx, graph, 0));
     }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(ctx, e, "capturing the batch graph");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+    b.eg = graph;
+    qe_status pst = add_pdl_edges(ctx, graph);
+    if (pst != QE_OK) return pst;
+    QE_CUDA(ctx, cudaGraphInstantiate(&b.ex, graph, 0));
     b.key = key;
   }
   // pinned host staging: the top-k lists and, after them, the error word
@@ -1395,13 +1379,8 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
   if (n_total)
     QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, base + lay.fit, n_total * fb, cudaMemcpyDeviceToHost,
                                  b.st));
-  if (!rank)
-    QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.err, 4, cudaMemcpyDeviceToHost, b.st));
-  QE_CUDA(ctx, cudaEventRecord(b.ev_fit, b.st));
-  if (rank) {
-    QE_CUDA(ctx, cudaGraphLaunch(b.rx, b.st));
-    QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.topk, hb, cudaMemcpyDeviceToHost, b.st));
-  }
+  if (rank) QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.topk, hb, cudaMemcpyDeviceToHost, b.st));
+  else QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.err, 4, cudaMemcpyDeviceToHost, b.st));
   QE_CUDA(ctx, cudaEventRecord(b.ev_done, b.st));
   b.busy = true;
   b.ticket = ctx->next_ticket++;
@@ -1414,7 +1393,6 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
 // Wait for a slot's call and hand out its top-k lists and error status.
 static qe_status batch_complete(qe_ctx *ctx, BatchSlot &b) {
   b.busy = false;
-  QE_CUDA(ctx, cudaEventSynchronize(b.ev_fit));
   QE_CUDA(ctx, cudaEventSynchronize(b.ev_done));
   const Ranked *r = (const Ranked *)b.h;
   for (size_t s = 0; s < b.k_total; ++s) {

@@ -321,9 +321,9 @@ def test_async_calls_in_flight_match_the_oracle(qe, prec):
     S = qe.QE_BATCH_SLOTS
     assert S >= 2
     with qe.Context(ss) as ctx:
-        for r, start in enumerate(range(0, len(calls) - S + 1, S)):
-            ts = [calls[start + i].submit(ctx) for i in range(S)]
-            assert len(set(ts)) == S
+        for r, start in enumerate(range(0, len(calls), S)):
+            ts = [c.submit(ctx) for c in calls[start:start + S]]
+            assert len(set(ts)) == len(ts)
             order = ts if r % 3 == 0 else (ts[::-1] if r % 3 == 1 else ts[1:] + ts[:1])
             for t in order:
                 ctx.eval_host_batch_wait(t)
@@ -344,8 +344,8 @@ def test_async_slot_and_ticket_errors(qe):
     ss = searches(W.PREC_FP32)
     rng = np.random.default_rng(43)
     S = qe.QE_BATCH_SLOTS
-    sizes = [(0, 500), (1, 300), (2, 64), (3, 33), (4, 700)]
-    calls = [_Call(qe, ss, [(q, gates_for(ss[q], n, rng))]) for q, n in sizes[:S + 1]]
+    sizes = [(q % 5, min(ss[q % 5].P, 20 + 37 * q)) for q in range(S + 1)]
+    calls = [_Call(qe, ss, [(q, gates_for(ss[q], n, rng))]) for q, n in sizes]
     with qe.Context(ss) as ctx:
         ts = [calls[i].submit(ctx) for i in range(S)]
         with pytest.raises(qe.QeError) as e:
