@@ -172,6 +172,17 @@ def _need(t, dtype, numel, name):
         raise TypeError("%s must be a contiguous %s tensor with >= %d elements" % (name, dtype, numel))
 
 
+class BatchCall:
+    """A qe_eval_host_batch_async call in flight (see Context.eval_host_batch_async)."""
+
+    def __init__(self, ctx, ticket, keep):
+        self.ctx, self.ticket, self._keep = ctx, ticket, keep
+
+    def wait(self):
+        self.ctx.eval_host_batch_wait(self.ticket)
+        return Context._batch_results(self._keep)
+
+
 class Context:
     """One qe_ctx: n independent searches sharing every launch."""
 
@@ -283,9 +294,7 @@ class Context:
         return _check(self.h, lib().qe_eval_host(self.h, prob, C.c_void_p(h_gates_ptr), n,
                                                  C.c_void_p(h_fit_ptr), topk_buf))
 
-    def eval_host_batch(self, items, topk=False):
-        """qe_eval_host_batch: items = [(prob, gate_idx ndarray [n, L]), ...]; returns
-        one fitness array per item and, with topk, one ranked list per item"""
+    def _batch_args(self, items, topk):
         probs = [int(q) for q, _ in items]
         known = [p if 0 <= p < len(self._probs) else None for p in probs]
         gs = [np.ascontiguousarray(g, np.uint8) for _, g in items]
@@ -300,10 +309,14 @@ class Context:
               for q, n in zip(known, ns)]
         out = (qe_ranked * max(sum(ks), 1))() if topk else None
         u32a = C.c_uint32 * max(len(probs), 1)
-        _check(self.h, lib().qe_eval_host_batch(
-            self.h, len(probs), u32a(*probs), u32a(*ns),
-            flat.ctypes.data_as(C.c_void_p) if flat.size else None,
-            fit.ctypes.data_as(C.c_void_p), out))
+        args = (len(probs), u32a(*probs), u32a(*ns),
+                flat.ctypes.data_as(C.c_void_p) if flat.size else None,
+                fit.ctypes.data_as(C.c_void_p), out)
+        return args, (ns, ks, flat, fit, out, topk)
+
+    @staticmethod
+    def _batch_results(keep):
+        ns, ks, _, fit, out, topk = keep
         fits, tops, fo, ko = [], [], 0, 0
         for n, k in zip(ns, ks):
             fits.append(fit[fo:fo + n].copy())
@@ -312,6 +325,22 @@ class Context:
             fo += n
             ko += k
         return (fits, tops) if topk else fits
+
+    def eval_host_batch(self, items, topk=False):
+        """qe_eval_host_batch: items = [(prob, gate_idx ndarray [n, L]), ...]; returns
+        one fitness array per item and, with topk, one ranked list per item"""
+        args, keep = self._batch_args(items, topk)
+        _check(self.h, lib().qe_eval_host_batch(self.h, *args))
+        return self._batch_results(keep)
+
+    def eval_host_batch_async(self, items, topk=False):
+        """qe_eval_host_batch_async: enqueues the call and returns a handle whose
+        wait() returns what eval_host_batch returns (up to QE_BATCH_SLOTS calls
+        in flight; the handle keeps the call's host buffers alive)"""
+        args, keep = self._batch_args(items, topk)
+        t = C.c_uint64()
+        _check(self.h, lib().qe_eval_host_batch_async(self.h, *args, C.byref(t)))
+        return BatchCall(self, t.value, keep)
 
     def eval_host_batch_ptr(self, probs_arr, n_arr, h_gates_ptr, h_fit_ptr, topk_buf=None):
         """qe_eval_host_batch on raw host pointers (pinned buffers, for timing);

@@ -421,3 +421,26 @@ def test_async_call_across_generations_leaves_the_run_unchanged(qe):
             for (q, g), f, tk in zip(c.items, fits, tops):
                 check_item(ss[q], g, f, tk)
         assert a.step(1) == b.step(1)
+
+
+def test_async_handles_from_numpy_equal_the_synchronous_call(qe):
+    """Context.eval_host_batch_async on pageable numpy arrays: as many calls in
+    flight as there are slots, waited for out of order, each equal to the
+    synchronous call and checked against the oracle"""
+    ss = searches(W.PREC_FP32)
+    rng = np.random.default_rng(61)
+    S = qe.QE_BATCH_SLOTS
+    plans = [[(q % 5, min(ss[q % 5].P, 50 + 90 * q)), ((q + 2) % 5, ss[(q + 2) % 5].P)]
+             for q in range(S)]
+    all_items = [[(q, gates_for(ss[q], n, rng)) for q, n in plan] for plan in plans]
+    with qe.Context(ss) as ctx:
+        handles = [ctx.eval_host_batch_async(items, topk=True) for items in all_items]
+        results = [None] * S
+        for i in list(range(1, S)) + [0]:
+            results[i] = handles[i].wait()
+        for items, (fits, tops) in zip(all_items, results):
+            fits2, tops2 = ctx.eval_host_batch(items, topk=True)
+            for (q, g), f, t, f2, t2 in zip(items, fits, tops, fits2, tops2):
+                assert np.array_equal(f.view(np.uint8), f2.view(np.uint8))
+                assert t == t2
+                check_item(ss[q], g, f, t)
