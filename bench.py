@@ -538,20 +538,22 @@ def end_to_end(qe, ctx_unused, searches, last, steps):
         for _ in range(k):
             ctx.eval_host_batch_ptr(probs, counts, hg.data_ptr(), hf.data_ptr(), tops)
 
-    out = {}
-    for name, fn in (("sync", synchronous), ("pipelined", pipelined)):
-        fn(4)
+    def timed(fn, d):
+        # every slot in use warmed first (its first call allocates and
+        # captures), then enough calls that filling and draining the pipeline
+        # is a small part of the interval
+        calls = max(steps, 16 * d)
+        fn(2 * d + 2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        fn(steps)
-        out[name] = n * steps / (time.perf_counter() - t0)
+        fn(calls)
+        return n * calls / (time.perf_counter() - t0)
+
+    out = {"sync": timed(synchronous, 1), "pipelined": timed(pipelined, depth)}
     by_depth = {}
-    for d in sorted({1, 2, depth - 1} - {depth, 0}):
-        pipelined(4, d)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pipelined(steps, d)
-        by_depth[d] = n * steps / (time.perf_counter() - t0)
+    for d in sorted({1, 2, 4, 8, depth // 2} - {depth, 0}):
+        if d < depth:
+            by_depth[d] = timed(lambda k, d=d: pipelined(k, d), d)
     by_depth[depth] = out["pipelined"]
     # every buffer set holds the same circuits: the same results
     assert all(torch.equal(bufs[0][1], b[1]) for b in bufs[1:])

@@ -116,7 +116,7 @@ typedef enum {
 #define QE_ERRW_GUARD_BAND 4u
 
 /* calls of qe_eval_host_batch_async that can be in flight at once */
-#define QE_BATCH_SLOTS 4u
+#define QE_BATCH_SLOTS 16u
 
 /* One search.  sizeOfIndividual = circuit_len, sizeOfPopulation = population,
  * numberOfWires = n_qubits (Sec. IV-B). */

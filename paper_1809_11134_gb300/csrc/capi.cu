@@ -1338,7 +1338,8 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
           for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq)
             if (e == cudaSuccess && ((widths >> nq) & 1))
               e = launch_rescore(ctx->lc, nq, false, sprobs, nullptr, nullptr, false, gs, cs,
-                                 (const uint8_t *const *)(base + lay.gtab));
+                                 (const uint8_t *const *)(base + lay.gtab),
+                                 (uint32_t)(4 * k_total));
         }
         if (e == cudaSuccess) e = launch_rank_sort(sprobs, dj, n_jobs, RankJob{}, gs, cs);
         if (e == cudaSuccess) e = launch_reset_counter(gs, cs);

@@ -1524,6 +1524,7 @@ template <int NQ>
 constexpr int rescore_split() {
   return NQ == 3 ? 1 : (NQ >= 4 ? 2 : 0);
 }
+constexpr int rescore_split_of(uint32_t nq) { return nq == 3 ? 1 : (nq >= 4 ? 2 : 0); }
 
 template <int NQ, bool ISING>
 __global__ void __launch_bounds__(256) k_rescore(const DevProblem *__restrict__ probs,
@@ -1676,8 +1677,16 @@ cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *prob
 
 cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, bool ising, const DevProblem *probs,
                            const uint8_t *gsrc, const float2 *asrc, bool pipelined,
-                           const DevGlobal &g, cudaStream_t st, const uint8_t *const *gtab) {
-  const uint32_t blocks = lc.num_sms * lc.step64[nq];
+                           const DevGlobal &g, cudaStream_t st, const uint8_t *const *gtab,
+                           uint32_t expect) {
+  // enough blocks for `expect` candidates (any count is handled: the loop
+  // strides over the queue), at most the resident grid
+  uint32_t blocks = lc.num_sms * lc.step64[nq];
+  if (expect) {
+    const uint32_t per_block = (256 / 32) >> rescore_split_of(nq);
+    const uint32_t want = (expect + per_block - 1) / per_block;
+    if (want < blocks) blocks = want;
+  }
   const int pl = pipelined ? 1 : 0;
 #define QE_L(NQ)                                                                           \
   if (ising)                                                                               \

@@ -69,10 +69,12 @@ cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *prob
 // that buffer is the one of generation *gen - 1, and nothing runs unless the
 // chain is active.  gtab != NULL (device array indexed by problem): each
 // candidate's gates come from gtab[its problem] instead.
+// expect != 0: the grid is sized for that many candidates (at most the
+// resident grid); 0: the resident grid
 cudaError_t launch_rescore(const LaunchCfg &lc, uint32_t nq, bool ising, const DevProblem *probs,
                            const uint8_t *gsrc, const float2 *asrc, bool pipelined,
                            const DevGlobal &g, cudaStream_t st,
-                           const uint8_t *const *gtab = nullptr);
+                           const uint8_t *const *gtab = nullptr, uint32_t expect = 0);
 
 // k_update.cu
 bool is_update_kernel(const void *f);  // an update kernel (graph node priorities)

@@ -25,7 +25,7 @@ QE_PREC_FP64, QE_PREC_FP32, QE_PREC_SPLIT_TC = 0, 1, 2
 QE_FIT_TRACE, QE_FIT_PROB = 0, 1
 QE_ENC_QEQEA, QE_ENC_GA = 0, 1
 QE_ERRW_BAD_GATE, QE_ERRW_NONFINITE, QE_ERRW_GUARD_BAND = 1, 2, 4
-QE_BATCH_SLOTS = 4  # qe_eval_host_batch_async calls in flight at once
+QE_BATCH_SLOTS = 16  # qe_eval_host_batch_async calls in flight at once
 
 # every symbol include/qe.h declares
 EXPORTS = ["qe_library_info", "qe_init", "qe_sample", "qe_eval", "qe_eval_amp", "qe_rank",
