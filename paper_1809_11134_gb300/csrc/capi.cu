@@ -1244,8 +1244,11 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
       QE_CUDA(ctx, cudaMalloc(&b.d, lay.total));
       b.d_bytes = lay.total;
       QE_CUDA(ctx, cudaMemsetAsync((char *)b.d + lay.err, 0, 4, b.st));
-      QE_CUDA(ctx, cudaMemsetAsync((char *)b.d + lay.words, 0, 256, b.st));
     }
+    // the rescoring queue's length and the generation words: a new layout
+    // puts them where the last one kept other data; from here on each
+    // ranking's sort leaves the length at zero for the next call
+    QE_CUDA(ctx, cudaMemsetAsync((char *)b.d + lay.words, 0, 256, b.st));
     b.err_off = lay.err;
     char *base = (char *)b.d;
     // this slot's copy of the context's device pointers, with its own error
@@ -1321,17 +1324,19 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join2, 0);
-    // then, in the same graph, the ranking of every item with circuits and the
-    // gathered top-k lists
+    // then, in the same graph, the ranking of every item with circuits: the
+    // jobs' descriptors send each sorted list straight to its place in the
+    // gathered output, and the sort writes the error word after them and
+    // clears the slot's rescoring queue (zero when the slot is allocated)
     if (rank && e == cudaSuccess) {
       const RankJob *dj = (const RankJob *)(base + lay.jobs);
       const DevProblem *sprobs = (const DevProblem *)(base + lay.probs);
+      Ranked *gathered = (Ranked *)(base + lay.topk);
       if (n_jobs) {
-        e = launch_reset_counter(gs, cs);
         uint32_t max_n = 0;
         for (uint32_t x = 0; x < n_jobs; ++x)
           max_n = h_n_circuits[items[x]] > max_n ? h_n_circuits[items[x]] : max_n;
-        if (e == cudaSuccess) e = launch_rank_select(sprobs, dj, n_jobs, RankJob{}, gs, cs, max_n);
+        e = launch_rank_select(sprobs, dj, n_jobs, RankJob{}, gs, cs, max_n);
         if (prec != 0) {
           uint32_t widths = 0;
           for (uint32_t x = 0; x < n_jobs; ++x) widths |= 1u << ctx->hp[h_probs[items[x]]].n;
@@ -1341,12 +1346,13 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
                                  (const uint8_t *const *)(base + lay.gtab),
                                  (uint32_t)(4 * k_total));
         }
-        if (e == cudaSuccess) e = launch_rank_sort(sprobs, dj, n_jobs, RankJob{}, gs, cs);
-        if (e == cudaSuccess) e = launch_reset_counter(gs, cs);
+        if (e == cudaSuccess)
+          e = launch_rank_sort(sprobs, dj, n_jobs, RankJob{}, gs, cs, gathered + k_total);
+      } else {
+        // nothing to rank: the error word alone
+        e = launch_gather_topk(sprobs, dj, (const uint32_t *)(base + lay.koff), 0, gathered, gs,
+                               cs);
       }
-      if (e == cudaSuccess)
-        e = launch_gather_topk(sprobs, dj, (const uint32_t *)(base + lay.koff), n_jobs,
-                               (Ranked *)(base + lay.topk), gs, cs);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);

@@ -592,10 +592,20 @@ __device__ __forceinline__ void keep_side(unsigned long long &h, unsigned long l
   }
 }
 
+// err_out != NULL: block 0 also writes the error word there (the batch path,
+// whose jobs' top-k lists are written in place) and clears the rescoring
+// queue for the next ranking on the same scratch
 __global__ void __launch_bounds__(kSortThreads) k_rank_sort(const DevProblem *__restrict__ probs,
                                                             const RankJob *__restrict__ jobs,
-                                                            RankJob single, DevGlobal g) {
+                                                            RankJob single, DevGlobal g,
+                                                            Ranked *err_out) {
   wait_predecessor();  // the candidates and their binary64 fitness
+  if (err_out && blockIdx.x == 0 && threadIdx.x == 0) {
+    Ranked e{};
+    e.circuit = *g.err;  // every kernel that sets it has completed
+    *err_out = e;
+    *g.rescore_n = 0;
+  }
   RankJob jb = jobs ? jobs[blockIdx.x] : single;
   const DevProblem &p = probs[jb.prob];
   uint32_t gen = 0;
@@ -768,9 +778,10 @@ cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uin
 }
 
 cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
-                             const RankJob &single, const DevGlobal &g, cudaStream_t st) {
+                             const RankJob &single, const DevGlobal &g, cudaStream_t st,
+                             Ranked *err_out) {
   if (!n_jobs) return cudaSuccess;
-  k_rank_sort<<<n_jobs, kSortThreads, 0, st>>>(probs, jobs, single, g);
+  k_rank_sort<<<n_jobs, kSortThreads, 0, st>>>(probs, jobs, single, g, err_out);
   return cudaGetLastError();
 }
 

@@ -104,8 +104,10 @@ bool rank_kernel_waits(const void *f);  // sort, top-k gather, finish: wait for 
 cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
                                const RankJob &single, const DevGlobal &g, cudaStream_t st,
                                uint32_t max_n);
+// err_out != NULL: also write the error word there and clear the rescoring queue
 cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
-                             const RankJob &single, const DevGlobal &g, cudaStream_t st);
+                             const RankJob &single, const DevGlobal &g, cudaStream_t st,
+                             Ranked *err_out = nullptr);
 cudaError_t launch_finish(const DevGlobal &g, cudaStream_t st);
 // the top-k lists of n_jobs ranked jobs back to back (job m's from out[koff[m]],
 // koff has n_jobs + 1 entries), then the device error word in the entry
