@@ -250,8 +250,10 @@ qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
  * NaN fitness and QE_ENUMERIC (the fitness is still written).  The call runs
  * on a stream and scratch memory of its own (not ordered after other work on
  * the context's stream, and touching no state of the context's searches: it
- * can run beside qe_step).  Equivalent to qe_eval_host_batch_async followed by
- * qe_eval_host_batch_wait; QE_ESTATE if every slot has a call in flight. */
+ * can run beside qe_step).  qe_set_target waits for batch calls in flight
+ * before it changes a target, and later calls use the new one.  Equivalent to
+ * qe_eval_host_batch_async followed by qe_eval_host_batch_wait; QE_ESTATE if
+ * every slot has a call in flight. */
 qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
                              const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
                              void *h_fitness, qe_ranked *h_topk);

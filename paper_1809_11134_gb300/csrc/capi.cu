@@ -65,6 +65,7 @@ struct BatchSlot {
   cudaStream_t st = nullptr;
   cudaEvent_t ev_done = nullptr;
   size_t err_off = 0;  // the slot's error word in its staging
+  uint32_t desc_version = 0;  // the context's descriptors the slot's copies were made from
   // the call in flight
   bool busy = false;
   uint64_t ticket = 0;
@@ -115,6 +116,9 @@ struct qe_ctx {
   // in flight overlap
   BatchSlot bslot[kBatchSlots];
   uint64_t next_ticket = 1;
+  // bumped whenever a search's descriptor changes after qe_init (qe_set_target):
+  // a batch slot whose copies are older recaptures its layout
+  uint32_t desc_version = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   // launch plan of the generation graph (qe_autotune picks it by timing)
@@ -1230,7 +1234,7 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     key.push_back(h_n_circuits[m]);
   }
   const bool regrow = lay.total > b.d_bytes;
-  if (regrow || key != b.key || !b.ex) {
+  if (regrow || key != b.key || !b.ex || b.desc_version != ctx->desc_version) {
     if (b.ex) cudaGraphExecDestroy(b.ex);
     if (b.eg) cudaGraphDestroy(b.eg);
     b.ex = nullptr;
@@ -1366,6 +1370,7 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     if (pst != QE_OK) return pst;
     QE_CUDA(ctx, cudaGraphInstantiate(&b.ex, graph, 0));
     b.key = key;
+    b.desc_version = ctx->desc_version;
   }
   // pinned host staging: the top-k lists and, after them, the error word
   // (the gathered lists end with it; without a ranking it is copied alone)
@@ -1790,6 +1795,10 @@ qe_status qe_set_state(qe_ctx *ctx, uint32_t prob, const void *h_buf, size_t byt
 static qe_status put_target(qe_ctx *ctx, uint32_t prob, const double *T) {
   DevProblem &d = ctx->hp[prob];
   cudaStream_t us = ctx->user;
+  // batch calls in flight read the target: let them finish first
+  for (BatchSlot &b : ctx->bslot)
+    if (b.busy) QE_CUDA(ctx, cudaStreamSynchronize(b.st));
+  ++ctx->desc_version;
   const uint32_t NN = d.N * d.N;
   std::vector<double> &keep = ctx->targets[prob];
   if (T) {

@@ -444,3 +444,28 @@ def test_async_handles_from_numpy_equal_the_synchronous_call(qe):
                 assert np.array_equal(f.view(np.uint8), f2.view(np.uint8))
                 assert t == t2
                 check_item(ss[q], g, f, t)
+
+
+def test_batch_follows_a_changed_target(qe):
+    """a layout captured against the permutation target is recaptured after
+    qe_set_target (dense target), and again when the permutation comes back;
+    a call in flight when the target changes finishes with the old one"""
+    import dataclasses
+    from test_gpu_dense import near_target
+    rng = np.random.default_rng(71)
+    s = W.Search(3, 16, 500, NCV | HT, W.cknot(3), seed=1, precision=W.PREC_FP32, topk=8)
+    dense = dataclasses.replace(s, target=near_target(rng, 3, NCV | HT, 6))
+    items = [(0, gates_for(s, 500, rng))]
+    g = items[0][1]
+    with qe.Context([s]) as ctx:
+        fits, tops = ctx.eval_host_batch(items, topk=True)
+        check_item(s, g, fits[0], tops[0])
+        ctx.set_target(0, dense.target)
+        fits, tops = ctx.eval_host_batch(items, topk=True)
+        check_item(dense, g, fits[0], tops[0])
+        call = ctx.eval_host_batch_async(items, topk=True)
+        ctx.set_target(0, None)  # waits for the call in flight
+        fits, tops = call.wait()
+        check_item(dense, g, fits[0], tops[0])
+        fits, tops = ctx.eval_host_batch(items, topk=True)
+        check_item(s, g, fits[0], tops[0])
