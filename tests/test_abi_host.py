@@ -154,3 +154,29 @@ def test_static_entry_rejects_bad_arguments_without_a_gpu(qe):
     p = qe.to_problem(s)
     assert L.qe_eval_rank_static(C.byref(p), None, 65537, None, None, None, msg, 256) == qe.QE_EINVAL
     assert b"65536" in msg.value
+
+
+def test_binding_constants_match_the_header(qe):
+    """every QE_* integer constant the binding defines has the header's value"""
+    import re
+    hdr = open(os.path.join(ROOT, "include", "qe.h")).read()
+    defines = {m.group(1): int(m.group(2).rstrip("uU"), 0)
+               for m in re.finditer(r"#define\s+(QE_[A-Z0-9_]+)\s+(\(?[0-9xXa-fA-F]+[uU]?)", hdr)
+               if not m.group(2).startswith("(")}
+    checked = 0
+    for name, value in defines.items():
+        if hasattr(qe, name):
+            assert getattr(qe, name) == value, name
+            checked += 1
+    assert checked >= 5 and "QE_BATCH_SLOTS" in defines
+
+
+def test_async_batch_entry_points_reject_a_null_context(qe):
+    import ctypes as C
+    L = qe.lib()
+    one = (C.c_uint32 * 1)(0)
+    t = C.c_uint64()
+    assert L.qe_eval_host_batch_async(None, 1, one, one, None, None, None, C.byref(t)) == \
+        qe.QE_EINVAL
+    assert L.qe_eval_host_batch_wait(None, 1) == qe.QE_EINVAL
+    assert L.qe_eval_host_batch(None, 1, one, one, None, None, None) == qe.QE_EINVAL
