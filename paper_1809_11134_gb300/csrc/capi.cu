@@ -1121,10 +1121,12 @@ qe_status qe_eval_host(qe_ctx *ctx, uint32_t prob, const uint8_t *h_gate_idx,
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Device staging of one batch (256-B aligned sections): the items' gates,
-// fitness and cost words back to back, the gathered top-k lists plus the
-// error word, the ranking jobs, their top-k offsets, and the per-problem gate
-// table the binary64 rescoring reads.
+// Device staging of one batch slot (256-B aligned sections): the error word,
+// the items' gates, fitness and cost words back to back, the top-k lists of
+// all items plus the error word after them (the call's output), the slot's
+// ranking scratch, and what is uploaded once per layout: the ranking jobs,
+// their top-k offsets, the per-job gate table the binary64 rescoring reads
+// and the jobs' search descriptors.
 struct BatchLayout {
   size_t err = 0, gates = 0, fit = 0, cost = 0, topk = 0;
   // the slot's own ranking scratch: candidates, their fitness and counts, the
@@ -1137,7 +1139,7 @@ struct BatchLayout {
 };
 
 static BatchLayout batch_layout(size_t gate_bytes, size_t n_total, size_t fb, size_t k_total,
-                         size_t n_items, size_t n_probs) {
+                                size_t n_items) {
   BatchLayout b;
   size_t o = 0;
   b.err = o;  // the slot's device error word
@@ -1169,7 +1171,6 @@ static BatchLayout batch_layout(size_t gate_bytes, size_t n_total, size_t fb, si
   b.probs = o;
   o += align256(n_items * sizeof(DevProblem));
   b.total = o;
-  (void)n_probs;
   return b;
 }
 
@@ -1224,7 +1225,7 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     QE_CUDA(ctx, cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming));
   }
 
-  const BatchLayout lay = batch_layout(gate_bytes, n_total, fb, k_total, n_items, np);
+  const BatchLayout lay = batch_layout(gate_bytes, n_total, fb, k_total, n_items);
   std::vector<uint32_t> key;
   key.reserve(2 + 2 * (size_t)n_items);
   key.push_back(rank ? 1u : 0u);
@@ -1286,7 +1287,7 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
         dp.cand = (uint32_t *)(base + lay.cand) + fo;
         dp.cand_f = (double *)(base + lay.cand_f) + fo;
         dp.cand_n = (uint32_t *)(base + lay.cand_n) + x;
-        // the sort writes the job's list where the gather expects it
+        // the sort writes the job's list straight into the call's output
         dp.topk_out = (Ranked *)(base + lay.topk) + ko;
         dp.rec = nullptr;  // no job of a batch updates a record
         hg[x] = (const uint8_t *)(base + lay.gates + go);
