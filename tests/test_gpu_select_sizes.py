@@ -80,3 +80,26 @@ def test_batch_mixing_small_and_large_searches(qe, prec):
         if prec == W.PREC_FP64:
             assert np.array_equal(f, F)
         _check_top(t, want)
+
+
+@pytest.mark.parametrize("n", [3, 4, 5])
+@pytest.mark.parametrize("form", ["trace", "prob", "dense"])
+def test_split_rescoring_every_width_and_score(qe, n, form):
+    """the binary64 rescoring splits a candidate's columns over 2 (n = 3) or 4
+    (n = 4, 5) warps, each score form folding its column terms in the oracle's
+    order: binary32 evaluation, top-k exact against the oracle"""
+    from test_gpu_dense import near_target
+    rng = np.random.default_rng(17 * n + len(form))
+    lib = NCV | HT
+    L = {3: 16, 4: 24, 5: 32}[n]
+    kw = {}
+    if form == "prob":
+        kw["fitness_kind"] = W.FIT_PROB
+    if form == "dense":
+        kw["target"] = near_target(rng, n, lib, 8)
+    s = W.Search(n, L, 600, lib, W.cknot(n), seed=n, precision=W.PREC_FP32, topk=24, **kw)
+    g = W.random_gates(rng, 600, L, oracle.num_gates(n, lib))
+    with qe.Context([s]) as ctx:
+        fit, top = ctx.eval_host(0, g, topk=True)
+    F, want = _expected(s, g)
+    _check_top(top, want)
