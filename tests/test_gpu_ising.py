@@ -200,3 +200,26 @@ def test_ising_calls_need_angles(qe, torch):
         with pytest.raises(qe.QeError):
             ctx.eval_host(0, np.zeros((16, 4), np.uint8))
         ctx.step(2)  # sampling supplies the angles itself
+
+
+@pytest.mark.parametrize("n,L,kind", [(3, 16, W.FIT_TRACE), (4, 20, W.FIT_TRACE),
+                                      (4, 20, W.FIT_PROB), (5, 33, W.FIT_TRACE)])
+def test_fp32_topk_exact_every_split_width(qe, torch, n, L, kind):
+    """binary32 Ising evaluation with the binary64 top-k: the rescoring splits
+    each candidate over 2 (n = 3) or 4 (n = 4, 5) warps; indices, costs and
+    binary64 fitness equal the oracle's"""
+    rng = np.random.default_rng(1000 + 10 * n + L + kind)
+    nc = 400
+    s32 = S(n, L, nc, seed=n, precision=W.PREC_FP32, fitness_kind=kind, topk=20)
+    gates = rng.integers(0, _G(s32), (nc, L)).astype(np.uint8)
+    amps = random_amps(rng, (nc, L))
+    F, C = oracle.eval_circuits(oracle_problem(s32, 0), gates, amps)
+    g = torch.from_numpy(gates).cuda()
+    a = torch.from_numpy(amps).cuda()
+    with qe.Context([s32]) as ctx:
+        f32 = torch.zeros(nc, dtype=torch.float32, device="cuda")
+        top = ctx.eval(0, g, f32, topk=True, amps=a)
+    order = oracle.topk(F, C, 20)
+    assert [t[0] for t in top] == list(order)
+    assert [t[1] for t in top] == list(C[order])
+    assert [t[2] for t in top] == list(F[order])
