@@ -96,8 +96,8 @@ struct qe_ctx {
   uint32_t n_upd = 0, upd_totalA = 0, upd_totalB = 0;
   uint32_t *d_upd_ids = nullptr, *d_upd_prefA = nullptr, *d_upd_prefB = nullptr;
   // all GA searches (breeding launches): ids and prefix sums of ceil(P/2) pairs
-  uint32_t n_ga = 0, ga_pairs = 0;
-  uint32_t *d_ga_ids = nullptr, *d_ga_prefix = nullptr;
+  uint32_t n_ga = 0, ga_pairs = 0, ga_tiles = 0;
+  uint32_t *d_ga_ids = nullptr, *d_ga_prefix = nullptr, *d_ga_tprefix = nullptr;
   // QEQEA searches measuring each qutrit K > 1 times (k_presample): ids and
   // prefix sums of P*L slots
   uint32_t n_shot = 0;
@@ -500,7 +500,8 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
     if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ctx->gjoin[k - 1], 0);
   mark(1, side);
   if (e == cudaSuccess && ctx->n_ga)
-    e = launch_ga_prep(ctx->d_probs, ctx->d_ga_ids, ctx->n_ga, ctx->g, side);
+    e = launch_ga_prep(ctx->d_probs, ctx->d_ga_ids, ctx->d_ga_tprefix, ctx->n_ga, ctx->ga_tiles,
+                       ctx->g, side);
   mark(5, side);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork2, side);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(side2, ctx->ev_fork2, 0);
@@ -734,7 +735,9 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
       ar.take(&d.mut_cnt, 2 * 4);
     } else {
       ar.take(&d.ga_cum, P * 8);
+      ar.take(&d.ga_tiles, ((P + 1023) / 1024) * sizeof(GaTile));
       ar.take(&d.ga_info, 16);
+      ar.take(&d.ga_parent, P * 4);
       // the Ising GA turns genes' angles with the same table as the qubit mutation
       if (d.ising) ar.take(&d.qubit_tab, (kQ + 1) * sizeof(float2));
     }
@@ -822,6 +825,7 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
   ctx->n_ga = (uint32_t)ga.size();
   ar.take(&ctx->d_ga_ids, (ga.size() + 1) * 4);
   ar.take(&ctx->d_ga_prefix, (ga.size() + 1) * 4);
+  ar.take(&ctx->d_ga_tprefix, (ga.size() + 1) * 4);
   ctx->n_shot = (uint32_t)shot.size();
   ar.take(&ctx->d_shot_ids, (shot.size() + 1) * 4);
   ar.take(&ctx->d_shot_prefix, (shot.size() + 1) * 8);
@@ -924,11 +928,16 @@ qe_status qe_init(qe_ctx **out, const qe_problem *probs, uint32_t n_probs, void 
     if (e == cudaSuccess) e = cudaStreamSynchronize(us);
   }
   {
-    std::vector<uint32_t> pg(ga.size() + 1, 0);
-    for (size_t k = 0; k < ga.size(); ++k) pg[k + 1] = pg[k] + (ctx->hp[ga[k]].P + 1) / 2;
+    std::vector<uint32_t> pg(ga.size() + 1, 0), pt(ga.size() + 1, 0);
+    for (size_t k = 0; k < ga.size(); ++k) {
+      pg[k + 1] = pg[k] + (ctx->hp[ga[k]].P + 1) / 2;
+      pt[k + 1] = pt[k] + (ctx->hp[ga[k]].P + 1023) / 1024;
+    }
     ctx->ga_pairs = pg.back();
+    ctx->ga_tiles = pt.back();
     if (e == cudaSuccess) e = put(ctx->d_ga_ids, ga);
     if (e == cudaSuccess) e = put(ctx->d_ga_prefix, pg);
+    if (e == cudaSuccess) e = put(ctx->d_ga_tprefix, pt);
     if (e == cudaSuccess) e = cudaStreamSynchronize(us);
   }
   {

@@ -7,12 +7,18 @@
 //
 // Per generation g (genome in gate_idx buffer g & 1, already evaluated into
 // fit/meta buffer g & 1 by the circuit kernel without sampling):
-//   k_ga_prep  one CTA per search: SUS weights floor(clamp(F,0,1) 2^32) and
-//              their inclusive prefix sums (integers, so exact in any order),
-//              the total W, and the elite = best by (F desc, cost asc, index asc)
-//              in the working precision;
-//   k_ga_next  one warp per pair of children: parents by SUS (pointer
-//              s + m floor(W/P), parent = first c with cum[c] > pointer),
+//   k_ga_tiles one CTA per tile of 1024 circuits: SUS weights
+//              floor(clamp(F,0,1) 2^32), their inclusive prefix sums within the
+//              tile (integers, so exact in any order), the tile's total and its
+//              elite = best by (F desc, cost asc, index asc) in the working
+//              precision;
+//   k_ga_top   one CTA per search: the tiles' offsets (exclusive scan of their
+//              totals), the total W and the search's elite;
+//   k_ga_parents one thread per circuit c: SUS pointers are s + m floor(W/P),
+//              and child m's parent is the first c with cum[c] > pointer, so c
+//              writes its own children's parent index (the m whose pointer
+//              lies in [cum[c-1], cum[c])) -- no search per child;
+//   k_ga_next  one warp per pair of children: parents from that table,
 //              one-point crossover at 1 + below(u, L-1) (Ising: genes in
 //              [min, max) of two such points swapped), per-gene mutation,
 //              child 0 = the elite; written to gate_idx buffer (g+1) & 1
@@ -69,57 +75,44 @@ __device__ __forceinline__ void elite_shfl(double &F, uint32_t &cost, uint32_t &
   }
 }
 
-// One CTA per GA search, tiles of kGaThreads circuits: each thread weighs one
-// circuit, a block scan gives the tile's prefix sums, a running carry the rest.
-__global__ void __launch_bounds__(kGaThreads) k_ga_prep(const DevProblem *__restrict__ probs,
-                                                        const uint32_t *__restrict__ ids,
-                                                        DevGlobal g) {
-  const DevProblem &p = probs[ids[blockIdx.x]];
+// The tile of 1024 circuits of GA search ids[q] that block b covers, from the
+// searches' tile prefix sums
+__device__ __forceinline__ void ga_tile_of(const uint32_t *tprefix, uint32_t n_ga, uint32_t b,
+                                           uint32_t &q, uint32_t &t) {
+  q = find_ga(tprefix, n_ga, b);
+  t = b - __ldg(tprefix + q);
+}
+
+// one tile: weights, their prefix sums within the tile, the tile's total and elite
+__global__ void __launch_bounds__(kGaThreads) k_ga_tiles(const DevProblem *__restrict__ probs,
+                                                         const uint32_t *__restrict__ ids,
+                                                         const uint32_t *__restrict__ tprefix,
+                                                         uint32_t n_ga, DevGlobal g) {
+  uint32_t q, t;
+  ga_tile_of(tprefix, n_ga, blockIdx.x, q, t);
+  const DevProblem &p = probs[ids[q]];
   const uint32_t par = *g.gen & 1u;
   const uint32_t P = p.P, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t c = t * kGaThreads + tid;
   __shared__ unsigned long long s_sum[kGaThreads / 32], s_tot;
   __shared__ double s_F[kGaThreads / 32];
   __shared__ uint32_t s_cost[kGaThreads / 32], s_idx[kGaThreads / 32];
   double bF = 0.0;
   uint32_t bcost = 0xffffffffu, bidx = 0xffffffffu;
-  unsigned long long carry = 0;
-  for (uint32_t base = 0; base < P; base += kGaThreads) {
-    const uint32_t c = base + tid;
-    unsigned long long w = 0;
-    if (c < P) {
-      const double F = ga_fitness(p, par, c);
-      w = sus_weight(F);
-      const uint32_t cost = p.meta[(size_t)par * P + c] & 0xffu;
-      if (bidx == 0xffffffffu || ga_better(F, cost, c, bF, bcost, bidx)) {
-        bF = F;
-        bcost = cost;
-        bidx = c;
-      }
-    }
-    unsigned long long v = w;  // warp inclusive scan
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long u = __shfl_up_sync(kFull, v, o);
-      if (lane >= (uint32_t)o) v += u;
-    }
-    if (lane == 31) s_sum[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-      const unsigned long long x0 = s_sum[lane];
-      unsigned long long x = x0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long u = __shfl_up_sync(kFull, x, o);
-        if (lane >= (uint32_t)o) x += u;
-      }
-      s_sum[lane] = x - x0;  // exclusive prefix of the warp totals
-      if (lane == 31) s_tot = x;
-    }
-    __syncthreads();
-    if (c < P) p.ga_cum[c] = carry + s_sum[wid] + v;
-    carry += s_tot;
+  unsigned long long w = 0;
+  if (c < P) {
+    bF = ga_fitness(p, par, c);
+    w = sus_weight(bF);
+    bcost = p.meta[(size_t)par * P + c] & 0xffu;
+    bidx = c;
   }
-  // the elite: warp reduction, then across warps
+  unsigned long long v = w;  // warp inclusive scan
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(kFull, v, o);
+    if (lane >= (uint32_t)o) v += u;
+  }
+  if (lane == 31) s_sum[wid] = v;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) elite_shfl(bF, bcost, bidx, o);
   if (lane == 0) {
@@ -129,15 +122,124 @@ __global__ void __launch_bounds__(kGaThreads) k_ga_prep(const DevProblem *__rest
   }
   __syncthreads();
   if (wid == 0) {
+    const unsigned long long x0 = s_sum[lane];
+    unsigned long long x = x0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(kFull, x, o);
+      if (lane >= (uint32_t)o) x += u;
+    }
+    s_sum[lane] = x - x0;  // exclusive prefix of the warp totals
+    if (lane == 31) s_tot = x;
     double F = s_F[lane];
     uint32_t cost = s_cost[lane], idx = s_idx[lane];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) elite_shfl(F, cost, idx, o);
     if (lane == 0) {
-      p.ga_info[0] = carry;  // W
-      p.ga_info[1] = idx;    // elite
+      s_F[0] = F;
+      s_cost[0] = cost;
+      s_idx[0] = idx;
     }
   }
+  __syncthreads();
+  if (c < P) p.ga_cum[c] = s_sum[wid] + v;
+  if (tid == 0) {
+    GaTile tl;
+    tl.sum = s_tot;
+    tl.F = s_F[0];
+    tl.cost = s_cost[0];
+    tl.idx = s_idx[0];
+    p.ga_tiles[t] = tl;
+  }
+}
+
+// one search: the tiles' offsets (in place of their totals), W and the elite
+__global__ void __launch_bounds__(kGaThreads) k_ga_top(const DevProblem *__restrict__ probs,
+                                                       const uint32_t *__restrict__ ids) {
+  const DevProblem &p = probs[ids[blockIdx.x]];
+  const uint32_t nt = (p.P + kGaThreads - 1) / kGaThreads;  // <= 1024 (P <= 2^20)
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  __shared__ unsigned long long s_sum[kGaThreads / 32], s_tot;
+  __shared__ double s_F[kGaThreads / 32];
+  __shared__ uint32_t s_cost[kGaThreads / 32], s_idx[kGaThreads / 32];
+  unsigned long long w = 0;
+  double bF = 0.0;
+  uint32_t bcost = 0xffffffffu, bidx = 0xffffffffu;
+  if (tid < nt) {
+    const GaTile tl = p.ga_tiles[tid];
+    w = tl.sum;
+    bF = tl.F;
+    bcost = tl.cost;
+    bidx = tl.idx;
+  }
+  unsigned long long v = w;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(kFull, v, o);
+    if (lane >= (uint32_t)o) v += u;
+  }
+  if (lane == 31) s_sum[wid] = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) elite_shfl(bF, bcost, bidx, o);
+  if (lane == 0) {
+    s_F[wid] = bF;
+    s_cost[wid] = bcost;
+    s_idx[wid] = bidx;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned long long x0 = s_sum[lane];
+    unsigned long long x = x0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(kFull, x, o);
+      if (lane >= (uint32_t)o) x += u;
+    }
+    s_sum[lane] = x - x0;
+    if (lane == 31) s_tot = x;
+    double F = s_F[lane];
+    uint32_t cost = s_cost[lane], idx = s_idx[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) elite_shfl(F, cost, idx, o);
+    if (lane == 0) p.ga_info[1] = idx;  // elite
+  }
+  __syncthreads();
+  if (tid < nt) p.ga_tiles[tid].sum = s_sum[wid] + v - w;  // tiles before this one
+  if (tid == 0) p.ga_info[0] = s_tot;                       // W
+}
+
+// one circuit c: the children whose SUS pointer s + m D lies in
+// [cum[c-1], cum[c]) get parent c (D = floor(W/P); no table when D = 0)
+__global__ void __launch_bounds__(kGaThreads) k_ga_parents(const DevProblem *__restrict__ probs,
+                                                           const uint32_t *__restrict__ ids,
+                                                           const uint32_t *__restrict__ tprefix,
+                                                           uint32_t n_ga, DevGlobal g) {
+  uint32_t q, t;
+  ga_tile_of(tprefix, n_ga, blockIdx.x, q, t);
+  const DevProblem &p = probs[ids[q]];
+  const uint32_t P = p.P;
+  const uint32_t c = t * kGaThreads + threadIdx.x;
+  if (c >= P) return;
+  const unsigned long long W = p.ga_info[0];
+  const unsigned long long D = W / P;
+  if (D == 0) return;
+  const uint32_t gen = *g.gen;
+  const uint4 u = draw(p, 0, 0, gen, kStGa);
+  const unsigned long long r64 = ((unsigned long long)u.y << 32) | u.x;
+  const unsigned long long s0 = __umul64hi(r64, D);
+  const unsigned long long incl = p.ga_cum[c] + p.ga_tiles[t].sum;
+  unsigned long long excl = 0;
+  if (c > 0) {
+    const uint32_t tp = (c - 1) / kGaThreads;
+    excl = p.ga_cum[c - 1] + p.ga_tiles[tp].sum;
+  }
+  // children m with s0 + m D < x
+  auto below_ptr = [&](unsigned long long x) -> unsigned long long {
+    return x <= s0 ? 0ull : (x - s0 + D - 1) / D;
+  };
+  unsigned long long m = below_ptr(excl), m_end = below_ptr(incl);
+  if (m_end > P) m_end = P;
+  for (; m < m_end; ++m) p.ga_parent[m] = c;
 }
 
 // Per-gene mutation: word x decides a fresh gene (gate from y; Ising: its
@@ -159,17 +261,6 @@ __device__ __forceinline__ void ga_mutate(const DevProblem &p, const DevGlobal &
 }
 
 // first c in [0, P) with cum[c] > ptr (P - 1 if none)
-__device__ __forceinline__ uint32_t sus_parent(const unsigned long long *cum, uint32_t P,
-                                               unsigned long long ptr) {
-  uint32_t lo = 0, hi = P - 1;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (cum[mid] > ptr) hi = mid;
-    else lo = mid + 1;
-  }
-  return lo;
-}
-
 __global__ void __launch_bounds__(256) k_ga_next(const DevProblem *__restrict__ probs,
                                                  const uint32_t *__restrict__ ids,
                                                  const uint32_t *__restrict__ prefix,
@@ -193,12 +284,9 @@ __global__ void __launch_bounds__(256) k_ga_next(const DevProblem *__restrict__ 
     const uint32_t elite = (uint32_t)p.ga_info[1];
     const unsigned long long D = W / P;
     uint32_t a = m0, b = m1 < P ? m1 : m0;
-    if (D > 0) {
-      const uint4 u = draw(p, 0, 0, gen, kStGa);
-      const unsigned long long r64 = ((unsigned long long)u.y << 32) | u.x;
-      const unsigned long long s0 = __umul64hi(r64, D);
-      a = sus_parent(p.ga_cum, P, s0 + (unsigned long long)m0 * D);
-      if (m1 < P) b = sus_parent(p.ga_cum, P, s0 + (unsigned long long)m1 * D);
+    if (D > 0) {  // SUS parents, from the table k_ga_parents wrote
+      a = p.ga_parent[m0];
+      if (m1 < P) b = p.ga_parent[m1];
     }
     // gene t of child m0 comes from parent b for t in [lo, hi), else from a
     uint32_t lo = L, hi = L;
@@ -262,10 +350,15 @@ cudaError_t launch_ga_init(const DevProblem *probs, uint32_t prob, uint32_t P, u
   return cudaGetLastError();
 }
 
-cudaError_t launch_ga_prep(const DevProblem *probs, const uint32_t *ids, uint32_t n_ga,
-                           const DevGlobal &g, cudaStream_t st) {
-  if (!n_ga) return cudaSuccess;
-  k_ga_prep<<<n_ga, kGaThreads, 0, st>>>(probs, ids, g);
+cudaError_t launch_ga_prep(const DevProblem *probs, const uint32_t *ids, const uint32_t *tprefix,
+                           uint32_t n_ga, uint32_t n_tiles, const DevGlobal &g, cudaStream_t st) {
+  if (!n_ga || !n_tiles) return cudaSuccess;
+  k_ga_tiles<<<n_tiles, kGaThreads, 0, st>>>(probs, ids, tprefix, n_ga, g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_ga_top<<<n_ga, kGaThreads, 0, st>>>(probs, ids);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_ga_parents<<<n_tiles, kGaThreads, 0, st>>>(probs, ids, tprefix, n_ga, g);
   return cudaGetLastError();
 }
 

@@ -14,7 +14,8 @@
 //                seg_id: P*L uint32 (QEQEA only)
 //   mut_list   : 2 x P individual ids, mut_cnt: 2 counters (QEQEA only)
 //   amps       : 2 x P*L float2 slot angles as qubit amplitudes (Ising only)
-//   ga_cum     : P uint64 SUS prefix sums (GA only)
+//   ga_cum     : P uint64 SUS prefix sums within tiles of 1024, ga_tiles: the
+//                tiles' offsets and elites, ga_parent: P SUS parents (GA only)
 //   fit32/fit64: 2 x P (working-precision fitness), meta: 2 x P (cost | work << 8)
 // where S = R*P*L and seg = r*L*P + i*L + t (Eq. (10)).
 #pragma once
@@ -65,6 +66,14 @@ struct Best {
   float2 best_amps[64];  // Ising: the best circuit's slot angles
 };
 
+// one scan tile of a GA search's SUS weights: the sum of its weights (after
+// the tile scan: the sum of all earlier tiles' weights) and its elite
+struct GaTile {
+  unsigned long long sum;
+  double F;
+  uint32_t cost, idx;
+};
+
 struct DevProblem {
   uint32_t n, N, L, P, R, G, LP;
   uint32_t lib, prec, fit_kind, enc, topk, k;  // k = max(topk, 1)
@@ -113,9 +122,12 @@ struct DevProblem {
   // generation g appends to half g & 1 and clears the counter of the other)
   uint32_t *mut_list;
   uint32_t *mut_cnt;
-  // GA buffers: SUS prefix sums of the weights, and {W, elite}
+  // GA buffers: SUS prefix sums of the weights within each scan tile, the
+  // tiles (offsets and elites), {W, elite}, and each child's SUS parent
   unsigned long long *ga_cum;
+  GaTile *ga_tiles;
   unsigned long long *ga_info;
+  uint32_t *ga_parent;
 };
 
 // context-wide device pointers

@@ -120,8 +120,9 @@ cudaError_t launch_gather_topk(const DevProblem *probs, const RankJob *jobs, con
 // next genome (one warp per pair of children; prefix = pair-count prefix sums)
 cudaError_t launch_ga_init(const DevProblem *probs, uint32_t prob, uint32_t P, uint32_t L,
                            const DevGlobal &g, cudaStream_t st);
-cudaError_t launch_ga_prep(const DevProblem *probs, const uint32_t *ids, uint32_t n_ga,
-                           const DevGlobal &g, cudaStream_t st);
+// tprefix: the searches' prefix sums of ceil(P / 1024) scan tiles, n_tiles their total
+cudaError_t launch_ga_prep(const DevProblem *probs, const uint32_t *ids, const uint32_t *tprefix,
+                           uint32_t n_ga, uint32_t n_tiles, const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_ga_next(const LaunchCfg &lc, const DevProblem *probs, const uint32_t *ids,
                            const uint32_t *prefix, uint32_t n_ga, uint32_t total_pairs,
                            const DevGlobal &g, cudaStream_t st);
