@@ -53,7 +53,7 @@ circuits = st.tuples(st.integers(1, 5), st.sampled_from(LIBS), st.integers(0, 2 
                      st.integers(0, 12), st.integers(0, 12))
 
 
-@settings(max_examples=60, deadline=None)
+@settings(max_examples=60, deadline=None, derandomize=True)
 @given(circuits)
 def test_composition_is_the_ordered_product(case):
     n, lib, seed, a, b = case
@@ -65,7 +65,7 @@ def test_composition_is_the_ordered_product(case):
     assert np.abs(S12 - _S(n, lib, g2) @ _S(n, lib, g1)).max() < 1e-12
 
 
-@settings(max_examples=60, deadline=None)
+@settings(max_examples=60, deadline=None, derandomize=True)
 @given(circuits)
 def test_circuit_then_its_inverse_is_the_identity(case):
     n, lib, seed, a, _ = case
@@ -79,7 +79,7 @@ def test_circuit_then_its_inverse_is_the_identity(case):
     assert oracle.score(n, S, list(range(1 << n))) == pytest.approx(1.0, abs=1e-12)
 
 
-@settings(max_examples=40, deadline=None)
+@settings(max_examples=40, deadline=None, derandomize=True)
 @given(circuits, st.floats(0.0, 2 * np.pi))
 def test_dense_fitness_ignores_a_global_phase(case, alpha):
     n, lib, seed, a, b = case
@@ -89,7 +89,11 @@ def test_dense_fitness_ignores_a_global_phase(case, alpha):
     T = _S(n, lib, rng.integers(0, G, b).astype(np.uint8))
     f0 = oracle.score_dense(n, S, T)
     f1 = oracle.score_dense(n, S, T * np.exp(1j * alpha))
-    assert abs(f0 - f1) < 1e-9
+    # Eq. (11) takes 1 - sqrt(d) with d = (N - |tr|) / N: the phase moves |tr|
+    # by a few rounding errors of an N-term sum, which the square root
+    # magnifies to sqrt(|delta d|) near d = 0 (e.g. S = T = I gives 1.5e-8)
+    N = 1 << n
+    assert abs(f0 - f1) <= np.sqrt(16 * N * np.finfo(float).eps)
     assert 0.0 <= f0 <= 1.0 + 1e-12
 
 
