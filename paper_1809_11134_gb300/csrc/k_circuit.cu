@@ -1329,6 +1329,13 @@ template <int NQ, bool CANON>
 constexpr int block_threads() {
   return (NQ == 5 && !CANON) ? 128 : 256;
 }
+// binary64 at 5 qubits: each circuit's columns on 4 warps (8 rows per lane:
+// ~110 registers without spills instead of 255 with spills, twice the warps
+// per SM), log2 of the warps per circuit
+template <int NQ, bool CANON>
+constexpr int circuit_split() {
+  return (CANON && NQ == 5) ? 2 : 0;
+}
 template <int NQ, bool CANON, bool ISING>
 constexpr int min_blocks() {
   return (NQ == 5 && !CANON) ? 6 : ((NQ <= 3 && !CANON) ? 6 : 1);
@@ -1341,10 +1348,17 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
                                               const uint32_t *__restrict__ group,
                                               const uint32_t *__restrict__ prefix,
                                               uint32_t n_group, uint32_t total, DevGlobal g) {
+  constexpr int WB = circuit_split<NQ, CANON>();
   const int lane = threadIdx.x & 31;
+  const int sub = (threadIdx.x >> 5) & ((1 << WB) - 1);  // warp within the circuit's group
+  __shared__ double2 s_terms[WB ? (block_threads<NQ, CANON>() / 32) >> WB : 1][32];
+  Split sp;
+  sp.sub = sub;
+  sp.bar = 1 + ((threadIdx.x >> 5) >> WB);
+  sp.sv = s_terms[WB ? (threadIdx.x >> 5) >> WB : 0];
   const uint32_t gen = *g.gen;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+  const uint32_t nw = (gridDim.x * blockDim.x) >> (5 + WB);
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> (5 + WB); w < total; w += nw) {
     const uint32_t q = find_problem(prefix, n_group, w);
     const DevProblem &p = probs[group[q]];
     const uint32_t c = w - prefix[q];
@@ -1369,26 +1383,32 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
         if ((uint32_t)lane < p.L) a0 = amps[lane];
         if ((uint32_t)lane + 32 < p.L) a1 = amps[lane + 32];
       }
-      prefetch_mutated(p, c, gen, lane);
+      if (sub == 0) prefetch_mutated(p, c, gen, lane);
     } else if (qeqea) {
       float2 *amps = ISING ? p.amps + (size_t)par * p.P * p.L + (size_t)c * p.L : nullptr;
+      // (with the columns split over a group of warps every warp samples the
+      // same slots; the first one writes them, lists the mutation and scatters)
       if ((uint32_t)lane < p.L) {
         uint32_t gg;
         sample_slot<ISING>(p, c, lane, gen, gg, seg0, a0);
-        gate_idx[(size_t)c * p.L + lane] = (uint8_t)gg;
-        p.seg_id[(size_t)c * p.L + lane] = seg0;
-        if constexpr (ISING) amps[lane] = a0;
+        if (sub == 0) {
+          gate_idx[(size_t)c * p.L + lane] = (uint8_t)gg;
+          p.seg_id[(size_t)c * p.L + lane] = seg0;
+          if constexpr (ISING) amps[lane] = a0;
+        }
         o0 = op_of(p, gg, bad);
       }
       if ((uint32_t)lane + 32 < p.L) {
         uint32_t gg;
         sample_slot<ISING>(p, c, lane + 32, gen, gg, seg1, a1);
-        gate_idx[(size_t)c * p.L + lane + 32] = (uint8_t)gg;
-        p.seg_id[(size_t)c * p.L + lane + 32] = seg1;
-        if constexpr (ISING) amps[lane + 32] = a1;
+        if (sub == 0) {
+          gate_idx[(size_t)c * p.L + lane + 32] = (uint8_t)gg;
+          p.seg_id[(size_t)c * p.L + lane + 32] = seg1;
+          if constexpr (ISING) amps[lane + 32] = a1;
+        }
         o1 = op_of(p, gg, bad);
       }
-      prefetch_mutated(p, c, gen, lane);
+      if (sub == 0) prefetch_mutated(p, c, gen, lane);
     } else {
       // GA: this generation's genome, bred by the previous generation (k_ga_next)
       if ((uint32_t)lane < p.L) o0 = op_of(p, gate_idx[(size_t)c * p.L + lane], bad);
@@ -1404,8 +1424,9 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
       half_angle(a0.x, a0.y, ic0, is0);
       half_angle(a1.x, a1.y, ic1, is1);
     }
-    CircuitOut out =
-        compose_score<NQ, R, CANON, ISING, EXT>(p, lane, o0, o1, (R *)nullptr, ic0, is0, ic1, is1);
+    CircuitOut out = compose_score<NQ, R, CANON, ISING, EXT, WB>(p, lane, o0, o1, (R *)nullptr,
+                                                                  ic0, is0, ic1, is1, sp);
+    if (sub != 0) continue;  // the score is on the group's first warp
     const bool nonfinite = !isfinite(out.F);
     if (lane == 0) {
       if constexpr (CANON) p.fit64[(size_t)par * p.P + c] = out.F;
@@ -1480,11 +1501,18 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
                                               const uint8_t *__restrict__ gates,
                                               const float2 *__restrict__ amps, uint32_t n,
                                               R *fit, uint32_t *cost, R *S, DevGlobal g) {
+  constexpr int WB = circuit_split<NQ, CANON>();
   const DevProblem &p = probs[prob];
   const int lane = threadIdx.x & 31;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const int sub = (threadIdx.x >> 5) & ((1 << WB) - 1);  // warp within the circuit's group
+  __shared__ double2 s_terms[WB ? (block_threads<NQ, CANON>() / 32) >> WB : 1][32];
+  Split sp;
+  sp.sub = sub;
+  sp.bar = 1 + ((threadIdx.x >> 5) >> WB);
+  sp.sv = s_terms[WB ? (threadIdx.x >> 5) >> WB : 0];
+  const uint32_t nw = (gridDim.x * blockDim.x) >> (5 + WB);
   const size_t NN2 = 2 * (size_t)p.N * p.N;
-  for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n; c += nw) {
+  for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> (5 + WB); c < n; c += nw) {
     bool bad = false;
     uint32_t o0 = kOpIdentity, o1 = kOpIdentity;
     if ((uint32_t)lane < p.L) o0 = op_of(p, gates[(size_t)c * p.L + lane], bad);
@@ -1501,9 +1529,9 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
         half_angle(a.x, a.y, ic1, is1);
       }
     }
-    CircuitOut out = compose_score<NQ, R, CANON, ISING>(
-        p, lane, o0, o1, S ? S + NN2 * c : (R *)nullptr, ic0, is0, ic1, is1);
-    if (lane == 0) {
+    CircuitOut out = compose_score<NQ, R, CANON, ISING, true, WB>(
+        p, lane, o0, o1, S ? S + NN2 * c : (R *)nullptr, ic0, is0, ic1, is1, sp);
+    if (lane == 0 && sub == 0) {
       double F = anybad ? __longlong_as_double(0x7ff8000000000000ll) : out.F;
       if (fit) fit[c] = (R)F;
       if (cost) cost[c] = out.cost;
@@ -1609,7 +1637,7 @@ cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs
 #define QE_LK(NQ, R, C, I)                                                                \
   {                                                                                       \
     constexpr int bt = block_threads<NQ, C>();                                            \
-    const dim3 grid = grid_for(lc, total, per, bt / 32);                                  \
+    const dim3 grid = grid_for(lc, total, per, (bt / 32) >> circuit_split<NQ, C>());      \
     if (ext)                                                                              \
       k_step<NQ, R, C, I, true><<<grid, bt, 0, st>>>(probs, group, prefix, n_group, total, g); \
     else                                                                                  \
@@ -1660,7 +1688,7 @@ cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *prob
 #define QE_LK(NQ, R, C, I)                                                                 \
   {                                                                                        \
     constexpr int bt = block_threads<NQ, C>();                                             \
-    k_eval<NQ, R, C, I><<<grid_for(lc, n, per, bt / 32), bt, 0, st>>>(                    \
+    k_eval<NQ, R, C, I><<<grid_for(lc, n, per, (bt / 32) >> circuit_split<NQ, C>()), bt, 0, st>>>( \
         probs, prob, gates, amps, n, (R *)fit, cost, (R *)S, g);                           \
   }
 #define QE_L(NQ)                                                                           \
