@@ -66,7 +66,7 @@ struct BatchSlot {
   cudaEvent_t ev_done = nullptr;
   size_t err_off = 0;  // the slot's error word in its staging
   uint32_t desc_version = 0;  // the context's descriptors the slot's copies were made from
-  // the call in flight
+  // the call in flight (ticket: also the slot's last call, for reuse order)
   bool busy = false;
   uint64_t ticket = 0;
   qe_ranked *h_topk = nullptr;
@@ -115,6 +115,8 @@ struct qe_ctx {
   // evaluations and ranking on its slot's stream and scratch, so that calls
   // in flight overlap
   BatchSlot bslot[kBatchSlots];
+  std::vector<char> b_seen;     // the batch call's argument check
+  std::vector<uint32_t> b_key;  // the batch call's graph key
   uint64_t next_ticket = 1;
   // bumped whenever a search's descriptor changes after qe_init (qe_set_target):
   // a batch slot whose copies are older recaptures its layout
@@ -1143,8 +1145,8 @@ struct BatchLayout {
   // ranking kernels may read
   size_t cand = 0, cand_f = 0, cand_n = 0, rq = 0, words = 0;
   // uploaded once per layout: jobs, top-k offsets, gate table, the jobs'
-  // search descriptors pointing at the slot's scratch
-  size_t jobs = 0, koff = 0, gtab = 0, probs = 0, total = 0;
+  // search descriptors pointing at the slot's scratch, the evaluation jobs
+  size_t jobs = 0, koff = 0, gtab = 0, probs = 0, ejobs = 0, total = 0;
 };
 
 static BatchLayout batch_layout(size_t gate_bytes, size_t n_total, size_t fb, size_t k_total,
@@ -1179,8 +1181,20 @@ static BatchLayout batch_layout(size_t gate_bytes, size_t n_total, size_t fb, si
   o += align256(n_items * sizeof(void *));
   b.probs = o;
   o += align256(n_items * sizeof(DevProblem));
+  b.ejobs = o;
+  o += align256(n_items * sizeof(EvalJob));
   b.total = o;
   return b;
+}
+
+// page-locked host memory (the only host memory a graph's copies may use)
+static bool host_pinned(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
 }
 
 // Enqueue one batched host evaluation in a free slot, all on the slot's
@@ -1198,7 +1212,8 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
   const uint32_t np = (uint32_t)ctx->probs.size();
   if (!h_probs || !h_n_circuits) return fail(ctx, QE_EINVAL, "null item array");
   if (n_items < 1 || n_items > np) return fail(ctx, QE_EINVAL, "n_items must be 1..n_probs");
-  std::vector<char> seen(np, 0);
+  std::vector<char> &seen = ctx->b_seen;  // reused: no allocation per call
+  seen.assign(np, 0);
   uint32_t prec = 0;
   size_t gate_bytes = 0, n_total = 0, k_total = 0;
   for (uint32_t m = 0; m < n_items; ++m) {
@@ -1219,32 +1234,65 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
   }
   if ((gate_bytes && !h_gate_idx) || (n_total && !h_fitness))
     return fail(ctx, QE_EINVAL, "null buffer");
-  BatchSlot *slot = nullptr;
-  for (BatchSlot &b : ctx->bslot)
-    if (!b.busy) {
-      slot = &b;
-      break;
-    }
-  if (!slot) return fail(ctx, QE_ESTATE, "every batch slot has a call in flight: wait for one first");
-  BatchSlot &b = *slot;
   const size_t fb = prec == 0 ? 8 : 4;
   const bool rank = h_topk != nullptr;
-  if (!b.st) {
-    QE_CUDA(ctx, cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking));
-    QE_CUDA(ctx, cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming));
-  }
-
-  const BatchLayout lay = batch_layout(gate_bytes, n_total, fb, k_total, n_items);
-  std::vector<uint32_t> key;
-  key.reserve(2 + 2 * (size_t)n_items);
+  // page-locked caller buffers are copied by the call's graph itself (one
+  // launch per call); other memory by copies around it.  Checked every call:
+  // a graph is only reused for the same addresses, still page-locked.
+  const bool fold = (!gate_bytes || host_pinned(h_gate_idx)) && (!n_total || host_pinned(h_fitness));
+  std::vector<uint32_t> &key = ctx->b_key;
+  key.clear();
   key.push_back(rank ? 1u : 0u);
   key.push_back(n_items);
   for (uint32_t m = 0; m < n_items; ++m) {
     key.push_back(h_probs[m]);
     key.push_back(h_n_circuits[m]);
   }
+  key.push_back(fold ? 1u : 0u);
+  if (fold) {
+    const uint64_t pg = (uint64_t)(uintptr_t)h_gate_idx, pf = (uint64_t)(uintptr_t)h_fitness;
+    key.push_back((uint32_t)pg);
+    key.push_back((uint32_t)(pg >> 32));
+    key.push_back((uint32_t)pf);
+    key.push_back((uint32_t)(pf >> 32));
+  }
+  // a free slot whose graph was made for this call; else an unused one; else
+  // the free slot used longest ago (callers that cycle through a ring of
+  // buffer sets keep one graph per set)
+  BatchSlot *slot = nullptr, *spare = nullptr;
+  for (BatchSlot &b : ctx->bslot) {
+    if (b.busy) continue;
+    if (b.ex && b.key == key && b.desc_version == ctx->desc_version) {
+      slot = &b;
+      break;
+    }
+    if (!spare || (spare->ex && (!b.ex || b.ticket < spare->ticket))) spare = &b;
+  }
+  if (!slot) slot = spare;
+  if (!slot) return fail(ctx, QE_ESTATE, "every batch slot has a call in flight: wait for one first");
+  BatchSlot &b = *slot;
+  if (!b.st) {
+    QE_CUDA(ctx, cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking));
+    QE_CUDA(ctx, cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming));
+  }
+  // pinned host staging: the top-k lists and, after them, the error word
+  // (the gathered lists end with it; without a ranking it is copied alone)
+  const size_t kt = rank ? k_total : 0;
+  const size_t hb = (kt + 1) * sizeof(Ranked);
+  bool new_h = false;
+  if (hb > b.h_bytes) {
+    QE_CUDA(ctx, cudaStreamSynchronize(b.st));
+    if (b.h) cudaFreeHost(b.h);
+    b.h = nullptr;
+    b.h_bytes = 0;
+    QE_CUDA(ctx, cudaHostAlloc(&b.h, hb, cudaHostAllocDefault));
+    b.h_bytes = hb;
+    new_h = true;  // a graph that copies into the old staging is stale
+  }
+
+  const BatchLayout lay = batch_layout(gate_bytes, n_total, fb, k_total, n_items);
   const bool regrow = lay.total > b.d_bytes;
-  if (regrow || key != b.key || !b.ex || b.desc_version != ctx->desc_version) {
+  if (regrow || new_h || key != b.key || !b.ex || b.desc_version != ctx->desc_version) {
     if (b.ex) cudaGraphExecDestroy(b.ex);
     if (b.eg) cudaGraphDestroy(b.eg);
     b.ex = nullptr;
@@ -1318,33 +1366,79 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     }
     const uint32_t n_jobs = (uint32_t)items.size();
     hk[n_jobs] = (uint32_t)ko;
+    // the evaluation jobs grouped by width: one launch per width present, its
+    // jobs' circuits numbered consecutively
+    EvalJob *he = (EvalJob *)(b.meta.data() + (lay.ejobs - lay.jobs));
+    uint32_t w_first[QE_MAX_QUBITS + 1] = {0}, w_jobs[QE_MAX_QUBITS + 1] = {0};
+    uint32_t w_total[QE_MAX_QUBITS + 1] = {0};
+    uint32_t ne = 0;
+    for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq) {
+      w_first[nq] = ne;
+      for (uint32_t x = 0; x < n_jobs; ++x) {
+        const uint32_t m = items[x];
+        if (ctx->hp[h_probs[m]].n != nq) continue;
+        EvalJob &ej = he[ne++];
+        ej.prob = x;
+        ej.first = w_total[nq];
+        ej.n = h_n_circuits[m];
+        ej.pad = 0;
+        ej.gates = (const uint8_t *)(base + lay.gates + goff[m]);
+        ej.fit = base + lay.fit + foff[m] * fb;
+        ej.cost = (uint32_t *)(base + lay.cost) + foff[m];
+        w_total[nq] += h_n_circuits[m];
+        ++w_jobs[nq];
+      }
+    }
     QE_CUDA(ctx, cudaMemcpyAsync(base + lay.jobs, b.meta.data(), b.meta.size(),
                                  cudaMemcpyHostToDevice, b.st));
-    // the evaluations, spread over three captured streams
+    // the evaluations: one launch per width, on up to three captured streams
+    // when there are several widths (one width: a single chain)
+    const DevProblem *sprobs = (const DevProblem *)(base + lay.probs);
+    const EvalJob *dej = (const EvalJob *)(base + lay.ejobs);
+    uint32_t n_widths = 0;
+    for (uint32_t nq = 1; nq <= QE_MAX_QUBITS; ++nq) n_widths += w_jobs[nq] ? 1u : 0u;
     cudaStream_t cs = ctx->cap;
     cudaStream_t lanes[3] = {cs, ctx->side, ctx->side2};
     QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaEventRecord(ctx->ev_fork, cs);
-    for (int l = 1; l < 3 && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(lanes[l], ctx->ev_fork, 0);
-    for (uint32_t x = 0; x < n_jobs && e == cudaSuccess; ++x) {
-      const uint32_t m = items[x];
-      const DevProblem &d = ctx->hp[h_probs[m]];
-      e = launch_eval(ctx->lc, d.n, ctx->d_probs, h_probs[m], prec == 0,
-                      (const uint8_t *)(base + lay.gates + goff[m]), nullptr, h_n_circuits[m],
-                      base + lay.fit + foff[m] * fb, (uint32_t *)(base + lay.cost) + foff[m],
-                      nullptr, gs, lanes[x % 3]);
+    cudaError_t e = cudaSuccess;
+    if (fold && gate_bytes)  // the circuits in, ahead of every evaluation
+      e = cudaMemcpyAsync(base + lay.gates, h_gate_idx, gate_bytes, cudaMemcpyHostToDevice, cs);
+    const bool forked = n_widths > 1;
+    if (forked) {
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, cs);
+      for (int l = 1; l < 3 && e == cudaSuccess; ++l)
+        e = cudaStreamWaitEvent(lanes[l], ctx->ev_fork, 0);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join2, 0);
+    for (uint32_t nq = 1, wi = 0; nq <= QE_MAX_QUBITS && e == cudaSuccess; ++nq) {
+      if (!w_jobs[nq]) continue;
+      e = launch_eval_jobs(ctx->lc, nq, prec == 0, sprobs, dej + w_first[nq], w_jobs[nq],
+                           w_total[nq], gs, lanes[forked ? wi % 3 : 0]);
+      ++wi;
+    }
+    if (forked) {
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join2, ctx->side2);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join2, 0);
+    }
+    if (fold && n_total && e == cudaSuccess) {
+      // the fitness out on a side stream once every evaluation has finished
+      // (plain dependencies on all of them), beside the ranking
+      e = cudaEventRecord(ctx->ev_fork2, cs);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork2, 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h_fitness, base + lay.fit, n_total * fb, cudaMemcpyDeviceToHost,
+                            ctx->side);
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+    }
+    if (fold && !rank && e == cudaSuccess)  // the error word the evaluations set
+      e = cudaMemcpyAsync(b.h, base + lay.err, 4, cudaMemcpyDeviceToHost, cs);
     // then, in the same graph, the ranking of every item with circuits: the
     // jobs' descriptors send each sorted list straight to its place in the
     // gathered output, and the sort writes the error word after them and
     // clears the slot's rescoring queue (zero when the slot is allocated)
     if (rank && e == cudaSuccess) {
       const RankJob *dj = (const RankJob *)(base + lay.jobs);
-      const DevProblem *sprobs = (const DevProblem *)(base + lay.probs);
       Ranked *gathered = (Ranked *)(base + lay.topk);
       if (n_jobs) {
         uint32_t max_n = 0;
@@ -1368,6 +1462,11 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
                                cs);
       }
     }
+    if (fold && e == cudaSuccess) {
+      // the lists and error word out after the sort, and the fitness copy joined
+      if (rank) e = cudaMemcpyAsync(b.h, base + lay.topk, hb, cudaMemcpyDeviceToHost, cs);
+      if (n_total && e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
+    }
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e != cudaSuccess) {
@@ -1382,28 +1481,22 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     b.key = key;
     b.desc_version = ctx->desc_version;
   }
-  // pinned host staging: the top-k lists and, after them, the error word
-  // (the gathered lists end with it; without a ranking it is copied alone)
-  const size_t kt = rank ? k_total : 0;
-  const size_t hb = (kt + 1) * sizeof(Ranked);
-  if (hb > b.h_bytes) {
-    if (b.h) cudaFreeHost(b.h);
-    b.h = nullptr;
-    b.h_bytes = 0;
-    QE_CUDA(ctx, cudaHostAlloc(&b.h, hb, cudaHostAllocDefault));
-    b.h_bytes = hb;
-  }
   char *base = (char *)b.d;
-  if (gate_bytes)
-    QE_CUDA(ctx, cudaMemcpyAsync(base + lay.gates, h_gate_idx, gate_bytes, cudaMemcpyHostToDevice,
-                                 b.st));
-  QE_CUDA(ctx, cudaGraphLaunch(b.ex, b.st));
-  if (n_total)
-    QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, base + lay.fit, n_total * fb, cudaMemcpyDeviceToHost,
-                                 b.st));
-  if (rank) QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.topk, hb, cudaMemcpyDeviceToHost, b.st));
-  else QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.err, 4, cudaMemcpyDeviceToHost, b.st));
-  QE_CUDA(ctx, cudaEventRecord(b.ev_done, b.st));
+  if (fold) {
+    QE_CUDA(ctx, cudaGraphLaunch(b.ex, b.st));
+    QE_CUDA(ctx, cudaEventRecord(b.ev_done, b.st));
+  } else {
+    if (gate_bytes)
+      QE_CUDA(ctx, cudaMemcpyAsync(base + lay.gates, h_gate_idx, gate_bytes,
+                                   cudaMemcpyHostToDevice, b.st));
+    QE_CUDA(ctx, cudaGraphLaunch(b.ex, b.st));
+    if (n_total)
+      QE_CUDA(ctx, cudaMemcpyAsync(h_fitness, base + lay.fit, n_total * fb,
+                                   cudaMemcpyDeviceToHost, b.st));
+    if (rank) QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.topk, hb, cudaMemcpyDeviceToHost, b.st));
+    else QE_CUDA(ctx, cudaMemcpyAsync(b.h, base + lay.err, 4, cudaMemcpyDeviceToHost, b.st));
+    QE_CUDA(ctx, cudaEventRecord(b.ev_done, b.st));
+  }
   b.busy = true;
   b.ticket = ctx->next_ticket++;
   b.h_topk = h_topk;

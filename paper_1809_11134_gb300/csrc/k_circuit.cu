@@ -1494,6 +1494,56 @@ __global__ void __launch_bounds__(256) k_sample(const DevProblem *__restrict__ p
   }
 }
 
+// One caller-provided circuit: its gate string g_c (and Ising slot angles a_c)
+// composed and scored by the circuit's warp group; lane 0 of its first warp
+// stores the fitness (NaN for an invalid gate index) and cost, and sets the
+// error word.
+template <int NQ, typename R, bool CANON, bool ISING>
+__device__ __forceinline__ void eval_one(const DevProblem &p, int lane, const Split &sp,
+                                         const uint8_t *__restrict__ g_c,
+                                         const float2 *__restrict__ a_c, R *fit_c,
+                                         uint32_t *cost_c, R *S_c, const DevGlobal &g) {
+  constexpr int WB = circuit_split<NQ, CANON>();
+  bool bad = false;
+  uint32_t o0 = kOpIdentity, o1 = kOpIdentity;
+  if ((uint32_t)lane < p.L) o0 = op_of(p, g_c[lane], bad);
+  if ((uint32_t)lane + 32 < p.L) o1 = op_of(p, g_c[lane + 32], bad);
+  const bool anybad = __any_sync(kFull, bad);
+  R ic0 = R(1), is0 = R(0), ic1 = R(1), is1 = R(0);
+  if constexpr (ISING) {
+    if ((uint32_t)lane < p.L) {
+      const float2 a = a_c[lane];
+      half_angle(a.x, a.y, ic0, is0);
+    }
+    if ((uint32_t)lane + 32 < p.L) {
+      const float2 a = a_c[lane + 32];
+      half_angle(a.x, a.y, ic1, is1);
+    }
+  }
+  CircuitOut out =
+      compose_score<NQ, R, CANON, ISING, true, WB>(p, lane, o0, o1, S_c, ic0, is0, ic1, is1, sp);
+  if (lane == 0 && sp.sub == 0) {
+    double F = anybad ? __longlong_as_double(0x7ff8000000000000ll) : out.F;
+    if (fit_c) *fit_c = (R)F;
+    if (cost_c) *cost_c = out.cost;
+    if (anybad) atomicOr(g.err, kErrBadGate);
+    else if (!isfinite(F)) atomicOr(g.err, kErrNonFinite);
+  }
+}
+
+// this thread's place in its circuit's warp group (binary64 at 5 qubits: four
+// warps per circuit, the score's terms in s_terms)
+#define QE_EVAL_SPLIT(NQ, CANON)                                                    \
+  constexpr int WB = circuit_split<NQ, CANON>();                                    \
+  const int lane = threadIdx.x & 31;                                                \
+  __shared__ double2 s_terms[WB ? (block_threads<NQ, CANON>() / 32) >> WB : 1][32]; \
+  Split sp;                                                                         \
+  sp.sub = (threadIdx.x >> 5) & ((1 << WB) - 1);                                    \
+  sp.bar = 1 + ((threadIdx.x >> 5) >> WB);                                          \
+  sp.sv = s_terms[WB ? (threadIdx.x >> 5) >> WB : 0];                               \
+  const uint32_t nw = (gridDim.x * blockDim.x) >> (5 + WB);                         \
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> (5 + WB);
+
 // Fitness (and optionally the unitaries) of caller-provided gate strings
 // (Ising: with every slot's angle as qubit amplitudes in amps).
 template <int NQ, typename R, bool CANON, bool ISING>
@@ -1501,45 +1551,39 @@ __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CAN
                                               const uint8_t *__restrict__ gates,
                                               const float2 *__restrict__ amps, uint32_t n,
                                               R *fit, uint32_t *cost, R *S, DevGlobal g) {
-  constexpr int WB = circuit_split<NQ, CANON>();
+  QE_EVAL_SPLIT(NQ, CANON)
   const DevProblem &p = probs[prob];
-  const int lane = threadIdx.x & 31;
-  const int sub = (threadIdx.x >> 5) & ((1 << WB) - 1);  // warp within the circuit's group
-  __shared__ double2 s_terms[WB ? (block_threads<NQ, CANON>() / 32) >> WB : 1][32];
-  Split sp;
-  sp.sub = sub;
-  sp.bar = 1 + ((threadIdx.x >> 5) >> WB);
-  sp.sv = s_terms[WB ? (threadIdx.x >> 5) >> WB : 0];
-  const uint32_t nw = (gridDim.x * blockDim.x) >> (5 + WB);
   const size_t NN2 = 2 * (size_t)p.N * p.N;
-  for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> (5 + WB); c < n; c += nw) {
-    bool bad = false;
-    uint32_t o0 = kOpIdentity, o1 = kOpIdentity;
-    if ((uint32_t)lane < p.L) o0 = op_of(p, gates[(size_t)c * p.L + lane], bad);
-    if ((uint32_t)lane + 32 < p.L) o1 = op_of(p, gates[(size_t)c * p.L + lane + 32], bad);
-    const bool anybad = __any_sync(kFull, bad);
-    R ic0 = R(1), is0 = R(0), ic1 = R(1), is1 = R(0);
-    if constexpr (ISING) {
-      if ((uint32_t)lane < p.L) {
-        const float2 a = amps[(size_t)c * p.L + lane];
-        half_angle(a.x, a.y, ic0, is0);
-      }
-      if ((uint32_t)lane + 32 < p.L) {
-        const float2 a = amps[(size_t)c * p.L + lane + 32];
-        half_angle(a.x, a.y, ic1, is1);
-      }
+  for (uint32_t c = w0; c < n; c += nw)
+    eval_one<NQ, R, CANON, ISING>(p, lane, sp, gates + (size_t)c * p.L,
+                                  ISING ? amps + (size_t)c * p.L : nullptr,
+                                  fit ? fit + c : nullptr, cost ? cost + c : nullptr,
+                                  S ? S + NN2 * c : nullptr, g);
+}
+
+// Several searches' caller-provided circuits of one width in one launch (the
+// batched host call): circuit w of the launch belongs to the job whose first
+// circuit is the largest first <= w.
+template <int NQ, typename R, bool CANON>
+__global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CANON, false>()) k_eval_jobs(const DevProblem *__restrict__ probs,
+                                                   const EvalJob *__restrict__ jobs,
+                                                   uint32_t n_jobs, uint32_t total, DevGlobal g) {
+  QE_EVAL_SPLIT(NQ, CANON)
+  for (uint32_t w = w0; w < total; w += nw) {
+    uint32_t lo = 0, hi = n_jobs;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (jobs[mid].first <= w) lo = mid;
+      else hi = mid;
     }
-    CircuitOut out = compose_score<NQ, R, CANON, ISING, true, WB>(
-        p, lane, o0, o1, S ? S + NN2 * c : (R *)nullptr, ic0, is0, ic1, is1, sp);
-    if (lane == 0 && sub == 0) {
-      double F = anybad ? __longlong_as_double(0x7ff8000000000000ll) : out.F;
-      if (fit) fit[c] = (R)F;
-      if (cost) cost[c] = out.cost;
-      if (anybad) atomicOr(g.err, kErrBadGate);
-      else if (!isfinite(F)) atomicOr(g.err, kErrNonFinite);
-    }
+    const EvalJob &j = jobs[lo];
+    const DevProblem &p = probs[j.prob];
+    const uint32_t c = w - j.first;
+    eval_one<NQ, R, CANON, false>(p, lane, sp, j.gates + (size_t)c * p.L, nullptr,
+                                  (R *)j.fit + c, j.cost + c, nullptr, g);
   }
 }
+#undef QE_EVAL_SPLIT
 
 // Binary64 rescoring of ranking candidates: list entries are problem << 20 | slot,
 // the circuit is cand[slot] of that problem, gates (and Ising angles) come from
@@ -1697,6 +1741,25 @@ cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *prob
   } else {                                                                                 \
     if (ising) QE_LK(NQ, float, false, true) else QE_LK(NQ, float, false, false)           \
   }
+  QE_NQ_SWITCH(nq, QE_L)
+#undef QE_L
+#undef QE_LK
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_jobs(const LaunchCfg &lc, uint32_t nq, bool canon,
+                             const DevProblem *probs, const EvalJob *jobs, uint32_t n_jobs,
+                             uint32_t total, const DevGlobal &g, cudaStream_t st) {
+  if (total == 0 || n_jobs == 0) return cudaSuccess;
+  const uint32_t per = canon ? lc.step64[nq] : lc.step32[nq];
+#define QE_LK(NQ, R, C)                                                                    \
+  {                                                                                        \
+    constexpr int bt = block_threads<NQ, C>();                                             \
+    k_eval_jobs<NQ, R, C><<<grid_for(lc, total, per, (bt / 32) >> circuit_split<NQ, C>()), bt, 0, \
+                            st>>>(probs, jobs, n_jobs, total, g);                          \
+  }
+#define QE_L(NQ)                                                                           \
+  if (canon) QE_LK(NQ, double, true) else QE_LK(NQ, float, false)
   QE_NQ_SWITCH(nq, QE_L)
 #undef QE_L
 #undef QE_LK

@@ -34,6 +34,19 @@ inline uint32_t grid_for(const LaunchCfg &lc, uint64_t warps, uint32_t per_sm, u
 // pipelined: the buffers are the search's double-buffered generation buffers
 // and the job ranks generation *gen - 1 (buffer (gen-1) & 1); the chain is
 // skipped when that generation is already ranked (or gen == 0).
+// one search's caller circuits in a batched evaluation launch: circuits
+// [first, first + n) of the launch are this job's, gate strings at gates,
+// fitness (float or double by the launch's precision) and costs out
+struct EvalJob {
+  uint32_t prob;   // descriptor index
+  uint32_t first;  // circuits of the launch before this job's
+  uint32_t n;
+  uint32_t pad;
+  const uint8_t *gates;
+  void *fit;
+  uint32_t *cost;
+};
+
 struct RankJob {
   uint32_t prob;
   uint32_t n;
@@ -65,6 +78,11 @@ cudaError_t launch_eval(const LaunchCfg &lc, uint32_t nq, const DevProblem *prob
                         bool canon, const uint8_t *gates, const float2 *amps, uint32_t n,
                         void *fit, uint32_t *cost, void *S, const DevGlobal &g,
                         cudaStream_t st);
+// the batched evaluation: n_jobs jobs of width nq (ascending first), total
+// circuits, one launch
+cudaError_t launch_eval_jobs(const LaunchCfg &lc, uint32_t nq, bool canon,
+                             const DevProblem *probs, const EvalJob *jobs, uint32_t n_jobs,
+                             uint32_t total, const DevGlobal &g, cudaStream_t st);
 // gsrc == NULL: each candidate's search's own generation buffer; pipelined:
 // that buffer is the one of generation *gen - 1, and nothing runs unless the
 // chain is active.  gtab != NULL (device array indexed by problem): each

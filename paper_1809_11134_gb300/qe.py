@@ -353,16 +353,18 @@ class Context:
                                   topk_buf=None):
         """qe_eval_host_batch_async on raw host pointers; returns the ticket.  The
         buffers must stay alive and untouched until eval_host_batch_wait(ticket)."""
+        # (integers pass as void * through the declared argument types)
         t = C.c_uint64()
-        _check(self.h, lib().qe_eval_host_batch_async(self.h, len(probs_arr), probs_arr, n_arr,
-                                                      C.c_void_p(h_gates_ptr),
-                                                      C.c_void_p(h_fit_ptr), topk_buf,
-                                                      C.byref(t)))
+        st = _lib.qe_eval_host_batch_async(self.h, len(probs_arr), probs_arr, n_arr, h_gates_ptr,
+                                           h_fit_ptr, topk_buf, C.byref(t))
+        if st != QE_OK:
+            _check(self.h, st)
         return t.value
 
     def eval_host_batch_wait(self, ticket):
         """qe_eval_host_batch_wait: the call's fitness and top-k buffers are filled."""
-        return _check(self.h, lib().qe_eval_host_batch_wait(self.h, C.c_uint64(ticket)))
+        st = _lib.qe_eval_host_batch_wait(self.h, ticket)
+        return st if st == QE_OK else _check(self.h, st)
 
     def compose(self, prob, gate_idx, unitary, n_circuits=None, amps=None):
         import torch

@@ -469,3 +469,70 @@ def test_batch_follows_a_changed_target(qe):
         check_item(dense, g, fits[0], tops[0])
         fits, tops = ctx.eval_host_batch(items, topk=True)
         check_item(s, g, fits[0], tops[0])
+
+
+@pytest.mark.parametrize("prec", [W.PREC_FP32, W.PREC_FP64])
+def test_async_pipeline_rotating_pinned_buffers(qe, prec):
+    """the pattern of a pipelined caller: fewer calls in flight than slots, a
+    ring of page-locked buffer sets refilled with new circuits before each
+    reuse (each slot's graph copies its buffers itself and is matched to them
+    again), a second layout on the same buffers, and calls with pinned gates
+    but pageable fitness (copies around the graph); every result against the
+    oracle"""
+    import torch
+    ss = searches(prec)
+    rng = np.random.default_rng(81 + prec)
+    plans = [[(0, 1000), (4, 4096)], [(4, 4096), (0, 1000)]]
+    nb, depth = 5, 3
+    ring = []
+    for b in range(nb):
+        c = _Call(qe, ss, [(q, gates_for(ss[q], n, rng)) for q, n in plans[0]])
+        ring.append(c)
+    flight = []
+
+    def finish(entry):
+        call, t, items = entry
+        ctx.eval_host_batch_wait(t)
+        fits, tops = call.results()
+        for (q, g), f, tk in zip(items, fits, tops):
+            check_item(ss[q], g, f, tk)
+
+    with qe.Context(ss) as ctx:
+        for i in range(4 * nb + 3):
+            if len(flight) == depth:
+                finish(flight.pop(0))
+            c = ring[i % nb]
+            # a new layout on the same buffers every seventh call
+            plan = plans[1] if i % 7 == 6 else plans[0]
+            items = [(q, gates_for(ss[q], n, rng)) for q, n in plan]
+            c.items = items
+            c.ns = [len(g) for _, g in items]
+            c.ks = [min(max(ss[q].topk, 1), n) for (q, _), n in zip(items, c.ns)]
+            c.hg.copy_(torch.from_numpy(np.concatenate([g.ravel() for _, g in items])))
+            for j, (q, _) in enumerate(items):
+                c.probs[j] = q
+                c.counts[j] = c.ns[j]
+            flight.append((c, c.submit(ctx), items))
+        while flight:
+            finish(flight.pop(0))
+        # pinned gates, pageable fitness: the same results
+        items = [(q, gates_for(ss[q], n, rng)) for q, n in plans[0]]
+        c = ring[0]
+        c.items, c.ns = items, [len(g) for _, g in items]
+        c.ks = [min(max(ss[q].topk, 1), n) for (q, _), n in zip(items, c.ns)]
+        c.hg.copy_(torch.from_numpy(np.concatenate([g.ravel() for _, g in items])))
+        for j, (q, _) in enumerate(items):
+            c.probs[j] = q
+            c.counts[j] = c.ns[j]
+        hf = np.full(sum(c.ns), -7.0, np.float64 if prec == W.PREC_FP64 else np.float32)
+        t = ctx.eval_host_batch_async_ptr(c.probs, c.counts, c.hg.data_ptr(), hf.ctypes.data,
+                                          c.tops)
+        ctx.eval_host_batch_wait(t)
+        fo = ko = 0
+        fits2, tops2 = ctx.eval_host_batch(items, topk=True)
+        for (q, g), n, k, f2, t2 in zip(items, c.ns, c.ks, fits2, tops2):
+            assert np.array_equal(hf[fo:fo + n].view(np.uint8), f2.view(np.uint8))
+            assert [(t.circuit, t.cost, t.fitness) for t in c.tops[ko:ko + k]] == t2
+            check_item(ss[q], g, hf[fo:fo + n], t2)
+            fo += n
+            ko += k
