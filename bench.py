@@ -410,11 +410,11 @@ def run_ours(args):
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_step launch (a timed
 # step, right after the L2 flush) from an ncu capture of this workload
 # (summarised under profiles/): the reads include the update's L2 prefetch
-TRAFFIC = {(2, None): 41.165e6}
+TRAFFIC = {(2, None): 41.504e6}
 # warp instructions of one k_step launch (smsp__inst_executed.sum) from the same
 # capture: the circuit kernel at n = 3 is bound by instruction issue, not by
 # the FP32 pipe, so its issue rate is reported beside the arithmetic roofline
-INSTR = {(2, None): 9797975}
+INSTR = {(2, None): 9675705}
 
 
 def issue_roofline(roof, instr):
