@@ -1198,11 +1198,12 @@ static bool host_pinned(const void *p) {
 }
 
 // Enqueue one batched host evaluation in a free slot, all on the slot's
-// stream: the copy of the gates, the evaluations, the fitness copy back, the
-// ranking (on the slot's own scratch: the jobs' search descriptors are slot
-// copies whose candidate lists, counts and top-k lists live in the slot's
-// staging, with the slot's own rescoring queue and error word) and the top-k
-// copy back.  Calls in different slots share no device memory, so their
+// stream: the copy of the gates, the evaluations, the ranking (on the slot's
+// own scratch: the jobs' search descriptors are slot copies whose candidate
+// lists, counts and top-k lists live in the slot's staging, with the slot's
+// own rescoring queue and error word) and the fitness and top-k copies back,
+// the copies inside the slot's graph when the caller's buffers are
+// page-locked.  Calls in different slots share no device memory, so their
 // rankings, latency chains on a few SMs each, run concurrently.
 static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
                               const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
