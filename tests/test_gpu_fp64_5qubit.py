@@ -127,3 +127,29 @@ def test_ga_generations_bit_exact(qe, torch):
             assert [t[0] for t in last["topk"]] == list(oracle.topk(F, C, s.topk)), gen
             genome = oracle.ga_next(p, G, gen, s.ga_mutation_rate, genome, F, C)
         assert np.array_equal(ctx.get_state(0), genome)
+
+
+def test_4qubit_generations_bit_exact(qe, torch):
+    """the same at 4 qubits, where binary64 circuits run on two warps each: one
+    search with more circuits than the GPU has resident two-warp groups, one
+    with a dense target (and K = 2 measurements), three generations"""
+    rng = np.random.default_rng(44)
+    T = _haar(rng, 16)
+    searches = [W.Search(4, 8, 2000, NCV | HT, W.cknot(4), seed=41, precision=FP64, topk=6),
+                W.Search(4, 21, 70, NCV | HT | ID, W.random_perm(rng, 4), seed=42,
+                         precision=FP64, topk=4, shots=2, target=T)]
+    gens = 3
+    ref = _oracle_run(searches, gens)
+    with qe.Context(searches) as ctx:
+        for gen in range(gens):
+            reps = ctx.step(1)
+            for run, s in enumerate(searches):
+                gi, sid, F, tk, bfit, bcost, bgates = ref[run][0][gen]
+                last = ctx.last_generation(run)
+                assert np.array_equal(last["gate_idx"], gi), (gen, run)
+                assert np.array_equal(last["fitness"], F), (gen, run)
+                assert [t[0] for t in last["topk"]] == list(tk[:s.topk]), (gen, run)
+                assert reps[run]["best_fitness"] == bfit and reps[run]["best_cost"] == bcost
+        for run in range(len(searches)):
+            c, b, bf = ctx.get_state(run)
+            assert state_equal(c, ref[run][1]) and state_equal(bf, ref[run][3]), run
