@@ -401,6 +401,7 @@ def run_ours(args):
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         if not args.no_extra:
             line["per_config"] = per_config(qe, torch, args)
+            line["by_qubits"] = by_qubits(line["per_config"])
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
@@ -722,6 +723,26 @@ def _fp32_error(qe, torch, ctx32, searches, n_unitary=256):
     if bad:
         raise RuntimeError("%d non-finite binary32/binary64 differences" % bad)
     return f_err, u_err, hi_err, hi_n
+
+
+def by_qubits(pc):
+    """The metric at n = 3/4/5 in one flat table: for each width's benchmark
+    search (3: the three searches of P = 4096, 4: C3NOT at P = 65536, 5: C4NOT
+    at P = 262144), circuits/s of the circuit kernel and of the whole
+    generation, binary32 (binary64 top-k) against plain binary64."""
+    out = {}
+    for n, cfg in ((3, "config2"), (4, "config3"), (5, "config5")):
+        res = pc.get(cfg, {})
+        row = {}
+        for prec in ("fp32", "fp64"):
+            r = res.get(prec)
+            if r:
+                row[prec + "_circuit_kernel"] = r["circuit_kernel_circuits_per_s"]
+                row[prec + "_generation"] = r["generation_circuits_per_s"]
+        if "fp32_generation" in row and "fp64_generation" in row:
+            row["fp32_over_fp64_generation"] = row["fp32_generation"] / row["fp64_generation"]
+        out[str(n)] = row
+    return out
 
 
 def per_config(qe, torch, args):

@@ -80,3 +80,21 @@ def test_oracle_generation_threads_match_the_oracle_step():
             oracle.step(p, *b, g, 32, rep)
     for x, y in zip(a, b):
         assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+
+
+def test_by_qubits_table():
+    """the flat n = 3/4/5 table is read off the per-set results, binary32
+    against plain binary64, and tolerates a missing arithmetic"""
+    def r(k, g):
+        return {"circuit_kernel_circuits_per_s": k, "generation_circuits_per_s": g}
+    pc = {"config2": {"fp32": r(600.0, 300.0), "fp64": r(90.0, 75.0)},
+          "config3": {"fp32": r(290.0, 140.0), "fp64": r(14.0, 14.0)},
+          "config5": {"fp32": r(87.0, 50.0)},
+          "config4": {"fp32": r(230.0, 100.0)}}
+    t = bench.by_qubits(pc)
+    assert sorted(t) == ["3", "4", "5"]
+    assert t["3"] == {"fp32_circuit_kernel": 600.0, "fp32_generation": 300.0,
+                      "fp64_circuit_kernel": 90.0, "fp64_generation": 75.0,
+                      "fp32_over_fp64_generation": 4.0}
+    assert t["4"]["fp32_over_fp64_generation"] == 10.0
+    assert t["5"] == {"fp32_circuit_kernel": 87.0, "fp32_generation": 50.0}
