@@ -2,6 +2,8 @@
 // host-built tables, CUDA-graph capture of one generation, and the calls.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -53,6 +55,10 @@ constexpr int kBatchSlots = (int)QE_BATCH_SLOTS;  // qe_eval_host_batch_async ca
 // graph of the evaluations and the ranking, run on the slot's stream -- and
 // the call in flight.
 
+// the staging's error-word slot while a call's graph has not yet copied the
+// word there (no error word has every bit set)
+constexpr uint32_t kErrwPending = 0xffffffffu;
+
 struct BatchSlot {
   void *d = nullptr;
   size_t d_bytes = 0;
@@ -66,8 +72,11 @@ struct BatchSlot {
   cudaEvent_t ev_done = nullptr;
   size_t err_off = 0;  // the slot's error word in its staging
   uint32_t desc_version = 0;  // the context's descriptors the slot's copies were made from
-  // the call in flight (ticket: also the slot's last call, for reuse order)
+  // the call in flight (ticket: also the slot's last call, for reuse order);
+  // flag: the call's graph ends with the copy of its error word, which the
+  // wait polls in the staging instead of synchronising on ev_done
   bool busy = false;
+  bool flag = false;
   uint64_t ticket = 0;
   qe_ranked *h_topk = nullptr;
   size_t k_total = 0;
@@ -1422,8 +1431,6 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
       if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join, 0);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_join2, 0);
     }
-    if (fold && !rank && e == cudaSuccess)  // the error word the evaluations set
-      e = cudaMemcpyAsync(b.h, base + lay.err, 4, cudaMemcpyDeviceToHost, cs);
     // then, in the same graph, the ranking of every item with circuits: the
     // jobs' descriptors send each sorted list straight to its place in the
     // gathered output, and the sort writes the error word after them and
@@ -1454,13 +1461,20 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
       }
     }
     if (fold && e == cudaSuccess) {
-      // the fitness, then the lists and error word out, after the sort, in
+      // the fitness, the lists, then the error word out, after the sort, in
       // one chain (the fitness copy on a forked stream beside the ranking
-      // measured 0.3 us more per call to launch and gained nothing)
+      // measured 0.3 us more per call to launch and gained nothing).  The
+      // error word's copy is the graph's last node: the wait polls for it in
+      // the staging (every earlier copy of the chain has landed by then).
       if (n_total)
         e = cudaMemcpyAsync(h_fitness, base + lay.fit, n_total * fb, cudaMemcpyDeviceToHost, cs);
-      if (rank && e == cudaSuccess)
-        e = cudaMemcpyAsync(b.h, base + lay.topk, hb, cudaMemcpyDeviceToHost, cs);
+      if (rank && kt && e == cudaSuccess)
+        e = cudaMemcpyAsync(b.h, base + lay.topk, kt * sizeof(Ranked), cudaMemcpyDeviceToHost,
+                            cs);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char *)b.h + kt * sizeof(Ranked),
+                            base + (rank ? lay.topk + kt * sizeof(Ranked) : lay.err), 4,
+                            cudaMemcpyDeviceToHost, cs);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -1478,8 +1492,10 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
   }
   char *base = (char *)b.d;
   if (fold) {
+    // the slot is idle: nothing of its last call writes the staging any more
+    ((volatile uint32_t *)((char *)b.h + kt * sizeof(Ranked)))[0] = kErrwPending;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
     QE_CUDA(ctx, cudaGraphLaunch(b.ex, b.st));
-    QE_CUDA(ctx, cudaEventRecord(b.ev_done, b.st));
   } else {
     if (gate_bytes)
       QE_CUDA(ctx, cudaMemcpyAsync(base + lay.gates, h_gate_idx, gate_bytes,
@@ -1493,6 +1509,7 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     QE_CUDA(ctx, cudaEventRecord(b.ev_done, b.st));
   }
   b.busy = true;
+  b.flag = fold;
   b.ticket = ctx->next_ticket++;
   b.h_topk = h_topk;
   b.k_total = kt;
@@ -1503,7 +1520,24 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
 // Wait for a slot's call and hand out its top-k lists and error status.
 static qe_status batch_complete(qe_ctx *ctx, BatchSlot &b) {
   b.busy = false;
-  QE_CUDA(ctx, cudaEventSynchronize(b.ev_done));
+  if (b.flag) {
+    // poll the error word's slot for up to 2 ms, then block on the stream (a
+    // long call, or a failed one whose copies never ran: the stream's error)
+    const volatile uint32_t *w =
+        (const volatile uint32_t *)((const char *)b.h + b.k_total * sizeof(Ranked));
+    bool seen = false;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (uint32_t i = 0; !seen; ++i) {
+      seen = *w != kErrwPending;
+      if (!seen && (i & 255u) == 255u &&
+          std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(2))
+        break;
+    }
+    if (seen) std::atomic_thread_fence(std::memory_order_acquire);
+    else QE_CUDA(ctx, cudaStreamSynchronize(b.st));
+  } else {
+    QE_CUDA(ctx, cudaEventSynchronize(b.ev_done));
+  }
   const Ranked *r = (const Ranked *)b.h;
   for (size_t s = 0; s < b.k_total; ++s) {
     b.h_topk[s].circuit = r[s].circuit;
