@@ -279,7 +279,9 @@ qe_status qe_eval_host_batch_async(qe_ctx *ctx, uint32_t n_items, const uint32_t
                                    const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
                                    void *h_fitness, qe_ranked *h_topk, uint64_t *ticket);
 
-/* Waits for the call with this ticket, fills its h_topk and frees its slot;
+/* Waits for the call with this ticket (for page-locked buffers by polling
+ * the call's staged error word for up to 2 ms, then by blocking on its
+ * slot's stream), fills its h_topk and frees its slot;
  * QE_ENUMERIC as qe_eval_host_batch; QE_EINVAL for a ticket that is not in
  * flight (never issued, or already waited for).  Calls may be waited for in
  * any order. */
