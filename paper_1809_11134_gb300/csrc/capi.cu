@@ -63,6 +63,7 @@ struct BatchSlot {
   void *d = nullptr;
   size_t d_bytes = 0;
   void *h = nullptr;
+  void *hd = nullptr;  // the staging's device mapping
   size_t h_bytes = 0;
   std::vector<uint32_t> key;
   std::vector<unsigned char> meta;  // host copy of the jobs, offsets and gate table
@@ -1180,7 +1181,7 @@ static BatchLayout batch_layout(size_t gate_bytes, size_t n_total, size_t fb, si
   o += align256(n_items * 4);
   b.rq = o;
   o += align256((n_total ? n_total : 1) * 4);
-  b.words = o;  // rescore_n, gen, ranked, rank_active
+  b.words = o;  // rescore_n, gen, ranked, rank_active, the copy-out counter
   o += 256;
   b.jobs = o;
   o += align256(n_items * sizeof(RankJob));
@@ -1196,14 +1197,15 @@ static BatchLayout batch_layout(size_t gate_bytes, size_t n_total, size_t fb, si
   return b;
 }
 
-// page-locked host memory (the only host memory a graph's copies may use)
-static bool host_pinned(const void *p) {
+// the device address of page-locked host memory, or NULL for other memory
+// (the batch graph's copy kernels reach the caller's buffers through it)
+static void *host_mapping(const void *p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return nullptr;
   }
-  return a.type == cudaMemoryTypeHost;
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 // Enqueue one batched host evaluation in a free slot, all on the slot's
@@ -1246,10 +1248,13 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     return fail(ctx, QE_EINVAL, "null buffer");
   const size_t fb = prec == 0 ? 8 : 4;
   const bool rank = h_topk != nullptr;
-  // page-locked caller buffers are copied by the call's graph itself (one
-  // launch per call); other memory by copies around it.  Checked every call:
-  // a graph is only reused for the same addresses, still page-locked.
-  const bool fold = (!gate_bytes || host_pinned(h_gate_idx)) && (!n_total || host_pinned(h_fitness));
+  // page-locked caller buffers are copied by kernels of the call's graph
+  // through their device mappings (one launch per call); other memory by
+  // copies around the graph.  Checked every call: a graph is only reused for
+  // the same mappings.
+  void *dg = gate_bytes ? host_mapping(h_gate_idx) : nullptr;
+  void *df = n_total ? host_mapping(h_fitness) : nullptr;
+  bool fold = (!gate_bytes || dg) && (!n_total || df);
   std::vector<uint32_t> &key = ctx->b_key;
   key.clear();
   key.push_back(rank ? 1u : 0u);
@@ -1260,7 +1265,7 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
   }
   key.push_back(fold ? 1u : 0u);
   if (fold) {
-    const uint64_t pg = (uint64_t)(uintptr_t)h_gate_idx, pf = (uint64_t)(uintptr_t)h_fitness;
+    const uint64_t pg = (uint64_t)(uintptr_t)dg, pf = (uint64_t)(uintptr_t)df;
     key.push_back((uint32_t)pg);
     key.push_back((uint32_t)(pg >> 32));
     key.push_back((uint32_t)pf);
@@ -1294,10 +1299,22 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     QE_CUDA(ctx, cudaStreamSynchronize(b.st));
     if (b.h) cudaFreeHost(b.h);
     b.h = nullptr;
+    b.hd = nullptr;
     b.h_bytes = 0;
-    QE_CUDA(ctx, cudaHostAlloc(&b.h, hb, cudaHostAllocDefault));
+    QE_CUDA(ctx, cudaHostAlloc(&b.h, hb, cudaHostAllocMapped));
     b.h_bytes = hb;
+    if (cudaHostGetDevicePointer(&b.hd, b.h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      b.hd = nullptr;
+    }
     new_h = true;  // a graph that copies into the old staging is stale
+  }
+  if (fold && !b.hd) {
+    // no device mapping of the staging: copies around the graph after all
+    fold = false;
+    const size_t at = 2 + 2 * (size_t)n_items;
+    key.resize(at + 1);
+    key[at] = 0u;
   }
 
   const BatchLayout lay = batch_layout(gate_bytes, n_total, fb, k_total, n_items);
@@ -1412,7 +1429,7 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     QE_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     if (fold && gate_bytes)  // the circuits in, ahead of every evaluation
-      e = cudaMemcpyAsync(base + lay.gates, h_gate_idx, gate_bytes, cudaMemcpyHostToDevice, cs);
+      e = launch_copy_in(base + lay.gates, dg, gate_bytes, ctx->lc.num_sms, cs);
     const bool forked = n_widths > 1;
     if (forked) {
       if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, cs);
@@ -1461,20 +1478,16 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
       }
     }
     if (fold && e == cudaSuccess) {
-      // the fitness, the lists, then the error word out, after the sort, in
-      // one chain (the fitness copy on a forked stream beside the ranking
-      // measured 0.3 us more per call to launch and gained nothing).  The
-      // error word's copy is the graph's last node: the wait polls for it in
-      // the staging (every earlier copy of the chain has landed by then).
-      if (n_total)
-        e = cudaMemcpyAsync(h_fitness, base + lay.fit, n_total * fb, cudaMemcpyDeviceToHost, cs);
-      if (rank && kt && e == cudaSuccess)
-        e = cudaMemcpyAsync(b.h, base + lay.topk, kt * sizeof(Ranked), cudaMemcpyDeviceToHost,
-                            cs);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync((char *)b.h + kt * sizeof(Ranked),
-                            base + (rank ? lay.topk + kt * sizeof(Ranked) : lay.err), 4,
-                            cudaMemcpyDeviceToHost, cs);
+      // the fitness and the lists out after the sort, and then, once all of
+      // them are visible to the host, the error word: the wait polls for it
+      // in the staging.  (Copy-engine nodes for these copies measured ~0.8 us
+      // of host launch time each against ~0.2 us for a kernel node.)
+      e = launch_copy_out(df, base + lay.fit, n_total * fb, b.hd, base + lay.topk,
+                          rank ? kt * sizeof(Ranked) : 0,
+                          (uint32_t *)((char *)b.hd + kt * sizeof(Ranked)),
+                          (const uint32_t *)(base + (rank ? lay.topk + kt * sizeof(Ranked)
+                                                          : lay.err)),
+                          (uint32_t *)(base + lay.words) + 4, ctx->lc.num_sms, cs);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);

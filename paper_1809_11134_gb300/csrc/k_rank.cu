@@ -766,6 +766,80 @@ __global__ void k_finish(DevGlobal g) {
 
 __global__ void k_reset_counter(DevGlobal g) { *g.rescore_n = 0; }
 
+// ------------------------------------------------------------ batch copies
+// The batched host call's copies between page-locked host memory (through its
+// device mapping) and the slot's device staging, done by the GPU's threads so
+// that the call's graph holds kernels only.
+
+// bytes [0, n) from src to dst, grid-stride, in 16-, 4- or 1-byte words as the
+// addresses and the length allow
+__device__ __forceinline__ void copy_span(char *dst, const char *src, size_t n, size_t t0,
+                                          size_t nt) {
+  if ((((uintptr_t)dst | (uintptr_t)src | n) & 15u) == 0) {
+    for (size_t i = t0; i < n / 16; i += nt)
+      reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+  } else if ((((uintptr_t)dst | (uintptr_t)src | n) & 3u) == 0) {
+    for (size_t i = t0; i < n / 4; i += nt)
+      reinterpret_cast<uint32_t *>(dst)[i] = reinterpret_cast<const uint32_t *>(src)[i];
+  } else {
+    for (size_t i = t0; i < n; i += nt) dst[i] = src[i];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_copy_in(char *dst, const char *src, size_t n) {
+  copy_span(dst, src, n, (size_t)blockIdx.x * blockDim.x + threadIdx.x,
+            (size_t)gridDim.x * blockDim.x);
+}
+
+// The call's outputs to the host: the fitness (fit_n bytes) and the top-k
+// lists (list_n bytes); then the last block to finish writes the error word
+// to its host slot, after every block's writes are visible system-wide (a
+// system fence before each block's arrival on the counter, which the last
+// block resets for the slot's next call).  The host polls that word.
+__global__ void __launch_bounds__(256) k_copy_out(char *h_fit, const char *d_fit, size_t fit_n,
+                                                  char *h_list, const char *d_list,
+                                                  size_t list_n, uint32_t *h_errw,
+                                                  const uint32_t *d_errw, uint32_t *count) {
+  const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nt = (size_t)gridDim.x * blockDim.x;
+  if (fit_n) copy_span(h_fit, d_fit, fit_n, t0, nt);
+  if (list_n) copy_span(h_list, d_list, list_n, t0, nt);
+  __threadfence_system();
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    *count = 0;
+    __threadfence_system();
+    *(volatile uint32_t *)h_errw = *(volatile const uint32_t *)d_errw;
+  }
+}
+
+cudaError_t launch_copy_in(void *dst, const void *src, size_t n, uint32_t num_sms,
+                           cudaStream_t st) {
+  if (!n) return cudaSuccess;
+  uint64_t blocks = (n / 16 + 255) / 256;
+  if (blocks > (uint64_t)num_sms * 4) blocks = (uint64_t)num_sms * 4;
+  if (!blocks) blocks = 1;
+  k_copy_in<<<(uint32_t)blocks, 256, 0, st>>>((char *)dst, (const char *)src, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_out(void *h_fit, const void *d_fit, size_t fit_n, void *h_list,
+                            const void *d_list, size_t list_n, uint32_t *h_errw,
+                            const uint32_t *d_errw, uint32_t *count, uint32_t num_sms,
+                            cudaStream_t st) {
+  const size_t n = fit_n > list_n ? fit_n : list_n;
+  uint64_t blocks = (n / 16 + 255) / 256;
+  if (blocks > (uint64_t)num_sms * 4) blocks = (uint64_t)num_sms * 4;
+  if (!blocks) blocks = 1;
+  k_copy_out<<<(uint32_t)blocks, 256, 0, st>>>((char *)h_fit, (const char *)d_fit, fit_n,
+                                               (char *)h_list, (const char *)d_list, list_n,
+                                               h_errw, d_errw, count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rank_select(const DevProblem *probs, const RankJob *jobs, uint32_t n_jobs,
                                const RankJob &single, const DevGlobal &g, cudaStream_t st,
                                uint32_t max_n) {

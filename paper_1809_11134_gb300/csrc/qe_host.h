@@ -145,5 +145,15 @@ cudaError_t launch_ga_next(const LaunchCfg &lc, const DevProblem *probs, const u
                            const uint32_t *prefix, uint32_t n_ga, uint32_t total_pairs,
                            const DevGlobal &g, cudaStream_t st);
 cudaError_t launch_reset_counter(const DevGlobal &g, cudaStream_t st);
+// the batched host call's copies through the device mappings of page-locked
+// host memory: n bytes in; the fitness and lists out, then the error word
+// (written last, after a system fence, by the last block; count: a zeroed
+// device word the kernel leaves zero)
+cudaError_t launch_copy_in(void *dst, const void *src, size_t n, uint32_t num_sms,
+                           cudaStream_t st);
+cudaError_t launch_copy_out(void *h_fit, const void *d_fit, size_t fit_n, void *h_list,
+                            const void *d_list, size_t list_n, uint32_t *h_errw,
+                            const uint32_t *d_errw, uint32_t *count, uint32_t num_sms,
+                            cudaStream_t st);
 
 }  // namespace qe
