@@ -271,10 +271,11 @@ qe_status qe_eval_host_batch(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_pr
  * QE_EINVAL for a NULL ticket.  Each slot's graphs follow the layout of its
  * last call, so repeating fixed layouts replays captured graphs.  When
  * h_gate_idx and h_fitness are page-locked (cudaHostAlloc, cudaHostRegister;
- * checked on every call) the slot's graph also holds the copies and a call is
- * one graph launch; such a graph is replayed only for the same addresses, and
- * a call goes to a free slot whose graph matches it when there is one.  Other
- * host memory is copied by separate asynchronous copies around the graph. */
+ * checked on every call) kernels of the slot's graph copy them through their
+ * device mappings and a call is one graph launch; such a graph is replayed
+ * only for the same mappings, and a call goes to a free slot whose graph
+ * matches it when there is one.  Other host memory is copied by separate
+ * asynchronous copies around the graph. */
 qe_status qe_eval_host_batch_async(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_probs,
                                    const uint32_t *h_n_circuits, const uint8_t *h_gate_idx,
                                    void *h_fitness, qe_ranked *h_topk, uint64_t *ticket);
