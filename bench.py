@@ -565,9 +565,10 @@ def end_to_end(qe, ctx_unused, searches, last, steps):
             "sync_value": out["sync"],
             "by_calls_in_flight": {str(d): round(v) for d, v in by_depth.items()},
             "call": "qe_eval_host_batch_async / _wait: every search's circuits in one call "
-                    "(binary32 eval + binary64 top-k), pinned host buffers, %d calls in "
-                    "flight; sync_value: qe_eval_host_batch, one synchronisation per step"
-                    % depth}
+                    "(binary32 eval + binary64 top-k), pinned host buffers (the gate strings "
+                    "in and the fitness and top-k out are copied by the call's kernels "
+                    "through the buffers' device mappings), %d calls in flight; sync_value: "
+                    "qe_eval_host_batch, one synchronisation per step" % depth}
 
 
 def _stage_rates(qe, torch, searches, gens):
