@@ -536,3 +536,44 @@ def test_async_pipeline_rotating_pinned_buffers(qe, prec):
             check_item(ss[q], g, hf[fo:fo + n], t2)
             fo += n
             ko += k
+
+
+@pytest.mark.parametrize("prec", [W.PREC_FP32, W.PREC_FP64])
+def test_pinned_buffers_at_unaligned_addresses(qe, prec):
+    """page-locked buffers that the graph's copy kernels reach through their
+    device mappings, at addresses and lengths that take each copy width (16-,
+    4- and 1-byte words): the results equal those of pageable buffers"""
+    import ctypes as C
+    import torch
+    ss = searches(prec)
+    rng = np.random.default_rng(91 + prec)
+    fb = 8 if prec == W.PREC_FP64 else 4
+    for plan, g_off, f_off in (([(0, 1000), (1, 300)], 0, 0),    # 16-byte words
+                               ([(0, 999), (1, 300)], 4, fb),     # 4-byte words
+                               ([(1, 299), (2, 77)], 1, fb)):     # bytes in
+        items = [(q, gates_for(ss[q], n, rng)) for q, n in plan]
+        flat = np.concatenate([g.ravel() for _, g in items])
+        n_tot = sum(n for _, n in plan)
+        gbuf = torch.zeros(flat.size + 16, dtype=torch.uint8).pin_memory()
+        gbuf[g_off:g_off + flat.size].copy_(torch.from_numpy(flat))
+        fbuf = torch.zeros(n_tot * fb + 16, dtype=torch.uint8).pin_memory()
+        ks = [min(max(ss[q].topk, 1), n) for q, n in plan]
+        tops = (qe.qe_ranked * sum(ks))()
+        probs = (C.c_uint32 * len(plan))(*[q for q, _ in plan])
+        counts = (C.c_uint32 * len(plan))(*[n for _, n in plan])
+        with qe.Context(ss) as ctx:
+            for _ in range(2):  # the second call replays the slot's graph
+                fbuf.zero_()
+                ctx.eval_host_batch_wait(ctx.eval_host_batch_async_ptr(
+                    probs, counts, gbuf.data_ptr() + g_off, fbuf.data_ptr() + f_off, tops))
+                fits2, tops2 = ctx.eval_host_batch(items, topk=True)  # pageable
+                raw = fbuf.numpy()[f_off:f_off + n_tot * fb].copy()
+                got = raw.view(np.float64 if prec == W.PREC_FP64 else np.float32)
+                fo = ko = 0
+                for (q, g), k, f2, t2 in zip(items, ks, fits2, tops2):
+                    n = len(g)
+                    assert np.array_equal(got[fo:fo + n].view(np.uint8), f2.view(np.uint8))
+                    assert [(t.circuit, t.cost, t.fitness) for t in tops[ko:ko + k]] == t2
+                    check_item(ss[q], g, got[fo:fo + n], t2)
+                    fo += n
+                    ko += k
