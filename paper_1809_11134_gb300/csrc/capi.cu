@@ -409,7 +409,9 @@ qe_status add_select_first_edge(qe_ctx *ctx, cudaGraph_t graph) {
 // is launched while its predecessor's last blocks still run instead of after
 // the predecessor has completed; it then waits on the device for that
 // completion before reading what the predecessor wrote.
-qe_status add_pdl_edges(qe_ctx *ctx, cudaGraph_t graph) {
+// batch: the batched host call's graph, whose evaluation, one-CTA selection
+// and copy out also wait for their predecessors
+qe_status add_pdl_edges(qe_ctx *ctx, cudaGraph_t graph, bool batch) {
   size_t nn = 0;
   QE_CUDA(ctx, cudaGraphGetNodes(graph, nullptr, &nn));
   std::vector<cudaGraphNode_t> nodes(nn);
@@ -432,7 +434,9 @@ qe_status add_pdl_edges(qe_ctx *ctx, cudaGraph_t graph) {
     const void *f = nullptr;
     qe_status st = kernel_of(nd, &f);
     if (st != QE_OK) return st;
-    if (!f || !(is_update_kernel(f) || is_rescore_kernel(f) || rank_kernel_waits(f))) continue;
+    if (!f || !(is_update_kernel(f) || is_rescore_kernel(f) || rank_kernel_waits(f) ||
+                (batch && (is_eval_jobs_kernel(f) || batch_kernel_waits(f)))))
+      continue;
     size_t nd_deps = 0;
     QE_CUDA(ctx, cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &nd_deps));
     if (!nd_deps) continue;
@@ -553,7 +557,7 @@ qe_status build_gen_graph(qe_ctx *ctx, const Plan &plan, cudaGraph_t *out_graph,
   }
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
   qe_status st = set_priorities(ctx, graph);
-  if (st == QE_OK) st = add_pdl_edges(ctx, graph);
+  if (st == QE_OK) st = add_pdl_edges(ctx, graph, false);
   if (st == QE_OK && plan.select_first && !serial) st = add_select_first_edge(ctx, graph);
   if (st != QE_OK) {
     cudaGraphDestroy(graph);
@@ -596,7 +600,7 @@ qe_status build_graph(qe_ctx *ctx) {
   }
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
   ctx->dgraph = graph;
-  qe_status pst = add_pdl_edges(ctx, graph);
+  qe_status pst = add_pdl_edges(ctx, graph, false);
   if (pst != QE_OK) return pst;
   QE_CUDA(ctx, cudaGraphInstantiate(&ctx->dexec, graph, 0));
   return QE_OK;
@@ -1497,7 +1501,7 @@ static qe_status batch_submit(qe_ctx *ctx, uint32_t n_items, const uint32_t *h_p
     }
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
     b.eg = graph;
-    qe_status pst = add_pdl_edges(ctx, graph);
+    qe_status pst = add_pdl_edges(ctx, graph, true);
     if (pst != QE_OK) return pst;
     QE_CUDA(ctx, cudaGraphInstantiate(&b.ex, graph, 0));
     b.key = key;

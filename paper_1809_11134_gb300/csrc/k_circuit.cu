@@ -1570,6 +1570,7 @@ template <int NQ, typename R, bool CANON>
 __global__ void __launch_bounds__(block_threads<NQ, CANON>(), min_blocks<NQ, CANON, false>()) k_eval_jobs(const DevProblem *__restrict__ probs,
                                                    const EvalJob *__restrict__ jobs,
                                                    uint32_t n_jobs, uint32_t total, DevGlobal g) {
+  wait_predecessor();  // the batch graph's copy of the gate strings
   QE_EVAL_SPLIT(NQ, CANON)
   for (uint32_t w = w0; w < total; w += nw) {
     uint32_t lo = 0, hi = n_jobs;
@@ -1801,6 +1802,16 @@ bool is_circuit_kernel(const void *f) {
       f == (const void *)k_step<NQ, double, true, false, true> ||                         \
       f == (const void *)k_step<NQ, float, false, true, true> ||                          \
       f == (const void *)k_step<NQ, double, true, true, true>)                            \
+    return true;
+  QE_K(1) QE_K(2) QE_K(3) QE_K(4) QE_K(5)
+#undef QE_K
+  return false;
+}
+
+bool is_eval_jobs_kernel(const void *f) {
+#define QE_K(NQ)                                                                             \
+  if (f == (const void *)k_eval_jobs<NQ, float, false> ||                                    \
+      f == (const void *)k_eval_jobs<NQ, double, true>)                                      \
     return true;
   QE_K(1) QE_K(2) QE_K(3) QE_K(4) QE_K(5)
 #undef QE_K

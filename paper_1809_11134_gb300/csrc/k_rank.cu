@@ -195,6 +195,7 @@ __device__ __forceinline__ RankJob resolve(RankJob jb, const DevProblem &p, uint
 __global__ void __launch_bounds__(kRankThreads) k_rank_select(const DevProblem *__restrict__ probs,
                                                               const RankJob *__restrict__ jobs,
                                                               RankJob single, DevGlobal g) {
+  wait_predecessor();  // in the batch graph: the evaluations' fitness and costs
   RankJob jb = jobs ? jobs[blockIdx.x] : single;
   const DevProblem &p = probs[jb.prob];
   if (jb.pipelined) {
@@ -800,6 +801,7 @@ __global__ void __launch_bounds__(256) k_copy_out(char *h_fit, const char *d_fit
                                                   char *h_list, const char *d_list,
                                                   size_t list_n, uint32_t *h_errw,
                                                   const uint32_t *d_errw, uint32_t *count) {
+  wait_predecessor();  // the sort's lists and error word
   const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nt = (size_t)gridDim.x * blockDim.x;
   if (fit_n) copy_span(h_fit, d_fit, fit_n, t0, nt);
@@ -861,6 +863,9 @@ cudaError_t launch_rank_sort(const DevProblem *probs, const RankJob *jobs, uint3
 
 bool is_select_kernel(const void *f) {
   return f == (const void *)k_rank_select || f == (const void *)k_rank_select_cl;
+}
+bool batch_kernel_waits(const void *f) {
+  return f == (const void *)k_rank_select || f == (const void *)k_copy_out;
 }
 bool rank_kernel_waits(const void *f) {
   return f == (const void *)k_rank_sort || f == (const void *)k_finish ||

@@ -62,6 +62,7 @@ struct RankJob {
 cudaError_t query_circuit_occupancy(LaunchCfg &lc);
 bool is_circuit_kernel(const void *f);  // a generation circuit kernel (graph node priorities)
 bool is_rescore_kernel(const void *f);  // binary64 rescoring (waits for its predecessor)
+bool is_eval_jobs_kernel(const void *f);  // the batch evaluation (waits for its predecessor)
 // all searches of a launch have n qubits
 cudaError_t launch_step(const LaunchCfg &lc, uint32_t n, const DevProblem *probs,
                         const uint32_t *group, const uint32_t *prefix, uint32_t n_group,
@@ -114,6 +115,9 @@ cudaError_t launch_update(const LaunchCfg &lc, const DevProblem *probs, const ui
 cudaError_t rank_init();  // once per device before the first ranking launch
 // jobs == NULL: one job given by value in `single`
 bool is_select_kernel(const void *f);  // the ranking's selection kernel (graph edges)
+// kernels that wait for their predecessor in the batch graph only (the
+// one-CTA selection, the copy out)
+bool batch_kernel_waits(const void *f);
 // threads of a selection launch over n_jobs searches of at most max_n
 // circuits, in units of 512 (a quarter of an SM's 2048)
 uint32_t select_quarters(uint32_t n_jobs, uint32_t max_n);
